@@ -1,0 +1,447 @@
+/*
+ * lap5_oracle.c -- plain, slow, obviously correct CPU oracle for matrix-free
+ * conjugate gradient on the 2D Dirichlet 5-point Laplacian
+ * (arxiv 1803.03797, "Efficient FPGA Implementation of Conjugate Gradient
+ * Methods for Laplacian System using HLS").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path (the CUDA library and
+ * its Python binding) may call, link or include this file.  It shares no code,
+ * header, table or helper with the GPU path.  Only the test suite, the smoke
+ * check and the CPU-baseline leg of the benchmark use it.
+ *
+ * Build: gcc -O2 -std=c11 -ffp-contract=off -fPIC -shared (see oracle/build.py).
+ * -ffp-contract=off matters: every a*b+c below is two roundings, as written.
+ *
+ * Conventions (shared with the public C-ABI only by meaning, not by code):
+ *   grid: nx columns (i, fastest) by ny rows (j); element (i,j) at j*ld + i,
+ *   ld >= nx; the Dirichlet boundary is implicit zeros, never stored.
+ *   A = the paper's 3x3 mask [0 -1 0; -1 4 -1; 0 -1 0] (Sec. II-B), no 1/h^2.
+ *
+ * Readings of the paper taken here (each one is listed in the design doc):
+ *   - stencil add order: acc = 4*xC; acc -= xW; acc -= xE; acc -= xS; acc -= xN
+ *     (W = i-1, E = i+1, S = j-1, N = j+1).  The paper fixes only the mask.
+ *   - Alg. 2 garbles: "r = r + alpha*s" read as r = r - alpha*q;
+ *     "w = w + alpha*z" read as w = w - alpha*z; the unbalanced line 17 read as
+ *     alpha = 1/(delta/gamma - beta/alpha_old); line 6 delta is delta_new.
+ *     These follow the cited Ghysels-Vanroose pipelined CG with M = I.
+ *   - stopping test: recursive gamma = (r,r) <= tol^2 (b,b); tol <= 0 means
+ *     "never stop early" (threshold 0).  iters = number of x updates.
+ *   - b = 0 gives x = 0, iters = 0, status OK.
+ *   - breakdown: (p,Ap) <= 0 (classic) or delta/gamma - beta/alpha_old <= 0
+ *     (NewCG), or any non-finite reduction.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+enum { ORA_OK = 0, ORA_NOT_CONVERGED = 1, ORA_ERR_INVALID_ARG = -1,
+       ORA_ERR_BREAKDOWN = -3, ORA_ERR_NONFINITE = -5 };
+
+typedef struct {
+  int32_t status;
+  int32_t iters;        /* x updates (classic/NewCG), total inner iterations (IR) */
+  int32_t outer_iters;  /* refinement steps (IR), 0 otherwise */
+  int32_t pad;
+  double relres_recursive;  /* sqrt(gamma_last / (b,b)) */
+  double relres_true;       /* ||b - A x|| / ||b|| recomputed at the end */
+} ora_info;
+
+/* Optional per-iteration record, used by the invariant tests.  Every pointer
+ * may be NULL.  Vector traces hold ntrace snapshots of ny*ld doubles each:
+ * snapshot k is taken after k x-updates (k = 0 is the initial state).  For
+ * classic CG, p[k] is the direction used by update k+1; for NewCG, p[k], q[k],
+ * z[k] are the values used by update k+1 and w[k] the w after update k. */
+typedef struct {
+  double* x; double* r; double* p; double* w; double* q; double* z;
+  double* alpha;   /* [ntrace] alpha of update k+1 */
+  double* beta;    /* [ntrace] beta used to form p of update k+1 */
+  double* relres;  /* [maxit+1] sqrt(gamma_k/(b,b)) after k updates */
+  int32_t ntrace;
+  int32_t pad;
+} ora_trace;
+
+/* ------------------------------------------------------------------ */
+/* Stencil y = A x (Sec. II-B mask; fixed add order).                   */
+/* ------------------------------------------------------------------ */
+
+static double at64(const double* x, int nx, int ny, int ld, int i, int j) {
+  if (i < 0 || i >= nx || j < 0 || j >= ny) return 0.0;   /* zero Dirichlet */
+  return x[(size_t)j * ld + i];
+}
+
+void ora_lap5_apply_f64(int nx, int ny, int ld, const double* x, double* y) {
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      double acc = 4.0 * at64(x, nx, ny, ld, i, j);
+      acc -= at64(x, nx, ny, ld, i - 1, j);
+      acc -= at64(x, nx, ny, ld, i + 1, j);
+      acc -= at64(x, nx, ny, ld, i, j - 1);
+      acc -= at64(x, nx, ny, ld, i, j + 1);
+      y[(size_t)j * ld + i] = acc;
+    }
+}
+
+static float at32(const float* x, int nx, int ny, int ld, int i, int j) {
+  if (i < 0 || i >= nx || j < 0 || j >= ny) return 0.0f;
+  return x[(size_t)j * ld + i];
+}
+
+/* Same stencil with every operation rounded to binary32. */
+void ora_lap5_apply_f32(int nx, int ny, int ld, const float* x, float* y) {
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      float acc = 4.0f * at32(x, nx, ny, ld, i, j);
+      acc -= at32(x, nx, ny, ld, i - 1, j);
+      acc -= at32(x, nx, ny, ld, i + 1, j);
+      acc -= at32(x, nx, ny, ld, i, j - 1);
+      acc -= at32(x, nx, ny, ld, i, j + 1);
+      y[(size_t)j * ld + i] = acc;
+    }
+}
+
+/* bfloat16 <-> binary32.  bf16 is the upper half of a binary32 word, so the
+ * widening is exact; narrowing rounds to nearest, ties to even. */
+static float bf16_to_f32(uint16_t h) {
+  uint32_t u = (uint32_t)h << 16; float f; memcpy(&f, &u, 4); return f;
+}
+static uint16_t f32_to_bf16(float f) {
+  uint32_t u; memcpy(&u, &f, 4);
+  if ((u & 0x7fffffffu) > 0x7f800000u) return (uint16_t)((u >> 16) | 0x0040u); /* NaN stays NaN */
+  uint32_t keep = u >> 16;
+  uint32_t rest = u & 0xffffu;
+  /* round half to even on the discarded 16 bits */
+  if (rest > 0x8000u || (rest == 0x8000u && (keep & 1u))) keep += 1u;
+  return (uint16_t)keep;
+}
+
+uint16_t ora_f32_to_bf16(float f) { return f32_to_bf16(f); }
+float ora_bf16_to_f32(uint16_t h) { return bf16_to_f32(h); }
+
+/* bf16 storage, binary32 arithmetic in the fixed order, result rounded to bf16. */
+void ora_lap5_apply_bf16(int nx, int ny, int ld, const uint16_t* x, uint16_t* y) {
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+#define XB(ii, jj) (((ii) < 0 || (ii) >= nx || (jj) < 0 || (jj) >= ny) ? 0.0f : bf16_to_f32(x[(size_t)(jj) * ld + (ii)]))
+      float acc = 4.0f * XB(i, j);
+      acc -= XB(i - 1, j);
+      acc -= XB(i + 1, j);
+      acc -= XB(i, j - 1);
+      acc -= XB(i, j + 1);
+#undef XB
+      y[(size_t)j * ld + i] = f32_to_bf16(acc);
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Vector helpers over the nx-by-ny interior (padding columns ignored). */
+/* ------------------------------------------------------------------ */
+
+/* (a, b) summed in index order (row by row, i fastest), binary64. */
+double ora_dot_f64(int nx, int ny, int ld, const double* a, const double* b) {
+  double s = 0.0;
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) s += a[(size_t)j * ld + i] * b[(size_t)j * ld + i];
+  return s;
+}
+
+static void axpy64(int nx, int ny, int ld, double* y, double a, const double* x) {
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) y[(size_t)j * ld + i] = y[(size_t)j * ld + i] + a * x[(size_t)j * ld + i];
+}
+
+/* y = x + beta * y */
+static void xpby64(int nx, int ny, int ld, const double* x, double beta, double* y) {
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) y[(size_t)j * ld + i] = x[(size_t)j * ld + i] + beta * y[(size_t)j * ld + i];
+}
+
+static void copy64(int nx, int ny, int ld, double* y, const double* x) {
+  for (int j = 0; j < ny; ++j) memcpy(y + (size_t)j * ld, x + (size_t)j * ld, sizeof(double) * (size_t)nx);
+}
+
+static void zero64(int nx, int ny, int ld, double* y) {
+  for (int j = 0; j < ny; ++j) memset(y + (size_t)j * ld, 0, sizeof(double) * (size_t)nx);
+}
+
+/* r = b - A x */
+static void residual64(int nx, int ny, int ld, const double* b, const double* x, double* r) {
+  ora_lap5_apply_f64(nx, ny, ld, x, r);
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) r[(size_t)j * ld + i] = b[(size_t)j * ld + i] - r[(size_t)j * ld + i];
+}
+
+static double true_relres(int nx, int ny, int ld, const double* b, const double* x, double bb) {
+  size_t n = (size_t)ny * ld;
+  double* r = (double*)calloc(n, sizeof(double));
+  if (!r) return NAN;
+  residual64(nx, ny, ld, b, x, r);
+  double rr = ora_dot_f64(nx, ny, ld, r, r);
+  free(r);
+  return sqrt(rr / bb);
+}
+
+static void snap(double* dst, int k, int ntrace, size_t n, const double* src) {
+  if (dst && k >= 0 && k < ntrace) memcpy(dst + (size_t)k * n, src, n * sizeof(double));
+}
+
+static int arg_ok(int nx, int ny, int ld, int maxit) {
+  return nx >= 1 && ny >= 1 && ld >= nx && maxit >= 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Algorithm 1 (classic CG), with an initial guess x0 allowed.           */
+/* ------------------------------------------------------------------ */
+int ora_cg_classic(int nx, int ny, int ld, const double* b, double* x, double tol, int maxit,
+                   ora_trace* tr, ora_info* info) {
+  ora_info inf; memset(&inf, 0, sizeof inf);
+  if (!arg_ok(nx, ny, ld, maxit) || !b || !x) { inf.status = ORA_ERR_INVALID_ARG; if (info) *info = inf; return inf.status; }
+  const size_t n = (size_t)ny * ld;
+  const int nt = tr ? tr->ntrace : 0;
+  double bb = ora_dot_f64(nx, ny, ld, b, b);
+  if (!isfinite(bb)) { inf.status = ORA_ERR_NONFINITE; inf.relres_recursive = NAN; inf.relres_true = NAN; if (info) *info = inf; return inf.status; }
+  if (bb == 0.0) {  /* A x = 0 has the unique solution x = 0 */
+    zero64(nx, ny, ld, x);
+    inf.status = ORA_OK; if (info) *info = inf; return inf.status;
+  }
+  const double thr = tol > 0.0 ? tol * tol * bb : 0.0;
+  double* r = (double*)calloc(n, sizeof(double));
+  double* p = (double*)calloc(n, sizeof(double));
+  double* z = (double*)calloc(n, sizeof(double));
+  if (!r || !p || !z) { free(r); free(p); free(z); inf.status = ORA_ERR_INVALID_ARG; if (info) *info = inf; return inf.status; }
+
+  residual64(nx, ny, ld, b, x, r);                 /* r_old = b - A x0 (= b for x0 = 0) */
+  double gamma = ora_dot_f64(nx, ny, ld, r, r);    /* (r_old, r_old) */
+  copy64(nx, ny, ld, p, r);                        /* p = r_old */
+  if (tr && tr->relres) tr->relres[0] = sqrt(gamma / bb);
+  if (tr) { snap(tr->x, 0, nt, n, x); snap(tr->r, 0, nt, n, r); snap(tr->p, 0, nt, n, p);
+            if (tr->beta && nt > 0) tr->beta[0] = 0.0; }
+  int status = ORA_NOT_CONVERGED, k = 0;
+  if (!isfinite(gamma)) status = ORA_ERR_NONFINITE;
+  else if (gamma <= thr) status = ORA_OK;
+  while (status == ORA_NOT_CONVERGED && k < maxit) {
+    ora_lap5_apply_f64(nx, ny, ld, p, z);            /* z = A p */
+    double pz = ora_dot_f64(nx, ny, ld, z, p);       /* (z, p) */
+    if (!(pz > 0.0) || !isfinite(pz)) { status = ORA_ERR_BREAKDOWN; break; }
+    double alpha = gamma / pz;
+    if (tr && tr->alpha && k < nt) tr->alpha[k] = alpha;
+    axpy64(nx, ny, ld, x, alpha, p);                 /* x = x + alpha p */
+    axpy64(nx, ny, ld, r, -alpha, z);                /* r = r_old - alpha z */
+    double gnew = ora_dot_f64(nx, ny, ld, r, r);     /* (r, r) */
+    ++k;
+    if (tr) { snap(tr->x, k, nt, n, x); snap(tr->r, k, nt, n, r); if (tr->relres) tr->relres[k] = sqrt(gnew / bb); }
+    if (!isfinite(gnew)) { status = ORA_ERR_NONFINITE; gamma = gnew; break; }
+    double beta = gnew / gamma;                      /* (r,r)/(r_old,r_old) */
+    gamma = gnew;                                    /* r_old = r */
+    if (gnew <= thr) { status = ORA_OK; break; }
+    xpby64(nx, ny, ld, r, beta, p);                  /* p = r + beta p */
+    if (tr) { snap(tr->p, k, nt, n, p); if (tr->beta && k < nt) tr->beta[k] = beta; }
+  }
+  inf.status = status; inf.iters = k;
+  inf.relres_recursive = sqrt(gamma / bb);
+  inf.relres_true = true_relres(nx, ny, ld, b, x, bb);
+  free(r); free(p); free(z);
+  if (info) *info = inf;
+  return status;
+}
+
+/* ------------------------------------------------------------------ */
+/* Algorithm 2 (NewCG = pipelined CG of Ghysels & Vanroose, M = I).      */
+/* rr_period > 0 enables residual replacement every rr_period updates:   */
+/* r = b - A x, w = A r, q = A p, z = A q are recomputed from x and p.   */
+/* ------------------------------------------------------------------ */
+int ora_cg_newcg(int nx, int ny, int ld, const double* b, double* x, double tol, int maxit,
+                 int rr_period, ora_trace* tr, ora_info* info) {
+  ora_info inf; memset(&inf, 0, sizeof inf);
+  if (!arg_ok(nx, ny, ld, maxit) || !b || !x || rr_period < 0) { inf.status = ORA_ERR_INVALID_ARG; if (info) *info = inf; return inf.status; }
+  const size_t n = (size_t)ny * ld;
+  const int nt = tr ? tr->ntrace : 0;
+  double bb = ora_dot_f64(nx, ny, ld, b, b);
+  if (!isfinite(bb)) { inf.status = ORA_ERR_NONFINITE; inf.relres_recursive = NAN; inf.relres_true = NAN; if (info) *info = inf; return inf.status; }
+  if (bb == 0.0) { zero64(nx, ny, ld, x); inf.status = ORA_OK; if (info) *info = inf; return inf.status; }
+  const double thr = tol > 0.0 ? tol * tol * bb : 0.0;
+  double *r = calloc(n, 8), *w = calloc(n, 8), *nv = calloc(n, 8), *z = calloc(n, 8), *q = calloc(n, 8), *p = calloc(n, 8);
+  if (!r || !w || !nv || !z || !q || !p) { free(r); free(w); free(nv); free(z); free(q); free(p); inf.status = ORA_ERR_INVALID_ARG; if (info) *info = inf; return inf.status; }
+
+  int status = ORA_NOT_CONVERGED, k = 0;
+  residual64(nx, ny, ld, b, x, r);                    /* line 1: r = b - A x */
+  ora_lap5_apply_f64(nx, ny, ld, r, w);               /* line 2: w = A r */
+  double gamma = ora_dot_f64(nx, ny, ld, r, r);       /* line 3 */
+  if (tr && tr->relres) tr->relres[0] = sqrt(gamma / bb);
+  if (tr) { snap(tr->x, 0, nt, n, x); snap(tr->r, 0, nt, n, r); snap(tr->w, 0, nt, n, w); }
+  double alpha = 0.0;
+  if (!isfinite(gamma)) status = ORA_ERR_NONFINITE;
+  else if (gamma <= thr) status = ORA_OK;
+  else if (maxit > 0) {
+    double delta = ora_dot_f64(nx, ny, ld, w, r);     /* line 4 */
+    ora_lap5_apply_f64(nx, ny, ld, w, nv);            /* line 5: n = A w */
+    if (!(delta > 0.0) || !isfinite(delta)) status = ORA_ERR_BREAKDOWN;
+    else {
+      alpha = gamma / delta;                          /* line 6 (beta = 0) */
+      copy64(nx, ny, ld, z, nv);                      /* line 7: z = n, q = w, p = r */
+      copy64(nx, ny, ld, q, w);
+      copy64(nx, ny, ld, p, r);
+      if (tr) { snap(tr->p, 0, nt, n, p); snap(tr->q, 0, nt, n, q); snap(tr->z, 0, nt, n, z);
+                if (tr->alpha && nt > 0) tr->alpha[0] = alpha;
+                if (tr->beta && nt > 0) tr->beta[0] = 0.0; }
+      axpy64(nx, ny, ld, x, alpha, p);                /* line 8 */
+      axpy64(nx, ny, ld, r, -alpha, q);               /* line 9 (read as r - alpha q) */
+      axpy64(nx, ny, ld, w, -alpha, z);               /* line 10 (read as w - alpha z) */
+      k = 1;
+      if (tr) { snap(tr->x, 1, nt, n, x); snap(tr->r, 1, nt, n, r); snap(tr->w, 1, nt, n, w); }
+    }
+  }
+  while (status == ORA_NOT_CONVERGED && k >= 1) {
+    if (rr_period > 0 && k % rr_period == 0) {        /* residual replacement */
+      residual64(nx, ny, ld, b, x, r);
+      ora_lap5_apply_f64(nx, ny, ld, r, w);
+      ora_lap5_apply_f64(nx, ny, ld, p, q);
+      ora_lap5_apply_f64(nx, ny, ld, q, z);
+    }
+    double gamma_old = gamma;                         /* line 12 */
+    gamma = ora_dot_f64(nx, ny, ld, r, r);            /* line 13 */
+    if (tr && tr->relres) tr->relres[k] = sqrt(gamma / bb);
+    if (!isfinite(gamma)) { status = ORA_ERR_NONFINITE; break; }
+    if (gamma <= thr) { status = ORA_OK; break; }
+    if (k >= maxit) break;
+    double delta = ora_dot_f64(nx, ny, ld, w, r);     /* line 14 */
+    ora_lap5_apply_f64(nx, ny, ld, w, nv);            /* line 15: n = A w */
+    double beta = gamma / gamma_old;                  /* line 16 */
+    double denom = delta / gamma - beta / alpha;      /* line 17, de-garbled */
+    if (!(denom > 0.0) || !isfinite(denom)) { status = ORA_ERR_BREAKDOWN; break; }
+    alpha = 1.0 / denom;
+    xpby64(nx, ny, ld, nv, beta, z);                  /* line 18: z = n + beta z */
+    xpby64(nx, ny, ld, w, beta, q);                   /* line 19: q = w + beta q */
+    xpby64(nx, ny, ld, r, beta, p);                   /* line 20: p = r + beta p */
+    if (tr) { snap(tr->p, k, nt, n, p); snap(tr->q, k, nt, n, q); snap(tr->z, k, nt, n, z);
+              if (tr->alpha && k < nt) tr->alpha[k] = alpha;
+              if (tr->beta && k < nt) tr->beta[k] = beta; }
+    axpy64(nx, ny, ld, x, alpha, p);                  /* line 21 */
+    axpy64(nx, ny, ld, r, -alpha, q);                 /* line 22 */
+    axpy64(nx, ny, ld, w, -alpha, z);                 /* line 23 */
+    ++k;
+    if (tr) { snap(tr->x, k, nt, n, x); snap(tr->r, k, nt, n, r); snap(tr->w, k, nt, n, w); }
+  }
+  inf.status = status; inf.iters = k;
+  inf.relres_recursive = sqrt(gamma / bb);
+  inf.relres_true = true_relres(nx, ny, ld, b, x, bb);
+  free(r); free(w); free(nv); free(z); free(q); free(p);
+  if (info) *info = inf;
+  return status;
+}
+
+/* ------------------------------------------------------------------ */
+/* Compensated binary32 dot product, Dot2 of Ogita, Rump & Oishi,        */
+/* "Accurate sum and dot product", SIAM J. Sci. Comput. 26 (2005):       */
+/* TwoProduct by an exact fused multiply-add, TwoSum by Knuth.  Returns   */
+/* the unevaluated pair (s, c); the result is s + c.                     */
+/* ------------------------------------------------------------------ */
+static void two_sum_f(float a, float b, float* s, float* e) {
+  float x = a + b;
+  float z = x - a;
+  *s = x;
+  *e = (a - (x - z)) + (b - z);
+}
+
+void ora_dot2_f32(int nx, int ny, int ld, const float* a, const float* b, double* out_s, double* out_c) {
+  float s = 0.0f, c = 0.0f;
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      float ai = a[(size_t)j * ld + i], bi = b[(size_t)j * ld + i];
+      float h = ai * bi;
+      float l = fmaf(ai, bi, -h);   /* exact low part of the product */
+      float t, e;
+      two_sum_f(s, h, &t, &e);
+      s = t;
+      c = c + (e + l);
+    }
+  *out_s = s; *out_c = c;
+}
+
+/* ------------------------------------------------------------------ */
+/* Mixed precision: FP64 iterative refinement around a low-precision     */
+/* inner CG.  Inner storage: 1 = binary32 everywhere; 2 = bf16 p and r,   */
+/* binary32 d and z.  Inner arithmetic is binary32; inner dots are Dot2;  */
+/* inner scalars (alpha, beta) are formed in binary64 and rounded to      */
+/* binary32 for the vector updates.  Inner variant: classic CG (Alg. 1).  */
+/* ------------------------------------------------------------------ */
+static float stor(float v, int bf) { return bf ? bf16_to_f32(f32_to_bf16(v)) : v; }
+
+static double dot2_pair(int nx, int ny, int ld, const float* a, const float* b) {
+  double s, c; ora_dot2_f32(nx, ny, ld, a, b, &s, &c); return s + c;
+}
+
+/* Inner classic CG on A d = rin from d = 0; returns iterations used. */
+static int inner_cg_f32(int nx, int ny, int ld, const float* rin, float* d, double tol_in, int maxit_in,
+                        int bf, float* r, float* p, float* z, int* brk) {
+  size_t n = (size_t)ny * ld;
+  memset(d, 0, n * sizeof(float));
+  for (size_t t = 0; t < n; ++t) { r[t] = stor(rin[t], bf); p[t] = r[t]; }
+  double g = dot2_pair(nx, ny, ld, r, r);
+  double thr = tol_in * tol_in * g;
+  int k = 0;
+  *brk = 0;
+  while (k < maxit_in && g > thr) {
+    ora_lap5_apply_f32(nx, ny, ld, p, z);
+    double pz = dot2_pair(nx, ny, ld, p, z);
+    if (!(pz > 0.0) || !isfinite(pz)) { *brk = 1; break; }
+    float a = (float)(g / pz);
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        size_t t = (size_t)j * ld + i;
+        d[t] = d[t] + a * p[t];
+        r[t] = stor(r[t] - a * z[t], bf);
+      }
+    double gn = dot2_pair(nx, ny, ld, r, r);
+    ++k;
+    if (!isfinite(gn)) { *brk = 1; break; }
+    float bt = (float)(gn / g);
+    g = gn;
+    if (g <= thr) break;
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        size_t t = (size_t)j * ld + i;
+        p[t] = stor(r[t] + bt * p[t], bf);
+      }
+  }
+  return k;
+}
+
+int ora_cg_ir(int nx, int ny, int ld, const double* b, double* x, double tol, int max_outer,
+              int inner_storage, double tol_in, int maxit_in, ora_info* info) {
+  ora_info inf; memset(&inf, 0, sizeof inf);
+  if (!arg_ok(nx, ny, ld, max_outer) || !b || !x || (inner_storage != 1 && inner_storage != 2) || maxit_in < 1) {
+    inf.status = ORA_ERR_INVALID_ARG; if (info) *info = inf; return inf.status;
+  }
+  const size_t n = (size_t)ny * ld;
+  double bb = ora_dot_f64(nx, ny, ld, b, b);
+  if (!isfinite(bb)) { inf.status = ORA_ERR_NONFINITE; inf.relres_recursive = NAN; inf.relres_true = NAN; if (info) *info = inf; return inf.status; }
+  if (bb == 0.0) { zero64(nx, ny, ld, x); inf.status = ORA_OK; if (info) *info = inf; return inf.status; }
+  const double thr = tol > 0.0 ? tol * tol * bb : 0.0;
+  const int bf = inner_storage == 2;
+  double* r = calloc(n, 8);
+  float *rin = calloc(n, 4), *d = calloc(n, 4), *ri = calloc(n, 4), *pi = calloc(n, 4), *zi = calloc(n, 4);
+  if (!r || !rin || !d || !ri || !pi || !zi) { free(r); free(rin); free(d); free(ri); free(pi); free(zi); inf.status = ORA_ERR_INVALID_ARG; if (info) *info = inf; return inf.status; }
+  int status = ORA_NOT_CONVERGED, outer = 0, total_inner = 0;
+  double rr = 0.0;
+  for (;;) {
+    residual64(nx, ny, ld, b, x, r);                    /* FP64 residual */
+    rr = ora_dot_f64(nx, ny, ld, r, r);
+    if (!isfinite(rr)) { status = ORA_ERR_NONFINITE; break; }
+    if (rr <= thr) { status = ORA_OK; break; }
+    if (outer >= max_outer) break;
+    for (size_t t = 0; t < n; ++t) rin[t] = (float)r[t]; /* round to nearest */
+    int brk = 0;
+    total_inner += inner_cg_f32(nx, ny, ld, rin, d, tol_in, maxit_in, bf, ri, pi, zi, &brk);
+    if (brk) { status = ORA_ERR_BREAKDOWN; break; }
+    for (int j = 0; j < ny; ++j)                        /* FP64 update */
+      for (int i = 0; i < nx; ++i) x[(size_t)j * ld + i] = x[(size_t)j * ld + i] + (double)d[(size_t)j * ld + i];
+    ++outer;
+  }
+  inf.status = status; inf.iters = total_inner; inf.outer_iters = outer;
+  inf.relres_recursive = sqrt(rr / bb);
+  inf.relres_true = true_relres(nx, ny, ld, b, x, bb);
+  free(r); free(rin); free(d); free(ri); free(pi); free(zi);
+  if (info) *info = inf;
+  return status;
+}

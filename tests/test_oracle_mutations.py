@@ -1,0 +1,114 @@
+"""Planted mistakes: each test compiles a copy of the oracle with one plausible
+error (a flipped sign, a wrong index, a dropped term, a swapped operand) and
+checks that the pins catch it.  The mistakes are planted in a temporary copy on
+the CPU; the committed oracle is never modified."""
+
+import os
+import subprocess
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+import lap5_inputs as gen
+import oracle
+from tests.helpers import flat, kron_laplacian
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "lap5_oracle.c")
+
+MUTATIONS = {
+    "stencil_sign_west": ("acc -= at64(x, nx, ny, ld, i - 1, j);", "acc += at64(x, nx, ny, ld, i - 1, j);"),
+    "stencil_index_north": ("acc -= at64(x, nx, ny, ld, i, j + 1);", "acc -= at64(x, nx, ny, ld, i + 1, j + 1);"),
+    "classic_beta_inverted": ("double beta = gnew / gamma;", "double beta = gamma / gnew;"),
+    "classic_alpha_transposed": ("double alpha = gamma / pz;", "double alpha = pz / gamma;"),
+    "newcg_r_sign": ("axpy64(nx, ny, ld, r, -alpha, q);                 /* line 22 */",
+                     "axpy64(nx, ny, ld, r, alpha, q);                 /* line 22 */"),
+    "newcg_w_uses_q": ("axpy64(nx, ny, ld, w, -alpha, z);                 /* line 23 */",
+                       "axpy64(nx, ny, ld, w, -alpha, q);                 /* line 23 */"),
+    "newcg_z_drops_beta": ("xpby64(nx, ny, ld, nv, beta, z);                  /* line 18: z = n + beta z */",
+                           "xpby64(nx, ny, ld, nv, 0.0, z);                  /* line 18: z = n + beta z */"),
+    "newcg_alpha_sign": ("double denom = delta / gamma - beta / alpha;", "double denom = delta / gamma + beta / alpha;"),
+}
+
+
+@pytest.fixture(scope="module")
+def mutant_dir(tmp_path_factory):
+    return tmp_path_factory.mktemp("mutants")
+
+
+def _load_mutant(name, mutant_dir):
+    src = open(SRC).read()
+    old, new = MUTATIONS[name]
+    assert src.count(old) == 1, name
+    path_c = os.path.join(mutant_dir, name + ".c")
+    path_so = os.path.join(mutant_dir, name + ".so")
+    with open(path_c, "w") as f:
+        f.write(src.replace(old, new))
+    subprocess.run(["gcc", "-O1", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-o", path_so, path_c, "-lm"],
+                   check=True)
+    return path_so
+
+
+class _Swap:
+    def __init__(self, path):
+        self.path = path
+
+    def __enter__(self):
+        self.saved = oracle._lib
+        oracle._lib = None
+        real_build = oracle._build.build
+        oracle._build.build = lambda force=False: self.path
+        try:
+            oracle.lib()
+        finally:
+            oracle._build.build = real_build
+        return self
+
+    def __exit__(self, *exc):
+        oracle._lib = self.saved
+        return False
+
+
+def _pins_pass():
+    """A compact subset of the oracle pins; True iff all hold."""
+    nx, ny = 9, 7
+    xi = np.random.default_rng(0).integers(-50, 51, size=(ny, nx)).astype(np.float64)
+    if not np.array_equal(flat(oracle.lap5_apply(xi), nx), kron_laplacian(nx, ny) @ flat(xi, nx)):
+        return False
+    A = kron_laplacian(nx, ny).toarray()
+    b = gen.uniform_rhs(nx, ny, seed=3)
+    x_ref = sla.cho_solve(sla.cho_factor(A), flat(b, nx))
+    for variant in ("classic", "newcg"):
+        x, info = oracle.cg_solve(b, variant=variant, tol=1e-12, maxit=400)
+        if info["status"] != oracle.OK:
+            return False
+        if np.linalg.norm(flat(x, nx) - x_ref) > 1e-9 * np.linalg.norm(x_ref):
+            return False
+    n, K = 24, 12
+    bb = gen.uniform_rhs(n, n, seed=5)
+    tc = oracle.Trace(n, n, K + 1, K)
+    tn = oracle.Trace(n, n, K + 1, K, newcg=True)
+    oracle.cg_classic(bb, tol=0.0, maxit=K, trace=tc)
+    oracle.cg_newcg(bb, tol=0.0, maxit=K, trace=tn)
+    if not np.all(np.isfinite(tn.x[K])) or np.linalg.norm(tc.x[K] - tn.x[K]) > 1e-10 * np.linalg.norm(tc.x[K]):
+        return False
+    A2 = kron_laplacian(n, n)
+    for k in range(K):
+        w, r, z, q = (tn.w[k].reshape(-1), tn.r[k].reshape(-1), tn.z[k].reshape(-1), tn.q[k].reshape(-1))
+        if np.linalg.norm(w - A2 @ r) > 1e-10 * np.linalg.norm(A2 @ r) or \
+                np.linalg.norm(z - A2 @ q) > 1e-10 * np.linalg.norm(A2 @ q):
+            return False
+    return True
+
+
+def test_unmutated_oracle_passes_pins():
+    assert _pins_pass()
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistake_is_caught(name, mutant_dir):
+    path = _load_mutant(name, mutant_dir)
+    with _Swap(path):
+        caught = not _pins_pass()
+    assert caught, "pins did not catch the planted mistake " + name
+
