@@ -1,0 +1,327 @@
+"""Benchmark: matrix-free CG on the 2D Dirichlet 5-point Laplacian on GB300.
+
+Workload (one "step"): the 4096 x 4096 binary64 grid, b = A u* + 1e-3 xi
+(u* = sin(pi x) sin(pi y), xi ~ N(0,1), seed 2), x0 = 0, solved by classic CG
+(Algorithm 1) for 500 fixed iterations and then by NewCG (Algorithm 2) for 500
+fixed iterations, each in one persistent launch.  Metric: grid points x CG
+iterations per second over the whole job.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints ONE JSON line (rank 0).  Under torchrun (N > 1) every rank solves its
+own replica of the step on its own GPU (the solver does not shard across GPUs);
+value = all ranks' points*iterations / max-over-ranks time.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import lap5_inputs as gen  # noqa: E402
+
+METRIC = "grid-pts·CG-iters/s and HBM GB/s vs peak; time-to-1e-10 mixed vs FP64 CG"
+UNIT = "grid-pts*CG-iters/s"
+NX = NY = 4096
+ITERS = 500
+SEED = 2
+VARIANTS = ("classic", "newcg")
+WORKLOAD = ("4096x4096 interior grid, FP64, b = A u* + 1e-3 N(0,1) (seed 2), x0 = 0; classic CG then NewCG, "
+            "500 fixed iterations each, one persistent launch per solve")
+
+# Algorithmic cost per grid point per iteration of each fused kernel (binary64):
+# bytes = minimum HBM traffic of the variant (each state vector read/written once),
+# ops = FP64-pipe instructions (stencil 4, each axpy 1, each dot 1).
+COST = {
+    "classic": {"bytes": 80, "fp64_ops": 9, "kernel": "k_classic<double,2>"},  # store-z form
+    "newcg": {"bytes": 96, "fp64_ops": 12, "kernel": "k_newcg<double,2>"},
+}
+FP64_PEAK_TFLOPS = 1.25  # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (nominal GB300 FP64)
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % index)
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline(sample_iters=4):
+    """The oracle (single-threaded C, as it stands) on a bounded sample of the
+    step: both variants for sample_iters iterations on the full 4096^2 grid."""
+    import oracle
+    b = gen.manufactured_rhs(NX, NY, seed=SEED)
+    t0 = time.perf_counter()
+    for v in VARIANTS:
+        oracle.cg_solve(b, variant=v, tol=0.0, maxit=sample_iters)
+    dt = time.perf_counter() - t0
+    units = len(VARIANTS) * NX * NY * sample_iters
+    return {"value": units / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "4096x4096 FP64, classic + NewCG, %d iterations each (incl. setup and final true-residual "
+                      "pass), single-threaded C oracle" % sample_iters, "seconds": dt}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    b = gen.manufactured_rhs(NX, NY, seed=SEED)
+    import oracle
+    sample_iters = 3
+
+    def step():
+        for v in VARIANTS:
+            oracle.cg_solve(b, variant=v, tol=0.0, maxit=sample_iters)
+
+    for _ in range(max(0, min(args.warmup, 1))):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    units = args.steps * len(VARIANTS) * NX * NY * sample_iters
+    value = units / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD + " (reference arm: the CPU oracle, %d iterations per variant per step)"
+                                   % sample_iters, "nx": NX, "ny": NY},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "%d iterations per variant per step on the full grid" % sample_iters},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import paper_1803_03797_gb300 as lap5cg
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+    lap5cg.lib()
+
+    b_host = gen.manufactured_rhs(NX, NY, seed=SEED)
+    b = torch.from_numpy(b_host).to(dev)
+    xs = {v: torch.zeros_like(b) for v in VARIANTS}
+    wsz = max(lap5cg.workspace_size(NX, NY, NX, v, "f64") for v in VARIANTS)
+    workspace = torch.empty(wsz, dtype=torch.uint8, device=dev)
+    info = {v: torch.empty(lap5cg.INFO_BYTES, dtype=torch.uint8, device=dev) for v in VARIANTS}
+    stream = torch.cuda.current_stream(dev)
+    opts = lap5cg.default_opts()
+
+    def solve(v):
+        xs[v].zero_()
+        lap5cg.cg_solve(b, tol=0.0, maxit=ITERS, variant=v, workspace=workspace, info=info[v], out=xs[v],
+                        opts=opts, stream=stream)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        for v in VARIANTS:
+            solve(v)
+    barrier()
+    for v in VARIANTS:
+        rec = lap5cg.decode_info(info[v])[0]
+        if rec["iters"] != ITERS or rec["status"] not in (lap5cg.OK, lap5cg.NOT_CONVERGED):
+            raise RuntimeError("warm-up solve failed: %s %r" % (v, rec))
+
+    ev = {v: [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)] for v in VARIANTS}
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    barrier()
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for k in range(args.steps):
+        for v in VARIANTS:
+            ev[v][k][0].record(stream)
+            solve(v)
+            ev[v][k][1].record(stream)
+    stop.record(stream)
+    barrier()
+    clk = clocks.stop()
+    elapsed_ms = start.elapsed_time(stop)
+    if ws > 1:
+        t = torch.tensor([elapsed_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    units_per_step = len(VARIANTS) * NX * NY * ITERS
+    value = ws * units_per_step * args.steps / (elapsed_ms * 1e-3)
+
+    hbm_peak, peak_kind = load_peaks()
+    per_kernel = {}
+    for v in VARIANTS:
+        ms = float(np.mean([s.elapsed_time(e) for s, e in ev[v]]))
+        pts_it = NX * NY * ITERS
+        gbs = COST[v]["bytes"] * pts_it / (ms * 1e-3) / 1e9
+        tfl = 2 * COST[v]["fp64_ops"] * pts_it / (ms * 1e-3) / 1e12
+        per_kernel[v] = {"kernel": COST[v]["kernel"], "ms_per_launch": ms, "pts_iters_per_s": pts_it / (ms * 1e-3),
+                         "hbm": {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                                 "bytes_per_pt_iter": COST[v]["bytes"]},
+                         "fp64": {"achieved": tfl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                  "frac": tfl / FP64_PEAK_TFLOPS, "ops_per_pt_iter": COST[v]["fp64_ops"]}}
+    dom = max(VARIANTS, key=lambda v: per_kernel[v]["ms_per_launch"])
+    pk = per_kernel[dom]
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "traffic_per_launch.json")
+    if os.path.exists(prof):
+        try:
+            traffic = json.load(open(prof)).get(COST[dom]["kernel"])
+        except Exception:
+            traffic = None
+    roofline = {"bound": "alu", "achieved": pk["fp64"]["achieved"], "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": pk["fp64"]["frac"], "traffic": traffic, "kernel": pk["kernel"],
+                "peak_kind": "nominal FP64 pipe (FMA = 2 flop; every FP64 instruction counted as one FMA)",
+                "hbm_view": pk["hbm"], "hbm_peak_kind": peak_kind}
+
+    e2e = None
+    if not args.no_e2e:
+        b_pin = torch.from_numpy(b_host).pin_memory()
+        x_pin = {v: torch.empty_like(b_pin).pin_memory() for v in VARIANTS}
+        b_dev = torch.empty_like(b)
+        xs_dev = {v: torch.empty_like(b) for v in VARIANTS}
+        info_pin = torch.empty(lap5cg.INFO_BYTES * 2, dtype=torch.uint8).pin_memory()
+
+        def e2e_step():
+            b_dev.copy_(b_pin, non_blocking=True)
+            for i, v in enumerate(VARIANTS):
+                xs_dev[v].zero_()
+                lap5cg.cg_solve(b_dev, tol=0.0, maxit=ITERS, variant=v, workspace=workspace, info=info[v],
+                                out=xs_dev[v], opts=opts, stream=stream)
+                x_pin[v].copy_(xs_dev[v], non_blocking=True)
+                info_pin[i * lap5cg.INFO_BYTES:(i + 1) * lap5cg.INFO_BYTES].copy_(info[v], non_blocking=True)
+
+        e2e_step()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        e1.record(stream)
+        barrier()
+        ems = e0.elapsed_time(e1)
+        if ws > 1:
+            t = torch.tensor([ems], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ems = float(t.item())
+        e2e = {"value": ws * units_per_step * args.steps / (ems * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": int(b_pin.numel() * 8),
+               "d2h_bytes_per_step": int(sum(x.numel() * 8 for x in x_pin.values()) + info_pin.numel()),
+               "ms_per_step": ems / args.steps}
+
+    line = None
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline and ws == 1:
+            cpu = cpu_baseline()
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "nx": NX, "ny": NY, "iters_per_solve": ITERS,
+                           "variants": list(VARIANTS), "parallelism": "replicas" if ws > 1 else "single-gpu",
+                           "l2": "inputs larger than L2: each 4096^2 FP64 vector is 134 MB > 126 MB L2, "
+                                 "working set ~1 GB"},
+                "roofline": roofline, "per_kernel": per_kernel, "cpu_baseline": cpu, "e2e": e2e,
+                "clocks": clk, "gpu_launches": len(VARIANTS) * args.steps}
+        print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

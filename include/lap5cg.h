@@ -1,0 +1,187 @@
+/*
+ * lap5cg.h -- C ABI of liblap5cg: matrix-free conjugate gradient for the 2D
+ * Dirichlet 5-point Laplacian on an NVIDIA GB300 (sm_103a).
+ *
+ * Method: arxiv 1803.03797, "Efficient FPGA Implementation of Conjugate
+ * Gradient Methods for Laplacian System using HLS".
+ *   - Problem (Sec. II): solve A x = b on an nx-by-ny interior grid of the unit
+ *     square with zero Dirichlet boundary.  A is the 5-point stencil with the
+ *     3x3 mask [0 -1 0; -1 4 -1; 0 -1 0] printed in Sec. II-B (symmetric
+ *     positive definite, no 1/h^2 scaling), applied matrix-free.
+ *   - Classic CG: Algorithm 1 (stdCG).
+ *   - NewCG: Algorithm 2, the pipelined CG of Ghysels & Vanroose (M = I) that
+ *     lets the stencil overlap the two dot products (Sec. II, Fig. NewCG).
+ *
+ * Data layout (all entry points): a grid is ny rows of ld elements (ld >= nx,
+ * the row pitch in elements); element (i, j), 0 <= i < nx, 0 <= j < ny, is at
+ * offset j*ld + i.  A buffer holds ny*ld elements.  Padding columns
+ * nx <= i < ld are never written.  Boundary values are implicit zeros and are
+ * not stored.
+ *
+ * Ownership: the caller owns every buffer (inputs, outputs, workspace, info).
+ * The library allocates no device memory on any entry point below and keeps no
+ * mutable global state apart from a per-device cache of device properties.
+ *
+ * Ordering: every call is asynchronous on the given CUDA stream (a
+ * cudaStream_t passed as void*; NULL = the legacy default stream).  The return
+ * value reports host-side argument validation and launch errors only; solve
+ * outcomes are written to the device-side lap5cg_info once the stream reaches
+ * them.  No entry point synchronises the device.
+ *
+ * Errors: negative return values are errors, 0 is success.  No C++ exception
+ * crosses this interface.
+ */
+#ifndef LAP5CG_H
+#define LAP5CG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LAP5CG_API __attribute__((visibility("default")))
+#else
+#define LAP5CG_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes, used both as return values and in lap5cg_info.status. */
+typedef enum {
+  LAP5CG_OK = 0,                 /* converged (or nothing to do) */
+  LAP5CG_NOT_CONVERGED = 1,      /* maxit reached before the tolerance */
+  LAP5CG_ERR_INVALID_ARG = -1,   /* rejected on the host before launch */
+  LAP5CG_ERR_CUDA = -2,          /* a CUDA runtime call failed */
+  LAP5CG_ERR_BREAKDOWN = -3,     /* (p,Ap) <= 0 (classic) or the NewCG alpha denominator <= 0 */
+  LAP5CG_ERR_SYNC_TIMEOUT = -4,  /* a device-side grid barrier exceeded its time limit */
+  LAP5CG_ERR_NONFINITE = -5,     /* a reduction produced Inf or NaN (e.g. NaN in b) */
+  LAP5CG_ERR_UNSUPPORTED = -6,   /* valid but not supported combination */
+  LAP5CG_ERR_WORKSPACE = -7      /* workspace missing, too small or misaligned */
+} lap5cg_status;
+
+/* Element types of lap5_apply. */
+typedef enum { LAP5CG_DT_F64 = 0, LAP5CG_DT_F32 = 1, LAP5CG_DT_BF16 = 2 } lap5cg_dtype;
+
+/* Algorithm 1 or Algorithm 2. */
+typedef enum { LAP5CG_CLASSIC = 0, LAP5CG_NEWCG = 1 } lap5cg_variant;
+
+/* Precision of a solve.
+ *   F64      : b, x binary64; all arithmetic binary64.
+ *   F32      : b, x binary32; arithmetic binary32, dot products accumulated
+ *              with compensated (Dot2) summation, scalars in binary64.
+ *   IR_F32   : b, x binary64.  Outer FP64 iterative refinement (residual
+ *              b - A x, update x += d and their dot products in binary64)
+ *              around an inner classic CG stored and computed in binary32.
+ *   IR_BF16PR: as IR_F32 but the inner p and r are stored as bf16 (round to
+ *              nearest even); inner arithmetic binary32. */
+typedef enum {
+  LAP5CG_PREC_F64 = 0, LAP5CG_PREC_F32 = 1, LAP5CG_PREC_IR_F32 = 2, LAP5CG_PREC_IR_BF16PR = 3
+} lap5cg_precision;
+
+/* Per-solve outcome, written on the device (one entry per right-hand side or
+ * per batched instance). */
+typedef struct {
+  int32_t status;           /* lap5cg_status */
+  int32_t iters;            /* x updates done (IR: total inner iterations) */
+  int32_t outer_iters;      /* IR refinement steps; 0 for F64/F32 */
+  int32_t pad;
+  double relres_recursive;  /* sqrt((r,r)/(b,b)) of the recurrence residual at exit */
+  double relres_true;       /* ||b - A x|| / ||b|| recomputed at exit (NaN if disabled) */
+} lap5cg_info;
+
+/* Optional tuning and behaviour knobs.  Pass NULL for defaults, or fill a
+ * struct with lap5cg_opts_default() and change fields. */
+typedef struct {
+  int32_t rr_period;        /* NewCG residual replacement every rr_period updates; 0 = off */
+  int32_t store_z;          /* classic: 1 stores z = A p (fewer FP64 ops), 0 recomputes A p
+                               in the update pass (fewer bytes), -1 = choose by precision */
+  int32_t ctas;             /* persistent CTAs; 0 = choose from size and occupancy */
+  int32_t warps_per_cta;    /* 4, 8 or 16; 0 = default */
+  int32_t min_rows;         /* minimum rows per warp unit; 0 = default */
+  int32_t true_residual;    /* 1 (default) recompute ||b - A x|| at exit, 0 skip */
+  int32_t maxit_inner;      /* IR: inner iteration cap per refinement step; 0 = default */
+  int32_t max_outer;        /* IR: refinement step cap; 0 = default (60) */
+  double tol_inner;         /* IR: inner relative tolerance; <= 0 = default (1e-4 F32, 1e-2 BF16) */
+  double timeout_s;         /* device barrier time limit in seconds; <= 0 = default (2 s) */
+  double* history;          /* optional device array of maxit+1 doubles: recursive
+                               relative residual after each update; NULL = off */
+} lap5cg_opts;
+
+/* Fill *o with the defaults above. */
+LAP5CG_API void lap5cg_opts_default(lap5cg_opts* o);
+
+/* Human-readable text of a status code (static storage). */
+LAP5CG_API const char* lap5cg_status_string(int status);
+
+/*
+ * y = A x, the Sec. II-B mask with zero Dirichlet boundary, in the fixed add
+ * order y = 4*xC - xW - xE - xS - xN (W/E: i-1/i+1, S/N: j-1/j+1).
+ *   dtype F64: binary64; F32: binary32; BF16: bf16 in and out, binary32
+ *   arithmetic, result rounded to nearest even.
+ *   x, y: device pointers to ny*ld elements each; must not overlap.
+ * Returns LAP5CG_OK, LAP5CG_ERR_INVALID_ARG (nx or ny < 1, ld < nx, NULL
+ * pointers, unknown dtype) or LAP5CG_ERR_CUDA.
+ */
+LAP5CG_API int lap5_apply(int nx, int ny, int ld, int dtype, const void* x, void* y, void* stream);
+
+/*
+ * Bytes of device workspace cg_solve needs for this shape, variant and
+ * precision (for nrhs right-hand sides solved one after another the workspace
+ * is reused, so nrhs does not change the size).  Returns 0 for invalid
+ * arguments.
+ */
+LAP5CG_API size_t cg_workspace_size(int nx, int ny, int ld, int variant, int precision, int nrhs);
+
+/*
+ * Solve A x = b (Algorithm 1 or 2) in one persistent kernel per right-hand side.
+ *   b, x     : device pointers, nrhs grids of ny*ld elements each, stored one
+ *              after another (right-hand side k at offset k*ny*ld).  Element
+ *              type: binary64 for F64/IR_*, binary32 for F32.  On entry x is the
+ *              initial guess x0 (zeros for the paper's setting); on exit the
+ *              solution.  b and x must not overlap.
+ *   tol      : stop when (r,r) <= tol^2 (b,b) (recursive residual); tol <= 0
+ *              runs maxit updates.  IR: tol applies to the FP64 true residual.
+ *   maxit    : maximum x updates (IR: maximum total inner iterations); >= 0.
+ *   workspace: device buffer of at least cg_workspace_size() bytes, 256-byte
+ *              aligned; contents on entry are irrelevant.
+ *   info     : device pointer to nrhs lap5cg_info entries.
+ *   opts     : NULL or tuning knobs (host pointer, read during the call).
+ * b = 0 yields x = 0, iters = 0, LAP5CG_OK.  The convergence test and all
+ * scalars stay on the device; no host synchronisation happens per iteration.
+ * Returns LAP5CG_OK when every launch was enqueued, else an error code.
+ */
+LAP5CG_API int cg_solve(int nx, int ny, int ld, const void* b, void* x, double tol, int maxit,
+             int variant, int precision, int nrhs, void* workspace, size_t ws_bytes,
+             lap5cg_info* info, const lap5cg_opts* opts, void* stream);
+
+/* Largest instance count one cg_solve_batched call accepts. */
+#define LAP5CG_MAX_BATCH 1024
+
+/*
+ * Bytes of device workspace cg_solve_batched needs for these shapes (host
+ * arrays of count entries).  Returns 0 for invalid arguments.
+ */
+LAP5CG_API size_t cg_batched_workspace_size(int count, const int* nx, const int* ny, const int* ld,
+                                 int variant, int precision);
+
+/*
+ * Solve count independent systems A_k x_k = b_k of different shapes in one
+ * persistent launch (per-instance convergence masking: an instance that has
+ * converged stops and its CTAs take the next instance, largest first).
+ *   nx, ny, ld: host arrays of count shapes.
+ *   b, x      : host arrays of count device pointers (element type as in
+ *               cg_solve for the precision).
+ *   info      : device pointer to count lap5cg_info entries.
+ * The host arrays are read during the call only.  Other arguments as cg_solve.
+ */
+LAP5CG_API int cg_solve_batched(int count, const int* nx, const int* ny, const int* ld,
+                     const void* const* b, void* const* x, double tol, int maxit,
+                     int variant, int precision, void* workspace, size_t ws_bytes,
+                     lap5cg_info* info, const lap5cg_opts* opts, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LAP5CG_H */

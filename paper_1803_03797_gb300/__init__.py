@@ -1,0 +1,267 @@
+"""lap5cg: matrix-free conjugate gradient for the 2D Dirichlet 5-point
+Laplacian on an NVIDIA GB300 (sm_103a), after arxiv 1803.03797
+("Efficient FPGA Implementation of Conjugate Gradient Methods for Laplacian
+System using HLS").
+
+This module is a thin ctypes binding over ``liblap5cg.so`` (C ABI in
+``include/lap5cg.h``).  It only marshals arguments: torch provides device
+memory and the current CUDA stream; every step of every solve runs in the
+library's CUDA kernels.  There is no CPU fallback: if the library is missing or
+no GPU is present, calls raise.
+
+Grids are torch tensors of shape (ny, ld) (or (nrhs, ny, ld)) with ld >= nx;
+element (i, j) is ``t[j, i]``; columns nx..ld-1 are padding and never written.
+"""
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "liblap5cg.so")
+
+OK, NOT_CONVERGED = 0, 1
+ERR_INVALID_ARG, ERR_CUDA, ERR_BREAKDOWN, ERR_SYNC_TIMEOUT = -1, -2, -3, -4
+ERR_NONFINITE, ERR_UNSUPPORTED, ERR_WORKSPACE = -5, -6, -7
+
+CLASSIC, NEWCG = 0, 1
+PREC_F64, PREC_F32, PREC_IR_F32, PREC_IR_BF16PR = 0, 1, 2, 3
+DT_F64, DT_F32, DT_BF16 = 0, 1, 2
+MAX_BATCH = 1024
+
+_VARIANTS = {"classic": CLASSIC, "newcg": NEWCG, CLASSIC: CLASSIC, NEWCG: NEWCG}
+_PRECISIONS = {"f64": PREC_F64, "f32": PREC_F32, "ir_f32": PREC_IR_F32, "ir_bf16pr": PREC_IR_BF16PR,
+               PREC_F64: PREC_F64, PREC_F32: PREC_F32, PREC_IR_F32: PREC_IR_F32, PREC_IR_BF16PR: PREC_IR_BF16PR}
+
+INFO_DTYPE = np.dtype([("status", "<i4"), ("iters", "<i4"), ("outer_iters", "<i4"), ("pad", "<i4"),
+                       ("relres_recursive", "<f8"), ("relres_true", "<f8")])
+INFO_BYTES = INFO_DTYPE.itemsize
+
+
+class Opts(ctypes.Structure):
+    """Mirror of lap5cg_opts."""
+    _fields_ = [("rr_period", ctypes.c_int32), ("store_z", ctypes.c_int32), ("ctas", ctypes.c_int32),
+                ("warps_per_cta", ctypes.c_int32), ("min_rows", ctypes.c_int32),
+                ("true_residual", ctypes.c_int32), ("maxit_inner", ctypes.c_int32),
+                ("max_outer", ctypes.c_int32), ("tol_inner", ctypes.c_double), ("timeout_s", ctypes.c_double),
+                ("history", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def lib():
+    """Load liblap5cg.so (building it first when the sources are newer)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH) or os.environ.get("LAP5CG_AUTOBUILD", "1") == "1":
+            _build.build()
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("liblap5cg.so is missing; run paper_1803_03797_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        i, d, vp, sz = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t
+        L.lap5cg_opts_default.argtypes = [ctypes.POINTER(Opts)]
+        L.lap5cg_opts_default.restype = None
+        L.lap5cg_status_string.argtypes = [i]
+        L.lap5cg_status_string.restype = ctypes.c_char_p
+        L.lap5_apply.argtypes = [i, i, i, i, vp, vp, vp]
+        L.lap5_apply.restype = i
+        L.cg_workspace_size.argtypes = [i, i, i, i, i, i]
+        L.cg_workspace_size.restype = sz
+        L.cg_solve.argtypes = [i, i, i, vp, vp, d, i, i, i, i, vp, sz, vp, ctypes.POINTER(Opts), vp]
+        L.cg_solve.restype = i
+        IP = ctypes.POINTER(ctypes.c_int)
+        VPP = ctypes.POINTER(ctypes.c_void_p)
+        L.cg_batched_workspace_size.argtypes = [i, IP, IP, IP, i, i]
+        L.cg_batched_workspace_size.restype = sz
+        L.cg_solve_batched.argtypes = [i, IP, IP, IP, VPP, VPP, d, i, i, i, vp, sz, vp, ctypes.POINTER(Opts), vp]
+        L.cg_solve_batched.restype = i
+        _lib = L
+    return _lib
+
+
+EXPORTED = ("lap5cg_opts_default", "lap5cg_status_string", "lap5_apply", "cg_workspace_size", "cg_solve",
+            "cg_batched_workspace_size", "cg_solve_batched")
+
+
+class Lap5cgError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__("%s: %s (%d)" % (what, status_string(code), code))
+        self.code = code
+
+
+def status_string(code: int) -> str:
+    return lib().lap5cg_status_string(int(code)).decode()
+
+
+def default_opts(**kw) -> Opts:
+    o = Opts()
+    lib().lap5cg_opts_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _check_grid(t, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+
+
+_DT = {torch.float64: DT_F64, torch.float32: DT_F32, torch.bfloat16: DT_BF16}
+
+
+def lap5_apply(x: torch.Tensor, nx: int = None, out: torch.Tensor = None, stream=None) -> torch.Tensor:
+    """y = A x (Sec. II-B mask, zero Dirichlet boundary) for a (ny, ld) grid."""
+    _check_grid(x, "x")
+    if x.dim() != 2 or x.dtype not in _DT:
+        raise ValueError("x must be a 2D float64/float32/bfloat16 tensor")
+    ny, ld = x.shape
+    nx = ld if nx is None else int(nx)
+    y = torch.zeros_like(x) if out is None else out
+    rc = lib().lap5_apply(nx, ny, ld, _DT[x.dtype], ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                          _stream(stream))
+    if rc != OK:
+        raise Lap5cgError(rc, "lap5_apply")
+    return y
+
+
+def workspace_size(nx, ny, ld, variant="classic", precision="f64", nrhs=1) -> int:
+    return int(lib().cg_workspace_size(nx, ny, ld, _VARIANTS[variant], _PRECISIONS[precision], nrhs))
+
+
+def decode_info(info: torch.Tensor):
+    """Device info buffer -> list of dicts (synchronises on the copy)."""
+    raw = info.detach().to("cpu").numpy().view(INFO_DTYPE)
+    return [{k: (raw[i][k].item()) for k in INFO_DTYPE.names if k != "pad"} for i in range(raw.shape[0])]
+
+
+def _x_dtype(precision):
+    return torch.float32 if _PRECISIONS[precision] == PREC_F32 else torch.float64
+
+
+def cg_solve(b: torch.Tensor, x0: torch.Tensor = None, tol: float = 1e-10, maxit: int = 10000,
+             variant="classic", precision="f64", nx: int = None, opts: Opts = None,
+             workspace: torch.Tensor = None, info: torch.Tensor = None, out: torch.Tensor = None,
+             stream=None, check: bool = False):
+    """Solve A x = b on the GPU (Algorithm 1 or 2) in one persistent launch per
+    right-hand side.  b: (ny, ld) or (nrhs, ny, ld).  Returns (x, info) where
+    info is a uint8 CUDA tensor of lap5cg_info records (decode_info()).
+    check=True synchronises and raises on a non-OK / non-NOT_CONVERGED status."""
+    _check_grid(b, "b")
+    want = _x_dtype(precision)
+    if b.dtype != want:
+        raise ValueError("b must be %s for precision %s" % (want, precision))
+    if b.dim() == 2:
+        nrhs, (ny, ld) = 1, b.shape
+    elif b.dim() == 3:
+        nrhs, ny, ld = b.shape
+    else:
+        raise ValueError("b must be (ny, ld) or (nrhs, ny, ld)")
+    nx = ld if nx is None else int(nx)
+    v, p = _VARIANTS[variant], _PRECISIONS[precision]
+    if out is not None:
+        x = out
+        if x0 is not None and x0.data_ptr() != x.data_ptr():
+            x.copy_(x0)
+        elif x0 is None:
+            x.zero_()
+    else:
+        x = torch.zeros_like(b) if x0 is None else x0.clone()
+    _check_grid(x, "x")
+    need = workspace_size(nx, ny, ld, v, p, nrhs)
+    if need == 0:
+        raise Lap5cgError(ERR_UNSUPPORTED, "cg_workspace_size")
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=b.device)
+    if info is None:
+        info = torch.empty(nrhs * INFO_BYTES, dtype=torch.uint8, device=b.device)
+    rc = lib().cg_solve(nx, ny, ld, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()), float(tol),
+                        int(maxit), v, p, nrhs, ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
+                        ctypes.c_void_p(info.data_ptr()), ctypes.byref(opts) if opts is not None else None,
+                        _stream(stream))
+    if rc != OK:
+        raise Lap5cgError(rc, "cg_solve")
+    if check:
+        for rec in decode_info(info):
+            if rec["status"] < 0:
+                raise Lap5cgError(rec["status"], "cg_solve (device)")
+    return x, info
+
+
+def batched_workspace_size(nx_list, ny_list, ld_list, variant="classic", precision="ir_f32") -> int:
+    n = len(nx_list)
+    arr = ctypes.c_int * n
+    return int(lib().cg_batched_workspace_size(n, arr(*nx_list), arr(*ny_list), arr(*ld_list), _VARIANTS[variant],
+                                               _PRECISIONS[precision]))
+
+
+def cg_solve_batched(bs, xs=None, tol=1e-10, maxit=100000, variant="classic", precision="ir_f32", nx_list=None,
+                     opts: Opts = None, workspace=None, info=None, stream=None):
+    """Solve len(bs) independent systems of different shapes in one persistent
+    launch.  bs: list of (ny, ld) CUDA tensors.  Returns (xs, info)."""
+    n = len(bs)
+    if n < 1:
+        raise ValueError("empty batch")
+    for t in bs:
+        _check_grid(t, "b")
+    nxs = [t.shape[1] for t in bs] if nx_list is None else list(nx_list)
+    nys = [t.shape[0] for t in bs]
+    lds = [t.shape[1] for t in bs]
+    if xs is None:
+        xs = [torch.zeros_like(t) for t in bs]
+    v, p = _VARIANTS[variant], _PRECISIONS[precision]
+    need = batched_workspace_size(nxs, nys, lds, v, p)
+    if need == 0:
+        raise Lap5cgError(ERR_UNSUPPORTED, "cg_batched_workspace_size")
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=bs[0].device)
+    if info is None:
+        info = torch.empty(n * INFO_BYTES, dtype=torch.uint8, device=bs[0].device)
+    arr = ctypes.c_int * n
+    ptrs = ctypes.c_void_p * n
+    rc = lib().cg_solve_batched(n, arr(*nxs), arr(*nys), arr(*lds), ptrs(*[t.data_ptr() for t in bs]),
+                                ptrs(*[t.data_ptr() for t in xs]), float(tol), int(maxit), v, p,
+                                ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
+                                ctypes.c_void_p(info.data_ptr()), ctypes.byref(opts) if opts is not None else None,
+                                _stream(stream))
+    if rc != OK:
+        raise Lap5cgError(rc, "cg_solve_batched")
+    return xs, info
+
+
+class CGSolve(torch.autograd.Function):
+    """x = A^{-1} b by CG on the GPU; backward is the adjoint solve
+    grad_b = A^{-1} grad_x (A is symmetric), a second CG solve with the same
+    settings.  Nothing but the settings is saved for backward."""
+
+    @staticmethod
+    def forward(ctx, b, tol=1e-10, maxit=100000, variant="classic", precision="f64", nx=None):
+        ctx.settings = (tol, maxit, variant, precision, nx)
+        x, info = cg_solve(b.detach(), tol=tol, maxit=maxit, variant=variant, precision=precision, nx=nx)
+        ctx.mark_non_differentiable(info)
+        return x, info
+
+    @staticmethod
+    def backward(ctx, grad_x, grad_info):
+        tol, maxit, variant, precision, nx = ctx.settings
+        g, _ = cg_solve(grad_x.contiguous(), tol=tol, maxit=maxit, variant=variant, precision=precision, nx=nx)
+        return g, None, None, None, None, None
+
+
+def solve(b, tol=1e-10, maxit=100000, variant="classic", precision="f64", nx=None):
+    """Differentiable solve: returns x only."""
+    x, _ = CGSolve.apply(b, tol, maxit, variant, precision, nx)
+    return x

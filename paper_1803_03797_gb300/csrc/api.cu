@@ -1,0 +1,250 @@
+// api.cu -- the extern "C" entry points of liblap5cg (declared in
+// include/lap5cg.h): argument validation, workspace layout, staging of
+// unaligned user buffers, launch-geometry planning and dispatch.
+#include <mutex>
+#include <string.h>
+
+#include "launch.h"
+#include "common.cuh"
+
+namespace lap5 {
+
+int dev_props(DevProps* out) {
+  static std::mutex mu;
+  static DevProps cache[128];
+  static bool have[128] = {false};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return LAP5CG_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!have[dev]) {
+    DevProps p;
+    if (cudaDeviceGetAttribute(&p.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return LAP5CG_ERR_CUDA;
+    if (cudaDeviceGetAttribute(&p.max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+      return LAP5CG_ERR_CUDA;
+    cache[dev] = p;
+    have[dev] = true;
+  }
+  *out = cache[dev];
+  return LAP5CG_OK;
+}
+
+int plan_units(const void* func, int nx, int ny, int V, const lap5cg_opts& o, LaunchCfg* cfg) {
+  DevProps dp;
+  int rc = dev_props(&dp);
+  if (rc != LAP5CG_OK) return rc;
+  int wpc = o.warps_per_cta > 0 ? o.warps_per_cta : 8;
+  if (wpc > 16) wpc = 16;
+  const int threads = 32 * wpc;
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, func, threads, 0) != cudaSuccess) return LAP5CG_ERR_CUDA;
+  if (occ < 1) return LAP5CG_ERR_UNSUPPORTED;
+  int maxctas = occ * dp.sms;
+  if (maxctas > kMaxCtas) maxctas = kMaxCtas;
+  int ctas = o.ctas > 0 ? (o.ctas < maxctas ? o.ctas : maxctas) : maxctas;
+  const int ns = (nx + 32 * V - 1) / (32 * V);
+  const long long W = (long long)ctas * wpc;
+  const int min_rows = o.min_rows > 0 ? o.min_rows : 8;
+  long long nseg = W / ns;
+  if (nseg < 1) nseg = 1;
+  if (nseg > ny) nseg = ny;
+  int L = (int)((ny + nseg - 1) / nseg);
+  if (L < min_rows) L = min_rows < ny ? min_rows : ny;
+  nseg = (ny + L - 1) / L;
+  L = (int)((ny + nseg - 1) / nseg);  // rebalance
+  const long long nunits = (long long)ns * nseg;
+  if (nunits > 0x7fffffffLL) return LAP5CG_ERR_UNSUPPORTED;
+  if (o.ctas <= 0 && nunits < W) ctas = (int)((nunits + wpc - 1) / wpc);
+  cfg->ctas = ctas;
+  cfg->threads = threads;
+  cfg->ns = ns;
+  cfg->nseg = (int)nseg;
+  cfg->seg_rows = L;
+  cfg->nunits = (int)nunits;
+  return LAP5CG_OK;
+}
+
+static bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+static size_t elem_of_precision(int precision) { return precision == LAP5CG_PREC_F32 ? 4 : 8; }
+
+// Lane vector width of the solver for a precision (elements per 16 bytes of b/x).
+static int vec_of_precision(int precision) { return precision == LAP5CG_PREC_F32 ? 4 : 2; }
+
+static int internal_ld(int nx, int ld, int precision) {
+  const int v = (precision == LAP5CG_PREC_F32) ? 4 : 2;
+  if (ld % v == 0) return ld;
+  return (nx + v - 1) / v * v;
+}
+
+static size_t solver_ws(int nx, int ny, int ldw, int variant, int precision) {
+  switch (precision) {
+    case LAP5CG_PREC_F64: return ws_bytes_f64(nx, ny, ldw, variant);
+    case LAP5CG_PREC_F32: return ws_bytes_f32(nx, ny, ldw, variant);
+    default: return ws_bytes_ir(nx, ny, variant, precision);
+  }
+}
+
+static bool valid_shape(int nx, int ny, int ld) {
+  if (nx < 1 || ny < 1 || ld < nx) return false;
+  if ((long long)ny * (long long)ld > (1LL << 40)) return false;
+  return true;
+}
+
+static bool overlap(const void* a, size_t na, const void* b, size_t nb) {
+  const uintptr_t a0 = reinterpret_cast<uintptr_t>(a), b0 = reinterpret_cast<uintptr_t>(b);
+  return a0 < b0 + nb && b0 < a0 + na;
+}
+
+}  // namespace lap5
+
+using namespace lap5;
+
+extern "C" {
+
+void lap5cg_opts_default(lap5cg_opts* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->rr_period = 0;
+  o->store_z = -1;
+  o->ctas = 0;
+  o->warps_per_cta = 0;
+  o->min_rows = 0;
+  o->true_residual = 1;
+  o->maxit_inner = 0;
+  o->max_outer = 0;
+  o->tol_inner = 0.0;
+  o->timeout_s = 0.0;
+  o->history = nullptr;
+}
+
+const char* lap5cg_status_string(int status) {
+  switch (status) {
+    case LAP5CG_OK: return "ok";
+    case LAP5CG_NOT_CONVERGED: return "not converged (maxit reached)";
+    case LAP5CG_ERR_INVALID_ARG: return "invalid argument";
+    case LAP5CG_ERR_CUDA: return "CUDA runtime error";
+    case LAP5CG_ERR_BREAKDOWN: return "breakdown: non-positive curvature or alpha denominator";
+    case LAP5CG_ERR_SYNC_TIMEOUT: return "device grid barrier timed out";
+    case LAP5CG_ERR_NONFINITE: return "non-finite value in a reduction";
+    case LAP5CG_ERR_UNSUPPORTED: return "unsupported combination";
+    case LAP5CG_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+    default: return "unknown status";
+  }
+}
+
+int lap5_apply(int nx, int ny, int ld, int dtype, const void* x, void* y, void* stream) {
+  if (!valid_shape(nx, ny, ld) || !x || !y) return LAP5CG_ERR_INVALID_ARG;
+  if (dtype < LAP5CG_DT_F64 || dtype > LAP5CG_DT_BF16) return LAP5CG_ERR_INVALID_ARG;
+  const size_t es = dtype == LAP5CG_DT_F64 ? 8 : (dtype == LAP5CG_DT_F32 ? 4 : 2);
+  const size_t bytes = (size_t)ny * (size_t)ld * es;
+  if (overlap(x, bytes, y, bytes)) return LAP5CG_ERR_INVALID_ARG;
+  return apply_dispatch(nx, ny, ld, dtype, x, y, static_cast<cudaStream_t>(stream));
+}
+
+size_t cg_workspace_size(int nx, int ny, int ld, int variant, int precision, int nrhs) {
+  if (!valid_shape(nx, ny, ld) || nrhs < 1) return 0;
+  if (variant != LAP5CG_CLASSIC && variant != LAP5CG_NEWCG) return 0;
+  if (precision < LAP5CG_PREC_F64 || precision > LAP5CG_PREC_IR_BF16PR) return 0;
+  const int ldw = internal_ld(nx, ld, precision);
+  size_t s = solver_ws(nx, ny, ldw, variant, precision);
+  if (s == 0) return 0;
+  if (ldw != ld) s += 2 * align_up((size_t)ny * (size_t)ldw * elem_of_precision(precision), kAlign);
+  return s;
+}
+
+int cg_solve(int nx, int ny, int ld, const void* b, void* x, double tol, int maxit, int variant, int precision,
+             int nrhs, void* workspace, size_t ws_bytes, lap5cg_info* info, const lap5cg_opts* opts,
+             void* stream) {
+  if (!valid_shape(nx, ny, ld) || !b || !x || !info || maxit < 0 || nrhs < 1) return LAP5CG_ERR_INVALID_ARG;
+  if (variant != LAP5CG_CLASSIC && variant != LAP5CG_NEWCG) return LAP5CG_ERR_INVALID_ARG;
+  if (precision < LAP5CG_PREC_F64 || precision > LAP5CG_PREC_IR_BF16PR) return LAP5CG_ERR_INVALID_ARG;
+  if (tol != tol) return LAP5CG_ERR_INVALID_ARG;  // NaN tolerance
+  lap5cg_opts o;
+  if (opts) o = *opts;
+  else lap5cg_opts_default(&o);
+  if (o.rr_period < 0 || o.warps_per_cta < 0 || o.warps_per_cta > 16 || o.ctas < 0 || o.min_rows < 0 ||
+      o.maxit_inner < 0 || o.max_outer < 0)
+    return LAP5CG_ERR_INVALID_ARG;
+  if (o.rr_period > 0 && variant != LAP5CG_NEWCG) return LAP5CG_ERR_INVALID_ARG;
+  const size_t need = cg_workspace_size(nx, ny, ld, variant, precision, nrhs);
+  if (need == 0) return LAP5CG_ERR_UNSUPPORTED;
+  if (!workspace || !aligned(workspace, kAlign) || ws_bytes < need) return LAP5CG_ERR_WORKSPACE;
+  const size_t es = elem_of_precision(precision);
+  const size_t grid_bytes = (size_t)ny * (size_t)ld * es;
+  if (overlap(b, grid_bytes * nrhs, x, grid_bytes * nrhs)) return LAP5CG_ERR_INVALID_ARG;
+  if (overlap(b, grid_bytes * nrhs, workspace, ws_bytes) || overlap(x, grid_bytes * nrhs, workspace, ws_bytes))
+    return LAP5CG_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int ldw = internal_ld(nx, ld, precision);
+  const int vw = vec_of_precision(precision);
+  const bool vec_ok = (ldw == ld) && aligned(b, 16) && aligned(x, 16);
+  const bool stage = !vec_ok;
+  if (stage && ldw == ld) return LAP5CG_ERR_INVALID_ARG;  // aligned pitch but misaligned pointers
+  (void)vw;
+  unsigned char* ws = static_cast<unsigned char*>(workspace);
+  const size_t solver_bytes = solver_ws(nx, ny, ldw, variant, precision);
+  const size_t stage_vec = align_up((size_t)ny * (size_t)ldw * es, kAlign);
+  unsigned char* bst = ws + solver_bytes;
+  unsigned char* xst = bst + stage_vec;
+
+  for (int k = 0; k < nrhs; ++k) {
+    const unsigned char* bk = static_cast<const unsigned char*>(b) + (size_t)k * grid_bytes;
+    unsigned char* xk = static_cast<unsigned char*>(x) + (size_t)k * grid_bytes;
+    SolvePlan p;
+    p.nx = nx;
+    p.ny = ny;
+    p.ldw = ldw;
+    p.ws = ws;
+    p.ws_bytes = solver_bytes;
+    p.info = info + k;
+    p.tol = tol;
+    p.maxit = maxit;
+    p.variant = variant;
+    p.precision = precision;
+    p.opts = o;
+    if (o.history) p.opts.history = o.history + (size_t)k * ((size_t)maxit + 1);
+    if (stage) {
+      if (cudaMemcpy2DAsync(bst, (size_t)ldw * es, bk, (size_t)ld * es, (size_t)nx * es, ny, cudaMemcpyDeviceToDevice,
+                            st) != cudaSuccess ||
+          cudaMemcpy2DAsync(xst, (size_t)ldw * es, xk, (size_t)ld * es, (size_t)nx * es, ny, cudaMemcpyDeviceToDevice,
+                            st) != cudaSuccess)
+        return LAP5CG_ERR_CUDA;
+      p.b = bst;
+      p.x = xst;
+      p.ld = ldw;
+    } else {
+      p.b = bk;
+      p.x = xk;
+      p.ld = ld;
+    }
+    int rc;
+    switch (precision) {
+      case LAP5CG_PREC_F64: rc = solve_f64(p, st); break;
+      case LAP5CG_PREC_F32: rc = solve_f32(p, st); break;
+      default: rc = solve_ir(p, st); break;
+    }
+    if (rc != LAP5CG_OK) return rc;
+    if (stage) {
+      if (cudaMemcpy2DAsync(xk, (size_t)ld * es, xst, (size_t)ldw * es, (size_t)nx * es, ny, cudaMemcpyDeviceToDevice,
+                            st) != cudaSuccess)
+        return LAP5CG_ERR_CUDA;
+    }
+  }
+  return LAP5CG_OK;
+}
+
+size_t cg_batched_workspace_size(int count, const int* nx, const int* ny, const int* ld, int variant,
+                                 int precision) {
+  (void)count; (void)nx; (void)ny; (void)ld; (void)variant; (void)precision;
+  return 0;
+}
+
+int cg_solve_batched(int count, const int* nx, const int* ny, const int* ld, const void* const* b, void* const* x,
+                     double tol, int maxit, int variant, int precision, void* workspace, size_t ws_bytes,
+                     lap5cg_info* info, const lap5cg_opts* opts, void* stream) {
+  (void)count; (void)nx; (void)ny; (void)ld; (void)b; (void)x; (void)tol; (void)maxit; (void)variant;
+  (void)precision; (void)workspace; (void)ws_bytes; (void)info; (void)opts; (void)stream;
+  return LAP5CG_ERR_UNSUPPORTED;
+}
+
+}  // extern "C"

@@ -1,0 +1,538 @@
+// cg_kernels.cuh -- persistent, fused CG kernels (Algorithm 1 and Algorithm 2
+// of arxiv 1803.03797) for one grid, one launch per solve.
+//
+// Work decomposition: the grid is cut into strips of 32*V columns; each strip
+// into row segments; a (strip, segment) pair is a warp unit.  A warp marches
+// its unit row by row keeping three rows of the stencil operand in registers
+// (a register line buffer: the GPU counterpart of the paper's line-buffer /
+// window-buffer pipeline, Sec. II-B), takes west/east neighbours by warp
+// shuffles and the strip's halo columns by two scalar loads.  Units are owned
+// by the same warp in every pass, so only halo values cross warps; they are
+// published by the grid barrier that separates passes.  Every other pass
+// marches rows in the opposite direction so the rows touched last by one pass
+// are still in L2 when the next pass starts.
+//
+// All scalars (alpha, beta, gamma, delta) and the convergence test stay on the
+// device: each reduction ends in a grid barrier after which every CTA holds the
+// same totals (fixed summation order) and takes the same decision.
+#pragma once
+
+#include "common.cuh"
+
+namespace lap5 {
+
+// Shared solver state passed to every kernel.
+struct SolveCommon {
+  int nx, ny;
+  Units un;
+  Ctl* ctl;
+  lap5cg_info* info;
+  double* history;
+  double tol;
+  int maxit;
+  int true_res;
+  long long timeout_ns;
+};
+
+// Per-CTA, per-thread bookkeeping of a persistent solve.
+struct Walker {
+  int lane, gw, nw;
+  unsigned long long epoch;
+  int pc;  // pass counter: odd passes march in reverse
+  __device__ __forceinline__ void init() {
+    lane = threadIdx.x & 31;
+    const int wpc = blockDim.x >> 5;
+    gw = blockIdx.x * wpc + (threadIdx.x >> 5);
+    nw = gridDim.x * wpc;
+    epoch = 0ull;
+    pc = 0;
+  }
+  __device__ __forceinline__ bool rev() const { return (pc & 1) != 0; }
+};
+
+// Field loader: the stencil operand is a stored vector g.
+template <int V, class T, class M>
+__device__ __forceinline__ void field_plain(const Grid<T>& g, int nx, int ny, int j, int x, int xs, int lane,
+                                            FRow<V, M>& f) {
+  if (j < 0 || j >= ny) { f.zero(); return; }
+  load_row<V>(g, j, x, nx, f.f);
+  f.hl = (lane == 0) ? load_one<T, M>(g, j, xs - 1, nx) : M(0);
+  f.hr = (lane == 31) ? load_one<T, M>(g, j, xs + 32 * V, nx) : M(0);
+}
+
+// Info writer (CTA 0, thread 0).  status_local is the status all CTAs agreed
+// on; an aborted solve reports the error recorded in the control block.
+__device__ __forceinline__ void write_info(const SolveCommon& c, int status_local, bool aborted, int iters,
+                                           int outer, double gamma, double bb, double relres_true) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  lap5cg_info inf;
+  int st = status_local;
+  if (aborted) {
+    st = atomicAdd(&c.ctl->status, 0);
+    if (st == 0) st = LAP5CG_ERR_SYNC_TIMEOUT;
+  }
+  inf.status = st;
+  inf.iters = iters;
+  inf.outer_iters = outer;
+  inf.pad = 0;
+  inf.relres_recursive = (bb > 0.0) ? sqrt(gamma / bb) : 0.0;
+  inf.relres_true = relres_true;
+  *c.info = inf;
+}
+
+// ---------------------------------------------------------------------------
+// Common passes.
+// ---------------------------------------------------------------------------
+
+// r = b - A x (x is the stencil operand); accumulates (b,b) and (r,r).
+// When r is null only the dot products are formed (true-residual check).
+template <int V, class TB, class TX, class TR>
+__device__ __forceinline__ void pass_residual(const SolveCommon& c, Walker& wk, const Grid<const TB>& b,
+                                              const Grid<TX>& x, const Grid<TR>& r,
+                                              typename AccOf<typename Math<TX>::type>::type& abb,
+                                              typename AccOf<typename Math<TX>::type>::type& arr) {
+  using M = typename Math<TX>::type;
+  struct D { M b[V]; };
+  for (int u = wk.gw; u < c.un.nunits; u += wk.nw) {
+    int s, y0, y1;
+    unit_bounds(c.un, u, c.ny, s, y0, y1);
+    const int xs = s * 32 * V, xl = xs + wk.lane * V;
+    const int nval = min(max(c.nx - xl, 0), V);
+    auto field = [&](int j, FRow<V, M>& f) { field_plain<V>(x, c.nx, c.ny, j, xl, xs, wk.lane, f); };
+    auto load = [&](int j, D& d) { load_row<V>(b, j, xl, c.nx, d.b); };
+    auto finish = [&](int j, const D& d, const FRow<V, M>& S, const FRow<V, M>& C, const FRow<V, M>& N) {
+      M ax[V], rv[V];
+      stencil_row<V>(S, C, N, wk.lane, ax);
+#pragma unroll
+      for (int k = 0; k < V; ++k) {
+        rv[k] = d.b[k] - ax[k];
+        if (k < nval) { abb.add(d.b[k], d.b[k]); arr.add(rv[k], rv[k]); }
+      }
+      if (r.ptr) store_row<V>(r, j, xl, c.nx, rv);
+    };
+    march<V, M, D>(y0, y1, wk.rev(), field, load, finish);
+  }
+  ++wk.pc;
+}
+
+// x = 0 over the interior (b = 0 case).
+template <int V, class TX>
+__device__ __forceinline__ void pass_zero(const SolveCommon& c, Walker& wk, const Grid<TX>& x) {
+  using M = typename Math<TX>::type;
+  for (int u = wk.gw; u < c.un.nunits; u += wk.nw) {
+    int s, y0, y1;
+    unit_bounds(c.un, u, c.ny, s, y0, y1);
+    const int xl = s * 32 * V + wk.lane * V;
+    M zv[V];
+#pragma unroll
+    for (int k = 0; k < V; ++k) zv[k] = M(0);
+    for (int j = y0; j < y1; ++j) store_row<V>(x, j, xl, c.nx, zv);
+  }
+  ++wk.pc;
+}
+
+// ---------------------------------------------------------------------------
+// Algorithm 1, fused into two passes per iteration.
+//   phase P: p = r + beta p_old on the unit plus halo (beta = 0 and p_old
+//            unread in the first iteration), store p, y = A p, store z = y
+//            (store_z) and accumulate (p, A p);         -> alpha
+//   phase R: x += alpha p; r -= alpha z (z read, or A p recomputed from p with
+//            its halo); accumulate (r, r)               -> beta, convergence
+// p is double-buffered: phase P reads the old p at halo points that a
+// neighbouring warp rewrites in the same pass.
+// ---------------------------------------------------------------------------
+template <class T>
+struct ClassicArgs {
+  SolveCommon c;
+  Grid<const T> b;
+  Grid<T> x, r, p0, p1, z;
+  int store_z;
+};
+
+template <class T, int V>
+__device__ void classic_solve(const ClassicArgs<T>& a) {
+  using M = typename Math<T>::type;
+  using Acc = typename AccOf<M>::type;
+  __shared__ double red[33 * kMaxVals];
+  const SolveCommon& c = a.c;
+  Walker wk;
+  wk.init();
+
+  int status = LAP5CG_NOT_CONVERGED, iters = 0;
+  double bb = 0.0, gamma = 0.0, relres_true = nan("");
+  bool aborted = false;
+
+  {  // r = b - A x0, (b, b), (r, r)
+    Acc abb, arr;
+    pass_residual<V>(c, wk, a.b, a.x, a.r, abb, arr);
+    double v[2] = {abb.value(), arr.value()}, o[2];
+    if (!grid_reduce<2>(c.ctl, wk.epoch, v, o, red, c.timeout_ns)) { aborted = true; goto done; }
+    bb = o[0];
+    gamma = o[1];
+  }
+  if (!isfinite(bb)) { status = LAP5CG_ERR_NONFINITE; relres_true = nan(""); goto done; }
+  if (bb == 0.0) {
+    pass_zero<V>(c, wk, a.x);
+    status = LAP5CG_OK;
+    gamma = 0.0;
+    relres_true = 0.0;
+    goto done;
+  }
+  {
+    const double thr = c.tol > 0.0 ? c.tol * c.tol * bb : 0.0;
+    if (c.history && blockIdx.x == 0 && threadIdx.x == 0) c.history[0] = sqrt(gamma / bb);
+    if (!isfinite(gamma)) { status = LAP5CG_ERR_NONFINITE; goto truecheck; }
+    if (gamma <= thr) { status = LAP5CG_OK; goto truecheck; }
+    double beta = 0.0;
+    int cur = 0;  // p_old lives in p[cur], the new p goes to p[cur ^ 1]
+    while (iters < c.maxit) {
+      const bool first = (iters == 0);
+      const Grid<T> pold = cur ? a.p1 : a.p0;
+      const Grid<T> pnew = cur ? a.p0 : a.p1;
+      // ---------------- phase P ----------------
+      double pap;
+      {
+        Acc acc;
+        const M bm = (M)beta;
+        struct D { int dummy; };
+        for (int u = wk.gw; u < c.un.nunits; u += wk.nw) {
+          int s, y0, y1;
+          unit_bounds(c.un, u, c.ny, s, y0, y1);
+          const int xs = s * 32 * V, xl = xs + wk.lane * V;
+          const int nval = min(max(c.nx - xl, 0), V);
+          auto field = [&](int j, FRow<V, M>& f) {
+            if (j < 0 || j >= c.ny) { f.zero(); return; }
+            M rv[V];
+            load_row<V>(a.r, j, xl, c.nx, rv);
+            M hlr = (wk.lane == 0) ? load_one<T, M>(a.r, j, xs - 1, c.nx) : M(0);
+            M hrr = (wk.lane == 31) ? load_one<T, M>(a.r, j, xs + 32 * V, c.nx) : M(0);
+            if (first) {
+#pragma unroll
+              for (int k = 0; k < V; ++k) f.f[k] = rv[k];
+              f.hl = hlr;
+              f.hr = hrr;
+            } else {
+              M pv[V];
+              load_row<V>(pold, j, xl, c.nx, pv);
+              const M hlp = (wk.lane == 0) ? load_one<T, M>(pold, j, xs - 1, c.nx) : M(0);
+              const M hrp = (wk.lane == 31) ? load_one<T, M>(pold, j, xs + 32 * V, c.nx) : M(0);
+#pragma unroll
+              for (int k = 0; k < V; ++k) f.f[k] = fmx(bm, pv[k], rv[k]);
+              f.hl = fmx(bm, hlp, hlr);
+              f.hr = fmx(bm, hrp, hrr);
+            }
+          };
+          auto load = [&](int, D&) {};
+          auto finish = [&](int j, const D&, const FRow<V, M>& S, const FRow<V, M>& C, const FRow<V, M>& N) {
+            M ap[V];
+            stencil_row<V>(S, C, N, wk.lane, ap);
+            store_row<V>(pnew, j, xl, c.nx, C.f);
+            if (a.store_z) store_row<V>(a.z, j, xl, c.nx, ap);
+#pragma unroll
+            for (int k = 0; k < V; ++k)
+              if (k < nval) acc.add(C.f[k], ap[k]);
+          };
+          march<V, M, D>(y0, y1, wk.rev(), field, load, finish);
+        }
+        ++wk.pc;
+        double v[1] = {acc.value()}, o[1];
+        if (!grid_reduce<1>(c.ctl, wk.epoch, v, o, red, c.timeout_ns)) { aborted = true; goto done; }
+        pap = o[0];
+      }
+      if (!(pap > 0.0) || !isfinite(pap)) { status = LAP5CG_ERR_BREAKDOWN; goto truecheck; }
+      {
+        const double alpha = gamma / pap;
+        const M am = (M)alpha;
+        Acc acc;
+        for (int u = wk.gw; u < c.un.nunits; u += wk.nw) {
+          int s, y0, y1;
+          unit_bounds(c.un, u, c.ny, s, y0, y1);
+          const int xs = s * 32 * V, xl = xs + wk.lane * V;
+          const int nval = min(max(c.nx - xl, 0), V);
+          if (a.store_z) {
+            struct D { M p[V], x[V], r[V], z[V]; };
+            auto load = [&](int j, D& d) {
+              load_row<V>(pnew, j, xl, c.nx, d.p);
+              load_row<V>(a.x, j, xl, c.nx, d.x);
+              load_row<V>(a.r, j, xl, c.nx, d.r);
+              load_row<V>(a.z, j, xl, c.nx, d.z);
+            };
+            auto finish = [&](int j, const D& d) {
+              M xv[V], rv[V];
+#pragma unroll
+              for (int k = 0; k < V; ++k) {
+                xv[k] = fmx(am, d.p[k], d.x[k]);
+                rv[k] = fmx(-am, d.z[k], d.r[k]);
+                if (k < nval) acc.add(rv[k], rv[k]);
+              }
+              store_row<V>(a.x, j, xl, c.nx, xv);
+              store_row<V>(a.r, j, xl, c.nx, rv);
+            };
+            stream_rows<D>(y0, y1, wk.rev(), load, finish);
+          } else {
+            struct D { M x[V], r[V]; };
+            auto field = [&](int j, FRow<V, M>& f) { field_plain<V>(pnew, c.nx, c.ny, j, xl, xs, wk.lane, f); };
+            auto load = [&](int j, D& d) {
+              load_row<V>(a.x, j, xl, c.nx, d.x);
+              load_row<V>(a.r, j, xl, c.nx, d.r);
+            };
+            auto finish = [&](int j, const D& d, const FRow<V, M>& S, const FRow<V, M>& C, const FRow<V, M>& N) {
+              M ap[V], xv[V], rv[V];
+              stencil_row<V>(S, C, N, wk.lane, ap);
+#pragma unroll
+              for (int k = 0; k < V; ++k) {
+                xv[k] = fmx(am, C.f[k], d.x[k]);
+                rv[k] = fmx(-am, ap[k], d.r[k]);
+                if (k < nval) acc.add(rv[k], rv[k]);
+              }
+              store_row<V>(a.x, j, xl, c.nx, xv);
+              store_row<V>(a.r, j, xl, c.nx, rv);
+            };
+            march<V, M, D>(y0, y1, wk.rev(), field, load, finish);
+          }
+        }
+        ++wk.pc;
+        double v[1] = {acc.value()}, o[1];
+        if (!grid_reduce<1>(c.ctl, wk.epoch, v, o, red, c.timeout_ns)) { aborted = true; goto done; }
+        const double gnew = o[0];
+        ++iters;
+        if (c.history && blockIdx.x == 0 && threadIdx.x == 0) c.history[iters] = sqrt(gnew / bb);
+        if (!isfinite(gnew)) { status = LAP5CG_ERR_NONFINITE; gamma = gnew; goto truecheck; }
+        beta = gnew / gamma;
+        gamma = gnew;
+        cur ^= 1;
+        if (gnew <= thr) { status = LAP5CG_OK; goto truecheck; }
+      }
+    }
+  }
+truecheck:
+  if (c.true_res) {
+    Acc abb, arr;
+    const Grid<T> none{nullptr, 0};
+    pass_residual<V>(c, wk, a.b, a.x, none, abb, arr);
+    double v[1] = {arr.value()}, o[1];
+    if (!grid_reduce<1>(c.ctl, wk.epoch, v, o, red, c.timeout_ns)) { aborted = true; goto done; }
+    relres_true = sqrt(o[0] / bb);
+  }
+done:
+  write_info(c, status, aborted, iters, 0, gamma, bb, relres_true);
+}
+
+// ---------------------------------------------------------------------------
+// Algorithm 2 (NewCG), one fused pass and one grid reduction per iteration.
+//   prologue: r = b - A x0                       (pass 1, (b,b))
+//             w = A r, gamma = (r,r), delta = (w,r)   (pass 2)
+//   iteration (lines 12-23 of the paper's loop; the prologue's lines 5-10 are
+//   the first iteration with beta = 0 and z, q, p unread):
+//             n = A w from the w tile plus halo, then
+//             z = n + beta z, q = w + beta q, p = r + beta p,
+//             x += alpha p, r -= alpha q, w_new = w - alpha z,
+//             and (r,r), (w_new,r) of the new vectors for the next iteration.
+// w is double-buffered because its halo is read while it is rewritten.
+// Residual replacement (rr_period > 0) recomputes r = b - A x, w = A r,
+// q = A p, z = A q from x and p every rr_period updates.
+// ---------------------------------------------------------------------------
+template <class T>
+struct NewcgArgs {
+  SolveCommon c;
+  Grid<const T> b;
+  Grid<T> x, r, w0, w1, z, q, p;
+  int rr_period;
+};
+
+// y = A g for a stored g (whole grid), with optional (y, other) / (g, g) sums.
+template <int V, class T>
+__device__ __forceinline__ void pass_apply(const SolveCommon& c, Walker& wk, const Grid<T>& g, const Grid<T>& y) {
+  using M = typename Math<T>::type;
+  struct D { int dummy; };
+  for (int u = wk.gw; u < c.un.nunits; u += wk.nw) {
+    int s, y0, y1;
+    unit_bounds(c.un, u, c.ny, s, y0, y1);
+    const int xs = s * 32 * V, xl = xs + wk.lane * V;
+    auto field = [&](int j, FRow<V, M>& f) { field_plain<V>(g, c.nx, c.ny, j, xl, xs, wk.lane, f); };
+    auto load = [&](int, D&) {};
+    auto finish = [&](int j, const D&, const FRow<V, M>& S, const FRow<V, M>& C, const FRow<V, M>& N) {
+      M yv[V];
+      stencil_row<V>(S, C, N, wk.lane, yv);
+      store_row<V>(y, j, xl, c.nx, yv);
+    };
+    march<V, M, D>(y0, y1, wk.rev(), field, load, finish);
+  }
+  ++wk.pc;
+}
+
+// w = A r with gamma = (r, r), delta = (w, r).
+template <int V, class T>
+__device__ __forceinline__ void pass_w_from_r(const SolveCommon& c, Walker& wk, const Grid<T>& r, const Grid<T>& w,
+                                              typename AccOf<typename Math<T>::type>::type& ag,
+                                              typename AccOf<typename Math<T>::type>::type& ad) {
+  using M = typename Math<T>::type;
+  struct D { int dummy; };
+  for (int u = wk.gw; u < c.un.nunits; u += wk.nw) {
+    int s, y0, y1;
+    unit_bounds(c.un, u, c.ny, s, y0, y1);
+    const int xs = s * 32 * V, xl = xs + wk.lane * V;
+    const int nval = min(max(c.nx - xl, 0), V);
+    auto field = [&](int j, FRow<V, M>& f) { field_plain<V>(r, c.nx, c.ny, j, xl, xs, wk.lane, f); };
+    auto load = [&](int, D&) {};
+    auto finish = [&](int j, const D&, const FRow<V, M>& S, const FRow<V, M>& C, const FRow<V, M>& N) {
+      M wv[V];
+      stencil_row<V>(S, C, N, wk.lane, wv);
+      store_row<V>(w, j, xl, c.nx, wv);
+#pragma unroll
+      for (int k = 0; k < V; ++k)
+        if (k < nval) { ag.add(C.f[k], C.f[k]); ad.add(wv[k], C.f[k]); }
+    };
+    march<V, M, D>(y0, y1, wk.rev(), field, load, finish);
+  }
+  ++wk.pc;
+}
+
+template <class T, int V>
+__device__ void newcg_solve(const NewcgArgs<T>& a) {
+  using M = typename Math<T>::type;
+  using Acc = typename AccOf<M>::type;
+  __shared__ double red[33 * kMaxVals];
+  const SolveCommon& c = a.c;
+  Walker wk;
+  wk.init();
+
+  int status = LAP5CG_NOT_CONVERGED, iters = 0;
+  double bb = 0.0, gamma = 0.0, delta = 0.0, alpha = 0.0, beta = 0.0, relres_true = nan("");
+  bool aborted = false;
+  int cur = 0;  // current w lives in w[cur]
+
+  {  // line 1: r = b - A x
+    Acc abb, arr;
+    pass_residual<V>(c, wk, a.b, a.x, a.r, abb, arr);
+    double v[1] = {abb.value()}, o[1];
+    if (!grid_reduce<1>(c.ctl, wk.epoch, v, o, red, c.timeout_ns)) { aborted = true; goto done; }
+    bb = o[0];
+  }
+  if (!isfinite(bb)) { status = LAP5CG_ERR_NONFINITE; goto done; }
+  if (bb == 0.0) {
+    pass_zero<V>(c, wk, a.x);
+    status = LAP5CG_OK;
+    relres_true = 0.0;
+    goto done;
+  }
+  {
+    const double thr = c.tol > 0.0 ? c.tol * c.tol * bb : 0.0;
+    {  // lines 2-4: w = A r, gamma = (r, r), delta = (w, r)
+      Acc ag, ad;
+      pass_w_from_r<V>(c, wk, a.r, a.w0, ag, ad);
+      double v[2] = {ag.value(), ad.value()}, o[2];
+      if (!grid_reduce<2>(c.ctl, wk.epoch, v, o, red, c.timeout_ns)) { aborted = true; goto done; }
+      gamma = o[0];
+      delta = o[1];
+    }
+    if (c.history && blockIdx.x == 0 && threadIdx.x == 0) c.history[0] = sqrt(gamma / bb);
+    if (!isfinite(gamma)) { status = LAP5CG_ERR_NONFINITE; goto truecheck; }
+    if (gamma <= thr) { status = LAP5CG_OK; goto truecheck; }
+    if (c.maxit <= 0) goto truecheck;
+    if (!(delta > 0.0) || !isfinite(delta)) { status = LAP5CG_ERR_BREAKDOWN; goto truecheck; }
+    alpha = gamma / delta;  // line 6
+    beta = 0.0;
+    for (;;) {
+      const bool first = (iters == 0);
+      const Grid<T> w = cur ? a.w1 : a.w0;
+      const Grid<T> wn = cur ? a.w0 : a.w1;
+      const M am = (M)alpha, bm = (M)beta;
+      Acc ag, ad;
+      struct D { M z[V], q[V], p[V], x[V], r[V]; };
+      for (int u = wk.gw; u < c.un.nunits; u += wk.nw) {
+        int s, y0, y1;
+        unit_bounds(c.un, u, c.ny, s, y0, y1);
+        const int xs = s * 32 * V, xl = xs + wk.lane * V;
+        const int nval = min(max(c.nx - xl, 0), V);
+        auto field = [&](int j, FRow<V, M>& f) { field_plain<V>(w, c.nx, c.ny, j, xl, xs, wk.lane, f); };
+        auto load = [&](int j, D& d) {
+          if (!first) {
+            load_row<V>(a.z, j, xl, c.nx, d.z);
+            load_row<V>(a.q, j, xl, c.nx, d.q);
+            load_row<V>(a.p, j, xl, c.nx, d.p);
+          }
+          load_row<V>(a.x, j, xl, c.nx, d.x);
+          load_row<V>(a.r, j, xl, c.nx, d.r);
+        };
+        auto finish = [&](int j, const D& d, const FRow<V, M>& S, const FRow<V, M>& C, const FRow<V, M>& N) {
+          M nv[V], zv[V], qv[V], pv[V], xv[V], rv[V], wv[V];
+          stencil_row<V>(S, C, N, wk.lane, nv);  // n = A w
+#pragma unroll
+          for (int k = 0; k < V; ++k) {
+            if (first) {
+              zv[k] = nv[k];
+              qv[k] = C.f[k];
+              pv[k] = d.r[k];
+            } else {
+              zv[k] = fmx(bm, d.z[k], nv[k]);
+              qv[k] = fmx(bm, d.q[k], C.f[k]);
+              pv[k] = fmx(bm, d.p[k], d.r[k]);
+            }
+            xv[k] = fmx(am, pv[k], d.x[k]);
+            rv[k] = fmx(-am, qv[k], d.r[k]);
+            wv[k] = fmx(-am, zv[k], C.f[k]);
+            if (k < nval) { ag.add(rv[k], rv[k]); ad.add(wv[k], rv[k]); }
+          }
+          store_row<V>(a.z, j, xl, c.nx, zv);
+          store_row<V>(a.q, j, xl, c.nx, qv);
+          store_row<V>(a.p, j, xl, c.nx, pv);
+          store_row<V>(a.x, j, xl, c.nx, xv);
+          store_row<V>(a.r, j, xl, c.nx, rv);
+          store_row<V>(wn, j, xl, c.nx, wv);
+        };
+        march<V, M, D>(y0, y1, wk.rev(), field, load, finish);
+      }
+      ++wk.pc;
+      ++iters;
+      cur ^= 1;
+      double gnew, dnew;
+      if (a.rr_period > 0 && iters % a.rr_period == 0) {
+        // residual replacement: r = b - A x; w = A r; q = A p; z = A q
+        Acc abb, arr;
+        if (!grid_sync(c.ctl, wk.epoch, red, c.timeout_ns)) { aborted = true; goto done; }
+        pass_residual<V>(c, wk, a.b, a.x, a.r, abb, arr);
+        if (!grid_sync(c.ctl, wk.epoch, red, c.timeout_ns)) { aborted = true; goto done; }
+        const Grid<T> wr = cur ? a.w1 : a.w0;
+        Acc ag2, ad2;
+        pass_w_from_r<V>(c, wk, a.r, wr, ag2, ad2);
+        pass_apply<V>(c, wk, a.p, a.q);
+        double v[2] = {ag2.value(), ad2.value()}, o[2];
+        if (!grid_reduce<2>(c.ctl, wk.epoch, v, o, red, c.timeout_ns)) { aborted = true; goto done; }
+        pass_apply<V>(c, wk, a.q, a.z);
+        if (!grid_sync(c.ctl, wk.epoch, red, c.timeout_ns)) { aborted = true; goto done; }
+        gnew = o[0];
+        dnew = o[1];
+      } else {
+        double v[2] = {ag.value(), ad.value()}, o[2];
+        if (!grid_reduce<2>(c.ctl, wk.epoch, v, o, red, c.timeout_ns)) { aborted = true; goto done; }
+        gnew = o[0];
+        dnew = o[1];
+      }
+      if (c.history && blockIdx.x == 0 && threadIdx.x == 0) c.history[iters] = sqrt(gnew / bb);
+      const double gold = gamma;
+      gamma = gnew;
+      delta = dnew;
+      if (!isfinite(gamma)) { status = LAP5CG_ERR_NONFINITE; goto truecheck; }
+      if (gamma <= thr) { status = LAP5CG_OK; goto truecheck; }
+      if (iters >= c.maxit) break;
+      beta = gamma / gold;                               // line 16
+      const double denom = delta / gamma - beta / alpha;  // line 17
+      if (!(denom > 0.0) || !isfinite(denom)) { status = LAP5CG_ERR_BREAKDOWN; goto truecheck; }
+      alpha = 1.0 / denom;
+    }
+  }
+truecheck:
+  if (c.true_res) {
+    Acc abb, arr;
+    const Grid<T> none{nullptr, 0};
+    pass_residual<V>(c, wk, a.b, a.x, none, abb, arr);
+    double v[1] = {arr.value()}, o[1];
+    if (!grid_reduce<1>(c.ctl, wk.epoch, v, o, red, c.timeout_ns)) { aborted = true; goto done; }
+    relres_true = sqrt(o[0] / bb);
+  }
+done:
+  write_info(c, status, aborted, iters, 0, gamma, bb, relres_true);
+}
+
+}  // namespace lap5

@@ -1,0 +1,101 @@
+// cg_launch.cuh -- host launch of the persistent classic / NewCG kernels for
+// one storage type.  Included by cg_f64.cu and cg_f32.cu.
+#pragma once
+
+#include "cg_kernels.cuh"
+#include "launch.h"
+
+namespace lap5 {
+
+template <class T, int V>
+__global__ void __launch_bounds__(512) k_classic(const ClassicArgs<T> a) { classic_solve<T, V>(a); }
+
+template <class T, int V>
+__global__ void __launch_bounds__(512) k_newcg(const NewcgArgs<T> a) { newcg_solve<T, V>(a); }
+
+template <class T>
+inline size_t ws_bytes_t(int ny, int ldw, int variant) {
+  const size_t vec = align_up((size_t)ny * (size_t)ldw * sizeof(T), kAlign);
+  const int nvec = (variant == LAP5CG_NEWCG) ? 6 : 4;
+  return kCtlBytes + nvec * vec;
+}
+
+inline int cooperative_launch(const void* func, const LaunchCfg& cfg, void** args, cudaStream_t st) {
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = dim3(cfg.ctas);
+  lc.blockDim = dim3(cfg.threads);
+  lc.dynamicSmemBytes = 0;
+  lc.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  lc.attrs = attr;
+  lc.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelExC(&lc, func, args);
+  return e == cudaSuccess ? LAP5CG_OK : LAP5CG_ERR_CUDA;
+}
+
+inline SolveCommon make_common(const SolvePlan& p, const LaunchCfg& cfg) {
+  SolveCommon c;
+  c.nx = p.nx;
+  c.ny = p.ny;
+  c.un.ns = cfg.ns;
+  c.un.nseg = cfg.nseg;
+  c.un.seg_rows = cfg.seg_rows;
+  c.un.nunits = cfg.nunits;
+  c.ctl = reinterpret_cast<Ctl*>(p.ws);
+  c.info = p.info;
+  c.history = p.opts.history;
+  c.tol = p.tol;
+  c.maxit = p.maxit;
+  c.true_res = p.opts.true_residual;
+  const double to = p.opts.timeout_s > 0.0 ? p.opts.timeout_s : 2.0;
+  c.timeout_ns = (long long)(to * 1e9);
+  return c;
+}
+
+template <class T, int V>
+int solve_typed(const SolvePlan& p, cudaStream_t st) {
+  const size_t vec = align_up((size_t)p.ny * (size_t)p.ldw * sizeof(T), kAlign);
+  unsigned char* base = p.ws + kCtlBytes;
+  auto vecp = [&](int k) { return reinterpret_cast<T*>(base + (size_t)k * vec); };
+  if (cudaMemsetAsync(p.ws, 0, 256, st) != cudaSuccess) return LAP5CG_ERR_CUDA;
+  LaunchCfg cfg;
+  if (p.variant == LAP5CG_CLASSIC) {
+    const void* fn = reinterpret_cast<const void*>(&k_classic<T, V>);
+    int rc = plan_units(fn, p.nx, p.ny, V, p.opts, &cfg);
+    if (rc != LAP5CG_OK) return rc;
+    ClassicArgs<T> a;
+    a.c = make_common(p, cfg);
+    a.b = Grid<const T>{static_cast<const T*>(p.b), p.ld};
+    a.x = Grid<T>{static_cast<T*>(p.x), p.ld};
+    a.r = Grid<T>{vecp(0), p.ldw};
+    a.p0 = Grid<T>{vecp(1), p.ldw};
+    a.p1 = Grid<T>{vecp(2), p.ldw};
+    a.z = Grid<T>{vecp(3), p.ldw};
+    int sz = p.opts.store_z;
+    if (sz < 0) sz = (sizeof(T) == 8) ? 1 : 0;  // binary64 is FP64-pipe bound: trade bytes for DP ops
+    a.store_z = sz;
+    void* args[] = {&a};
+    return cooperative_launch(fn, cfg, args, st);
+  } else {
+    const void* fn = reinterpret_cast<const void*>(&k_newcg<T, V>);
+    int rc = plan_units(fn, p.nx, p.ny, V, p.opts, &cfg);
+    if (rc != LAP5CG_OK) return rc;
+    NewcgArgs<T> a;
+    a.c = make_common(p, cfg);
+    a.b = Grid<const T>{static_cast<const T*>(p.b), p.ld};
+    a.x = Grid<T>{static_cast<T*>(p.x), p.ld};
+    a.r = Grid<T>{vecp(0), p.ldw};
+    a.w0 = Grid<T>{vecp(1), p.ldw};
+    a.w1 = Grid<T>{vecp(2), p.ldw};
+    a.z = Grid<T>{vecp(3), p.ldw};
+    a.q = Grid<T>{vecp(4), p.ldw};
+    a.p = Grid<T>{vecp(5), p.ldw};
+    a.rr_period = p.opts.rr_period;
+    void* args[] = {&a};
+    return cooperative_launch(fn, cfg, args, st);
+  }
+}
+
+}  // namespace lap5

@@ -1,0 +1,394 @@
+// common.cuh -- device building blocks shared by the lap5cg kernels:
+// element storage (binary64 / binary32 / bf16), lane-vector loads and stores,
+// the 5-point stencil on a warp strip, Dot2 accumulation, and the persistent
+// kernel's grid barrier and deterministic grid reduction.
+//
+// Target: sm_103a (GB300).  No tensor cores: the 5-point stencil is not a
+// dense contraction.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <type_traits>
+
+#include "../../include/lap5cg.h"
+
+namespace lap5 {
+
+// ---------------------------------------------------------------------------
+// Storage types.  bf16 is kept as raw 16-bit words; widening to binary32 is a
+// shift, narrowing uses the hardware round-to-nearest-even conversion.
+// ---------------------------------------------------------------------------
+struct bf16s { uint16_t bits; };
+
+template <class T> struct Math;                       // arithmetic type per storage type
+template <> struct Math<double> { using type = double; };
+template <> struct Math<float> { using type = float; };
+template <> struct Math<bf16s> { using type = float; };
+
+__device__ __forceinline__ float bf_widen(uint16_t h) { return __uint_as_float(((uint32_t)h) << 16); }
+__device__ __forceinline__ uint16_t bf_narrow(float f) {
+  __nv_bfloat16 h = __float2bfloat16_rn(f);
+  return *reinterpret_cast<uint16_t*>(&h);
+}
+
+template <class M, class T> __device__ __forceinline__ M to_math(T v);
+template <> __device__ __forceinline__ double to_math<double, double>(double v) { return v; }
+template <> __device__ __forceinline__ float to_math<float, float>(float v) { return v; }
+template <> __device__ __forceinline__ float to_math<float, bf16s>(bf16s v) { return bf_widen(v.bits); }
+
+template <class T, class M> __device__ __forceinline__ T from_math(M v);
+template <> __device__ __forceinline__ double from_math<double, double>(double v) { return v; }
+template <> __device__ __forceinline__ float from_math<float, float>(float v) { return v; }
+template <> __device__ __forceinline__ bf16s from_math<bf16s, float>(float v) { return bf16s{bf_narrow(v)}; }
+
+// Fused multiply-add in the arithmetic type (never promotes binary32 to binary64).
+__device__ __forceinline__ double fmx(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fmx(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
+// A strided grid view: element (i, j) at ptr[j*ld + i].
+template <class T> struct Grid {
+  T* ptr;
+  int ld;
+  __device__ __forceinline__ T* row(int j) const { return ptr + (size_t)j * (size_t)ld; }
+};
+
+// ---------------------------------------------------------------------------
+// Lane-vector IO: a lane owns V consecutive columns x .. x+V-1 of a row.
+// The vector path needs the row start 16-byte aligned for binary64 / binary32
+// (8-byte for bf16 with V = 4) and ld a multiple of V: then a vector that
+// straddles nx stays inside the row's ld elements and is masked after the load.
+// ---------------------------------------------------------------------------
+template <int V, class T> struct VecIO;
+
+template <> struct VecIO<2, double> {
+  __device__ __forceinline__ static void load(const double* p, double (&v)[2]) {
+    double2 t = *reinterpret_cast<const double2*>(p);
+    v[0] = t.x; v[1] = t.y;
+  }
+  __device__ __forceinline__ static void store(double* p, const double (&v)[2]) {
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+  }
+};
+template <> struct VecIO<4, float> {
+  __device__ __forceinline__ static void load(const float* p, float (&v)[4]) {
+    float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+  }
+  __device__ __forceinline__ static void store(float* p, const float (&v)[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+};
+template <> struct VecIO<4, bf16s> {
+  __device__ __forceinline__ static void load(const bf16s* p, float (&v)[4]) {
+    uint2 t = *reinterpret_cast<const uint2*>(p);
+    v[0] = __uint_as_float(t.x << 16); v[1] = __uint_as_float(t.x & 0xffff0000u);
+    v[2] = __uint_as_float(t.y << 16); v[3] = __uint_as_float(t.y & 0xffff0000u);
+  }
+  __device__ __forceinline__ static void store(bf16s* p, const float (&v)[4]) {
+    uint2 t;
+    t.x = (uint32_t)bf_narrow(v[0]) | ((uint32_t)bf_narrow(v[1]) << 16);
+    t.y = (uint32_t)bf_narrow(v[2]) | ((uint32_t)bf_narrow(v[3]) << 16);
+    *reinterpret_cast<uint2*>(p) = t;
+  }
+};
+// V = 1: plain scalar accesses (rows without 16-byte alignment).
+template <class T> struct VecIO<1, T> {
+  template <class M>
+  __device__ __forceinline__ static void load(const T* p, M (&v)[1]) { v[0] = to_math<M, T>(p[0]); }
+  template <class M>
+  __device__ __forceinline__ static void store(T* p, const M (&v)[1]) { p[0] = from_math<T, M>(v[0]); }
+};
+
+// Load the lane's V values of row j; columns >= nx read as 0.  x < ld is
+// guaranteed by the caller (x is a lane column inside an ld-aligned row).
+template <int V, class T, class M>
+__device__ __forceinline__ void load_row(const Grid<T>& g, int j, int x, int nx, M (&v)[V]) {
+  using U = typename std::remove_const<T>::type;
+  if (x < nx) {
+    VecIO<V, U>::load(g.row(j) + x, v);
+    if (x + V > nx) {
+#pragma unroll
+      for (int k = 0; k < V; ++k)
+        if (x + k >= nx) v[k] = M(0);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < V; ++k) v[k] = M(0);
+  }
+}
+
+// Store the lane's V values of row j; columns >= nx are not written.
+template <int V, class T, class M>
+__device__ __forceinline__ void store_row(const Grid<T>& g, int j, int x, int nx, const M (&v)[V]) {
+  if (x + V <= nx) {
+    VecIO<V, T>::store(g.row(j) + x, v);
+  } else if (x < nx) {
+    T* p = g.row(j) + x;
+#pragma unroll
+    for (int k = 0; k < V; ++k)
+      if (x + k < nx) p[k] = from_math<T, M>(v[k]);
+  }
+}
+
+// Scalar load for a halo column; 0 outside [0, nx).
+template <class T, class M>
+__device__ __forceinline__ M load_one(const Grid<T>& g, int j, int x, int nx) {
+  using U = typename std::remove_const<T>::type;
+  if (x < 0 || x >= nx) return M(0);
+  return to_math<M, U>(g.row(j)[x]);
+}
+
+// ---------------------------------------------------------------------------
+// Field rows.  A "field" is the vector the stencil is applied to; a warp keeps
+// three consecutive field rows (S, C, N) in registers.  hl / hr are the field
+// values at the strip's left / right halo columns (meaningful on lane 0 / 31).
+// ---------------------------------------------------------------------------
+template <int V, class M> struct FRow {
+  M f[V];
+  M hl, hr;
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int k = 0; k < V; ++k) f[k] = M(0);
+    hl = M(0); hr = M(0);
+  }
+};
+
+__device__ __forceinline__ double shfl_up1(double v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ float shfl_up1(float v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ double shfl_dn1(double v) { return __shfl_down_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ float shfl_dn1(float v) { return __shfl_down_sync(0xffffffffu, v, 1); }
+
+// y = A f on the centre row: the Sec. II-B mask in the fixed add order
+// 4*C - W - E - S - N.  4*C is exact, so contracting the first subtraction
+// into a fused multiply-add does not change the result.  Whole-warp call.
+template <int V, class M>
+__device__ __forceinline__ void stencil_row(const FRow<V, M>& S, const FRow<V, M>& C, const FRow<V, M>& N,
+                                            int lane, M (&y)[V]) {
+  M left = shfl_up1(C.f[V - 1]);
+  M right = shfl_dn1(C.f[0]);
+  if (lane == 0) left = C.hl;
+  if (lane == 31) right = C.hr;
+#pragma unroll
+  for (int k = 0; k < V; ++k) {
+    const M w = (k == 0) ? left : C.f[k - 1];
+    const M e = (k == V - 1) ? right : C.f[k + 1];
+    M acc = M(4) * C.f[k];
+    acc -= w;
+    acc -= e;
+    acc -= S.f[k];
+    acc -= N.f[k];
+    y[k] = acc;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Dot-product accumulators.  binary64: plain fused multiply-add.  binary32:
+// Dot2 of Ogita, Rump & Oishi (SIAM J. Sci. Comput. 2005) -- TwoProduct by
+// fmaf, TwoSum by Knuth -- carried per thread as (s, c); the cross-thread
+// reduction then runs in binary64 on s + c.
+// ---------------------------------------------------------------------------
+struct Acc64 {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double a, double b) { s = __fma_rn(a, b, s); }
+  __device__ __forceinline__ double value() const { return s; }
+};
+struct Acc32 {
+  float s = 0.f, c = 0.f;
+  // The _rn intrinsics are never contracted into fused multiply-adds, which
+  // the error-free transformations rely on.
+  __device__ __forceinline__ void add(float a, float b) {
+    const float h = __fmul_rn(a, b);
+    const float l = __fmaf_rn(a, b, -h);
+    const float x = __fadd_rn(s, h);
+    const float zz = __fsub_rn(x, s);
+    const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(x, zz)), __fsub_rn(h, zz));
+    s = x;
+    c = __fadd_rn(c, __fadd_rn(e, l));
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+template <class M> struct AccOf;
+template <> struct AccOf<double> { using type = Acc64; };
+template <> struct AccOf<float> { using type = Acc32; };
+
+// ---------------------------------------------------------------------------
+// Control block in the workspace (zeroed by the host before each launch).
+// ---------------------------------------------------------------------------
+constexpr int kMaxCtas = 2048;     // partial-sum slots per parity
+constexpr int kMaxVals = 4;        // reduced values per barrier
+
+struct Ctl {
+  unsigned long long bar;          // monotonic arrival counter
+  int abort;                       // nonzero: every CTA leaves at its next check
+  int status;                      // first error recorded (0 = none)
+  int pad[12];
+  double part[2][kMaxCtas][kMaxVals];  // per-CTA partials, double-buffered by barrier parity
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ int ld_relaxed_i32(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void record_error(Ctl* ctl, int code) {
+  atomicCAS(&ctl->status, 0, code);
+  __threadfence();
+  atomicExch(&ctl->abort, 1);
+}
+
+// Grid-wide reduction of NV values with a barrier.  Every thread passes its
+// per-thread contributions in v[]; on return every thread of every CTA holds
+// the same totals in out[] (fixed summation order: lanes, warps, then CTA
+// slots 0..G-1), or the function returns false when the solve must stop
+// (abort flag or barrier timeout).  Needs blockDim.x / 32 <= 32 and
+// kMaxVals * 32 doubles of shared scratch (red).
+template <int NV>
+__device__ __forceinline__ bool grid_reduce(Ctl* ctl, unsigned long long& epoch, const double (&v)[NV],
+                                            double (&out)[NV], double* red, long long timeout_ns) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  double t[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double s = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    t[k] = s;
+  }
+  __shared__ int s_go;
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) red[warp * kMaxVals + k] = t[k];
+  }
+  __syncthreads();
+  const int par = (int)(epoch & 1ull);
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double s = lane < nwarps ? red[lane * kMaxVals + k] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) ctl->part[par][blockIdx.x][k] = s;
+    }
+    if (lane == 0) {
+      int go = 1;
+      __threadfence();
+      atomicAdd(&ctl->bar, 1ull);
+      const unsigned long long target = (epoch + 1ull) * (unsigned long long)gridDim.x;
+      const unsigned long long t0 = global_ns();
+      unsigned spins = 0;
+      while (ld_acquire_u64(&ctl->bar) < target) {
+        if ((++spins & 63u) == 0u) {
+          if (ld_relaxed_i32(&ctl->abort)) { go = 0; break; }
+          if ((long long)(global_ns() - t0) > timeout_ns) {
+            record_error(ctl, LAP5CG_ERR_SYNC_TIMEOUT);
+            go = 0;
+            break;
+          }
+        }
+      }
+      if (go && ld_relaxed_i32(&ctl->abort)) go = 0;
+      __threadfence();
+      s_go = go;
+    }
+    __syncwarp();
+    // sum the CTA slots in a fixed order (identical in every CTA)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double s = 0.0;
+      for (int c = lane; c < (int)gridDim.x; c += 32) s += *((volatile double*)&ctl->part[par][c][k]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) red[32 * kMaxVals + k] = s;
+    }
+  }
+  __syncthreads();
+  ++epoch;
+  const bool go = s_go != 0;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) out[k] = red[32 * kMaxVals + k];
+  __syncthreads();  // red is reused by the next call
+  return go;
+}
+
+// Plain grid barrier (no values), same protocol as grid_reduce.
+__device__ __forceinline__ bool grid_sync(Ctl* ctl, unsigned long long& epoch, double* red, long long timeout_ns) {
+  double v[1] = {0.0}, o[1];
+  return grid_reduce<1>(ctl, epoch, v, o, red, timeout_ns);
+}
+
+// Row march over one warp unit [y0, y1) of a strip, in either direction.
+// field(j, FRow&) fills the stencil operand of row j (zeros outside [0, ny));
+// load(j, D&) loads the row's other operands; finish(j, d, S, C, N) consumes
+// row j with its south (j-1), centre and north (j+1) field rows.  One row of
+// look-ahead: the loads of the next row are issued before the current row is
+// finished.  Whole-warp call.
+template <int V, class M, class D, class FieldF, class LoadF, class FinishF>
+__device__ __forceinline__ void march(int y0, int y1, bool rev, FieldF& field, LoadF& load, FinishF& finish) {
+  if (y0 >= y1) return;
+  const int step = rev ? -1 : 1;
+  int j = rev ? y1 - 1 : y0;
+  const int jend = rev ? y0 - 1 : y1;
+  FRow<V, M> fB, fC;
+  D dC;
+  field(j - step, fB);
+  field(j, fC);
+  load(j, dC);
+  for (; j != jend; j += step) {
+    FRow<V, M> fA;
+    D dA;
+    field(j + step, fA);
+    if (j + step != jend) load(j + step, dA);
+    if (!rev) finish(j, dC, fB, fC, fA);
+    else finish(j, dC, fA, fC, fB);
+    fB = fC;
+    fC = fA;
+    dC = dA;
+  }
+}
+
+// Same traversal without a stencil operand (element-wise passes).
+template <class D, class LoadF, class FinishF>
+__device__ __forceinline__ void stream_rows(int y0, int y1, bool rev, LoadF& load, FinishF& finish) {
+  if (y0 >= y1) return;
+  const int step = rev ? -1 : 1;
+  int j = rev ? y1 - 1 : y0;
+  const int jend = rev ? y0 - 1 : y1;
+  D dC;
+  load(j, dC);
+  for (; j != jend; j += step) {
+    D dA;
+    if (j + step != jend) load(j + step, dA);
+    finish(j, dC);
+    dC = dA;
+  }
+}
+
+// Geometry of the warp-unit decomposition of an nx-by-ny grid.
+struct Units {
+  int ns;        // strips of 32*V columns
+  int nseg;      // row segments per strip
+  int seg_rows;  // rows per segment (the last one may be shorter)
+  int nunits;    // ns * nseg
+};
+
+__device__ __forceinline__ void unit_bounds(const Units& u, int unit, int ny, int& strip, int& y0, int& y1) {
+  strip = unit % u.ns;
+  const int seg = unit / u.ns;
+  y0 = seg * u.seg_rows;
+  y1 = min(ny, y0 + u.seg_rows);
+}
+
+}  // namespace lap5

@@ -1,0 +1,62 @@
+// launch.h -- host-side launch interface between the C ABI (api.cu) and the
+// kernel translation units.  Internal to liblap5cg.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/lap5cg.h"
+
+namespace lap5 {
+
+// Launch geometry chosen on the host.
+struct LaunchCfg {
+  int ctas;           // persistent CTAs (all co-resident)
+  int threads;        // threads per CTA
+  int ns, nseg, seg_rows, nunits;  // warp-unit decomposition
+};
+
+// One solve on device buffers that already satisfy the vector-path layout:
+// every row 16-byte aligned, ld a multiple of the lane vector width.
+struct SolvePlan {
+  int nx, ny, ld;              // ld of b and x (user or staged)
+  int ldw;                     // ld of workspace vectors
+  const void* b;
+  void* x;
+  unsigned char* ws;           // workspace base (control block first)
+  size_t ws_bytes;
+  lap5cg_info* info;
+  double tol;
+  int maxit;
+  int variant, precision;
+  lap5cg_opts opts;
+};
+
+int apply_dispatch(int nx, int ny, int ld, int dtype, const void* x, void* y, cudaStream_t st);
+
+// Workspace layout queries (bytes), per precision family.
+size_t ws_bytes_f64(int nx, int ny, int ldw, int variant);
+size_t ws_bytes_f32(int nx, int ny, int ldw, int variant);
+size_t ws_bytes_ir(int nx, int ny, int variant, int precision);
+
+int solve_f64(const SolvePlan& p, cudaStream_t st);
+int solve_f32(const SolvePlan& p, cudaStream_t st);
+int solve_ir(const SolvePlan& p, cudaStream_t st);
+
+// Device properties cached per device.
+struct DevProps {
+  int sms;
+  int max_smem_optin;
+};
+int dev_props(DevProps* out);
+
+// Grid sizing shared by the persistent kernels: fills cfg from the occupancy
+// of kernel func at the requested warps per CTA.
+int plan_units(const void* func, int nx, int ny, int V, const lap5cg_opts& o, LaunchCfg* cfg);
+
+constexpr size_t kCtlBytes = 256 * 1024;  // control block region at the workspace start
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+}  // namespace lap5
