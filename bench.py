@@ -162,6 +162,17 @@ def run_reference(args):
     return 0
 
 
+def _apply_overrides(args):
+    global NX, NY, ITERS, VARIANTS, WORKLOAD
+    v = tuple(x for x in args.variants.split(",") if x)
+    if (args.n, args.iters, v) != (NX, ITERS, VARIANTS):
+        NX = NY = args.n
+        ITERS = args.iters
+        VARIANTS = v
+        WORKLOAD = "PROFILING CASE (not the benchmark workload): %dx%d FP64, %s, %d iterations" % (
+            NX, NY, "+".join(VARIANTS), ITERS)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -170,7 +181,12 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    # profiling-size overrides (the defaults are the benchmark workload)
+    ap.add_argument("--n", type=int, default=NX, help="grid side (profiling only)")
+    ap.add_argument("--iters", type=int, default=ITERS, help="iterations per solve (profiling only)")
+    ap.add_argument("--variants", default=",".join(VARIANTS), help="comma list (profiling only)")
     args = ap.parse_args()
+    _apply_overrides(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

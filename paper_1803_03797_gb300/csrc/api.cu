@@ -67,11 +67,12 @@ static bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_
 
 static size_t elem_of_precision(int precision) { return precision == LAP5CG_PREC_F32 ? 4 : 8; }
 
-// Lane vector width of the solver for a precision (elements per 16 bytes of b/x).
-static int vec_of_precision(int precision) { return precision == LAP5CG_PREC_F32 ? 4 : 2; }
+// Lane vector width of the solver kernels for a precision: binary64 2,
+// binary32 4, mixed-precision kernels 4 (binary64 b and x read 32 bytes a lane).
+static int vec_of_precision(int precision) { return precision == LAP5CG_PREC_F64 ? 2 : 4; }
 
 static int internal_ld(int nx, int ld, int precision) {
-  const int v = (precision == LAP5CG_PREC_F32) ? 4 : 2;
+  const int v = vec_of_precision(precision);
   if (ld % v == 0) return ld;
   return (nx + v - 1) / v * v;
 }
@@ -176,11 +177,9 @@ int cg_solve(int nx, int ny, int ld, const void* b, void* x, double tol, int max
     return LAP5CG_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int ldw = internal_ld(nx, ld, precision);
-  const int vw = vec_of_precision(precision);
   const bool vec_ok = (ldw == ld) && aligned(b, 16) && aligned(x, 16);
   const bool stage = !vec_ok;
   if (stage && ldw == ld) return LAP5CG_ERR_INVALID_ARG;  // aligned pitch but misaligned pointers
-  (void)vw;
   unsigned char* ws = static_cast<unsigned char*>(workspace);
   const size_t solver_bytes = solver_ws(nx, ny, ldw, variant, precision);
   const size_t stage_vec = align_up((size_t)ny * (size_t)ldw * es, kAlign);

@@ -47,6 +47,11 @@ template <> __device__ __forceinline__ bf16s from_math<bf16s, float>(float v) { 
 __device__ __forceinline__ double fmx(double a, double b, double c) { return __fma_rn(a, b, c); }
 __device__ __forceinline__ float fmx(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 
+// Round a value of the arithmetic type to the storage type and back (identity
+// unless the storage is narrower, e.g. bf16).
+template <class T> __device__ __forceinline__ float quantize(float v) { return v; }
+template <> __device__ __forceinline__ float quantize<bf16s>(float v) { return bf_widen(bf_narrow(v)); }
+
 // A strided grid view: element (i, j) at ptr[j*ld + i].
 template <class T> struct Grid {
   T* ptr;
@@ -93,6 +98,18 @@ template <> struct VecIO<4, bf16s> {
     *reinterpret_cast<uint2*>(p) = t;
   }
 };
+template <> struct VecIO<4, double> {
+  __device__ __forceinline__ static void load(const double* p, double (&v)[4]) {
+    const double2 a = reinterpret_cast<const double2*>(p)[0];
+    const double2 b = reinterpret_cast<const double2*>(p)[1];
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+  }
+  __device__ __forceinline__ static void store(double* p, const double (&v)[4]) {
+    reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+  }
+};
+
 // V = 1: plain scalar accesses (rows without 16-byte alignment).
 template <class T> struct VecIO<1, T> {
   template <class M>

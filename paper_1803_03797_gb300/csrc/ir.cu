@@ -1,16 +1,63 @@
-// ir.cu -- FP64 iterative refinement around a binary32 / bf16-p,r inner CG.
-#include "launch.h"
+// ir.cu -- host launch of the mixed-precision kernels: FP64 iterative
+// refinement around an inner classic CG stored in binary32 (IR_F32) or with
+// bf16 p and r (IR_BF16PR).
+#include "ir_kernels.cuh"
+#include "cg_launch.cuh"
 
 namespace lap5 {
 
+template <class TR, int V>
+__global__ void __launch_bounds__(512) k_ir(const IrArgs<TR> a) { ir_solve<TR, V>(a); }
+
+static int inner_ld(int nx) { return (nx + 7) / 8 * 8; }
+
+template <class TR>
+static size_t ws_ir_t(int nx, int ny) {
+  const size_t ldi = (size_t)inner_ld(nx);
+  return kCtlBytes + 3 * align_up((size_t)ny * ldi * sizeof(TR), kAlign) + 2 * align_up((size_t)ny * ldi * 4, kAlign);
+}
+
 size_t ws_bytes_ir(int nx, int ny, int variant, int precision) {
-  (void)nx; (void)ny; (void)variant; (void)precision;
+  if (variant != LAP5CG_CLASSIC) return 0;  // the inner solver is Algorithm 1
+  if (precision == LAP5CG_PREC_IR_F32) return ws_ir_t<float>(nx, ny);
+  if (precision == LAP5CG_PREC_IR_BF16PR) return ws_ir_t<bf16s>(nx, ny);
   return 0;
 }
 
+template <class TR>
+static int solve_ir_t(const SolvePlan& p, cudaStream_t st) {
+  constexpr int V = 4;
+  const int ldi = inner_ld(p.nx);
+  const size_t vr = align_up((size_t)p.ny * ldi * sizeof(TR), kAlign);
+  const size_t vf = align_up((size_t)p.ny * ldi * 4, kAlign);
+  unsigned char* base = p.ws + kCtlBytes;
+  if (cudaMemsetAsync(p.ws, 0, 256, st) != cudaSuccess) return LAP5CG_ERR_CUDA;
+  const void* fn = reinterpret_cast<const void*>(&k_ir<TR, V>);
+  LaunchCfg cfg;
+  int rc = plan_units(fn, p.nx, p.ny, V, p.opts, &cfg);
+  if (rc != LAP5CG_OK) return rc;
+  IrArgs<TR> a;
+  a.c = make_common(p, cfg);
+  a.b = Grid<const double>{static_cast<const double*>(p.b), p.ld};
+  a.x = Grid<double>{static_cast<double*>(p.x), p.ld};
+  a.r = Grid<TR>{reinterpret_cast<TR*>(base), ldi};
+  a.p0 = Grid<TR>{reinterpret_cast<TR*>(base + vr), ldi};
+  a.p1 = Grid<TR>{reinterpret_cast<TR*>(base + 2 * vr), ldi};
+  a.z = Grid<float>{reinterpret_cast<float*>(base + 3 * vr), ldi};
+  a.d = Grid<float>{reinterpret_cast<float*>(base + 3 * vr + vf), ldi};
+  a.store_z = p.opts.store_z > 0 ? 1 : 0;  // binary32 inner passes are bandwidth bound: recompute A p
+  a.max_outer = p.opts.max_outer > 0 ? p.opts.max_outer : 60;
+  a.maxit_inner = p.opts.maxit_inner > 0 ? p.opts.maxit_inner : 4 * (p.nx + p.ny) + 50;
+  a.tol_inner = p.opts.tol_inner > 0.0 ? p.opts.tol_inner : (sizeof(TR) == 2 ? 1e-2 : 1e-4);
+  void* args[] = {&a};
+  return cooperative_launch(fn, cfg, args, st);
+}
+
 int solve_ir(const SolvePlan& p, cudaStream_t st) {
-  (void)p; (void)st;
-  return LAP5CG_ERR_UNSUPPORTED;
+  if (p.variant != LAP5CG_CLASSIC) return LAP5CG_ERR_UNSUPPORTED;
+  if (p.precision == LAP5CG_PREC_IR_F32) return solve_ir_t<float>(p, st);
+  if (p.precision == LAP5CG_PREC_IR_BF16PR) return solve_ir_t<bf16s>(p, st);
+  return LAP5CG_ERR_INVALID_ARG;
 }
 
 }  // namespace lap5

@@ -1,0 +1,252 @@
+// ir_kernels.cuh -- mixed-precision solve in one persistent launch: an outer
+// binary64 iterative-refinement loop around an inner classic CG
+// (Algorithm 1 of arxiv 1803.03797) stored in binary32, or with p and r
+// stored as bf16.
+//
+//   outer pass (binary64): x <- x + d on the unit plus halo, r = b - A x,
+//                          (r, r) and, once, (b, b); r is rounded to the inner
+//                          storage and becomes the inner right-hand side.
+//   inner CG (binary32 arithmetic, Dot2 dot products) on A d = r_in from d = 0,
+//   two fused passes per iteration as in the binary64 classic kernel.
+// The outer residual, the update of x and their dot products are the only
+// binary64 work; the inner iterations move 32 (binary32) or 20 (bf16 p, r)
+// bytes per point.
+#pragma once
+
+#include "cg_kernels.cuh"
+
+namespace lap5 {
+
+template <class TR>
+struct IrArgs {
+  SolveCommon c;                 // c.maxit caps the total inner iterations
+  Grid<const double> b;
+  Grid<double> x;
+  Grid<TR> r, p0, p1;            // inner r and p (binary32 or bf16)
+  Grid<float> z, d;              // inner A p (stored form) and correction d
+  int store_z;
+  int max_outer;
+  int maxit_inner;
+  double tol_inner;
+};
+
+template <class TR, int V>
+__device__ void ir_solve(const IrArgs<TR>& a) {
+  using Acc = Acc32;
+  __shared__ double red[33 * kMaxVals];
+  const SolveCommon& c = a.c;
+  Walker wk;
+  wk.init();
+
+  int status = LAP5CG_NOT_CONVERGED, total = 0, outer = 0;
+  double bb = 0.0, rr = 0.0, relres_true = nan("");
+  bool aborted = false, have_d = false;
+  double thr = 0.0;
+
+  for (;;) {
+    // ---------------- outer pass (binary64) ----------------
+    double g_in;
+    {
+      Acc64 abb, arr;
+      Acc32 agi;
+      const bool upd = have_d;
+      struct D { double b[V]; };
+      for (int u = wk.gw; u < c.un.nunits; u += wk.nw) {
+        int s, y0, y1;
+        unit_bounds(c.un, u, c.ny, s, y0, y1);
+        const int xs = s * 32 * V, xl = xs + wk.lane * V;
+        const int nval = min(max(c.nx - xl, 0), V);
+        auto field = [&](int j, FRow<V, double>& f) {
+          if (j < 0 || j >= c.ny) { f.zero(); return; }
+          load_row<V>(a.x, j, xl, c.nx, f.f);
+          f.hl = (wk.lane == 0) ? load_one<double, double>(a.x, j, xs - 1, c.nx) : 0.0;
+          f.hr = (wk.lane == 31) ? load_one<double, double>(a.x, j, xs + 32 * V, c.nx) : 0.0;
+          if (upd) {
+            float dv[V];
+            load_row<V>(a.d, j, xl, c.nx, dv);
+            const float dl = (wk.lane == 0) ? load_one<float, float>(a.d, j, xs - 1, c.nx) : 0.f;
+            const float dr = (wk.lane == 31) ? load_one<float, float>(a.d, j, xs + 32 * V, c.nx) : 0.f;
+#pragma unroll
+            for (int k = 0; k < V; ++k) f.f[k] = f.f[k] + (double)dv[k];
+            f.hl = f.hl + (double)dl;
+            f.hr = f.hr + (double)dr;
+          }
+        };
+        auto load = [&](int j, D& dd) { load_row<V>(a.b, j, xl, c.nx, dd.b); };
+        auto finish = [&](int j, const D& dd, const FRow<V, double>& S, const FRow<V, double>& C,
+                          const FRow<V, double>& N) {
+          double ax[V];
+          float ri[V];
+          stencil_row<V>(S, C, N, wk.lane, ax);
+#pragma unroll
+          for (int k = 0; k < V; ++k) {
+            const double rv = dd.b[k] - ax[k];
+            ri[k] = quantize<TR>(__double2float_rn(rv));
+            if (k < nval) {
+              if (outer == 0) abb.add(dd.b[k], dd.b[k]);
+              arr.add(rv, rv);
+              agi.add(ri[k], ri[k]);
+            }
+          }
+          if (upd) store_row<V>(a.x, j, xl, c.nx, C.f);
+          store_row<V>(a.r, j, xl, c.nx, ri);
+        };
+        march<V, double, D>(y0, y1, wk.rev(), field, load, finish);
+      }
+      ++wk.pc;
+      double v[3] = {abb.value(), arr.value(), agi.value()}, o[3];
+      if (!grid_reduce<3>(c.ctl, wk.epoch, v, o, red, c.timeout_ns)) { aborted = true; goto done; }
+      if (outer == 0) {
+        bb = o[0];
+        if (!isfinite(bb)) { status = LAP5CG_ERR_NONFINITE; goto done; }
+        if (bb == 0.0) {
+          pass_zero<V>(c, wk, a.x);
+          status = LAP5CG_OK;
+          rr = 0.0;
+          relres_true = 0.0;
+          goto done;
+        }
+        thr = c.tol > 0.0 ? c.tol * c.tol * bb : 0.0;
+      }
+      rr = o[1];
+      g_in = o[2];
+      relres_true = sqrt(rr / bb);
+      if (c.history && outer <= c.maxit && blockIdx.x == 0 && threadIdx.x == 0) c.history[outer] = relres_true;
+    }
+    if (!isfinite(rr)) { status = LAP5CG_ERR_NONFINITE; goto done; }
+    if (rr <= thr) { status = LAP5CG_OK; goto done; }
+    if (outer >= a.max_outer || total >= c.maxit) { status = LAP5CG_NOT_CONVERGED; goto done; }
+
+    // ---------------- inner classic CG on A d = r_in, d0 = 0 ----------------
+    {
+      double gamma = g_in;
+      const double thr_in = a.tol_inner * a.tol_inner * gamma;
+      double beta = 0.0;
+      int cur = 0, k = 0;
+      while (k < a.maxit_inner && total < c.maxit && gamma > thr_in) {
+        const bool first = (k == 0);
+        const Grid<TR> pold = cur ? a.p1 : a.p0;
+        const Grid<TR> pnew = cur ? a.p0 : a.p1;
+        double pz;
+        {  // phase P
+          Acc acc;
+          const float bm = (float)beta;
+          struct D { int dummy; };
+          for (int u = wk.gw; u < c.un.nunits; u += wk.nw) {
+            int s, y0, y1;
+            unit_bounds(c.un, u, c.ny, s, y0, y1);
+            const int xs = s * 32 * V, xl = xs + wk.lane * V;
+            const int nval = min(max(c.nx - xl, 0), V);
+            auto field = [&](int j, FRow<V, float>& f) {
+              if (j < 0 || j >= c.ny) { f.zero(); return; }
+              float rv[V];
+              load_row<V>(a.r, j, xl, c.nx, rv);
+              const float hlr = (wk.lane == 0) ? load_one<TR, float>(a.r, j, xs - 1, c.nx) : 0.f;
+              const float hrr = (wk.lane == 31) ? load_one<TR, float>(a.r, j, xs + 32 * V, c.nx) : 0.f;
+              if (first) {
+#pragma unroll
+                for (int q = 0; q < V; ++q) f.f[q] = rv[q];
+                f.hl = hlr;
+                f.hr = hrr;
+              } else {
+                float pv[V];
+                load_row<V>(pold, j, xl, c.nx, pv);
+                const float hlp = (wk.lane == 0) ? load_one<TR, float>(pold, j, xs - 1, c.nx) : 0.f;
+                const float hrp = (wk.lane == 31) ? load_one<TR, float>(pold, j, xs + 32 * V, c.nx) : 0.f;
+#pragma unroll
+                for (int q = 0; q < V; ++q) f.f[q] = quantize<TR>(fmx(bm, pv[q], rv[q]));
+                f.hl = quantize<TR>(fmx(bm, hlp, hlr));
+                f.hr = quantize<TR>(fmx(bm, hrp, hrr));
+              }
+            };
+            auto load = [&](int, D&) {};
+            auto finish = [&](int j, const D&, const FRow<V, float>& S, const FRow<V, float>& C,
+                              const FRow<V, float>& N) {
+              float ap[V];
+              stencil_row<V>(S, C, N, wk.lane, ap);
+              store_row<V>(pnew, j, xl, c.nx, C.f);
+              if (a.store_z) store_row<V>(a.z, j, xl, c.nx, ap);
+#pragma unroll
+              for (int q = 0; q < V; ++q)
+                if (q < nval) acc.add(C.f[q], ap[q]);
+            };
+            march<V, float, D>(y0, y1, wk.rev(), field, load, finish);
+          }
+          ++wk.pc;
+          double v[1] = {acc.value()}, o[1];
+          if (!grid_reduce<1>(c.ctl, wk.epoch, v, o, red, c.timeout_ns)) { aborted = true; goto done; }
+          pz = o[0];
+        }
+        if (!(pz > 0.0) || !isfinite(pz)) { status = LAP5CG_ERR_BREAKDOWN; goto done; }
+        {  // phase R
+          const float am = (float)(gamma / pz);
+          Acc acc;
+          for (int u = wk.gw; u < c.un.nunits; u += wk.nw) {
+            int s, y0, y1;
+            unit_bounds(c.un, u, c.ny, s, y0, y1);
+            const int xs = s * 32 * V, xl = xs + wk.lane * V;
+            const int nval = min(max(c.nx - xl, 0), V);
+            if (a.store_z) {
+              struct D { float p[V], d[V], r[V], z[V]; };
+              auto load = [&](int j, D& dd) {
+                load_row<V>(pnew, j, xl, c.nx, dd.p);
+                if (!first) load_row<V>(a.d, j, xl, c.nx, dd.d);
+                load_row<V>(a.r, j, xl, c.nx, dd.r);
+                load_row<V>(a.z, j, xl, c.nx, dd.z);
+              };
+              auto finish = [&](int j, const D& dd) {
+                float dv[V], rv[V];
+#pragma unroll
+                for (int q = 0; q < V; ++q) {
+                  dv[q] = first ? __fmul_rn(am, dd.p[q]) : fmx(am, dd.p[q], dd.d[q]);
+                  rv[q] = quantize<TR>(fmx(-am, dd.z[q], dd.r[q]));
+                  if (q < nval) acc.add(rv[q], rv[q]);
+                }
+                store_row<V>(a.d, j, xl, c.nx, dv);
+                store_row<V>(a.r, j, xl, c.nx, rv);
+              };
+              stream_rows<D>(y0, y1, wk.rev(), load, finish);
+            } else {
+              struct D { float d[V], r[V]; };
+              auto field = [&](int j, FRow<V, float>& f) { field_plain<V>(pnew, c.nx, c.ny, j, xl, xs, wk.lane, f); };
+              auto load = [&](int j, D& dd) {
+                if (!first) load_row<V>(a.d, j, xl, c.nx, dd.d);
+                load_row<V>(a.r, j, xl, c.nx, dd.r);
+              };
+              auto finish = [&](int j, const D& dd, const FRow<V, float>& S, const FRow<V, float>& C,
+                                const FRow<V, float>& N) {
+                float ap[V], dv[V], rv[V];
+                stencil_row<V>(S, C, N, wk.lane, ap);
+#pragma unroll
+                for (int q = 0; q < V; ++q) {
+                  dv[q] = first ? __fmul_rn(am, C.f[q]) : fmx(am, C.f[q], dd.d[q]);
+                  rv[q] = quantize<TR>(fmx(-am, ap[q], dd.r[q]));
+                  if (q < nval) acc.add(rv[q], rv[q]);
+                }
+                store_row<V>(a.d, j, xl, c.nx, dv);
+                store_row<V>(a.r, j, xl, c.nx, rv);
+              };
+              march<V, float, D>(y0, y1, wk.rev(), field, load, finish);
+            }
+          }
+          ++wk.pc;
+          double v[1] = {acc.value()}, o[1];
+          if (!grid_reduce<1>(c.ctl, wk.epoch, v, o, red, c.timeout_ns)) { aborted = true; goto done; }
+          const double gnew = o[0];
+          ++k;
+          ++total;
+          if (!isfinite(gnew)) { status = LAP5CG_ERR_BREAKDOWN; goto done; }
+          beta = gnew / gamma;
+          gamma = gnew;
+          cur ^= 1;
+        }
+      }
+      have_d = (k > 0);
+    }
+    ++outer;
+  }
+done:
+  write_info(c, status, aborted, total, outer, rr, bb, relres_true);
+}
+
+}  // namespace lap5

@@ -1,0 +1,87 @@
+"""GPU mixed-precision solves (FP64 iterative refinement around a binary32 or
+bf16-p/r inner classic CG) against the FP64 oracle.
+
+Bar: the FP64 true residual reaches tol = 1e-10 and the solution is within
+kappa * tol of a tightly converged FP64 oracle solution; refinement needs more
+than one outer step (a binary32 inner solve alone cannot reach 1e-10)."""
+import numpy as np
+import pytest
+import torch
+
+import lap5_inputs as gen
+import oracle
+import paper_1803_03797_gb300 as lap5cg
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(1, 1), (3, 5), (64, 64), (100, 100), (130, 67), (255, 257)]
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+@pytest.mark.parametrize("precision", ["ir_f32", "ir_bf16pr"])
+@pytest.mark.parametrize("nx,ny", SHAPES)
+def test_ir_reaches_fp64_accuracy(precision, nx, ny):
+    tol = 1e-10
+    b = gen.uniform_rhs(nx, ny, seed=nx * 31 + ny, ld=gen.pitch(nx, 32))
+    x, info = lap5cg.cg_solve(_dev(b), tol=tol, maxit=10 ** 6, precision=precision, nx=nx)
+    rec = lap5cg.decode_info(info)[0]
+    assert rec["status"] == lap5cg.OK, rec
+    assert rec["relres_true"] <= tol
+    xo, io = oracle.cg_classic(b, tol=1e-13, maxit=10 ** 6, nx=nx)
+    kappa = gen.condition_number(nx, ny)
+    assert _rel(x.cpu().numpy()[:, :nx], xo[:, :nx]) <= max(kappa * 2 * tol, 1e-13)
+    if nx * ny > 16:
+        assert rec["outer_iters"] >= 2
+    # the oracle's refinement takes a similar number of steps
+    xi, ii = oracle.cg_ir(b, tol=tol, inner="f32" if precision == "ir_f32" else "bf16pr", nx=nx)
+    assert ii["status"] == oracle.OK
+    assert abs(rec["outer_iters"] - ii["outer_iters"]) <= max(2, ii["outer_iters"] // 2)
+
+
+@pytest.mark.parametrize("precision", ["ir_f32", "ir_bf16pr"])
+def test_ir_edge_cases(precision):
+    n = 48
+    z = np.zeros((n, n))
+    x, info = lap5cg.cg_solve(_dev(z), x0=_dev(np.ones((n, n))), tol=1e-10, maxit=100, precision=precision)
+    rec = lap5cg.decode_info(info)[0]
+    assert rec["status"] == lap5cg.OK and not x.cpu().numpy().any()
+    b = gen.uniform_rhs(n, n, seed=1)
+    b[5, 5] = np.inf
+    x, info = lap5cg.cg_solve(_dev(b), tol=1e-10, maxit=100, precision=precision)
+    assert lap5cg.decode_info(info)[0]["status"] == lap5cg.ERR_NONFINITE
+    b = gen.uniform_rhs(n, n, seed=1)
+    x, info = lap5cg.cg_solve(_dev(b), tol=1e-10, maxit=10, precision=precision)
+    rec = lap5cg.decode_info(info)[0]
+    assert rec["status"] == lap5cg.NOT_CONVERGED and rec["iters"] == 10
+
+
+def test_ir_newcg_inner_is_unsupported():
+    b = _dev(gen.uniform_rhs(16, 16, seed=1))
+    with pytest.raises(lap5cg.Lap5cgError):
+        lap5cg.cg_solve(b, tol=1e-10, precision="ir_f32", variant="newcg")
+
+
+def test_ir_2048_time_to_solution_beats_fp64():
+    # config: 2048 x 2048 (the gradient workload's grid), to 1e-10
+    n = 2048
+    b = _dev(gen.uniform_rhs(n, n, seed=5))
+    times = {}
+    for precision in ("f64", "ir_f32"):
+        lap5cg.cg_solve(b, tol=1e-10, maxit=10 ** 6, precision=precision)  # warm-up
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        x, info = lap5cg.cg_solve(b, tol=1e-10, maxit=10 ** 6, precision=precision)
+        e1.record()
+        torch.cuda.synchronize()
+        rec = lap5cg.decode_info(info)[0]
+        assert rec["status"] == lap5cg.OK and rec["relres_true"] <= 1.5e-10, (precision, rec)
+        times[precision] = e0.elapsed_time(e1)
+    assert times["ir_f32"] < times["f64"], times
