@@ -46,6 +46,20 @@ COST = {
 FP64_PEAK_TFLOPS = 1.25  # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (nominal GB300 FP64)
 
 
+def captured_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary, or None when the
+    kernel sources changed since the capture (stale counters are not reported)."""
+    import hashlib
+    try:
+        d = json.load(open(os.path.join(ROOT, "profiles", "traffic_per_launch.json")))[kernel]
+        m = hashlib.sha1()
+        for f in d["files"]:
+            m.update(open(os.path.join(ROOT, "paper_1803_03797_gb300", "csrc", f), "rb").read())
+        return d["bytes_per_launch"] if m.hexdigest() == d["source_sha1"] else None
+    except Exception:
+        return None
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -270,13 +284,7 @@ def main():
                                   "frac": tfl / FP64_PEAK_TFLOPS, "ops_per_pt_iter": COST[v]["fp64_ops"]}}
     dom = max(VARIANTS, key=lambda v: per_kernel[v]["ms_per_launch"])
     pk = per_kernel[dom]
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "traffic_per_launch.json")
-    if os.path.exists(prof):
-        try:
-            traffic = json.load(open(prof)).get(COST[dom]["kernel"])
-        except Exception:
-            traffic = None
+    traffic = captured_traffic(COST[dom]["kernel"]) if (NX, ITERS) == (4096, 500) else None
     roofline = {"bound": "alu", "achieved": pk["fp64"]["achieved"], "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": pk["fp64"]["frac"], "traffic": traffic, "kernel": pk["kernel"],
                 "peak_kind": "nominal FP64 pipe (FMA = 2 flop; every FP64 instruction counted as one FMA)",

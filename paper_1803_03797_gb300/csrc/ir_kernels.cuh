@@ -3,9 +3,9 @@
 // (Algorithm 1 of arxiv 1803.03797) stored in binary32, or with p and r
 // stored as bf16.
 //
-//   outer pass (binary64): x <- x + d on the unit plus halo, r = b - A x,
-//                          (r, r) and, once, (b, b); r is rounded to the inner
-//                          storage and becomes the inner right-hand side.
+//   outer passes (binary64): x <- x + d, then r = b - A x with (r, r) and,
+//                          once, (b, b); r is rounded to the inner storage and
+//                          becomes the inner right-hand side.
 //   inner CG (binary32 arithmetic, Dot2 dot products) on A d = r_in from d = 0,
 //   two fused passes per iteration as in the binary64 classic kernel.
 // The outer residual, the update of x and their dot products are the only
@@ -44,34 +44,43 @@ __device__ void ir_solve(const IrArgs<TR>& a) {
   double thr = 0.0;
 
   for (;;) {
-    // ---------------- outer pass (binary64) ----------------
+    // ---------------- outer passes (binary64) ----------------
+    // x <- x + d touches only a warp's own points (d there was written by the
+    // same warp), but the residual pass reads x at halo points, so the update
+    // is a pass of its own followed by a grid barrier: updating x inside the
+    // stencil pass would let a neighbour read an already-updated halo value.
+    if (have_d) {
+      struct DU { double x[V]; float d[V]; };
+      for (int u = wk.gw; u < c.un.nunits; u += wk.nw) {
+        int s, y0, y1;
+        unit_bounds(c.un, u, c.ny, s, y0, y1);
+        const int xl = s * 32 * V + wk.lane * V;
+        auto load = [&](int j, DU& dd) {
+          load_row<V>(a.x, j, xl, c.nx, dd.x);
+          load_row<V>(a.d, j, xl, c.nx, dd.d);
+        };
+        auto finish = [&](int j, const DU& dd) {
+          double xv[V];
+#pragma unroll
+          for (int k = 0; k < V; ++k) xv[k] = dd.x[k] + (double)dd.d[k];
+          store_row<V>(a.x, j, xl, c.nx, xv);
+        };
+        stream_rows<DU>(y0, y1, wk.rev(), load, finish);
+      }
+      ++wk.pc;
+      if (!grid_sync(c.ctl, wk.epoch, red, c.timeout_ns)) { aborted = true; goto done; }
+    }
     double g_in;
     {
       Acc64 abb, arr;
       Acc32 agi;
-      const bool upd = have_d;
       struct D { double b[V]; };
       for (int u = wk.gw; u < c.un.nunits; u += wk.nw) {
         int s, y0, y1;
         unit_bounds(c.un, u, c.ny, s, y0, y1);
         const int xs = s * 32 * V, xl = xs + wk.lane * V;
         const int nval = min(max(c.nx - xl, 0), V);
-        auto field = [&](int j, FRow<V, double>& f) {
-          if (j < 0 || j >= c.ny) { f.zero(); return; }
-          load_row<V>(a.x, j, xl, c.nx, f.f);
-          f.hl = (wk.lane == 0) ? load_one<double, double>(a.x, j, xs - 1, c.nx) : 0.0;
-          f.hr = (wk.lane == 31) ? load_one<double, double>(a.x, j, xs + 32 * V, c.nx) : 0.0;
-          if (upd) {
-            float dv[V];
-            load_row<V>(a.d, j, xl, c.nx, dv);
-            const float dl = (wk.lane == 0) ? load_one<float, float>(a.d, j, xs - 1, c.nx) : 0.f;
-            const float dr = (wk.lane == 31) ? load_one<float, float>(a.d, j, xs + 32 * V, c.nx) : 0.f;
-#pragma unroll
-            for (int k = 0; k < V; ++k) f.f[k] = f.f[k] + (double)dv[k];
-            f.hl = f.hl + (double)dl;
-            f.hr = f.hr + (double)dr;
-          }
-        };
+        auto field = [&](int j, FRow<V, double>& f) { field_plain<V>(a.x, c.nx, c.ny, j, xl, xs, wk.lane, f); };
         auto load = [&](int j, D& dd) { load_row<V>(a.b, j, xl, c.nx, dd.b); };
         auto finish = [&](int j, const D& dd, const FRow<V, double>& S, const FRow<V, double>& C,
                           const FRow<V, double>& N) {
@@ -88,7 +97,6 @@ __device__ void ir_solve(const IrArgs<TR>& a) {
               agi.add(ri[k], ri[k]);
             }
           }
-          if (upd) store_row<V>(a.x, j, xl, c.nx, C.f);
           store_row<V>(a.r, j, xl, c.nx, ri);
         };
         march<V, double, D>(y0, y1, wk.rev(), field, load, finish);
