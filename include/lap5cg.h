@@ -180,6 +180,40 @@ LAP5CG_API int cg_solve_batched(int count, const int* nx, const int* ny, const i
                      int variant, int precision, void* workspace, size_t ws_bytes,
                      lap5cg_info* info, const lap5cg_opts* opts, void* stream);
 
+/* Largest ny*ld that cg_solve_classic_f64_noalloc accepts. */
+#define LAP5CG_NOALLOC_MAX_POINTS 262144
+
+/*
+ * The binary64 classic CG solve (as cg_solve with variant CLASSIC, precision
+ * F64, nrhs 1, default options) for callers that cannot allocate device
+ * memory: its scratch space is a fixed array inside this library, so no
+ * workspace argument is needed.  The paper has no counterpart; this entry
+ * point exists for the library's users.
+ *
+ * Who needs it: applications that fix their device-memory budget at start-up
+ * and forbid allocation afterwards (real-time and safety-certified code),
+ * plug-ins running inside a host framework that owns every device allocation
+ * through its own pool, and latency-critical loops that cannot afford the
+ * device synchronisation a cudaMalloc/cudaFree may imply.
+ *
+ * Limits and behaviour:
+ *   - ny*ld <= LAP5CG_NOALLOC_MAX_POINTS (e.g. 512 x 512); larger grids are
+ *     rejected with LAP5CG_ERR_INVALID_ARG.  ld must be even and b, x 16-byte
+ *     aligned (LAP5CG_ERR_INVALID_ARG otherwise): there is no staging space.
+ *   - The scratch array (8.25 MiB) is a static __device__ object: every GPU
+ *     that loads this library holds it until the process exits.
+ *   - The first call on a device, with that device current, looks up the
+ *     array's device address (cudaGetSymbolAddress) and caches it; make that
+ *     first call before any stream capture.
+ *   - All calls share the one array and the solver re-initialises what must
+ *     start at zero, but calls that overlap on the GPU (different streams, or
+ *     different host threads, on the same device) race on it: serialise them.
+ *   - Calls no cudaMalloc, cudaFree or other allocating routine.
+ * b, x, tol, maxit, info (one entry) and stream are as in cg_solve.
+ */
+LAP5CG_API int cg_solve_classic_f64_noalloc(int nx, int ny, int ld, const double* b, double* x, double tol,
+                                            int maxit, lap5cg_info* info, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

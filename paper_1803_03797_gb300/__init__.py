@@ -79,12 +79,15 @@ def lib():
         L.cg_batched_workspace_size.restype = sz
         L.cg_solve_batched.argtypes = [i, IP, IP, IP, VPP, VPP, d, i, i, i, vp, sz, vp, ctypes.POINTER(Opts), vp]
         L.cg_solve_batched.restype = i
+        L.cg_solve_classic_f64_noalloc.argtypes = [i, i, i, vp, vp, d, i, vp, vp]
+        L.cg_solve_classic_f64_noalloc.restype = i
         _lib = L
     return _lib
 
 
 EXPORTED = ("lap5cg_opts_default", "lap5cg_status_string", "lap5_apply", "cg_workspace_size", "cg_solve",
-            "cg_batched_workspace_size", "cg_solve_batched")
+            "cg_batched_workspace_size", "cg_solve_batched", "cg_solve_classic_f64_noalloc")
+NOALLOC_MAX_POINTS = 262144
 
 
 class Lap5cgError(RuntimeError):
@@ -240,6 +243,30 @@ def cg_solve_batched(bs, xs=None, tol=1e-10, maxit=100000, variant="classic", pr
     if rc != OK:
         raise Lap5cgError(rc, "cg_solve_batched")
     return xs, info
+
+
+def cg_solve_classic_f64_noalloc(b: torch.Tensor, x0: torch.Tensor = None, tol: float = 1e-10, maxit: int = 10000,
+                                 nx: int = None, out: torch.Tensor = None, info: torch.Tensor = None, stream=None):
+    """Classic binary64 CG through the entry point that allocates no device
+    memory (scratch lives in a fixed array inside the library; ny*ld must not
+    exceed NOALLOC_MAX_POINTS).  Returns (x, info)."""
+    _check_grid(b, "b")
+    if b.dtype != torch.float64 or b.dim() != 2:
+        raise ValueError("b must be a 2D float64 CUDA tensor")
+    ny, ld = b.shape
+    nx = ld if nx is None else int(nx)
+    x = out if out is not None else torch.zeros_like(b)
+    if x0 is not None:
+        x.copy_(x0)
+    elif out is not None:
+        x.zero_()
+    if info is None:
+        info = torch.empty(INFO_BYTES, dtype=torch.uint8, device=b.device)
+    rc = lib().cg_solve_classic_f64_noalloc(nx, ny, ld, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                                            float(tol), int(maxit), ctypes.c_void_p(info.data_ptr()), _stream(stream))
+    if rc != OK:
+        raise Lap5cgError(rc, "cg_solve_classic_f64_noalloc")
+    return x, info
 
 
 class CGSolve(torch.autograd.Function):
