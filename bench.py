@@ -143,6 +143,62 @@ def cpu_baseline(sample_iters=4):
                       "pass), single-threaded C oracle" % sample_iters, "seconds": dt}
 
 
+def fused_f32_roofline(lap5cg, torch, dev, hbm_peak, n=8192, iters=200, reps=3):
+    """Binary32 classic CG (the inner loop of the mixed-precision solve) on the
+    n x n uniform right-hand side, fixed iterations: HBM roofline of the fused
+    iteration (32 algorithmic bytes per point per iteration, A p recomputed)."""
+    b = torch.from_numpy(gen.uniform_rhs(n, n, seed=3).astype(np.float32)).to(dev)
+    x = torch.zeros_like(b)
+    ws = torch.empty(lap5cg.workspace_size(n, n, n, "classic", "f32"), dtype=torch.uint8, device=dev)
+    info = torch.empty(lap5cg.INFO_BYTES, dtype=torch.uint8, device=dev)
+    opts = lap5cg.default_opts(true_residual=0)
+
+    def run():
+        lap5cg.cg_solve(b, tol=0.0, maxit=iters, precision="f32", workspace=ws, info=info, out=x, opts=opts)
+
+    run()
+    torch.cuda.synchronize(dev)
+    ms = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        run()
+        e1.record()
+        torch.cuda.synchronize(dev)
+        ms.append(e0.elapsed_time(e1))
+    t = float(np.median(ms)) * 1e-3
+    pts_it = n * n * iters
+    gbs = 32 * pts_it / t / 1e9
+    del b, x, ws
+    return {"kernel": "k_classic<float,4>", "workload": "%dx%d binary32 classic CG, U[-1,1) (seed 3), %d fixed "
+            "iterations, A p recomputed" % (n, n, iters), "ms_per_launch": t * 1e3, "pts_iters_per_s": pts_it / t,
+            "hbm": {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                    "bytes_per_pt_iter": 32}}
+
+
+def time_to_solution(lap5cg, torch, dev, n, rhs, tol=1e-10):
+    """Wall time on the GPU (CUDA events, one solve after a warm-up) to reach
+    relative residual tol: FP64 classic and NewCG vs mixed precision."""
+    b = torch.from_numpy(rhs).to(dev)
+    out = {}
+    for name, variant, prec in (("f64_classic", "classic", "f64"), ("f64_newcg", "newcg", "f64"),
+                                ("ir_f32", "classic", "ir_f32"), ("ir_bf16pr", "classic", "ir_bf16pr")):
+        lap5cg.cg_solve(b, tol=tol, maxit=10 ** 6, variant=variant, precision=prec)  # warm-up
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        x, info = lap5cg.cg_solve(b, tol=tol, maxit=10 ** 6, variant=variant, precision=prec)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        rec = lap5cg.decode_info(info)[0]
+        out[name] = {"ms": e0.elapsed_time(e1), "iters": rec["iters"], "outer_iters": rec["outer_iters"],
+                     "status": rec["status"], "relres_true": rec["relres_true"]}
+        del x
+    out["speedup_ir_f32_vs_f64_classic"] = out["f64_classic"]["ms"] / out["ir_f32"]["ms"]
+    out["speedup_ir_bf16pr_vs_f64_classic"] = out["f64_classic"]["ms"] / out["ir_bf16pr"]["ms"]
+    return out
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -195,6 +251,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the f32 roofline and time-to-solution runs")
+    ap.add_argument("--tts", action="store_true", help="also time FP64 vs mixed precision to 1e-10 at 8192^2")
     # profiling-size overrides (the defaults are the benchmark workload)
     ap.add_argument("--n", type=int, default=NX, help="grid side (profiling only)")
     ap.add_argument("--iters", type=int, default=ITERS, help="iterations per solve (profiling only)")
@@ -326,6 +384,14 @@ def main():
                "d2h_bytes_per_step": int(sum(x.numel() * 8 for x in x_pin.values()) + info_pin.numel()),
                "ms_per_step": ems / args.steps}
 
+    extras = {}
+    if not args.no_extras and ws == 1 and (NX, ITERS) == (4096, 500):
+        extras["fused_f32_8192"] = fused_f32_roofline(lap5cg, torch, dev, hbm_peak)
+        extras["time_to_1e-10_4096"] = time_to_solution(lap5cg, torch, dev, 4096, b_host)
+        if args.tts:
+            extras["time_to_1e-10_8192"] = time_to_solution(lap5cg, torch, dev, 8192,
+                                                            gen.uniform_rhs(8192, 8192, seed=3))
+
     line = None
     if rank == 0:
         cpu = None
@@ -339,7 +405,7 @@ def main():
                            "l2": "inputs larger than L2: each 4096^2 FP64 vector is 134 MB > 126 MB L2, "
                                  "working set ~1 GB"},
                 "roofline": roofline, "per_kernel": per_kernel, "cpu_baseline": cpu, "e2e": e2e,
-                "clocks": clk, "gpu_launches": len(VARIANTS) * args.steps}
+                "clocks": clk, "gpu_launches": len(VARIANTS) * args.steps, "extras": extras}
         print(json.dumps(line))
     if ws > 1:
         torch.distributed.barrier()

@@ -1,0 +1,87 @@
+"""The differentiable solve: x = A^{-1} b by GPU CG, backward = the adjoint
+solve grad_b = A^{-1} grad_x (A symmetric).  Loss 0.5 ||x - x_target||^2, so
+dL/db = A^{-1}(x - x_target).  Checked against a dense solve at 32 x 32,
+central finite differences, and at the 2048 x 2048, 16-right-hand-side size
+through the residual of the adjoint equation computed by the oracle's stencil."""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import torch
+
+import lap5_inputs as gen
+import oracle
+import paper_1803_03797_gb300 as lap5cg
+from tests.helpers import flat, kron_laplacian
+
+pytestmark = pytest.mark.gpu
+
+
+def _loss(b, xt, **kw):
+    x = lap5cg.solve(b, **kw)
+    return 0.5 * ((x - xt) ** 2).sum()
+
+
+@pytest.mark.parametrize("variant", ["classic", "newcg"])
+def test_dense_gradient_32(variant):
+    n = 32
+    b = torch.from_numpy(gen.uniform_rhs(n, n, seed=5)).cuda().requires_grad_(True)
+    xt = torch.from_numpy(gen.gaussian_field(n, n, seed=6)).cuda()
+    loss = _loss(b, xt, tol=1e-13, maxit=10000, variant=variant)
+    loss.backward()
+    A = kron_laplacian(n, n).toarray()
+    cf = sla.cho_factor(A)
+    x = sla.cho_solve(cf, flat(b.detach().cpu().numpy(), n))
+    g_ref = sla.cho_solve(cf, x - flat(xt.cpu().numpy(), n))
+    g = flat(b.grad.cpu().numpy(), n)
+    kappa = gen.condition_number(n, n)
+    assert np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref) <= kappa * 1e-12
+    assert abs(loss.item() - 0.5 * np.sum((x - flat(xt.cpu().numpy(), n)) ** 2)) <= 1e-9 * loss.item()
+
+
+def test_finite_differences():
+    n = 32
+    rng = np.random.default_rng(17)
+    b0 = gen.uniform_rhs(n, n, seed=7)
+    xt = torch.from_numpy(gen.gaussian_field(n, n, seed=8)).cuda()
+    b = torch.from_numpy(b0).cuda().requires_grad_(True)
+    _loss(b, xt, tol=1e-13, maxit=10000).backward()
+    g = b.grad.cpu().numpy()
+    h = 1e-6 * np.linalg.norm(b0)
+
+    def L(bb):
+        with torch.no_grad():
+            return _loss(torch.from_numpy(bb).cuda(), xt, tol=1e-13, maxit=10000).item()
+
+    for _ in range(20):
+        j, i = rng.integers(0, n, 2)
+        e = np.zeros_like(b0)
+        e[j, i] = h
+        fd = (L(b0 + e) - L(b0 - e)) / (2 * h)
+        assert abs(fd - g[j, i]) <= 1e-6 * max(abs(g[j, i]), np.abs(g).max() * 1e-3)
+    for _ in range(3):
+        d = rng.standard_normal(b0.shape)
+        d /= np.linalg.norm(d)
+        fd = (L(b0 + h * d) - L(b0 - h * d)) / (2 * h)
+        assert abs(fd - float(np.sum(g * d))) <= 1e-6 * abs(fd)
+
+
+@pytest.mark.parametrize("precision,tol", [("f64", 1e-10), ("f32", 1e-5)])
+def test_gradient_workload_2048x16(precision, tol):
+    n, k = 2048, 16
+    dt = np.float64 if precision == "f64" else np.float32
+    b0 = np.stack([gen.uniform_rhs(n, n, seed=5000 + s) for s in range(k)]).astype(dt)
+    xt0 = np.stack([gen.gaussian_field(n, n, seed=6000 + s) for s in range(k)]).astype(dt)
+    b = torch.from_numpy(b0).cuda().requires_grad_(True)
+    xt = torch.from_numpy(xt0).cuda()
+    x, info = lap5cg.CGSolve.apply(b, tol, 100000, "classic", precision, None)
+    loss = 0.5 * ((x - xt) ** 2).sum()
+    loss.backward()
+    recs = lap5cg.decode_info(info)
+    assert all(r["status"] == lap5cg.OK for r in recs), recs
+    g = b.grad.detach().cpu().numpy().astype(np.float64)
+    rhs = (x.detach().cpu().numpy() - xt0).astype(np.float64)
+    # the adjoint equation A g = x - x_target, residual by the oracle's stencil
+    for s in (0, k // 2, k - 1):
+        res = rhs[s] - oracle.lap5_apply(g[s])
+        rel = np.linalg.norm(res) / np.linalg.norm(rhs[s])
+        assert rel <= (2 * tol if precision == "f64" else 5e-4), (s, rel)
