@@ -105,7 +105,12 @@ typedef struct {
   double tol_inner;         /* IR: inner relative tolerance; <= 0 = default (1e-4 F32, 1e-2 BF16) */
   double timeout_s;         /* device barrier time limit in seconds; <= 0 = default (2 s) */
   double* history;          /* optional device array of maxit+1 doubles: recursive
-                               relative residual after each update; NULL = off */
+                               relative residual after each update; NULL = off
+                               (single solves only) */
+  int32_t team_ctas;        /* cg_solve_batched: CTAs per instance team (one thread-block
+                               cluster: 1, 2, 4, 8 or 16); 0 = default (8).  For batched
+                               solves `ctas` caps the total CTAs. */
+  int32_t pad_;
 } lap5cg_opts;
 
 /* Fill *o with the defaults above. */
@@ -167,13 +172,23 @@ LAP5CG_API size_t cg_batched_workspace_size(int count, const int* nx, const int*
 
 /*
  * Solve count independent systems A_k x_k = b_k of different shapes in one
- * persistent launch (per-instance convergence masking: an instance that has
- * converged stops and its CTAs take the next instance, largest first).
- *   nx, ny, ld: host arrays of count shapes.
+ * persistent launch.  Each instance is solved by a team of CTAs forming one
+ * thread-block cluster (cluster barrier, reductions through distributed shared
+ * memory); teams take instances from a device-side queue ordered by estimated
+ * work, largest first, so an instance that has converged stops and its team
+ * takes the next one (per-instance convergence masking).  Per instance the
+ * arithmetic is that of cg_solve (Algorithm 1 / 2, same precisions).
+ *   count     : 1 .. LAP5CG_MAX_BATCH.
+ *   nx, ny, ld: host arrays of count shapes; every ld must be a multiple of
+ *               the lane vector width (2 for F64, 4 otherwise) and every b, x
+ *               16-byte aligned (no staging in batched mode).
  *   b, x      : host arrays of count device pointers (element type as in
- *               cg_solve for the precision).
- *   info      : device pointer to count lap5cg_info entries.
- * The host arrays are read during the call only.  Other arguments as cg_solve.
+ *               cg_solve for the precision); x holds x0 on entry.
+ *   info      : device pointer to count lap5cg_info entries (caller order).
+ *   workspace : at least cg_batched_workspace_size() bytes, 256-byte aligned.
+ * The host arrays are read during the call only; the call enqueues a few
+ * table-fill kernels, a memset and the solver launch on the stream.
+ * Returns LAP5CG_ERR_UNSUPPORTED for NEWCG with the IR precisions.
  */
 LAP5CG_API int cg_solve_batched(int count, const int* nx, const int* ny, const int* ld,
                      const void* const* b, void* const* x, double tol, int maxit,

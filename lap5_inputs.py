@@ -100,9 +100,10 @@ def batched_shapes(count: int = 256, lo: int = 64, hi: int = 1024, seed: int = 4
     return [int(v) for v in nx], [int(v) for v in ny]
 
 
-def batched_rhs(nx_list, ny_list, seed: int = 4, elem_bytes: int = 8, dtype=np.float64):
-    """One U[-1,1) right-hand side per instance, seeded seed*1000003 + k."""
+def batched_rhs(nx_list, ny_list, seed: int = 4, elem_bytes: int = 8, dtype=np.float64, align_bytes: int = 32):
+    """One U[-1,1) right-hand side per instance, seeded seed*1000003 + k, rows
+    padded to a multiple of align_bytes."""
     out = []
     for k, (nx, ny) in enumerate(zip(nx_list, ny_list)):
-        out.append(uniform_rhs(nx, ny, seed * 1000003 + k, ld=pitch(nx, elem_bytes), dtype=dtype))
+        out.append(uniform_rhs(nx, ny, seed * 1000003 + k, ld=pitch(nx, elem_bytes, align_bytes), dtype=dtype))
     return out

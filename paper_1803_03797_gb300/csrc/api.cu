@@ -41,25 +41,16 @@ int plan_units(const void* func, int nx, int ny, int V, const lap5cg_opts& o, La
   int maxctas = occ * dp.sms;
   if (maxctas > kMaxCtas) maxctas = kMaxCtas;
   int ctas = o.ctas > 0 ? (o.ctas < maxctas ? o.ctas : maxctas) : maxctas;
-  const int ns = (nx + 32 * V - 1) / (32 * V);
   const long long W = (long long)ctas * wpc;
-  const int min_rows = o.min_rows > 0 ? o.min_rows : 8;
-  long long nseg = W / ns;
-  if (nseg < 1) nseg = 1;
-  if (nseg > ny) nseg = ny;
-  int L = (int)((ny + nseg - 1) / nseg);
-  if (L < min_rows) L = min_rows < ny ? min_rows : ny;
-  nseg = (ny + L - 1) / L;
-  L = (int)((ny + nseg - 1) / nseg);  // rebalance
-  const long long nunits = (long long)ns * nseg;
-  if (nunits > 0x7fffffffLL) return LAP5CG_ERR_UNSUPPORTED;
+  const Units un = make_units(nx, ny, V, W, o.min_rows > 0 ? o.min_rows : 8);
+  const long long nunits = un.nunits;
   if (o.ctas <= 0 && nunits < W) ctas = (int)((nunits + wpc - 1) / wpc);
   cfg->ctas = ctas;
   cfg->threads = threads;
-  cfg->ns = ns;
-  cfg->nseg = (int)nseg;
-  cfg->seg_rows = L;
-  cfg->nunits = (int)nunits;
+  cfg->ns = un.ns;
+  cfg->nseg = un.nseg;
+  cfg->seg_rows = un.seg_rows;
+  cfg->nunits = un.nunits;
   return LAP5CG_OK;
 }
 
@@ -116,6 +107,8 @@ void lap5cg_opts_default(lap5cg_opts* o) {
   o->tol_inner = 0.0;
   o->timeout_s = 0.0;
   o->history = nullptr;
+  o->team_ctas = 0;
+  o->pad_ = 0;
 }
 
 const char* lap5cg_status_string(int status) {
@@ -234,16 +227,27 @@ int cg_solve(int nx, int ny, int ld, const void* b, void* x, double tol, int max
 
 size_t cg_batched_workspace_size(int count, const int* nx, const int* ny, const int* ld, int variant,
                                  int precision) {
-  (void)count; (void)nx; (void)ny; (void)ld; (void)variant; (void)precision;
-  return 0;
+  if (variant != LAP5CG_CLASSIC && variant != LAP5CG_NEWCG) return 0;
+  return batched_ws(count, nx, ny, ld, variant, precision);
 }
 
 int cg_solve_batched(int count, const int* nx, const int* ny, const int* ld, const void* const* b, void* const* x,
                      double tol, int maxit, int variant, int precision, void* workspace, size_t ws_bytes,
                      lap5cg_info* info, const lap5cg_opts* opts, void* stream) {
-  (void)count; (void)nx; (void)ny; (void)ld; (void)b; (void)x; (void)tol; (void)maxit; (void)variant;
-  (void)precision; (void)workspace; (void)ws_bytes; (void)info; (void)opts; (void)stream;
-  return LAP5CG_ERR_UNSUPPORTED;
+  if (count < 1 || count > LAP5CG_MAX_BATCH || !nx || !ny || !ld || !b || !x || !info || maxit < 0)
+    return LAP5CG_ERR_INVALID_ARG;
+  if (variant != LAP5CG_CLASSIC && variant != LAP5CG_NEWCG) return LAP5CG_ERR_INVALID_ARG;
+  if (precision < LAP5CG_PREC_F64 || precision > LAP5CG_PREC_IR_BF16PR) return LAP5CG_ERR_INVALID_ARG;
+  if (tol != tol) return LAP5CG_ERR_INVALID_ARG;
+  lap5cg_opts o;
+  if (opts) o = *opts;
+  else lap5cg_opts_default(&o);
+  if (o.rr_period < 0 || o.warps_per_cta < 0 || o.warps_per_cta > 16 || o.ctas < 0 || o.min_rows < 0 ||
+      o.maxit_inner < 0 || o.max_outer < 0 || o.team_ctas < 0)
+    return LAP5CG_ERR_INVALID_ARG;
+  if (o.rr_period > 0 && variant != LAP5CG_NEWCG) return LAP5CG_ERR_INVALID_ARG;
+  return solve_batched(count, nx, ny, ld, b, x, tol, maxit, variant, precision, workspace, ws_bytes, info, o,
+                       static_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"

@@ -34,17 +34,16 @@ struct SolveCommon {
   long long timeout_ns;
 };
 
-// Per-CTA, per-thread bookkeeping of a persistent solve.
+// Per-thread bookkeeping of a persistent solve: this warp's index among the
+// team's warps and the pass counter.
 struct Walker {
   int lane, gw, nw;
-  unsigned long long epoch;
   int pc;  // pass counter: odd passes march in reverse
-  __device__ __forceinline__ void init() {
+  __device__ __forceinline__ void init(int team_rank, int team_size) {
     lane = threadIdx.x & 31;
     const int wpc = blockDim.x >> 5;
-    gw = blockIdx.x * wpc + (threadIdx.x >> 5);
-    nw = gridDim.x * wpc;
-    epoch = 0ull;
+    gw = team_rank * wpc + (threadIdx.x >> 5);
+    nw = team_size * wpc;
     pc = 0;
   }
   __device__ __forceinline__ bool rev() const { return (pc & 1) != 0; }
@@ -60,11 +59,11 @@ __device__ __forceinline__ void field_plain(const Grid<T>& g, int nx, int ny, in
   f.hr = (lane == 31) ? load_one<T, M>(g, j, xs + 32 * V, nx) : M(0);
 }
 
-// Info writer (CTA 0, thread 0).  status_local is the status all CTAs agreed
-// on; an aborted solve reports the error recorded in the control block.
-__device__ __forceinline__ void write_info(const SolveCommon& c, int status_local, bool aborted, int iters,
-                                           int outer, double gamma, double bb, double relres_true) {
-  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+// Info writer (team rank 0, thread 0).  status_local is the status all CTAs
+// agreed on; an aborted solve reports the error recorded in the control block.
+__device__ __forceinline__ void write_info(const SolveCommon& c, int team_rank, int status_local, bool aborted,
+                                           int iters, int outer, double gamma, double bb, double relres_true) {
+  if (team_rank != 0 || threadIdx.x != 0) return;
   lap5cg_info inf;
   int st = status_local;
   if (aborted) {
@@ -149,14 +148,13 @@ struct ClassicArgs {
   int store_z;
 };
 
-template <class T, int V>
-__device__ void classic_solve(const ClassicArgs<T>& a) {
+template <class T, int V, class Team>
+__device__ void classic_solve(const ClassicArgs<T>& a, Team& tm, double* red) {
   using M = typename Math<T>::type;
   using Acc = typename AccOf<M>::type;
-  __shared__ double red[33 * kMaxVals];
   const SolveCommon& c = a.c;
   Walker wk;
-  wk.init();
+  wk.init(tm.rank(), tm.size());
 
   int status = LAP5CG_NOT_CONVERGED, iters = 0;
   double bb = 0.0, gamma = 0.0, relres_true = nan("");
@@ -166,7 +164,7 @@ __device__ void classic_solve(const ClassicArgs<T>& a) {
     Acc abb, arr;
     pass_residual<V>(c, wk, a.b, a.x, a.r, abb, arr);
     double v[2] = {abb.value(), arr.value()}, o[2];
-    if (!grid_reduce<2>(c.ctl, wk.epoch, v, o, red, c.timeout_ns)) { aborted = true; goto done; }
+    if (!tm.template reduce<2>(v, o, red)) { aborted = true; goto done; }
     bb = o[0];
     gamma = o[1];
   }
@@ -180,7 +178,7 @@ __device__ void classic_solve(const ClassicArgs<T>& a) {
   }
   {
     const double thr = c.tol > 0.0 ? c.tol * c.tol * bb : 0.0;
-    if (c.history && blockIdx.x == 0 && threadIdx.x == 0) c.history[0] = sqrt(gamma / bb);
+    if (c.history && tm.rank() == 0 && threadIdx.x == 0) c.history[0] = sqrt(gamma / bb);
     if (!isfinite(gamma)) { status = LAP5CG_ERR_NONFINITE; goto truecheck; }
     if (gamma <= thr) { status = LAP5CG_OK; goto truecheck; }
     double beta = 0.0;
@@ -236,7 +234,7 @@ __device__ void classic_solve(const ClassicArgs<T>& a) {
         }
         ++wk.pc;
         double v[1] = {acc.value()}, o[1];
-        if (!grid_reduce<1>(c.ctl, wk.epoch, v, o, red, c.timeout_ns)) { aborted = true; goto done; }
+        if (!tm.template reduce<1>(v, o, red)) { aborted = true; goto done; }
         pap = o[0];
       }
       if (!(pap > 0.0) || !isfinite(pap)) { status = LAP5CG_ERR_BREAKDOWN; goto truecheck; }
@@ -293,10 +291,10 @@ __device__ void classic_solve(const ClassicArgs<T>& a) {
         }
         ++wk.pc;
         double v[1] = {acc.value()}, o[1];
-        if (!grid_reduce<1>(c.ctl, wk.epoch, v, o, red, c.timeout_ns)) { aborted = true; goto done; }
+        if (!tm.template reduce<1>(v, o, red)) { aborted = true; goto done; }
         const double gnew = o[0];
         ++iters;
-        if (c.history && blockIdx.x == 0 && threadIdx.x == 0) c.history[iters] = sqrt(gnew / bb);
+        if (c.history && tm.rank() == 0 && threadIdx.x == 0) c.history[iters] = sqrt(gnew / bb);
         if (!isfinite(gnew)) { status = LAP5CG_ERR_NONFINITE; gamma = gnew; goto truecheck; }
         beta = gnew / gamma;
         gamma = gnew;
@@ -311,11 +309,11 @@ truecheck:
     const Grid<T> none{nullptr, 0};
     pass_residual<V>(c, wk, a.b, a.x, none, abb, arr);
     double v[1] = {arr.value()}, o[1];
-    if (!grid_reduce<1>(c.ctl, wk.epoch, v, o, red, c.timeout_ns)) { aborted = true; goto done; }
+    if (!tm.template reduce<1>(v, o, red)) { aborted = true; goto done; }
     relres_true = sqrt(o[0] / bb);
   }
 done:
-  write_info(c, status, aborted, iters, 0, gamma, bb, relres_true);
+  write_info(c, tm.rank(), status, aborted, iters, 0, gamma, bb, relres_true);
 }
 
 // ---------------------------------------------------------------------------
@@ -388,14 +386,13 @@ __device__ __forceinline__ void pass_w_from_r(const SolveCommon& c, Walker& wk, 
   ++wk.pc;
 }
 
-template <class T, int V>
-__device__ void newcg_solve(const NewcgArgs<T>& a) {
+template <class T, int V, class Team>
+__device__ void newcg_solve(const NewcgArgs<T>& a, Team& tm, double* red) {
   using M = typename Math<T>::type;
   using Acc = typename AccOf<M>::type;
-  __shared__ double red[33 * kMaxVals];
   const SolveCommon& c = a.c;
   Walker wk;
-  wk.init();
+  wk.init(tm.rank(), tm.size());
 
   int status = LAP5CG_NOT_CONVERGED, iters = 0;
   double bb = 0.0, gamma = 0.0, delta = 0.0, alpha = 0.0, beta = 0.0, relres_true = nan("");
@@ -406,7 +403,7 @@ __device__ void newcg_solve(const NewcgArgs<T>& a) {
     Acc abb, arr;
     pass_residual<V>(c, wk, a.b, a.x, a.r, abb, arr);
     double v[1] = {abb.value()}, o[1];
-    if (!grid_reduce<1>(c.ctl, wk.epoch, v, o, red, c.timeout_ns)) { aborted = true; goto done; }
+    if (!tm.template reduce<1>(v, o, red)) { aborted = true; goto done; }
     bb = o[0];
   }
   if (!isfinite(bb)) { status = LAP5CG_ERR_NONFINITE; goto done; }
@@ -422,11 +419,11 @@ __device__ void newcg_solve(const NewcgArgs<T>& a) {
       Acc ag, ad;
       pass_w_from_r<V>(c, wk, a.r, a.w0, ag, ad);
       double v[2] = {ag.value(), ad.value()}, o[2];
-      if (!grid_reduce<2>(c.ctl, wk.epoch, v, o, red, c.timeout_ns)) { aborted = true; goto done; }
+      if (!tm.template reduce<2>(v, o, red)) { aborted = true; goto done; }
       gamma = o[0];
       delta = o[1];
     }
-    if (c.history && blockIdx.x == 0 && threadIdx.x == 0) c.history[0] = sqrt(gamma / bb);
+    if (c.history && tm.rank() == 0 && threadIdx.x == 0) c.history[0] = sqrt(gamma / bb);
     if (!isfinite(gamma)) { status = LAP5CG_ERR_NONFINITE; goto truecheck; }
     if (gamma <= thr) { status = LAP5CG_OK; goto truecheck; }
     if (c.maxit <= 0) goto truecheck;
@@ -490,26 +487,26 @@ __device__ void newcg_solve(const NewcgArgs<T>& a) {
       if (a.rr_period > 0 && iters % a.rr_period == 0) {
         // residual replacement: r = b - A x; w = A r; q = A p; z = A q
         Acc abb, arr;
-        if (!grid_sync(c.ctl, wk.epoch, red, c.timeout_ns)) { aborted = true; goto done; }
+        if (!tm.sync(red)) { aborted = true; goto done; }
         pass_residual<V>(c, wk, a.b, a.x, a.r, abb, arr);
-        if (!grid_sync(c.ctl, wk.epoch, red, c.timeout_ns)) { aborted = true; goto done; }
+        if (!tm.sync(red)) { aborted = true; goto done; }
         const Grid<T> wr = cur ? a.w1 : a.w0;
         Acc ag2, ad2;
         pass_w_from_r<V>(c, wk, a.r, wr, ag2, ad2);
         pass_apply<V>(c, wk, a.p, a.q);
         double v[2] = {ag2.value(), ad2.value()}, o[2];
-        if (!grid_reduce<2>(c.ctl, wk.epoch, v, o, red, c.timeout_ns)) { aborted = true; goto done; }
+        if (!tm.template reduce<2>(v, o, red)) { aborted = true; goto done; }
         pass_apply<V>(c, wk, a.q, a.z);
-        if (!grid_sync(c.ctl, wk.epoch, red, c.timeout_ns)) { aborted = true; goto done; }
+        if (!tm.sync(red)) { aborted = true; goto done; }
         gnew = o[0];
         dnew = o[1];
       } else {
         double v[2] = {ag.value(), ad.value()}, o[2];
-        if (!grid_reduce<2>(c.ctl, wk.epoch, v, o, red, c.timeout_ns)) { aborted = true; goto done; }
+        if (!tm.template reduce<2>(v, o, red)) { aborted = true; goto done; }
         gnew = o[0];
         dnew = o[1];
       }
-      if (c.history && blockIdx.x == 0 && threadIdx.x == 0) c.history[iters] = sqrt(gnew / bb);
+      if (c.history && tm.rank() == 0 && threadIdx.x == 0) c.history[iters] = sqrt(gnew / bb);
       const double gold = gamma;
       gamma = gnew;
       delta = dnew;
@@ -528,11 +525,11 @@ truecheck:
     const Grid<T> none{nullptr, 0};
     pass_residual<V>(c, wk, a.b, a.x, none, abb, arr);
     double v[1] = {arr.value()}, o[1];
-    if (!grid_reduce<1>(c.ctl, wk.epoch, v, o, red, c.timeout_ns)) { aborted = true; goto done; }
+    if (!tm.template reduce<1>(v, o, red)) { aborted = true; goto done; }
     relres_true = sqrt(o[0] / bb);
   }
 done:
-  write_info(c, status, aborted, iters, 0, gamma, bb, relres_true);
+  write_info(c, tm.rank(), status, aborted, iters, 0, gamma, bb, relres_true);
 }
 
 }  // namespace lap5

@@ -8,10 +8,18 @@
 namespace lap5 {
 
 template <class T, int V>
-__global__ void __launch_bounds__(512) k_classic(const ClassicArgs<T> a) { classic_solve<T, V>(a); }
+__global__ void __launch_bounds__(512) k_classic(const ClassicArgs<T> a) {
+  __shared__ double red[kRedDoubles];
+  GridTeam tm{a.c.ctl, a.c.timeout_ns, 0ull};
+  classic_solve<T, V>(a, tm, red);
+}
 
 template <class T, int V>
-__global__ void __launch_bounds__(512) k_newcg(const NewcgArgs<T> a) { newcg_solve<T, V>(a); }
+__global__ void __launch_bounds__(512) k_newcg(const NewcgArgs<T> a) {
+  __shared__ double red[kRedDoubles];
+  GridTeam tm{a.c.ctl, a.c.timeout_ns, 0ull};
+  newcg_solve<T, V>(a, tm, red);
+}
 
 template <class T>
 inline size_t ws_bytes_t(int ny, int ldw, int variant) {

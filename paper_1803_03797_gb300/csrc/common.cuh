@@ -9,6 +9,7 @@
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cooperative_groups.h>
 #include <stdint.h>
 #include <type_traits>
 
@@ -399,6 +400,108 @@ struct Units {
   int nseg;      // row segments per strip
   int seg_rows;  // rows per segment (the last one may be shorter)
   int nunits;    // ns * nseg
+};
+
+// Units for W warps: as many row segments per strip as there are warps per
+// strip, but no segment shorter than min_rows (halo rows cost two extra row
+// loads per segment); segments rebalanced to equal height.
+__host__ __device__ inline Units make_units(int nx, int ny, int V, long long W, int min_rows) {
+  Units u;
+  u.ns = (nx + 32 * V - 1) / (32 * V);
+  long long nseg = W / u.ns;
+  if (nseg < 1) nseg = 1;
+  if (nseg > ny) nseg = ny;
+  int L = (int)((ny + nseg - 1) / nseg);
+  if (L < min_rows) L = min_rows < ny ? min_rows : ny;
+  nseg = (ny + L - 1) / L;
+  L = (int)((ny + nseg - 1) / nseg);
+  u.nseg = (int)nseg;
+  u.seg_rows = L;
+  u.nunits = (int)((long long)u.ns * nseg);
+  return u;
+}
+
+// Shared scratch every solve body needs: per-warp partials (32 x kMaxVals),
+// totals (kMaxVals) and, for cluster teams, the CTA partial by parity
+// (2 x kMaxVals).
+constexpr int kRedDoubles = 35 * kMaxVals;
+
+// A team is the set of CTAs that solve one system together.
+//  GridTeam: every CTA of a cooperative launch; the barrier is the bounded
+//  spin in grid_reduce.
+struct GridTeam {
+  Ctl* ctl;
+  long long timeout_ns;
+  unsigned long long epoch;
+  __device__ __forceinline__ int rank() const { return (int)blockIdx.x; }
+  __device__ __forceinline__ int size() const { return (int)gridDim.x; }
+  template <int NV>
+  __device__ __forceinline__ bool reduce(const double (&v)[NV], double (&o)[NV], double* red) {
+    return grid_reduce<NV>(ctl, epoch, v, o, red, timeout_ns);
+  }
+  __device__ __forceinline__ bool sync(double* red) { return grid_sync(ctl, epoch, red, timeout_ns); }
+};
+
+//  ClusterTeam: the CTAs of one thread-block cluster.  The barrier is the
+//  hardware cluster barrier (release/acquire at cluster scope, plus gpu-scope
+//  fences for the global-memory halos); partial sums move through distributed
+//  shared memory.  No spin-wait, so nothing to time out.
+struct ClusterTeam {
+  unsigned long long epoch;
+  __device__ __forceinline__ int rank() const { return (int)cooperative_groups::this_cluster().block_rank(); }
+  __device__ __forceinline__ int size() const { return (int)cooperative_groups::this_cluster().num_blocks(); }
+  __device__ __forceinline__ void barrier() {
+    __threadfence();
+    cooperative_groups::this_cluster().sync();
+    __threadfence();
+  }
+  template <int NV>
+  __device__ __forceinline__ bool reduce(const double (&v)[NV], double (&out)[NV], double* red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int par = (int)(epoch & 1ull);
+    double* slot = red + 33 * kMaxVals + par * kMaxVals;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double s = v[k];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) red[warp * kMaxVals + k] = s;
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+      for (int k = 0; k < NV; ++k) {
+        double s = lane < nwarps ? red[lane * kMaxVals + k] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) slot[k] = s;
+      }
+    }
+    barrier();
+    if (warp == 0) {
+      auto cl = cooperative_groups::this_cluster();
+      const int n = (int)cl.num_blocks();
+#pragma unroll
+      for (int k = 0; k < NV; ++k) {
+        double s = 0.0;
+        if (lane < n) s = *cl.map_shared_rank(slot + k, (unsigned)lane);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) red[32 * kMaxVals + k] = s;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) out[k] = red[32 * kMaxVals + k];
+    __syncthreads();
+    ++epoch;
+    return true;
+  }
+  __device__ __forceinline__ bool sync(double*) {
+    barrier();
+    ++epoch;
+    return true;
+  }
 };
 
 __device__ __forceinline__ void unit_bounds(const Units& u, int unit, int ny, int& strip, int& y0, int& y1) {

@@ -7,7 +7,11 @@
 namespace lap5 {
 
 template <class TR, int V>
-__global__ void __launch_bounds__(512) k_ir(const IrArgs<TR> a) { ir_solve<TR, V>(a); }
+__global__ void __launch_bounds__(512) k_ir(const IrArgs<TR> a) {
+  __shared__ double red[kRedDoubles];
+  GridTeam tm{a.c.ctl, a.c.timeout_ns, 0ull};
+  ir_solve<TR, V>(a, tm, red);
+}
 
 static int inner_ld(int nx) { return (nx + 7) / 8 * 8; }
 

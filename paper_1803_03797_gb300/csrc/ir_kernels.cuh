@@ -30,13 +30,12 @@ struct IrArgs {
   double tol_inner;
 };
 
-template <class TR, int V>
-__device__ void ir_solve(const IrArgs<TR>& a) {
+template <class TR, int V, class Team>
+__device__ void ir_solve(const IrArgs<TR>& a, Team& tm, double* red) {
   using Acc = Acc32;
-  __shared__ double red[33 * kMaxVals];
   const SolveCommon& c = a.c;
   Walker wk;
-  wk.init();
+  wk.init(tm.rank(), tm.size());
 
   int status = LAP5CG_NOT_CONVERGED, total = 0, outer = 0;
   double bb = 0.0, rr = 0.0, relres_true = nan("");
@@ -68,7 +67,7 @@ __device__ void ir_solve(const IrArgs<TR>& a) {
         stream_rows<DU>(y0, y1, wk.rev(), load, finish);
       }
       ++wk.pc;
-      if (!grid_sync(c.ctl, wk.epoch, red, c.timeout_ns)) { aborted = true; goto done; }
+      if (!tm.sync(red)) { aborted = true; goto done; }
     }
     double g_in;
     {
@@ -103,7 +102,7 @@ __device__ void ir_solve(const IrArgs<TR>& a) {
       }
       ++wk.pc;
       double v[3] = {abb.value(), arr.value(), agi.value()}, o[3];
-      if (!grid_reduce<3>(c.ctl, wk.epoch, v, o, red, c.timeout_ns)) { aborted = true; goto done; }
+      if (!tm.template reduce<3>(v, o, red)) { aborted = true; goto done; }
       if (outer == 0) {
         bb = o[0];
         if (!isfinite(bb)) { status = LAP5CG_ERR_NONFINITE; goto done; }
@@ -119,7 +118,7 @@ __device__ void ir_solve(const IrArgs<TR>& a) {
       rr = o[1];
       g_in = o[2];
       relres_true = sqrt(rr / bb);
-      if (c.history && outer <= c.maxit && blockIdx.x == 0 && threadIdx.x == 0) c.history[outer] = relres_true;
+      if (c.history && outer <= c.maxit && tm.rank() == 0 && threadIdx.x == 0) c.history[outer] = relres_true;
     }
     if (!isfinite(rr)) { status = LAP5CG_ERR_NONFINITE; goto done; }
     if (rr <= thr) { status = LAP5CG_OK; goto done; }
@@ -182,7 +181,7 @@ __device__ void ir_solve(const IrArgs<TR>& a) {
           }
           ++wk.pc;
           double v[1] = {acc.value()}, o[1];
-          if (!grid_reduce<1>(c.ctl, wk.epoch, v, o, red, c.timeout_ns)) { aborted = true; goto done; }
+          if (!tm.template reduce<1>(v, o, red)) { aborted = true; goto done; }
           pz = o[0];
         }
         if (!(pz > 0.0) || !isfinite(pz)) { status = LAP5CG_ERR_BREAKDOWN; goto done; }
@@ -239,7 +238,7 @@ __device__ void ir_solve(const IrArgs<TR>& a) {
           }
           ++wk.pc;
           double v[1] = {acc.value()}, o[1];
-          if (!grid_reduce<1>(c.ctl, wk.epoch, v, o, red, c.timeout_ns)) { aborted = true; goto done; }
+          if (!tm.template reduce<1>(v, o, red)) { aborted = true; goto done; }
           const double gnew = o[0];
           ++k;
           ++total;
@@ -254,7 +253,7 @@ __device__ void ir_solve(const IrArgs<TR>& a) {
     ++outer;
   }
 done:
-  write_info(c, status, aborted, total, outer, rr, bb, relres_true);
+  write_info(c, tm.rank(), status, aborted, total, outer, rr, bb, relres_true);
 }
 
 }  // namespace lap5

@@ -40,6 +40,11 @@ size_t ws_bytes_f64(int nx, int ny, int ldw, int variant);
 size_t ws_bytes_f32(int nx, int ny, int ldw, int variant);
 size_t ws_bytes_ir(int nx, int ny, int variant, int precision);
 
+size_t batched_ws(int count, const int* nx, const int* ny, const int* ld, int variant, int precision);
+int solve_batched(int count, const int* nx, const int* ny, const int* ld, const void* const* b, void* const* x,
+                  double tol, int maxit, int variant, int precision, void* workspace, size_t ws_bytes,
+                  lap5cg_info* info, const lap5cg_opts& o, cudaStream_t st);
+
 int solve_f64(const SolvePlan& p, cudaStream_t st);
 int solve_f32(const SolvePlan& p, cudaStream_t st);
 int solve_ir(const SolvePlan& p, cudaStream_t st);
@@ -57,6 +62,6 @@ int plan_units(const void* func, int nx, int ny, int V, const lap5cg_opts& o, La
 
 constexpr size_t kCtlBytes = 256 * 1024;  // control block region at the workspace start
 constexpr size_t kAlign = 256;
-inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+__host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 }  // namespace lap5
