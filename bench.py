@@ -181,13 +181,16 @@ def time_to_solution(lap5cg, torch, dev, n, rhs, tol=1e-10):
     relative residual tol: FP64 classic and NewCG vs mixed precision."""
     b = torch.from_numpy(rhs).to(dev)
     out = {}
-    for name, variant, prec in (("f64_classic", "classic", "f64"), ("f64_newcg", "newcg", "f64"),
-                                ("ir_f32", "classic", "ir_f32"), ("ir_bf16pr", "classic", "ir_bf16pr")):
-        lap5cg.cg_solve(b, tol=tol, maxit=10 ** 6, variant=variant, precision=prec)  # warm-up
+    # NewCG to 1e-10 at these condition numbers needs residual replacement
+    # (without it Algorithm 2 breaks down in binary64, on the oracle as well)
+    for name, variant, prec, rr in (("f64_classic", "classic", "f64", 0), ("f64_newcg_rr100", "newcg", "f64", 100),
+                                    ("ir_f32", "classic", "ir_f32", 0), ("ir_bf16pr", "classic", "ir_bf16pr", 0)):
+        opts = lap5cg.default_opts(rr_period=rr)
+        lap5cg.cg_solve(b, tol=tol, maxit=10 ** 6, variant=variant, precision=prec, opts=opts)  # warm-up
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        x, info = lap5cg.cg_solve(b, tol=tol, maxit=10 ** 6, variant=variant, precision=prec)
+        x, info = lap5cg.cg_solve(b, tol=tol, maxit=10 ** 6, variant=variant, precision=prec, opts=opts)
         e1.record()
         torch.cuda.synchronize(dev)
         rec = lap5cg.decode_info(info)[0]

@@ -423,12 +423,23 @@ int ora_cg_ir(int nx, int ny, int ld, const double* b, double* x, double tol, in
   float *rin = calloc(n, 4), *d = calloc(n, 4), *ri = calloc(n, 4), *pi = calloc(n, 4), *zi = calloc(n, 4);
   if (!r || !rin || !d || !ri || !pi || !zi) { free(r); free(rin); free(d); free(ri); free(pi); free(zi); inf.status = ORA_ERR_INVALID_ARG; if (info) *info = inf; return inf.status; }
   int status = ORA_NOT_CONVERGED, outer = 0, total_inner = 0;
-  double rr = 0.0;
+  double rr = 0.0, rr_prev = 0.0;
   for (;;) {
     residual64(nx, ny, ld, b, x, r);                    /* FP64 residual */
     rr = ora_dot_f64(nx, ny, ld, r, r);
     if (!isfinite(rr)) { status = ORA_ERR_NONFINITE; break; }
     if (rr <= thr) { status = ORA_OK; break; }
+    if (outer > 0 && !(rr < rr_prev)) {
+      /* stagnation guard: the last correction did not lower the FP64
+         residual (the inner precision cannot resolve this system); undo it
+         and stop with the better iterate */
+      for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) x[(size_t)j * ld + i] = x[(size_t)j * ld + i] - (double)d[(size_t)j * ld + i];
+      residual64(nx, ny, ld, b, x, r);
+      rr = ora_dot_f64(nx, ny, ld, r, r);
+      break;
+    }
+    rr_prev = rr;
     if (outer >= max_outer) break;
     for (size_t t = 0; t < n; ++t) rin[t] = (float)r[t]; /* round to nearest */
     int brk = 0;

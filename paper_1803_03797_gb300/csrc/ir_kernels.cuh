@@ -38,8 +38,8 @@ __device__ void ir_solve(const IrArgs<TR>& a, Team& tm, double* red) {
   wk.init(tm.rank(), tm.size());
 
   int status = LAP5CG_NOT_CONVERGED, total = 0, outer = 0;
-  double bb = 0.0, rr = 0.0, relres_true = nan("");
-  bool aborted = false, have_d = false;
+  double bb = 0.0, rr = 0.0, rr_prev = 0.0, relres_true = nan("");
+  bool aborted = false, have_d = false, reverting = false;
   double thr = 0.0;
 
   for (;;) {
@@ -49,6 +49,7 @@ __device__ void ir_solve(const IrArgs<TR>& a, Team& tm, double* red) {
     // is a pass of its own followed by a grid barrier: updating x inside the
     // stencil pass would let a neighbour read an already-updated halo value.
     if (have_d) {
+      const double sgn = reverting ? -1.0 : 1.0;  // x - d undoes a rejected correction
       struct DU { double x[V]; float d[V]; };
       for (int u = wk.gw; u < c.un.nunits; u += wk.nw) {
         int s, y0, y1;
@@ -61,7 +62,7 @@ __device__ void ir_solve(const IrArgs<TR>& a, Team& tm, double* red) {
         auto finish = [&](int j, const DU& dd) {
           double xv[V];
 #pragma unroll
-          for (int k = 0; k < V; ++k) xv[k] = dd.x[k] + (double)dd.d[k];
+          for (int k = 0; k < V; ++k) xv[k] = dd.x[k] + sgn * (double)dd.d[k];
           store_row<V>(a.x, j, xl, c.nx, xv);
         };
         stream_rows<DU>(y0, y1, wk.rev(), load, finish);
@@ -121,7 +122,17 @@ __device__ void ir_solve(const IrArgs<TR>& a, Team& tm, double* red) {
       if (c.history && outer <= c.maxit && tm.rank() == 0 && threadIdx.x == 0) c.history[outer] = relres_true;
     }
     if (!isfinite(rr)) { status = LAP5CG_ERR_NONFINITE; goto done; }
+    if (reverting) { status = LAP5CG_NOT_CONVERGED; goto done; }
     if (rr <= thr) { status = LAP5CG_OK; goto done; }
+    if (outer > 0 && !(rr < rr_prev)) {
+      // stagnation guard: the last correction did not lower the FP64 residual
+      // (the inner precision cannot resolve this system): undo it (x -= d),
+      // recompute the residual and stop with the better iterate
+      reverting = true;
+      have_d = true;
+      continue;
+    }
+    rr_prev = rr;
     if (outer >= a.max_outer || total >= c.maxit) { status = LAP5CG_NOT_CONVERGED; goto done; }
 
     // ---------------- inner classic CG on A d = r_in, d0 = 0 ----------------

@@ -80,8 +80,11 @@ def test_gradient_workload_2048x16(precision, tol):
     assert all(r["status"] == lap5cg.OK for r in recs), recs
     g = b.grad.detach().cpu().numpy().astype(np.float64)
     rhs = (x.detach().cpu().numpy() - xt0).astype(np.float64)
-    # the adjoint equation A g = x - x_target, residual by the oracle's stencil
+    # the adjoint equation A g = x - x_target, residual by the oracle's stencil.
+    # The solve stops on its recursive residual (tol); for this noise-like
+    # right-hand side at kappa = 1.7e6 the true residual of binary64 CG levels
+    # off near 1e-9 (attainable accuracy), of binary32 CG near 1e-4.
     for s in (0, k // 2, k - 1):
         res = rhs[s] - oracle.lap5_apply(g[s])
         rel = np.linalg.norm(res) / np.linalg.norm(rhs[s])
-        assert rel <= (2 * tol if precision == "f64" else 5e-4), (s, rel)
+        assert rel <= (5e-9 if precision == "f64" else 5e-4), (s, rel)
