@@ -110,7 +110,9 @@ typedef struct {
   int32_t team_ctas;        /* cg_solve_batched: CTAs per instance team (one thread-block
                                cluster: 1, 2, 4, 8 or 16); 0 = default (8).  For batched
                                solves `ctas` caps the total CTAs. */
-  int32_t pad_;
+  int32_t ring_slots;       /* rows each warp keeps in flight in its shared-memory ring
+                               (bulk asynchronous copies): 0 = automatic, 3..8 = that many,
+                               < 0 = no ring (rows loaded straight into registers) */
 } lap5cg_opts;
 
 /* Fill *o with the defaults above. */

@@ -47,7 +47,7 @@ class Opts(ctypes.Structure):
                 ("warps_per_cta", ctypes.c_int32), ("min_rows", ctypes.c_int32),
                 ("true_residual", ctypes.c_int32), ("maxit_inner", ctypes.c_int32),
                 ("max_outer", ctypes.c_int32), ("tol_inner", ctypes.c_double), ("timeout_s", ctypes.c_double),
-                ("history", ctypes.c_void_p), ("team_ctas", ctypes.c_int32), ("pad_", ctypes.c_int32)]
+                ("history", ctypes.c_void_p), ("team_ctas", ctypes.c_int32), ("ring_slots", ctypes.c_int32)]
 
 
 _lib = None

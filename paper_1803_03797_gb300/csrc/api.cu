@@ -28,7 +28,7 @@ int dev_props(DevProps* out) {
   return LAP5CG_OK;
 }
 
-int plan_units(const void* func, int nx, int ny, int V, const lap5cg_opts& o, LaunchCfg* cfg) {
+int plan_units(const void* func, int nx, int ny, int V, const lap5cg_opts& o, size_t dyn_smem, LaunchCfg* cfg) {
   DevProps dp;
   int rc = dev_props(&dp);
   if (rc != LAP5CG_OK) return rc;
@@ -36,7 +36,8 @@ int plan_units(const void* func, int nx, int ny, int V, const lap5cg_opts& o, La
   if (wpc > 16) wpc = 16;
   const int threads = 32 * wpc;
   int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, func, threads, 0) != cudaSuccess) return LAP5CG_ERR_CUDA;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, func, threads, dyn_smem) != cudaSuccess)
+    return LAP5CG_ERR_CUDA;
   if (occ < 1) return LAP5CG_ERR_UNSUPPORTED;
   int maxctas = occ * dp.sms;
   if (maxctas > kMaxCtas) maxctas = kMaxCtas;
@@ -47,10 +48,45 @@ int plan_units(const void* func, int nx, int ny, int V, const lap5cg_opts& o, La
   if (o.ctas <= 0 && nunits < W) ctas = (int)((nunits + wpc - 1) / wpc);
   cfg->ctas = ctas;
   cfg->threads = threads;
+  cfg->dyn_smem = dyn_smem;
   cfg->ns = un.ns;
   cfg->nseg = un.nseg;
   cfg->seg_rows = un.seg_rows;
   cfg->nunits = un.nunits;
+  return LAP5CG_OK;
+}
+
+int choose_ring(const void* func, int slot_bytes, const lap5cg_opts& o, RingGeom* g, size_t* dyn_smem) {
+  g->S = 0;
+  g->slot_bytes = slot_bytes;
+  g->warp_bytes = 0;
+  *dyn_smem = 0;
+  if (o.ring_slots < 0) return LAP5CG_OK;
+  int wpc = o.warps_per_cta > 0 ? o.warps_per_cta : 8;
+  if (wpc > 16) wpc = 16;
+  const int budget = 100 * 1024;  // two CTAs of this size fit one SM's 228 KB
+  int S;
+  if (o.ring_slots > 0) {
+    S = o.ring_slots < 3 ? 3 : (o.ring_slots > kRingMaxSlots ? kRingMaxSlots : o.ring_slots);
+  } else {
+    S = (budget / wpc - 128) / slot_bytes;
+    if (S > 6) S = 6;
+    if (S < 3) return LAP5CG_OK;  // too little room: register march
+  }
+  const int warp_bytes = (int)align_up(128 + (size_t)S * slot_bytes, 128);
+  const size_t dyn = (size_t)wpc * warp_bytes;
+  DevProps dp;
+  int rc = dev_props(&dp);
+  if (rc != LAP5CG_OK) return rc;
+  if (dyn > (size_t)dp.max_smem_optin) {
+    if (o.ring_slots > 0) return LAP5CG_ERR_UNSUPPORTED;
+    return LAP5CG_OK;
+  }
+  if (cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess)
+    return LAP5CG_ERR_CUDA;
+  g->S = S;
+  g->warp_bytes = warp_bytes;
+  *dyn_smem = dyn;
   return LAP5CG_OK;
 }
 
@@ -108,7 +144,7 @@ void lap5cg_opts_default(lap5cg_opts* o) {
   o->timeout_s = 0.0;
   o->history = nullptr;
   o->team_ctas = 0;
-  o->pad_ = 0;
+  o->ring_slots = 0;
 }
 
 const char* lap5cg_status_string(int status) {
@@ -157,7 +193,7 @@ int cg_solve(int nx, int ny, int ld, const void* b, void* x, double tol, int max
   if (opts) o = *opts;
   else lap5cg_opts_default(&o);
   if (o.rr_period < 0 || o.warps_per_cta < 0 || o.warps_per_cta > 16 || o.ctas < 0 || o.min_rows < 0 ||
-      o.maxit_inner < 0 || o.max_outer < 0)
+      o.maxit_inner < 0 || o.max_outer < 0 || o.ring_slots > kRingMaxSlots)
     return LAP5CG_ERR_INVALID_ARG;
   if (o.rr_period > 0 && variant != LAP5CG_NEWCG) return LAP5CG_ERR_INVALID_ARG;
   const size_t need = cg_workspace_size(nx, ny, ld, variant, precision, nrhs);

@@ -32,6 +32,8 @@ struct BatchCtl {
 };
 
 struct BatchArgs {
+  RingGeom rg;
+  int* errs;  // per-instance error words (caller order)
   int count;
   const BatchEntry* tab;
   BatchCtl* bctl;
@@ -86,8 +88,9 @@ template <> struct KindTraits<KIND_F32_NEWCG> { using T = float; static constexp
 template <> struct KindTraits<KIND_IR_F32> { using T = float; static constexpr int V = 4; };
 template <> struct KindTraits<KIND_IR_BF16> { using T = bf16s; static constexpr int V = 4; };
 
-template <int KIND>
-__device__ __forceinline__ void solve_instance(const BatchArgs& a, const BatchEntry& e, ClusterTeam& tm, double* red) {
+template <int KIND, bool R>
+__device__ __forceinline__ void solve_instance(const BatchArgs& a, const BatchEntry& e, ClusterTeam& tm, double* red,
+                                               unsigned char* dsm) {
   using T = typename KindTraits<KIND>::T;
   constexpr int V = KindTraits<KIND>::V;
   SolveCommon c;
@@ -100,7 +103,10 @@ __device__ __forceinline__ void solve_instance(const BatchArgs& a, const BatchEn
   c.tol = a.tol;
   c.maxit = a.maxit;
   c.true_res = a.true_res;
-  c.timeout_ns = 0;
+  c.timeout_ns = 2000000000LL;
+  c.rg = a.rg;
+  c.err = a.errs + e.idx;
+  c.abort_flag = nullptr;
   unsigned char* base = a.ws + e.ws_off;
   if constexpr (KIND == KIND_F64_CLASSIC || KIND == KIND_F32_CLASSIC) {
     const size_t vb = vec_bytes(e.ny, e.ld, sizeof(T));
@@ -113,7 +119,7 @@ __device__ __forceinline__ void solve_instance(const BatchArgs& a, const BatchEn
     s.p1 = Grid<T>{reinterpret_cast<T*>(base + 2 * vb), e.ld};
     s.z = Grid<T>{reinterpret_cast<T*>(base + 3 * vb), e.ld};
     s.store_z = a.store_z >= 0 ? a.store_z : (sizeof(T) == 8 ? 1 : 0);
-    classic_solve<T, V>(s, tm, red);
+    classic_solve<T, V, R>(s, tm, red, dsm);
   } else if constexpr (KIND == KIND_F64_NEWCG || KIND == KIND_F32_NEWCG) {
     const size_t vb = vec_bytes(e.ny, e.ld, sizeof(T));
     NewcgArgs<T> s;
@@ -127,7 +133,7 @@ __device__ __forceinline__ void solve_instance(const BatchArgs& a, const BatchEn
     s.q = Grid<T>{reinterpret_cast<T*>(base + 4 * vb), e.ld};
     s.p = Grid<T>{reinterpret_cast<T*>(base + 5 * vb), e.ld};
     s.rr_period = a.rr_period;
-    newcg_solve<T, V>(s, tm, red);
+    newcg_solve<T, V, R>(s, tm, red, dsm);
   } else {
     const int ldi = ir_ld(e.nx);
     const size_t vr = vec_bytes(e.ny, ldi, sizeof(T));
@@ -145,14 +151,15 @@ __device__ __forceinline__ void solve_instance(const BatchArgs& a, const BatchEn
     s.max_outer = a.max_outer;
     s.maxit_inner = a.maxit_inner > 0 ? a.maxit_inner : 4 * (e.nx + e.ny) + 50;
     s.tol_inner = a.tol_inner;
-    ir_solve<T, V>(s, tm, red);
+    ir_solve<T, V, R>(s, tm, red, dsm);
   }
 }
 
-template <int KIND>
+template <int KIND, bool R>
 __global__ void __launch_bounds__(512) k_batched(const BatchArgs a) {
   __shared__ double red[kRedDoubles];
   __shared__ int s_item;
+  extern __shared__ __align__(128) unsigned char dsm[];
   ClusterTeam tm{0ull};
   auto cl = cooperative_groups::this_cluster();
   for (;;) {
@@ -162,7 +169,7 @@ __global__ void __launch_bounds__(512) k_batched(const BatchArgs a) {
     tm.barrier();  // every CTA has read the item before rank 0 fetches the next
     if (item >= a.count) break;
     const BatchEntry e = a.tab[item];
-    solve_instance<KIND>(a, e, tm, red);
+    solve_instance<KIND, R>(a, e, tm, red, dsm);
   }
 }
 
@@ -176,22 +183,38 @@ static int kind_of(int variant, int precision) {
   }
 }
 
-static const void* kernel_of(int kind) {
+static const void* kernel_of(int kind, bool ring) {
+#define LAP5_K(K) (ring ? reinterpret_cast<const void*>(&k_batched<K, true>) \
+                        : reinterpret_cast<const void*>(&k_batched<K, false>))
   switch (kind) {
-    case KIND_F64_CLASSIC: return reinterpret_cast<const void*>(&k_batched<KIND_F64_CLASSIC>);
-    case KIND_F64_NEWCG: return reinterpret_cast<const void*>(&k_batched<KIND_F64_NEWCG>);
-    case KIND_F32_CLASSIC: return reinterpret_cast<const void*>(&k_batched<KIND_F32_CLASSIC>);
-    case KIND_F32_NEWCG: return reinterpret_cast<const void*>(&k_batched<KIND_F32_NEWCG>);
-    case KIND_IR_F32: return reinterpret_cast<const void*>(&k_batched<KIND_IR_F32>);
-    default: return reinterpret_cast<const void*>(&k_batched<KIND_IR_BF16>);
+    case KIND_F64_CLASSIC: return LAP5_K(KIND_F64_CLASSIC);
+    case KIND_F64_NEWCG: return LAP5_K(KIND_F64_NEWCG);
+    case KIND_F32_CLASSIC: return LAP5_K(KIND_F32_CLASSIC);
+    case KIND_F32_NEWCG: return LAP5_K(KIND_F32_NEWCG);
+    case KIND_IR_F32: return LAP5_K(KIND_IR_F32);
+    default: return LAP5_K(KIND_IR_BF16);
   }
+#undef LAP5_K
 }
 
 // Lane vector width of a kind (alignment requirement of the caller's rows).
 static int kind_vec(int kind) { return (kind == KIND_F64_CLASSIC || kind == KIND_F64_NEWCG) ? 2 : 4; }
 static size_t kind_elem(int kind) { return (kind == KIND_F32_CLASSIC || kind == KIND_F32_NEWCG) ? 4 : 8; }
 
-static size_t table_bytes(int count) { return align_up((size_t)count * sizeof(BatchEntry), kAlign); }
+static size_t table_bytes(int count) {
+  return align_up((size_t)count * sizeof(BatchEntry), kAlign) + align_up((size_t)count * sizeof(int), kAlign);
+}
+
+static int ring_slot_kind(int kind) {
+  switch (kind) {
+    case KIND_F64_CLASSIC: return ring_slot_classic(2, 8);
+    case KIND_F64_NEWCG: return ring_slot_newcg(2, 8);
+    case KIND_F32_CLASSIC: return ring_slot_classic(4, 4);
+    case KIND_F32_NEWCG: return ring_slot_newcg(4, 4);
+    case KIND_IR_F32: return ring_slot_ir(4, 4);
+    default: return ring_slot_ir(4, 2);
+  }
+}
 
 size_t batched_ws(int count, const int* nx, const int* ny, const int* ld, int variant, int precision) {
   const int kind = kind_of(variant, precision);
@@ -233,6 +256,7 @@ int solve_batched(int count, const int* nx, const int* ny, const int* ld, const 
   unsigned char* ws = static_cast<unsigned char*>(workspace);
   BatchCtl* bctl = reinterpret_cast<BatchCtl*>(ws);
   BatchEntry* dtab = reinterpret_cast<BatchEntry*>(ws + kAlign);
+  int* errs = reinterpret_cast<int*>(ws + kAlign + align_up((size_t)count * sizeof(BatchEntry), kAlign));
   const size_t inst0 = kAlign + table_bytes(count);
   size_t off = inst0;
   for (int k = 0; k < count; ++k) {
@@ -256,8 +280,10 @@ int solve_batched(int count, const int* nx, const int* ny, const int* ld, const 
     if (cudaGetLastError() != cudaSuccess) return LAP5CG_ERR_CUDA;
   }
   if (cudaMemsetAsync(bctl, 0, sizeof(BatchCtl), st) != cudaSuccess) return LAP5CG_ERR_CUDA;
+  if (cudaMemsetAsync(errs, 0, (size_t)count * sizeof(int), st) != cudaSuccess) return LAP5CG_ERR_CUDA;
 
   BatchArgs a;
+  a.errs = errs;
   a.count = count;
   a.tab = dtab;
   a.bctl = bctl;
@@ -277,7 +303,10 @@ int solve_batched(int count, const int* nx, const int* ny, const int* ld, const 
   if (wpc > 16) wpc = 16;
   int team = o.team_ctas > 0 ? o.team_ctas : 8;
   if (team != 1 && team != 2 && team != 4 && team != 8 && team != 16) return LAP5CG_ERR_INVALID_ARG;
-  const void* fn = kernel_of(kind);
+  size_t dyn = 0;
+  int rc = choose_ring(kernel_of(kind, true), ring_slot_kind(kind), o, &a.rg, &dyn);
+  if (rc != LAP5CG_OK) return rc;
+  const void* fn = kernel_of(kind, a.rg.S > 0);
   if (team > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
     return LAP5CG_ERR_CUDA;
   cudaLaunchConfig_t lc = {};
@@ -287,7 +316,7 @@ int solve_batched(int count, const int* nx, const int* ny, const int* ld, const 
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   lc.blockDim = dim3(32 * wpc);
-  lc.dynamicSmemBytes = 0;
+  lc.dynamicSmemBytes = dyn;
   lc.stream = st;
   lc.attrs = attr;
   lc.numAttrs = 1;

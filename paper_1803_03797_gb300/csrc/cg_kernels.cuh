@@ -18,6 +18,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "ring.cuh"
 
 namespace lap5 {
 
@@ -32,7 +33,19 @@ struct SolveCommon {
   int maxit;
   int true_res;
   long long timeout_ns;
+  RingGeom rg;     // shared-memory row ring (rg.S == 0: register march)
+  int* err;        // error word: ring wait timeouts are recorded here
+  int* abort_flag; // grid teams: set with err so every CTA leaves at its next barrier
 };
+
+// The warp's ring in the kernel's dynamic shared memory (S == 0: disabled).
+__device__ __forceinline__ void ring_setup(WarpRing& ring, const SolveCommon& c, unsigned char* dsm) {
+  if (c.rg.S > 0) {
+    ring.init(dsm + (size_t)(threadIdx.x >> 5) * (size_t)c.rg.warp_bytes, c.rg, c.timeout_ns, c.err, c.abort_flag);
+  } else {
+    ring.S = 0;
+  }
+}
 
 // Per-thread bookkeeping of a persistent solve: this warp's index among the
 // team's warps and the pass counter.
@@ -69,6 +82,9 @@ __device__ __forceinline__ void write_info(const SolveCommon& c, int team_rank, 
   if (aborted) {
     st = atomicAdd(&c.ctl->status, 0);
     if (st == 0) st = LAP5CG_ERR_SYNC_TIMEOUT;
+  } else if (c.err) {
+    const int e = atomicAdd(c.err, 0);
+    if (e != 0) st = e;
   }
   inf.status = st;
   inf.iters = iters;
@@ -148,13 +164,15 @@ struct ClassicArgs {
   int store_z;
 };
 
-template <class T, int V, class Team>
-__device__ void classic_solve(const ClassicArgs<T>& a, Team& tm, double* red) {
+template <class T, int V, bool R, class Team>
+__device__ void classic_solve(const ClassicArgs<T>& a, Team& tm, double* red, unsigned char* dsm) {
   using M = typename Math<T>::type;
   using Acc = typename AccOf<M>::type;
   const SolveCommon& c = a.c;
   Walker wk;
   wk.init(tm.rank(), tm.size());
+  WarpRing ring;
+  ring_setup(ring, c, dsm);
 
   int status = LAP5CG_NOT_CONVERGED, iters = 0;
   double bb = 0.0, gamma = 0.0, relres_true = nan("");
@@ -193,6 +211,50 @@ __device__ void classic_solve(const ClassicArgs<T>& a, Team& tm, double* red) {
         Acc acc;
         const M bm = (M)beta;
         struct D { int dummy; };
+        if constexpr (R) {
+          const RingVec vv[2] = {
+              {reinterpret_cast<const unsigned char*>(a.r.ptr), a.r.ld, (int)sizeof(T), RV_HALO | RV_ALWAYS},
+              {first ? nullptr : reinterpret_cast<const unsigned char*>(pold.ptr), pold.ld, (int)sizeof(T),
+               RV_HALO | RV_ALWAYS}};
+          int off[2];
+          ring_layout<V>(vv, off);
+          ring.fence_global_to_async();
+          for (int u = wk.gw; u < c.un.nunits; u += wk.nw) {
+            int s, y0, y1;
+            unit_bounds(c.un, u, c.ny, s, y0, y1);
+            const int xs = s * 32 * V, xl = xs + wk.lane * V;
+            const int nval = min(max(c.nx - xl, 0), V);
+            auto field = [&](const unsigned char* sl, FRow<V, M>& f) {
+              M rv[V];
+              ring_lane<V, T>(sl, off[0], true, wk.lane, xl, c.nx, rv);
+              const M hr = ring_halo<V, T, M>(sl, off[0], wk.lane, xs, c.nx);
+              if (first) {
+#pragma unroll
+                for (int k = 0; k < V; ++k) f.f[k] = rv[k];
+                f.hl = hr;
+              } else {
+                M pv[V];
+                ring_lane<V, T>(sl, off[1], true, wk.lane, xl, c.nx, pv);
+                const M hp = ring_halo<V, T, M>(sl, off[1], wk.lane, xs, c.nx);
+#pragma unroll
+                for (int k = 0; k < V; ++k) f.f[k] = fmx(bm, pv[k], rv[k]);
+                f.hl = fmx(bm, hp, hr);  // one operation serves both halo lanes
+              }
+              f.hr = f.hl;
+            };
+            auto finish = [&](int j, const unsigned char*, const FRow<V, M>& S, const FRow<V, M>& C,
+                              const FRow<V, M>& N) {
+              M ap[V];
+              stencil_row<V>(S, C, N, wk.lane, ap);
+              store_row<V>(pnew, j, xl, c.nx, C.f);
+              if (a.store_z) store_row<V>(a.z, j, xl, c.nx, ap);
+#pragma unroll
+              for (int k = 0; k < V; ++k)
+                if (k < nval) acc.add(C.f[k], ap[k]);
+            };
+            march_ring<V, M>(ring, c.ny, xs, y0, y1, wk.rev(), vv, off, field, finish);
+          }
+        } else
         for (int u = wk.gw; u < c.un.nunits; u += wk.nw) {
           int s, y0, y1;
           unit_bounds(c.un, u, c.ny, s, y0, y1);
@@ -242,6 +304,73 @@ __device__ void classic_solve(const ClassicArgs<T>& a, Team& tm, double* red) {
         const double alpha = gamma / pap;
         const M am = (M)alpha;
         Acc acc;
+        if constexpr (R) {
+          ring.fence_global_to_async();
+          if (a.store_z) {
+            const RingVec vv[4] = {{reinterpret_cast<const unsigned char*>(pnew.ptr), pnew.ld, (int)sizeof(T), 0},
+                                   {reinterpret_cast<const unsigned char*>(a.x.ptr), a.x.ld, (int)sizeof(T), 0},
+                                   {reinterpret_cast<const unsigned char*>(a.r.ptr), a.r.ld, (int)sizeof(T), 0},
+                                   {reinterpret_cast<const unsigned char*>(a.z.ptr), a.z.ld, (int)sizeof(T), 0}};
+            int off[4];
+            ring_layout<V>(vv, off);
+            for (int u = wk.gw; u < c.un.nunits; u += wk.nw) {
+              int s, y0, y1;
+              unit_bounds(c.un, u, c.ny, s, y0, y1);
+              const int xs = s * 32 * V, xl = xs + wk.lane * V;
+              const int nval = min(max(c.nx - xl, 0), V);
+              auto finish = [&](int j, const unsigned char* sl) {
+                M pv[V], xv[V], rv[V], zv[V];
+                ring_lane<V, T>(sl, off[0], false, wk.lane, xl, c.nx, pv);
+                ring_lane<V, T>(sl, off[1], false, wk.lane, xl, c.nx, xv);
+                ring_lane<V, T>(sl, off[2], false, wk.lane, xl, c.nx, rv);
+                ring_lane<V, T>(sl, off[3], false, wk.lane, xl, c.nx, zv);
+#pragma unroll
+                for (int k = 0; k < V; ++k) {
+                  xv[k] = fmx(am, pv[k], xv[k]);
+                  rv[k] = fmx(-am, zv[k], rv[k]);
+                  if (k < nval) acc.add(rv[k], rv[k]);
+                }
+                store_row<V>(a.x, j, xl, c.nx, xv);
+                store_row<V>(a.r, j, xl, c.nx, rv);
+              };
+              stream_ring<V>(ring, c.ny, xs, y0, y1, wk.rev(), vv, off, finish);
+            }
+          } else {
+            const RingVec vv[3] = {
+                {reinterpret_cast<const unsigned char*>(pnew.ptr), pnew.ld, (int)sizeof(T), RV_HALO | RV_ALWAYS},
+                {reinterpret_cast<const unsigned char*>(a.x.ptr), a.x.ld, (int)sizeof(T), 0},
+                {reinterpret_cast<const unsigned char*>(a.r.ptr), a.r.ld, (int)sizeof(T), 0}};
+            int off[3];
+            ring_layout<V>(vv, off);
+            for (int u = wk.gw; u < c.un.nunits; u += wk.nw) {
+              int s, y0, y1;
+              unit_bounds(c.un, u, c.ny, s, y0, y1);
+              const int xs = s * 32 * V, xl = xs + wk.lane * V;
+              const int nval = min(max(c.nx - xl, 0), V);
+              auto field = [&](const unsigned char* sl, FRow<V, M>& f) {
+                ring_lane<V, T>(sl, off[0], true, wk.lane, xl, c.nx, f.f);
+                f.hl = ring_halo<V, T, M>(sl, off[0], wk.lane, xs, c.nx);
+                f.hr = f.hl;
+              };
+              auto finish = [&](int j, const unsigned char* sl, const FRow<V, M>& S, const FRow<V, M>& C,
+                                const FRow<V, M>& N) {
+                M ap[V], xv[V], rv[V];
+                stencil_row<V>(S, C, N, wk.lane, ap);
+                ring_lane<V, T>(sl, off[1], false, wk.lane, xl, c.nx, xv);
+                ring_lane<V, T>(sl, off[2], false, wk.lane, xl, c.nx, rv);
+#pragma unroll
+                for (int k = 0; k < V; ++k) {
+                  xv[k] = fmx(am, C.f[k], xv[k]);
+                  rv[k] = fmx(-am, ap[k], rv[k]);
+                  if (k < nval) acc.add(rv[k], rv[k]);
+                }
+                store_row<V>(a.x, j, xl, c.nx, xv);
+                store_row<V>(a.r, j, xl, c.nx, rv);
+              };
+              march_ring<V, M>(ring, c.ny, xs, y0, y1, wk.rev(), vv, off, field, finish);
+            }
+          }
+        } else
         for (int u = wk.gw; u < c.un.nunits; u += wk.nw) {
           int s, y0, y1;
           unit_bounds(c.un, u, c.ny, s, y0, y1);
@@ -313,6 +442,7 @@ truecheck:
     relres_true = sqrt(o[0] / bb);
   }
 done:
+  if (ring.S > 0) ring.teardown();
   write_info(c, tm.rank(), status, aborted, iters, 0, gamma, bb, relres_true);
 }
 
@@ -386,13 +516,15 @@ __device__ __forceinline__ void pass_w_from_r(const SolveCommon& c, Walker& wk, 
   ++wk.pc;
 }
 
-template <class T, int V, class Team>
-__device__ void newcg_solve(const NewcgArgs<T>& a, Team& tm, double* red) {
+template <class T, int V, bool R, class Team>
+__device__ void newcg_solve(const NewcgArgs<T>& a, Team& tm, double* red, unsigned char* dsm) {
   using M = typename Math<T>::type;
   using Acc = typename AccOf<M>::type;
   const SolveCommon& c = a.c;
   Walker wk;
   wk.init(tm.rank(), tm.size());
+  WarpRing ring;
+  ring_setup(ring, c, dsm);
 
   int status = LAP5CG_NOT_CONVERGED, iters = 0;
   double bb = 0.0, gamma = 0.0, delta = 0.0, alpha = 0.0, beta = 0.0, relres_true = nan("");
@@ -437,6 +569,67 @@ __device__ void newcg_solve(const NewcgArgs<T>& a, Team& tm, double* red) {
       const M am = (M)alpha, bm = (M)beta;
       Acc ag, ad;
       struct D { M z[V], q[V], p[V], x[V], r[V]; };
+      if constexpr (R) {
+        ring.fence_global_to_async();
+        const unsigned char* nz = first ? nullptr : reinterpret_cast<const unsigned char*>(a.z.ptr);
+        const unsigned char* nq = first ? nullptr : reinterpret_cast<const unsigned char*>(a.q.ptr);
+        const unsigned char* np = first ? nullptr : reinterpret_cast<const unsigned char*>(a.p.ptr);
+        const RingVec vv[6] = {
+            {reinterpret_cast<const unsigned char*>(w.ptr), w.ld, (int)sizeof(T), RV_HALO | RV_ALWAYS},
+            {nz, a.z.ld, (int)sizeof(T), 0},
+            {nq, a.q.ld, (int)sizeof(T), 0},
+            {np, a.p.ld, (int)sizeof(T), 0},
+            {reinterpret_cast<const unsigned char*>(a.x.ptr), a.x.ld, (int)sizeof(T), 0},
+            {reinterpret_cast<const unsigned char*>(a.r.ptr), a.r.ld, (int)sizeof(T), 0}};
+        int off[6];
+        ring_layout<V>(vv, off);
+        for (int u = wk.gw; u < c.un.nunits; u += wk.nw) {
+          int s, y0, y1;
+          unit_bounds(c.un, u, c.ny, s, y0, y1);
+          const int xs = s * 32 * V, xl = xs + wk.lane * V;
+          const int nval = min(max(c.nx - xl, 0), V);
+          auto field = [&](const unsigned char* sl, FRow<V, M>& f) {
+            ring_lane<V, T>(sl, off[0], true, wk.lane, xl, c.nx, f.f);
+            f.hl = ring_halo<V, T, M>(sl, off[0], wk.lane, xs, c.nx);
+            f.hr = f.hl;
+          };
+          auto finish = [&](int j, const unsigned char* sl, const FRow<V, M>& S, const FRow<V, M>& C,
+                            const FRow<V, M>& N) {
+            M nv[V], zv[V], qv[V], pv[V], xv[V], rv[V], wv[V];
+            stencil_row<V>(S, C, N, wk.lane, nv);  // n = A w
+            ring_lane<V, T>(sl, off[4], false, wk.lane, xl, c.nx, xv);
+            ring_lane<V, T>(sl, off[5], false, wk.lane, xl, c.nx, rv);
+            if (!first) {
+              ring_lane<V, T>(sl, off[1], false, wk.lane, xl, c.nx, zv);
+              ring_lane<V, T>(sl, off[2], false, wk.lane, xl, c.nx, qv);
+              ring_lane<V, T>(sl, off[3], false, wk.lane, xl, c.nx, pv);
+            }
+#pragma unroll
+            for (int k = 0; k < V; ++k) {
+              if (first) {
+                zv[k] = nv[k];
+                qv[k] = C.f[k];
+                pv[k] = rv[k];
+              } else {
+                zv[k] = fmx(bm, zv[k], nv[k]);
+                qv[k] = fmx(bm, qv[k], C.f[k]);
+                pv[k] = fmx(bm, pv[k], rv[k]);
+              }
+              xv[k] = fmx(am, pv[k], xv[k]);
+              rv[k] = fmx(-am, qv[k], rv[k]);
+              wv[k] = fmx(-am, zv[k], C.f[k]);
+              if (k < nval) { ag.add(rv[k], rv[k]); ad.add(wv[k], rv[k]); }
+            }
+            store_row<V>(a.z, j, xl, c.nx, zv);
+            store_row<V>(a.q, j, xl, c.nx, qv);
+            store_row<V>(a.p, j, xl, c.nx, pv);
+            store_row<V>(a.x, j, xl, c.nx, xv);
+            store_row<V>(a.r, j, xl, c.nx, rv);
+            store_row<V>(wn, j, xl, c.nx, wv);
+          };
+          march_ring<V, M>(ring, c.ny, xs, y0, y1, wk.rev(), vv, off, field, finish);
+        }
+      } else
       for (int u = wk.gw; u < c.un.nunits; u += wk.nw) {
         int s, y0, y1;
         unit_bounds(c.un, u, c.ny, s, y0, y1);
@@ -529,6 +722,7 @@ truecheck:
     relres_true = sqrt(o[0] / bb);
   }
 done:
+  if (ring.S > 0) ring.teardown();
   write_info(c, tm.rank(), status, aborted, iters, 0, gamma, bb, relres_true);
 }
 

@@ -7,18 +7,32 @@
 
 namespace lap5 {
 
-template <class T, int V>
+// R: rows staged through the shared-memory ring (bulk asynchronous copies)
+// or loaded straight into registers.
+template <class T, int V, bool R>
 __global__ void __launch_bounds__(512) k_classic(const ClassicArgs<T> a) {
   __shared__ double red[kRedDoubles];
+  extern __shared__ __align__(128) unsigned char dsm[];
   GridTeam tm{a.c.ctl, a.c.timeout_ns, 0ull};
-  classic_solve<T, V>(a, tm, red);
+  classic_solve<T, V, R>(a, tm, red, dsm);
 }
 
-template <class T, int V>
+template <class T, int V, bool R>
 __global__ void __launch_bounds__(512) k_newcg(const NewcgArgs<T> a) {
   __shared__ double red[kRedDoubles];
+  extern __shared__ __align__(128) unsigned char dsm[];
   GridTeam tm{a.c.ctl, a.c.timeout_ns, 0ull};
-  newcg_solve<T, V>(a, tm, red);
+  newcg_solve<T, V, R>(a, tm, red, dsm);
+}
+
+// Ring geometry for a kernel pair: tries the ring kernel first; falls back to
+// the register kernel when the ring is off or does not fit.
+inline int pick_ring(const void* fn_ring, int slot_bytes, const lap5cg_opts& o, RingGeom* rg, size_t* dyn,
+                     bool* use_ring) {
+  int rc = choose_ring(fn_ring, slot_bytes, o, rg, dyn);
+  if (rc != LAP5CG_OK) return rc;
+  *use_ring = rg->S > 0;
+  return LAP5CG_OK;
 }
 
 template <class T>
@@ -32,7 +46,7 @@ inline int cooperative_launch(const void* func, const LaunchCfg& cfg, void** arg
   cudaLaunchConfig_t lc = {};
   lc.gridDim = dim3(cfg.ctas);
   lc.blockDim = dim3(cfg.threads);
-  lc.dynamicSmemBytes = 0;
+  lc.dynamicSmemBytes = cfg.dyn_smem;
   lc.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
@@ -43,7 +57,7 @@ inline int cooperative_launch(const void* func, const LaunchCfg& cfg, void** arg
   return e == cudaSuccess ? LAP5CG_OK : LAP5CG_ERR_CUDA;
 }
 
-inline SolveCommon make_common(const SolvePlan& p, const LaunchCfg& cfg) {
+inline SolveCommon make_common(const SolvePlan& p, const LaunchCfg& cfg, const RingGeom& rg) {
   SolveCommon c;
   c.nx = p.nx;
   c.ny = p.ny;
@@ -59,6 +73,9 @@ inline SolveCommon make_common(const SolvePlan& p, const LaunchCfg& cfg) {
   c.true_res = p.opts.true_residual;
   const double to = p.opts.timeout_s > 0.0 ? p.opts.timeout_s : 2.0;
   c.timeout_ns = (long long)(to * 1e9);
+  c.rg = rg;
+  c.err = &c.ctl->status;
+  c.abort_flag = &c.ctl->abort;
   return c;
 }
 
@@ -70,11 +87,18 @@ int solve_typed(const SolvePlan& p, cudaStream_t st) {
   if (cudaMemsetAsync(p.ws, 0, 256, st) != cudaSuccess) return LAP5CG_ERR_CUDA;
   LaunchCfg cfg;
   if (p.variant == LAP5CG_CLASSIC) {
-    const void* fn = reinterpret_cast<const void*>(&k_classic<T, V>);
-    int rc = plan_units(fn, p.nx, p.ny, V, p.opts, &cfg);
+    RingGeom rg;
+    size_t dyn = 0;
+    bool ring = false;
+    int rc = pick_ring(reinterpret_cast<const void*>(&k_classic<T, V, true>), ring_slot_classic(V, (int)sizeof(T)),
+                       p.opts, &rg, &dyn, &ring);
+    if (rc != LAP5CG_OK) return rc;
+    const void* fn = ring ? reinterpret_cast<const void*>(&k_classic<T, V, true>)
+                          : reinterpret_cast<const void*>(&k_classic<T, V, false>);
+    rc = plan_units(fn, p.nx, p.ny, V, p.opts, dyn, &cfg);
     if (rc != LAP5CG_OK) return rc;
     ClassicArgs<T> a;
-    a.c = make_common(p, cfg);
+    a.c = make_common(p, cfg, rg);
     a.b = Grid<const T>{static_cast<const T*>(p.b), p.ld};
     a.x = Grid<T>{static_cast<T*>(p.x), p.ld};
     a.r = Grid<T>{vecp(0), p.ldw};
@@ -87,11 +111,18 @@ int solve_typed(const SolvePlan& p, cudaStream_t st) {
     void* args[] = {&a};
     return cooperative_launch(fn, cfg, args, st);
   } else {
-    const void* fn = reinterpret_cast<const void*>(&k_newcg<T, V>);
-    int rc = plan_units(fn, p.nx, p.ny, V, p.opts, &cfg);
+    RingGeom rg;
+    size_t dyn = 0;
+    bool ring = false;
+    int rc = pick_ring(reinterpret_cast<const void*>(&k_newcg<T, V, true>), ring_slot_newcg(V, (int)sizeof(T)),
+                       p.opts, &rg, &dyn, &ring);
+    if (rc != LAP5CG_OK) return rc;
+    const void* fn = ring ? reinterpret_cast<const void*>(&k_newcg<T, V, true>)
+                          : reinterpret_cast<const void*>(&k_newcg<T, V, false>);
+    rc = plan_units(fn, p.nx, p.ny, V, p.opts, dyn, &cfg);
     if (rc != LAP5CG_OK) return rc;
     NewcgArgs<T> a;
-    a.c = make_common(p, cfg);
+    a.c = make_common(p, cfg, rg);
     a.b = Grid<const T>{static_cast<const T*>(p.b), p.ld};
     a.x = Grid<T>{static_cast<T*>(p.x), p.ld};
     a.r = Grid<T>{vecp(0), p.ldw};

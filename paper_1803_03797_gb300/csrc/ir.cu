@@ -6,11 +6,12 @@
 
 namespace lap5 {
 
-template <class TR, int V>
+template <class TR, int V, bool R>
 __global__ void __launch_bounds__(512) k_ir(const IrArgs<TR> a) {
   __shared__ double red[kRedDoubles];
+  extern __shared__ __align__(128) unsigned char dsm[];
   GridTeam tm{a.c.ctl, a.c.timeout_ns, 0ull};
-  ir_solve<TR, V>(a, tm, red);
+  ir_solve<TR, V, R>(a, tm, red, dsm);
 }
 
 static int inner_ld(int nx) { return (nx + 7) / 8 * 8; }
@@ -36,12 +37,19 @@ static int solve_ir_t(const SolvePlan& p, cudaStream_t st) {
   const size_t vf = align_up((size_t)p.ny * ldi * 4, kAlign);
   unsigned char* base = p.ws + kCtlBytes;
   if (cudaMemsetAsync(p.ws, 0, 256, st) != cudaSuccess) return LAP5CG_ERR_CUDA;
-  const void* fn = reinterpret_cast<const void*>(&k_ir<TR, V>);
   LaunchCfg cfg;
-  int rc = plan_units(fn, p.nx, p.ny, V, p.opts, &cfg);
+  RingGeom rg;
+  size_t dyn = 0;
+  bool ring = false;
+  int rc = pick_ring(reinterpret_cast<const void*>(&k_ir<TR, V, true>), ring_slot_ir(V, (int)sizeof(TR)), p.opts,
+                     &rg, &dyn, &ring);
+  if (rc != LAP5CG_OK) return rc;
+  const void* fn = ring ? reinterpret_cast<const void*>(&k_ir<TR, V, true>)
+                        : reinterpret_cast<const void*>(&k_ir<TR, V, false>);
+  rc = plan_units(fn, p.nx, p.ny, V, p.opts, dyn, &cfg);
   if (rc != LAP5CG_OK) return rc;
   IrArgs<TR> a;
-  a.c = make_common(p, cfg);
+  a.c = make_common(p, cfg, rg);
   a.b = Grid<const double>{static_cast<const double*>(p.b), p.ld};
   a.x = Grid<double>{static_cast<double*>(p.x), p.ld};
   a.r = Grid<TR>{reinterpret_cast<TR*>(base), ldi};

@@ -30,12 +30,15 @@ struct IrArgs {
   double tol_inner;
 };
 
-template <class TR, int V, class Team>
-__device__ void ir_solve(const IrArgs<TR>& a, Team& tm, double* red) {
+template <class TR, int V, bool R, class Team>
+__device__ void ir_solve(const IrArgs<TR>& a, Team& tm, double* red, unsigned char* dsm) {
   using Acc = Acc32;
   const SolveCommon& c = a.c;
   Walker wk;
   wk.init(tm.rank(), tm.size());
+  WarpRing ring;
+  ring_setup(ring, c, dsm);
+  constexpr int ES = (int)sizeof(TR);
 
   int status = LAP5CG_NOT_CONVERGED, total = 0, outer = 0;
   double bb = 0.0, rr = 0.0, rr_prev = 0.0, relres_true = nan("");
@@ -150,6 +153,49 @@ __device__ void ir_solve(const IrArgs<TR>& a, Team& tm, double* red) {
           Acc acc;
           const float bm = (float)beta;
           struct D { int dummy; };
+          if constexpr (R) {
+            const RingVec vv[2] = {
+                {reinterpret_cast<const unsigned char*>(a.r.ptr), a.r.ld, ES, RV_HALO | RV_ALWAYS},
+                {first ? nullptr : reinterpret_cast<const unsigned char*>(pold.ptr), pold.ld, ES, RV_HALO | RV_ALWAYS}};
+            int off[2];
+            ring_layout<V>(vv, off);
+            ring.fence_global_to_async();
+            for (int u = wk.gw; u < c.un.nunits; u += wk.nw) {
+              int s, y0, y1;
+              unit_bounds(c.un, u, c.ny, s, y0, y1);
+              const int xs = s * 32 * V, xl = xs + wk.lane * V;
+              const int nval = min(max(c.nx - xl, 0), V);
+              auto field = [&](const unsigned char* sl, FRow<V, float>& f) {
+                float rv[V];
+                ring_lane<V, TR>(sl, off[0], true, wk.lane, xl, c.nx, rv);
+                const float hr = ring_halo<V, TR, float>(sl, off[0], wk.lane, xs, c.nx);
+                if (first) {
+#pragma unroll
+                  for (int q = 0; q < V; ++q) f.f[q] = rv[q];
+                  f.hl = hr;
+                } else {
+                  float pv[V];
+                  ring_lane<V, TR>(sl, off[1], true, wk.lane, xl, c.nx, pv);
+                  const float hp = ring_halo<V, TR, float>(sl, off[1], wk.lane, xs, c.nx);
+#pragma unroll
+                  for (int q = 0; q < V; ++q) f.f[q] = quantize<TR>(fmx(bm, pv[q], rv[q]));
+                  f.hl = quantize<TR>(fmx(bm, hp, hr));
+                }
+                f.hr = f.hl;
+              };
+              auto finish = [&](int j, const unsigned char*, const FRow<V, float>& S, const FRow<V, float>& C,
+                                const FRow<V, float>& N) {
+                float ap[V];
+                stencil_row<V>(S, C, N, wk.lane, ap);
+                store_row<V>(pnew, j, xl, c.nx, C.f);
+                if (a.store_z) store_row<V>(a.z, j, xl, c.nx, ap);
+#pragma unroll
+                for (int q = 0; q < V; ++q)
+                  if (q < nval) acc.add(C.f[q], ap[q]);
+              };
+              march_ring<V, float>(ring, c.ny, xs, y0, y1, wk.rev(), vv, off, field, finish);
+            }
+          } else
           for (int u = wk.gw; u < c.un.nunits; u += wk.nw) {
             int s, y0, y1;
             unit_bounds(c.un, u, c.ny, s, y0, y1);
@@ -199,6 +245,42 @@ __device__ void ir_solve(const IrArgs<TR>& a, Team& tm, double* red) {
         {  // phase R
           const float am = (float)(gamma / pz);
           Acc acc;
+          if (R && !a.store_z) {
+            const RingVec vv[3] = {
+                {reinterpret_cast<const unsigned char*>(pnew.ptr), pnew.ld, ES, RV_HALO | RV_ALWAYS},
+                {first ? nullptr : reinterpret_cast<const unsigned char*>(a.d.ptr), a.d.ld, 4, 0},
+                {reinterpret_cast<const unsigned char*>(a.r.ptr), a.r.ld, ES, 0}};
+            int off[3];
+            ring_layout<V>(vv, off);
+            ring.fence_global_to_async();
+            for (int u = wk.gw; u < c.un.nunits; u += wk.nw) {
+              int s, y0, y1;
+              unit_bounds(c.un, u, c.ny, s, y0, y1);
+              const int xs = s * 32 * V, xl = xs + wk.lane * V;
+              const int nval = min(max(c.nx - xl, 0), V);
+              auto field = [&](const unsigned char* sl, FRow<V, float>& f) {
+                ring_lane<V, TR>(sl, off[0], true, wk.lane, xl, c.nx, f.f);
+                f.hl = ring_halo<V, TR, float>(sl, off[0], wk.lane, xs, c.nx);
+                f.hr = f.hl;
+              };
+              auto finish = [&](int j, const unsigned char* sl, const FRow<V, float>& S, const FRow<V, float>& C,
+                                const FRow<V, float>& N) {
+                float ap[V], dv[V], rv[V];
+                stencil_row<V>(S, C, N, wk.lane, ap);
+                ring_lane<V, TR>(sl, off[2], false, wk.lane, xl, c.nx, rv);
+                if (!first) ring_lane<V, float>(sl, off[1], false, wk.lane, xl, c.nx, dv);
+#pragma unroll
+                for (int q = 0; q < V; ++q) {
+                  dv[q] = first ? __fmul_rn(am, C.f[q]) : fmx(am, C.f[q], dv[q]);
+                  rv[q] = quantize<TR>(fmx(-am, ap[q], rv[q]));
+                  if (q < nval) acc.add(rv[q], rv[q]);
+                }
+                store_row<V>(a.d, j, xl, c.nx, dv);
+                store_row<V>(a.r, j, xl, c.nx, rv);
+              };
+              march_ring<V, float>(ring, c.ny, xs, y0, y1, wk.rev(), vv, off, field, finish);
+            }
+          } else
           for (int u = wk.gw; u < c.un.nunits; u += wk.nw) {
             int s, y0, y1;
             unit_bounds(c.un, u, c.ny, s, y0, y1);
@@ -264,6 +346,7 @@ __device__ void ir_solve(const IrArgs<TR>& a, Team& tm, double* red) {
     ++outer;
   }
 done:
+  if (ring.S > 0) ring.teardown();
   write_info(c, tm.rank(), status, aborted, total, outer, rr, bb, relres_true);
 }
 

@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include "../../include/lap5cg.h"
+#include "ring.cuh"
 
 namespace lap5 {
 
@@ -14,6 +15,7 @@ namespace lap5 {
 struct LaunchCfg {
   int ctas;           // persistent CTAs (all co-resident)
   int threads;        // threads per CTA
+  size_t dyn_smem;    // dynamic shared memory per CTA (row ring)
   int ns, nseg, seg_rows, nunits;  // warp-unit decomposition
 };
 
@@ -58,7 +60,25 @@ int dev_props(DevProps* out);
 
 // Grid sizing shared by the persistent kernels: fills cfg from the occupancy
 // of kernel func at the requested warps per CTA.
-int plan_units(const void* func, int nx, int ny, int V, const lap5cg_opts& o, LaunchCfg* cfg);
+int plan_units(const void* func, int nx, int ny, int V, const lap5cg_opts& o, size_t dyn_smem, LaunchCfg* cfg);
+
+// Row-ring geometry for a kernel whose largest ring slot is slot_bytes: sets
+// the kernel's dynamic shared memory limit and returns the bytes per CTA
+// (S = 0 and 0 bytes when the ring is off or does not fit).
+int choose_ring(const void* func, int slot_bytes, const lap5cg_opts& o, RingGeom* g, size_t* dyn_smem);
+
+// Largest ring slot (bytes) of each kernel family, V = lane vector width.
+inline int ring_slot_classic(int V, int es) {
+  const int M = 32 * V * es;
+  const int p = 2 * (M + 32), rz = 4 * M, rr = (M + 32) + 2 * M;
+  return p > rz ? (p > rr ? p : rr) : (rz > rr ? rz : rr);
+}
+inline int ring_slot_newcg(int V, int es) { return (32 * V * es + 32) + 5 * 32 * V * es; }
+inline int ring_slot_ir(int V, int es_r) {
+  const int Mr = 32 * V * es_r, Mf = 32 * V * 4;
+  const int p = 2 * (Mr + 32), r = (Mr + 32) + Mf + Mr;
+  return p > r ? p : r;
+}
 
 constexpr size_t kCtlBytes = 256 * 1024;  // control block region at the workspace start
 constexpr size_t kAlign = 256;

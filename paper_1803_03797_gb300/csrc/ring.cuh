@@ -1,0 +1,270 @@
+// ring.cuh -- per-warp shared-memory row ring filled by 1D bulk asynchronous
+// copies (cp.async.bulk, the TMA engine's non-tensor form) and completed on
+// mbarriers.
+//
+// A warp streams the rows of its unit in march order.  Lane 0 issues, S rows
+// ahead, one bulk copy per streamed vector and row into a ring slot; the whole
+// warp waits on the slot's mbarrier (bounded by %globaltimer), reads its 16-byte
+// lane vectors from shared memory, and releases the slot for the row S ahead.
+// Stencil operands are copied with the 16-byte chunks that hold the strip's
+// halo columns, so a unit needs no scalar halo loads and no registers for rows
+// in flight.  Bulk copies need 16-byte aligned rows and 16-byte multiples,
+// which the solver's row layout (ld a multiple of the lane vector, rows 16-byte
+// aligned) guarantees.
+#pragma once
+
+#include "common.cuh"
+
+namespace lap5 {
+
+constexpr int kRingMaxVecs = 6;
+constexpr int kRingMaxSlots = 8;
+
+enum { RV_HALO = 1, RV_ALWAYS = 2 };  // stencil operand; also needed on the unit's halo rows
+
+struct RingVec {
+  const unsigned char* base;  // element (0, 0)
+  int ld;                     // row pitch in elements
+  int es;                     // element bytes
+  int flags;
+};
+
+// Ring geometry chosen on the host: slots per warp and bytes per slot.
+struct RingGeom {
+  int S;           // slots per warp (0 = ring disabled)
+  int slot_bytes;  // >= the largest slot any pass of the kernel needs
+  int warp_bytes;  // shared bytes per warp: barriers + slots
+};
+
+__host__ __device__ inline int ring_seg_bytes(int V, int es, bool halo) { return 32 * V * es + (halo ? 32 : 0); }
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+struct WarpRing {
+  uint32_t bars;       // shared address of S mbarriers (8 bytes each)
+  uint32_t slots;      // shared address of slot 0
+  unsigned char* slots_ptr;
+  int S, slot_bytes;
+  unsigned q;          // sequence number of the next row to produce / consume
+  bool failed;
+  long long timeout_ns;
+  int* err;
+  int* abort_flag;
+
+  __device__ __forceinline__ void init(unsigned char* warp_smem, const RingGeom& g, long long to, int* err_word,
+                                       int* abort_word) {
+    S = g.S;
+    slot_bytes = g.slot_bytes;
+    bars = smem_u32(warp_smem);
+    slots_ptr = warp_smem + 128;  // 8 barriers padded to 128 bytes
+    slots = smem_u32(slots_ptr);
+    q = 0;
+    failed = false;
+    timeout_ns = to;
+    err = err_word;
+    abort_flag = abort_word;
+    if ((threadIdx.x & 31) == 0) {
+      for (int s = 0; s < S; ++s)
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bars + 8u * s) : "memory");
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+  }
+
+  // Lane 0: issue the copies of one row into slot (seq % S).  Out-of-grid rows
+  // only complete the slot's phase.
+  template <int V, int K>
+  __device__ __forceinline__ void produce(unsigned seq, int row, int ny, int xs, bool interior,
+                                          const RingVec (&v)[K], const int (&off)[K]) {
+    if ((threadIdx.x & 31) != 0) return;
+    const int s = (int)(seq % (unsigned)S);
+    const uint32_t bar = bars + 8u * s;
+    const uint32_t dst0 = slots + (uint32_t)(s * slot_bytes);
+    // the slot's previous contents were read through the generic proxy
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (row < 0 || row >= ny || failed) {
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+      return;
+    }
+    uint32_t tx = 0;
+    int cs[K], nb[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      nb[k] = 0;
+      if (!v[k].base) continue;  // vector not streamed in this pass
+      if (!interior && !(v[k].flags & RV_ALWAYS)) continue;
+      const int h = (v[k].flags & RV_HALO) ? 16 / v[k].es : 0;
+      const int c0 = max(xs - h, 0);
+      const int c1 = min(xs + 32 * V + h, v[k].ld);
+      cs[k] = c0;
+      nb[k] = (c1 - c0) * v[k].es;
+      tx += (uint32_t)nb[k];
+    }
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(tx) : "memory");
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      if (nb[k] == 0) continue;
+      const int h = (v[k].flags & RV_HALO) ? 16 / v[k].es : 0;
+      const unsigned char* src = v[k].base + ((size_t)row * (size_t)v[k].ld + (size_t)cs[k]) * (size_t)v[k].es;
+      const uint32_t dst = dst0 + (uint32_t)off[k] + (uint32_t)((cs[k] - (xs - h)) * v[k].es);
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+          "l"(src), "r"(nb[k]), "r"(bar)
+          : "memory");
+    }
+  }
+
+  // Whole warp: wait until the row with sequence number seq has landed.
+  __device__ __forceinline__ const unsigned char* wait(unsigned seq) {
+    const int s = (int)(seq % (unsigned)S);
+    const uint32_t bar = bars + 8u * s;
+    const uint32_t parity = (seq / (unsigned)S) & 1u;
+    if (!failed) {
+      const unsigned long long t0 = global_ns();
+      unsigned spins = 0;
+      for (;;) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) break;
+        if ((++spins & 15u) == 0u && (long long)(global_ns() - t0) > timeout_ns) {
+          failed = true;  // record once; later rows are not waited for
+          if ((threadIdx.x & 31) == 0) {
+            if (err) atomicCAS(err, 0, LAP5CG_ERR_SYNC_TIMEOUT);
+            __threadfence();
+            if (abort_flag) atomicExch(abort_flag, 1);
+          }
+          break;
+        }
+      }
+      failed = __any_sync(0xffffffffu, failed);
+    }
+    return slots_ptr + (size_t)s * slot_bytes;
+  }
+
+  // Invalidate the barriers (every produced row has been waited for) so the
+  // same shared memory can hold a fresh ring for the next solve.
+  __device__ __forceinline__ void teardown() {
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) {
+      for (int s = 0; s < S; ++s) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bars + 8u * s) : "memory");
+    }
+    __syncwarp();
+  }
+
+  __device__ __forceinline__ void fence_global_to_async() {
+    if ((threadIdx.x & 31) == 0) asm volatile("fence.proxy.async.global;" ::: "memory");
+  }
+};
+
+// Lane view of one ring slot.  Vector k's segment starts at off[k]; with a
+// halo the lane's first element sits 16 bytes further.
+template <int V, class T, class M>
+__device__ __forceinline__ void ring_lane(const unsigned char* slot, int off, bool halo, int lane, int x, int nx,
+                                          M (&v)[V]) {
+  using U = typename std::remove_const<T>::type;
+  const U* p = reinterpret_cast<const U*>(slot + off + (halo ? 16 : 0)) + lane * V;
+  if (x < nx) {
+    VecIO<V, U>::load(p, v);
+    if (x + V > nx) {
+#pragma unroll
+      for (int k = 0; k < V; ++k)
+        if (x + k >= nx) v[k] = M(0);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < V; ++k) v[k] = M(0);
+  }
+}
+
+// Halo columns of a stencil operand: left (column xs-1) for lane 0, right
+// (column xs+32V) for lane 31, 0 outside [0, nx).
+template <int V, class T, class M>
+__device__ __forceinline__ M ring_halo(const unsigned char* slot, int off, int lane, int xs, int nx) {
+  using U = typename std::remove_const<T>::type;
+  const U* p = reinterpret_cast<const U*>(slot + off);
+  constexpr int h = 16 / (int)sizeof(U);
+  if (lane == 0) return (xs - 1 >= 0 && xs - 1 < nx) ? to_math<M, U>(p[h - 1]) : M(0);
+  if (lane == 31) return (xs + 32 * V < nx) ? to_math<M, U>(p[h + 32 * V]) : M(0);
+  return M(0);
+}
+
+// Row march of one unit through the ring: rows y0-1 .. y1 (or reversed) are
+// streamed; field(slot, FRow&) builds the stencil operand of a row from its
+// slot, finish(j, slot, S, C, N) consumes row j.  Whole-warp call.
+template <int V, class M, int K, class FieldF, class FinishF>
+__device__ __forceinline__ void march_ring(WarpRing& ring, int ny, int xs, int y0, int y1, bool rev,
+                                           const RingVec (&vecs)[K], const int (&off)[K], FieldF& field,
+                                           FinishF& finish) {
+  if (y0 >= y1) return;
+  const int T = y1 - y0;
+  const int step = rev ? -1 : 1;
+  const int ystart = rev ? y1 - 1 : y0;
+  const unsigned q0 = ring.q;
+  auto row_of = [&](int t) { return ystart + (t - 1) * step; };
+  const int total = T + 2;
+  const int pre = min(ring.S, total);
+  for (int t = 0; t < pre; ++t) ring.produce<V, K>(q0 + t, row_of(t), ny, xs, t >= 1 && t <= T, vecs, off);
+  FRow<V, M> fB, fC;
+  {
+    const unsigned char* s0 = ring.wait(q0);
+    if (row_of(0) < 0 || row_of(0) >= ny) fB.zero(); else field(s0, fB);
+    __syncwarp();
+    if (ring.S < total) ring.produce<V, K>(q0 + ring.S, row_of(ring.S), ny, xs, ring.S <= T, vecs, off);
+  }
+  const unsigned char* sC = ring.wait(q0 + 1);
+  field(sC, fC);
+  for (int t = 1; t <= T; ++t) {
+    FRow<V, M> fA;
+    const unsigned char* sA = ring.wait(q0 + t + 1);
+    if (row_of(t + 1) < 0 || row_of(t + 1) >= ny) fA.zero(); else field(sA, fA);
+    if (!rev) finish(row_of(t), sC, fB, fC, fA);
+    else finish(row_of(t), sC, fA, fC, fB);
+    __syncwarp();
+    if (t + ring.S < total) ring.produce<V, K>(q0 + t + ring.S, row_of(t + ring.S), ny, xs, t + ring.S <= T, vecs, off);
+    fB = fC;
+    fC = fA;
+    sC = sA;
+  }
+  ring.q = q0 + (unsigned)total;
+}
+
+// Element-wise variant (no stencil operand): rows y0 .. y1-1 only.
+template <int V, int K, class FinishF>
+__device__ __forceinline__ void stream_ring(WarpRing& ring, int ny, int xs, int y0, int y1, bool rev,
+                                            const RingVec (&vecs)[K], const int (&off)[K], FinishF& finish) {
+  if (y0 >= y1) return;
+  const int T = y1 - y0;
+  const int step = rev ? -1 : 1;
+  const int ystart = rev ? y1 - 1 : y0;
+  const unsigned q0 = ring.q;
+  const int pre = min(ring.S, T);
+  for (int t = 0; t < pre; ++t) ring.produce<V, K>(q0 + t, ystart + t * step, ny, xs, true, vecs, off);
+  for (int t = 0; t < T; ++t) {
+    const unsigned char* sl = ring.wait(q0 + t);
+    finish(ystart + t * step, sl);
+    __syncwarp();
+    if (t + ring.S < T) ring.produce<V, K>(q0 + t + ring.S, ystart + (t + ring.S) * step, ny, xs, true, vecs, off);
+  }
+  ring.q = q0 + (unsigned)T;
+}
+
+// Byte offsets of K vectors inside a slot, each segment a multiple of 16 bytes.
+template <int V, int K>
+__host__ __device__ inline int ring_layout(const RingVec (&v)[K], int (&off)[K]) {
+  int o = 0;
+  for (int k = 0; k < K; ++k) {
+    off[k] = o;
+    o += ring_seg_bytes(V, v[k].es, (v[k].flags & RV_HALO) != 0);
+  }
+  return o;
+}
+
+}  // namespace lap5

@@ -240,3 +240,29 @@ def test_full_size_4096_500_iterations_properties():
         recs[variant] = rec
     # both variants follow the same Krylov sequence
     assert abs(recs["classic"]["relres_true"] - recs["newcg"]["relres_true"]) <= 1e-6 * recs["classic"]["relres_true"]
+
+
+@pytest.mark.parametrize("ring_slots", [-1, 3, 8])
+def test_ring_and_register_paths_agree(ring_slots):
+    # rows staged through the shared-memory ring (3 or 8 slots) or loaded into
+    # registers (-1): same arithmetic, same results against the oracle
+    nx, ny = 301, 170
+    b = gen.uniform_rhs(nx, ny, seed=77, ld=gen.pitch(nx, 32))
+    for variant in VARIANTS:
+        for store_z in (0, 1):
+            if variant == "newcg" and store_z:
+                continue
+            opts = lap5cg.default_opts(ring_slots=ring_slots, store_z=store_z)
+            x, info = _solve(b, tol=0.0, maxit=30, variant=variant, nx=nx, opts=opts)
+            xo, _ = oracle.cg_solve(b, variant=variant, tol=0.0, maxit=30, nx=nx)
+            assert info[0]["status"] == lap5cg.NOT_CONVERGED
+            assert _rel(x[:, :nx], xo[:, :nx]) <= 1e-10
+    bf = b.astype(np.float32)
+    x, info = _solve(bf, tol=0.0, maxit=30, variant="classic", precision="f32", nx=nx,
+                     opts=lap5cg.default_opts(ring_slots=ring_slots))
+    xo, _ = oracle.cg_classic(bf.astype(np.float64), tol=0.0, maxit=30, nx=nx)
+    assert _rel(x[:, :nx].astype(np.float64), xo[:, :nx]) <= 1e-4
+    for precision in ("ir_f32", "ir_bf16pr"):
+        x, info = _solve(b, tol=1e-10, maxit=10 ** 6, precision=precision, nx=nx,
+                         opts=lap5cg.default_opts(ring_slots=ring_slots))
+        assert info[0]["status"] == lap5cg.OK and info[0]["relres_true"] <= 1e-10
