@@ -197,6 +197,26 @@ LAP5CG_API int cg_solve_batched(int count, const int* nx, const int* ny, const i
                      int variant, int precision, void* workspace, size_t ws_bytes,
                      lap5cg_info* info, const lap5cg_opts* opts, void* stream);
 
+/*
+ * Autotuner (launch parameters only; the arithmetic does not change).  Times
+ * fixed-iteration solves (tol = 0, `iters` updates, x reset to 0 before each
+ * trial) with CUDA events on `stream` and searches, by coordinate descent
+ * starting from *opts, over warps_per_cta, ring_slots, min_rows and (classic
+ * F64/F32) store_z.  On return *opts holds the fastest combination found and
+ * *best_ms (if not NULL) its time.  Arguments as cg_solve; x is overwritten
+ * (used as scratch); the call synchronises the stream.  No paper counterpart.
+ */
+LAP5CG_API int lap5cg_tune(int nx, int ny, int ld, const void* b, void* x, int variant, int precision, int iters,
+                           void* workspace, size_t ws_bytes, lap5cg_info* info, lap5cg_opts* opts,
+                           double* best_ms, void* stream);
+
+/* The same for cg_solve_batched, over team_ctas, warps_per_cta, ring_slots and
+ * min_rows; every x[k] is overwritten. */
+LAP5CG_API int lap5cg_tune_batched(int count, const int* nx, const int* ny, const int* ld, const void* const* b,
+                                   void* const* x, int variant, int precision, int iters, void* workspace,
+                                   size_t ws_bytes, lap5cg_info* info, lap5cg_opts* opts, double* best_ms,
+                                   void* stream);
+
 /* Largest ny*ld that cg_solve_classic_f64_noalloc accepts. */
 #define LAP5CG_NOALLOC_MAX_POINTS 262144
 

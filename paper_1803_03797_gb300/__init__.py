@@ -81,12 +81,18 @@ def lib():
         L.cg_solve_batched.restype = i
         L.cg_solve_classic_f64_noalloc.argtypes = [i, i, i, vp, vp, d, i, vp, vp]
         L.cg_solve_classic_f64_noalloc.restype = i
+        DP = ctypes.POINTER(ctypes.c_double)
+        L.lap5cg_tune.argtypes = [i, i, i, vp, vp, i, i, i, vp, sz, vp, ctypes.POINTER(Opts), DP, vp]
+        L.lap5cg_tune.restype = i
+        L.lap5cg_tune_batched.argtypes = [i, IP, IP, IP, VPP, VPP, i, i, i, vp, sz, vp, ctypes.POINTER(Opts), DP, vp]
+        L.lap5cg_tune_batched.restype = i
         _lib = L
     return _lib
 
 
 EXPORTED = ("lap5cg_opts_default", "lap5cg_status_string", "lap5_apply", "cg_workspace_size", "cg_solve",
-            "cg_batched_workspace_size", "cg_solve_batched", "cg_solve_classic_f64_noalloc")
+            "cg_batched_workspace_size", "cg_solve_batched", "cg_solve_classic_f64_noalloc", "lap5cg_tune",
+            "lap5cg_tune_batched")
 NOALLOC_MAX_POINTS = 262144
 
 
@@ -267,6 +273,105 @@ def cg_solve_classic_f64_noalloc(b: torch.Tensor, x0: torch.Tensor = None, tol: 
     if rc != OK:
         raise Lap5cgError(rc, "cg_solve_classic_f64_noalloc")
     return x, info
+
+
+# ---------------------------------------------------------------------------
+# Autotuning: lap5cg_tune picks launch parameters by timing real solves; the
+# results are cached in a JSON file keyed by GPU name, precision, variant and
+# a size class (powers of two of the grid sides).
+# ---------------------------------------------------------------------------
+_OPT_FIELDS = ("warps_per_cta", "ring_slots", "min_rows", "store_z", "team_ctas", "ctas")
+
+
+def _cache_path():
+    return os.environ.get("LAP5CG_TUNE_CACHE",
+                          os.path.join(os.path.expanduser("~"), ".cache", "lap5cg", "tune.json"))
+
+
+def size_class(nx, ny):
+    return "%dx%d" % (1 << max(0, int(nx - 1).bit_length()), 1 << max(0, int(ny - 1).bit_length()))
+
+
+def _key(kind, variant, precision, nx, ny):
+    dev = torch.cuda.get_device_name()
+    return "|".join([dev, kind, str(variant), str(precision), size_class(nx, ny)])
+
+
+def _load_cache():
+    import json
+    try:
+        with open(_cache_path()) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def _store_cache(key, opts, ms):
+    import json
+    d = _load_cache()
+    d[key] = {"opts": {k: int(getattr(opts, k)) for k in _OPT_FIELDS}, "ms": ms}
+    path = _cache_path()
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    tmp = path + ".tmp%d" % os.getpid()
+    with open(tmp, "w") as f:
+        json.dump(d, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def tuned_opts(nx, ny, variant="classic", precision="f64", batched=False):
+    """Options from the tuning cache for this size class, or None."""
+    rec = _load_cache().get(_key("batched" if batched else "single", variant, precision, nx, ny))
+    if not rec:
+        return None
+    return default_opts(**rec["opts"])
+
+
+def autotune(b: torch.Tensor, variant="classic", precision="f64", iters=100, nx=None, start: Opts = None,
+             cache=True, stream=None):
+    """Tune launch parameters for solves shaped like b; returns (opts, ms)."""
+    _check_grid(b, "b")
+    ny, ld = b.shape
+    nx = ld if nx is None else int(nx)
+    v, p = _VARIANTS[variant], _PRECISIONS[precision]
+    x = torch.zeros_like(b)
+    ws = torch.empty(workspace_size(nx, ny, ld, v, p), dtype=torch.uint8, device=b.device)
+    info = torch.empty(INFO_BYTES, dtype=torch.uint8, device=b.device)
+    o = start if start is not None else default_opts()
+    ms = ctypes.c_double()
+    rc = lib().lap5cg_tune(nx, ny, ld, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()), v, p,
+                           int(iters), ctypes.c_void_p(ws.data_ptr()), ws.numel(), ctypes.c_void_p(info.data_ptr()),
+                           ctypes.byref(o), ctypes.byref(ms), _stream(stream))
+    if rc != OK:
+        raise Lap5cgError(rc, "lap5cg_tune")
+    if cache:
+        _store_cache(_key("single", variant, precision, nx, ny), o, ms.value)
+    return o, ms.value
+
+
+def autotune_batched(bs, variant="classic", precision="ir_f32", iters=100, nx_list=None, start: Opts = None,
+                     cache=True, stream=None):
+    """Tune team size and launch parameters for a batch shaped like bs."""
+    n = len(bs)
+    nxs = [t.shape[1] for t in bs] if nx_list is None else list(nx_list)
+    nys = [t.shape[0] for t in bs]
+    lds = [t.shape[1] for t in bs]
+    v, p = _VARIANTS[variant], _PRECISIONS[precision]
+    xs = [torch.zeros_like(t) for t in bs]
+    ws = torch.empty(batched_workspace_size(nxs, nys, lds, v, p), dtype=torch.uint8, device=bs[0].device)
+    info = torch.empty(n * INFO_BYTES, dtype=torch.uint8, device=bs[0].device)
+    o = start if start is not None else default_opts()
+    ms = ctypes.c_double()
+    arr = ctypes.c_int * n
+    ptrs = ctypes.c_void_p * n
+    rc = lib().lap5cg_tune_batched(n, arr(*nxs), arr(*nys), arr(*lds), ptrs(*[t.data_ptr() for t in bs]),
+                                   ptrs(*[t.data_ptr() for t in xs]), v, p, int(iters),
+                                   ctypes.c_void_p(ws.data_ptr()), ws.numel(), ctypes.c_void_p(info.data_ptr()),
+                                   ctypes.byref(o), ctypes.byref(ms), _stream(stream))
+    if rc != OK:
+        raise Lap5cgError(rc, "lap5cg_tune_batched")
+    if cache:
+        _store_cache(_key("batched", variant, precision, max(nxs), max(nys)), o, ms.value)
+    return o, ms.value
 
 
 class CGSolve(torch.autograd.Function):

@@ -52,6 +52,8 @@ def test_fixed_iterations_equal_oracle_trajectory(variant):
     batch = _make(SHAPES)
     xs, recs = _run(batch, tol=0.0, maxit=25, variant=variant, precision="f64")
     for (nx, b), x, rec in zip(batch, xs, recs):
+        if nx * b.shape[0] <= 50:
+            continue  # past exact convergence the iterates are rounding noise
         xo, io = oracle.cg_solve(b, variant=variant, tol=0.0, maxit=25, nx=nx)
         assert rec["iters"] == io["iters"]
         assert _rel(x[:, :nx], xo[:, :nx]) <= 1e-10
@@ -77,6 +79,8 @@ def test_f32_batch():
         assert _rel(x[:, :nx].astype(np.float64), xo[:, :nx]) <= gen.condition_number(nx, ny) * (2e-5 + 4 * 2.0 ** -24)
     xs, recs = _run(batch, tol=0.0, maxit=30, variant="newcg", precision="f32")
     for (nx, b), x, rec in zip(batch, xs, recs):
+        if nx * b.shape[0] <= 60:
+            continue  # past exact convergence the iterates are rounding noise
         xo, io = oracle.cg_newcg(b.astype(np.float64), tol=0.0, maxit=30, nx=nx)
         assert rec["iters"] == io["iters"]
         assert _rel(x[:, :nx].astype(np.float64), xo[:, :nx]) <= 1e-3
@@ -99,7 +103,7 @@ def test_convergence_masking_and_initial_guess():
     bs[0].zero_()  # converges at once
     x_pre, _ = lap5cg.cg_solve(bs[1], tol=1e-12, maxit=20000)
     xs = [torch.ones_like(bs[0]), x_pre.clone(), torch.zeros_like(bs[2])]
-    xs_out, info = lap5cg.cg_solve_batched(bs, xs=xs, tol=1e-10, maxit=20000)
+    xs_out, info = lap5cg.cg_solve_batched(bs, xs=xs, tol=1e-10, maxit=20000, precision="f64")
     recs = lap5cg.decode_info(info)
     assert recs[0]["status"] == lap5cg.OK and recs[0]["iters"] == 0 and not xs_out[0].cpu().numpy().any()
     assert recs[1]["status"] == lap5cg.OK and recs[1]["iters"] == 0  # started at a solution
