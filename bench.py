@@ -121,6 +121,22 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(ms, device=None):
+    """Slowest rank's time (the job finishes when the last replica does)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank_step, steps, world, max_ms):
+    """Whole-job throughput: every rank's units over the slowest rank's time."""
+    return world * units_per_rank_step * steps / (max_ms * 1e-3)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -363,13 +379,9 @@ def main():
     stop.record(stream)
     barrier()
     clk = clocks.stop()
-    elapsed_ms = start.elapsed_time(stop)
-    if ws > 1:
-        t = torch.tensor([elapsed_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = max_over_ranks(start.elapsed_time(stop), dev)
     units_per_step = len(VARIANTS) * NX * NY * ITERS
-    value = ws * units_per_step * args.steps / (elapsed_ms * 1e-3)
+    value = job_value(units_per_step, args.steps, ws, elapsed_ms)
 
     hbm_peak, peak_kind = load_peaks()
     per_kernel = {}
@@ -417,12 +429,8 @@ def main():
             e2e_step()
         e1.record(stream)
         barrier()
-        ems = e0.elapsed_time(e1)
-        if ws > 1:
-            t = torch.tensor([ems], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ems = float(t.item())
-        e2e = {"value": ws * units_per_step * args.steps / (ems * 1e-3), "unit": UNIT,
+        ems = max_over_ranks(e0.elapsed_time(e1), dev)
+        e2e = {"value": job_value(units_per_step, args.steps, ws, ems), "unit": UNIT,
                "h2d_bytes_per_step": int(b_pin.numel() * 8),
                "d2h_bytes_per_step": int(sum(x.numel() * 8 for x in x_pin.values()) + info_pin.numel()),
                "ms_per_step": ems / args.steps}

@@ -56,12 +56,12 @@ int plan_units(const void* func, int nx, int ny, int V, const lap5cg_opts& o, si
   return LAP5CG_OK;
 }
 
-int choose_ring(const void* func, int slot_bytes, const lap5cg_opts& o, RingGeom* g, size_t* dyn_smem) {
+int choose_ring(const void* func, int slot_bytes, const lap5cg_opts& o, RingGeom* g, size_t* dyn_smem, bool auto_on) {
   g->S = 0;
   g->slot_bytes = slot_bytes;
   g->warp_bytes = 0;
   *dyn_smem = 0;
-  if (o.ring_slots < 0) return LAP5CG_OK;
+  if (o.ring_slots < 0 || (o.ring_slots == 0 && !auto_on)) return LAP5CG_OK;
   int wpc = o.warps_per_cta > 0 ? o.warps_per_cta : 8;
   if (wpc > 16) wpc = 16;
   const int budget = 100 * 1024;  // two CTAs of this size fit one SM's 228 KB

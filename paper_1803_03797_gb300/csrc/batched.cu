@@ -304,7 +304,8 @@ int solve_batched(int count, const int* nx, const int* ny, const int* ld, const 
   int team = o.team_ctas > 0 ? o.team_ctas : 8;
   if (team != 1 && team != 2 && team != 4 && team != 8 && team != 16) return LAP5CG_ERR_INVALID_ARG;
   size_t dyn = 0;
-  int rc = choose_ring(kernel_of(kind, true), ring_slot_kind(kind), o, &a.rg, &dyn);
+  const bool auto_on = !(kind == KIND_IR_F32 || kind == KIND_IR_BF16);  // as for single solves
+  int rc = choose_ring(kernel_of(kind, true), ring_slot_kind(kind), o, &a.rg, &dyn, auto_on);
   if (rc != LAP5CG_OK) return rc;
   const void* fn = kernel_of(kind, a.rg.S > 0);
   if (team > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)

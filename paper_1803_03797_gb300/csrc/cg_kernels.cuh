@@ -177,6 +177,9 @@ __device__ void classic_solve(const ClassicArgs<T>& a, Team& tm, double* red, un
   int status = LAP5CG_NOT_CONVERGED, iters = 0;
   double bb = 0.0, gamma = 0.0, relres_true = nan("");
   bool aborted = false;
+  bool pending = false;   // a deferred x update is outstanding
+  double alpha_prev = 0.0;
+  Grid<T> plast = a.p0;
 
   {  // r = b - A x0, (b, b), (r, r)
     Acc abb, arr;
@@ -201,10 +204,16 @@ __device__ void classic_solve(const ClassicArgs<T>& a, Team& tm, double* red, un
     if (gamma <= thr) { status = LAP5CG_OK; goto truecheck; }
     double beta = 0.0;
     int cur = 0;  // p_old lives in p[cur], the new p goes to p[cur ^ 1]
+    // With z stored, x += alpha p of iteration k is applied in phase P of
+    // iteration k+1, which reads p_k anyway; phase R then streams only r and z.
+    // The last update is applied after the loop.  Same operands, same result.
+    const bool defer = a.store_z != 0;
     while (iters < c.maxit) {
       const bool first = (iters == 0);
       const Grid<T> pold = cur ? a.p1 : a.p0;
       const Grid<T> pnew = cur ? a.p0 : a.p1;
+      const bool upd_x = defer && !first;  // apply iteration k-1's x update in this phase P
+      const M ap_prev = (M)alpha_prev;
       // ---------------- phase P ----------------
       double pap;
       {
@@ -212,11 +221,12 @@ __device__ void classic_solve(const ClassicArgs<T>& a, Team& tm, double* red, un
         const M bm = (M)beta;
         struct D { int dummy; };
         if constexpr (R) {
-          const RingVec vv[2] = {
+          const RingVec vv[3] = {
               {reinterpret_cast<const unsigned char*>(a.r.ptr), a.r.ld, (int)sizeof(T), RV_HALO | RV_ALWAYS},
               {first ? nullptr : reinterpret_cast<const unsigned char*>(pold.ptr), pold.ld, (int)sizeof(T),
-               RV_HALO | RV_ALWAYS}};
-          int off[2];
+               RV_HALO | RV_ALWAYS},
+              {upd_x ? reinterpret_cast<const unsigned char*>(a.x.ptr) : nullptr, a.x.ld, (int)sizeof(T), 0}};
+          int off[3];
           ring_layout<V>(vv, off);
           ring.fence_global_to_async();
           for (int u = wk.gw; u < c.un.nunits; u += wk.nw) {
@@ -224,7 +234,7 @@ __device__ void classic_solve(const ClassicArgs<T>& a, Team& tm, double* red, un
             unit_bounds(c.un, u, c.ny, s, y0, y1);
             const int xs = s * 32 * V, xl = xs + wk.lane * V;
             const int nval = min(max(c.nx - xl, 0), V);
-            auto field = [&](const unsigned char* sl, FRow<V, M>& f) {
+            auto field = [&](int j, const unsigned char* sl, FRow<V, M>& f) {
               M rv[V];
               ring_lane<V, T>(sl, off[0], true, wk.lane, xl, c.nx, rv);
               const M hr = ring_halo<V, T, M>(sl, off[0], wk.lane, xs, c.nx);
@@ -239,6 +249,13 @@ __device__ void classic_solve(const ClassicArgs<T>& a, Team& tm, double* red, un
 #pragma unroll
                 for (int k = 0; k < V; ++k) f.f[k] = fmx(bm, pv[k], rv[k]);
                 f.hl = fmx(bm, hp, hr);  // one operation serves both halo lanes
+                if (upd_x && j >= y0 && j < y1) {  // deferred x += alpha_prev p_prev on the unit's rows
+                  M xv[V];
+                  ring_lane<V, T>(sl, off[2], false, wk.lane, xl, c.nx, xv);
+#pragma unroll
+                  for (int k = 0; k < V; ++k) xv[k] = fmx(ap_prev, pv[k], xv[k]);
+                  store_row<V>(a.x, j, xl, c.nx, xv);
+                }
               }
               f.hr = f.hl;
             };
@@ -280,6 +297,13 @@ __device__ void classic_solve(const ClassicArgs<T>& a, Team& tm, double* red, un
               for (int k = 0; k < V; ++k) f.f[k] = fmx(bm, pv[k], rv[k]);
               f.hl = fmx(bm, hlp, hlr);
               f.hr = fmx(bm, hrp, hrr);
+              if (upd_x && j >= y0 && j < y1) {  // deferred x += alpha_prev p_prev on the unit's rows
+                M xv[V];
+                load_row<V>(a.x, j, xl, c.nx, xv);
+#pragma unroll
+                for (int k = 0; k < V; ++k) xv[k] = fmx(ap_prev, pv[k], xv[k]);
+                store_row<V>(a.x, j, xl, c.nx, xv);
+              }
             }
           };
           auto load = [&](int, D&) {};
@@ -307,11 +331,9 @@ __device__ void classic_solve(const ClassicArgs<T>& a, Team& tm, double* red, un
         if constexpr (R) {
           ring.fence_global_to_async();
           if (a.store_z) {
-            const RingVec vv[4] = {{reinterpret_cast<const unsigned char*>(pnew.ptr), pnew.ld, (int)sizeof(T), 0},
-                                   {reinterpret_cast<const unsigned char*>(a.x.ptr), a.x.ld, (int)sizeof(T), 0},
-                                   {reinterpret_cast<const unsigned char*>(a.r.ptr), a.r.ld, (int)sizeof(T), 0},
+            const RingVec vv[2] = {{reinterpret_cast<const unsigned char*>(a.r.ptr), a.r.ld, (int)sizeof(T), 0},
                                    {reinterpret_cast<const unsigned char*>(a.z.ptr), a.z.ld, (int)sizeof(T), 0}};
-            int off[4];
+            int off[2];
             ring_layout<V>(vv, off);
             for (int u = wk.gw; u < c.un.nunits; u += wk.nw) {
               int s, y0, y1;
@@ -319,18 +341,14 @@ __device__ void classic_solve(const ClassicArgs<T>& a, Team& tm, double* red, un
               const int xs = s * 32 * V, xl = xs + wk.lane * V;
               const int nval = min(max(c.nx - xl, 0), V);
               auto finish = [&](int j, const unsigned char* sl) {
-                M pv[V], xv[V], rv[V], zv[V];
-                ring_lane<V, T>(sl, off[0], false, wk.lane, xl, c.nx, pv);
-                ring_lane<V, T>(sl, off[1], false, wk.lane, xl, c.nx, xv);
-                ring_lane<V, T>(sl, off[2], false, wk.lane, xl, c.nx, rv);
-                ring_lane<V, T>(sl, off[3], false, wk.lane, xl, c.nx, zv);
+                M rv[V], zv[V];
+                ring_lane<V, T>(sl, off[0], false, wk.lane, xl, c.nx, rv);
+                ring_lane<V, T>(sl, off[1], false, wk.lane, xl, c.nx, zv);
 #pragma unroll
                 for (int k = 0; k < V; ++k) {
-                  xv[k] = fmx(am, pv[k], xv[k]);
                   rv[k] = fmx(-am, zv[k], rv[k]);
                   if (k < nval) acc.add(rv[k], rv[k]);
                 }
-                store_row<V>(a.x, j, xl, c.nx, xv);
                 store_row<V>(a.r, j, xl, c.nx, rv);
               };
               stream_ring<V>(ring, c.ny, xs, y0, y1, wk.rev(), vv, off, finish);
@@ -347,7 +365,7 @@ __device__ void classic_solve(const ClassicArgs<T>& a, Team& tm, double* red, un
               unit_bounds(c.un, u, c.ny, s, y0, y1);
               const int xs = s * 32 * V, xl = xs + wk.lane * V;
               const int nval = min(max(c.nx - xl, 0), V);
-              auto field = [&](const unsigned char* sl, FRow<V, M>& f) {
+              auto field = [&](int, const unsigned char* sl, FRow<V, M>& f) {
                 ring_lane<V, T>(sl, off[0], true, wk.lane, xl, c.nx, f.f);
                 f.hl = ring_halo<V, T, M>(sl, off[0], wk.lane, xs, c.nx);
                 f.hr = f.hl;
@@ -377,22 +395,18 @@ __device__ void classic_solve(const ClassicArgs<T>& a, Team& tm, double* red, un
           const int xs = s * 32 * V, xl = xs + wk.lane * V;
           const int nval = min(max(c.nx - xl, 0), V);
           if (a.store_z) {
-            struct D { M p[V], x[V], r[V], z[V]; };
+            struct D { M r[V], z[V]; };
             auto load = [&](int j, D& d) {
-              load_row<V>(pnew, j, xl, c.nx, d.p);
-              load_row<V>(a.x, j, xl, c.nx, d.x);
               load_row<V>(a.r, j, xl, c.nx, d.r);
               load_row<V>(a.z, j, xl, c.nx, d.z);
             };
             auto finish = [&](int j, const D& d) {
-              M xv[V], rv[V];
+              M rv[V];
 #pragma unroll
               for (int k = 0; k < V; ++k) {
-                xv[k] = fmx(am, d.p[k], d.x[k]);
                 rv[k] = fmx(-am, d.z[k], d.r[k]);
                 if (k < nval) acc.add(rv[k], rv[k]);
               }
-              store_row<V>(a.x, j, xl, c.nx, xv);
               store_row<V>(a.r, j, xl, c.nx, rv);
             };
             stream_rows<D>(y0, y1, wk.rev(), load, finish);
@@ -423,14 +437,43 @@ __device__ void classic_solve(const ClassicArgs<T>& a, Team& tm, double* red, un
         if (!tm.template reduce<1>(v, o, red)) { aborted = true; goto done; }
         const double gnew = o[0];
         ++iters;
+        if (defer) {
+          pending = true;
+          alpha_prev = alpha;
+          plast = pnew;
+        }
         if (c.history && tm.rank() == 0 && threadIdx.x == 0) c.history[iters] = sqrt(gnew / bb);
-        if (!isfinite(gnew)) { status = LAP5CG_ERR_NONFINITE; gamma = gnew; goto truecheck; }
+        if (!isfinite(gnew)) { status = LAP5CG_ERR_NONFINITE; gamma = gnew; goto finalx; }
         beta = gnew / gamma;
         gamma = gnew;
         cur ^= 1;
-        if (gnew <= thr) { status = LAP5CG_OK; goto truecheck; }
+        if (gnew <= thr) { status = LAP5CG_OK; goto finalx; }
       }
     }
+  }
+finalx:
+  if (pending) {  // the deferred x += alpha p of the last iteration
+    const M am = (M)alpha_prev;
+    for (int u = wk.gw; u < c.un.nunits; u += wk.nw) {
+      int s, y0, y1;
+      unit_bounds(c.un, u, c.ny, s, y0, y1);
+      const int xl = s * 32 * V + wk.lane * V;
+      struct D { M x[V], p[V]; };
+      auto load = [&](int j, D& d) {
+        load_row<V>(a.x, j, xl, c.nx, d.x);
+        load_row<V>(plast, j, xl, c.nx, d.p);
+      };
+      auto finish = [&](int j, const D& d) {
+        M xv[V];
+#pragma unroll
+        for (int k = 0; k < V; ++k) xv[k] = fmx(am, d.p[k], d.x[k]);
+        store_row<V>(a.x, j, xl, c.nx, xv);
+      };
+      stream_rows<D>(y0, y1, wk.rev(), load, finish);
+    }
+    ++wk.pc;
+    pending = false;
+    if (!tm.sync(red)) { aborted = true; goto done; }
   }
 truecheck:
   if (c.true_res) {
@@ -588,7 +631,7 @@ __device__ void newcg_solve(const NewcgArgs<T>& a, Team& tm, double* red, unsign
           unit_bounds(c.un, u, c.ny, s, y0, y1);
           const int xs = s * 32 * V, xl = xs + wk.lane * V;
           const int nval = min(max(c.nx - xl, 0), V);
-          auto field = [&](const unsigned char* sl, FRow<V, M>& f) {
+          auto field = [&](int, const unsigned char* sl, FRow<V, M>& f) {
             ring_lane<V, T>(sl, off[0], true, wk.lane, xl, c.nx, f.f);
             f.hl = ring_halo<V, T, M>(sl, off[0], wk.lane, xs, c.nx);
             f.hr = f.hl;

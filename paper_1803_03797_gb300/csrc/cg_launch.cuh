@@ -28,8 +28,8 @@ __global__ void __launch_bounds__(512) k_newcg(const NewcgArgs<T> a) {
 // Ring geometry for a kernel pair: tries the ring kernel first; falls back to
 // the register kernel when the ring is off or does not fit.
 inline int pick_ring(const void* fn_ring, int slot_bytes, const lap5cg_opts& o, RingGeom* rg, size_t* dyn,
-                     bool* use_ring) {
-  int rc = choose_ring(fn_ring, slot_bytes, o, rg, dyn);
+                     bool* use_ring, bool auto_on = true) {
+  int rc = choose_ring(fn_ring, slot_bytes, o, rg, dyn, auto_on);
   if (rc != LAP5CG_OK) return rc;
   *use_ring = rg->S > 0;
   return LAP5CG_OK;

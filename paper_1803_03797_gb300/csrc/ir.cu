@@ -41,8 +41,10 @@ static int solve_ir_t(const SolvePlan& p, cudaStream_t st) {
   RingGeom rg;
   size_t dyn = 0;
   bool ring = false;
+  // automatic choice: register march (measured faster for these kernels,
+  // whose FP64 outer passes set the register budget); ring_slots > 0 forces the ring
   int rc = pick_ring(reinterpret_cast<const void*>(&k_ir<TR, V, true>), ring_slot_ir(V, (int)sizeof(TR)), p.opts,
-                     &rg, &dyn, &ring);
+                     &rg, &dyn, &ring, false);
   if (rc != LAP5CG_OK) return rc;
   const void* fn = ring ? reinterpret_cast<const void*>(&k_ir<TR, V, true>)
                         : reinterpret_cast<const void*>(&k_ir<TR, V, false>);

@@ -165,7 +165,7 @@ __device__ void ir_solve(const IrArgs<TR>& a, Team& tm, double* red, unsigned ch
               unit_bounds(c.un, u, c.ny, s, y0, y1);
               const int xs = s * 32 * V, xl = xs + wk.lane * V;
               const int nval = min(max(c.nx - xl, 0), V);
-              auto field = [&](const unsigned char* sl, FRow<V, float>& f) {
+              auto field = [&](int, const unsigned char* sl, FRow<V, float>& f) {
                 float rv[V];
                 ring_lane<V, TR>(sl, off[0], true, wk.lane, xl, c.nx, rv);
                 const float hr = ring_halo<V, TR, float>(sl, off[0], wk.lane, xs, c.nx);
@@ -258,7 +258,7 @@ __device__ void ir_solve(const IrArgs<TR>& a, Team& tm, double* red, unsigned ch
               unit_bounds(c.un, u, c.ny, s, y0, y1);
               const int xs = s * 32 * V, xl = xs + wk.lane * V;
               const int nval = min(max(c.nx - xl, 0), V);
-              auto field = [&](const unsigned char* sl, FRow<V, float>& f) {
+              auto field = [&](int, const unsigned char* sl, FRow<V, float>& f) {
                 ring_lane<V, TR>(sl, off[0], true, wk.lane, xl, c.nx, f.f);
                 f.hl = ring_halo<V, TR, float>(sl, off[0], wk.lane, xs, c.nx);
                 f.hr = f.hl;

@@ -64,13 +64,15 @@ int plan_units(const void* func, int nx, int ny, int V, const lap5cg_opts& o, si
 
 // Row-ring geometry for a kernel whose largest ring slot is slot_bytes: sets
 // the kernel's dynamic shared memory limit and returns the bytes per CTA
-// (S = 0 and 0 bytes when the ring is off or does not fit).
-int choose_ring(const void* func, int slot_bytes, const lap5cg_opts& o, RingGeom* g, size_t* dyn_smem);
+// (S = 0 and 0 bytes when the ring is off or does not fit).  auto_on: whether
+// ring_slots = 0 (automatic) turns the ring on for this kernel family.
+int choose_ring(const void* func, int slot_bytes, const lap5cg_opts& o, RingGeom* g, size_t* dyn_smem,
+                bool auto_on);
 
 // Largest ring slot (bytes) of each kernel family, V = lane vector width.
 inline int ring_slot_classic(int V, int es) {
   const int M = 32 * V * es;
-  const int p = 2 * (M + 32), rz = 4 * M, rr = (M + 32) + 2 * M;
+  const int p = 2 * (M + 32) + M, rz = 2 * M, rr = (M + 32) + 2 * M;  // phase P carries x for the deferred update
   return p > rz ? (p > rr ? p : rr) : (rz > rr ? rz : rr);
 }
 inline int ring_slot_newcg(int V, int es) { return (32 * V * es + 32) + 5 * 32 * V * es; }

@@ -48,6 +48,7 @@ struct WarpRing {
   unsigned char* slots_ptr;
   int S, slot_bytes;
   unsigned q;          // sequence number of the next row to produce / consume
+  unsigned q_issued;   // 1 + the last sequence number produced (lane 0)
   bool failed;
   long long timeout_ns;
   int* err;
@@ -61,6 +62,7 @@ struct WarpRing {
     slots_ptr = warp_smem + 128;  // 8 barriers padded to 128 bytes
     slots = smem_u32(slots_ptr);
     q = 0;
+    q_issued = 0;
     failed = false;
     timeout_ns = to;
     err = err_word;
@@ -78,13 +80,14 @@ struct WarpRing {
   template <int V, int K>
   __device__ __forceinline__ void produce(unsigned seq, int row, int ny, int xs, bool interior,
                                           const RingVec (&v)[K], const int (&off)[K]) {
-    if ((threadIdx.x & 31) != 0) return;
+    if ((threadIdx.x & 31) != 0 || failed) return;  // after a failure nothing more is issued
     const int s = (int)(seq % (unsigned)S);
     const uint32_t bar = bars + 8u * s;
     const uint32_t dst0 = slots + (uint32_t)(s * slot_bytes);
+    q_issued = seq + 1u;
     // the slot's previous contents were read through the generic proxy
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    if (row < 0 || row >= ny || failed) {
+    if (row < 0 || row >= ny) {
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
       return;
     }
@@ -150,8 +153,30 @@ struct WarpRing {
   }
 
   // Invalidate the barriers (every produced row has been waited for) so the
-  // same shared memory can hold a fresh ring for the next solve.
+  // same shared memory can hold a fresh ring for the next solve.  After a
+  // timed-out wait no new copies were issued, but earlier ones may still be in
+  // flight: drain them first (bounded, 1 s per slot).
   __device__ __forceinline__ void teardown() {
+    __syncwarp();
+    if (failed && (threadIdx.x & 31) == 0) {
+      const unsigned first = q_issued > (unsigned)S ? q_issued - (unsigned)S : 0u;
+      for (unsigned seq = first; seq < q_issued; ++seq) {
+        const uint32_t bar = bars + 8u * (seq % (unsigned)S);
+        const uint32_t parity = (seq / (unsigned)S) & 1u;
+        const unsigned long long t0 = global_ns();
+        for (;;) {
+          uint32_t ok;
+          asm volatile(
+              "{\n\t.reg .pred p;\n\t"
+              "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+              "selp.u32 %0, 1, 0, p;\n\t}"
+              : "=r"(ok)
+              : "r"(bar), "r"(parity)
+              : "memory");
+          if (ok || global_ns() - t0 > 1000000000ull) break;
+        }
+      }
+    }
     __syncwarp();
     if ((threadIdx.x & 31) == 0) {
       for (int s = 0; s < S; ++s) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bars + 8u * s) : "memory");
@@ -197,7 +222,7 @@ __device__ __forceinline__ M ring_halo(const unsigned char* slot, int off, int l
 }
 
 // Row march of one unit through the ring: rows y0-1 .. y1 (or reversed) are
-// streamed; field(slot, FRow&) builds the stencil operand of a row from its
+// streamed; field(j, slot, FRow&) builds the stencil operand of row j from its
 // slot, finish(j, slot, S, C, N) consumes row j.  Whole-warp call.
 template <int V, class M, int K, class FieldF, class FinishF>
 __device__ __forceinline__ void march_ring(WarpRing& ring, int ny, int xs, int y0, int y1, bool rev,
@@ -215,16 +240,16 @@ __device__ __forceinline__ void march_ring(WarpRing& ring, int ny, int xs, int y
   FRow<V, M> fB, fC;
   {
     const unsigned char* s0 = ring.wait(q0);
-    if (row_of(0) < 0 || row_of(0) >= ny) fB.zero(); else field(s0, fB);
+    if (row_of(0) < 0 || row_of(0) >= ny) fB.zero(); else field(row_of(0), s0, fB);
     __syncwarp();
     if (ring.S < total) ring.produce<V, K>(q0 + ring.S, row_of(ring.S), ny, xs, ring.S <= T, vecs, off);
   }
   const unsigned char* sC = ring.wait(q0 + 1);
-  field(sC, fC);
+  field(row_of(1), sC, fC);
   for (int t = 1; t <= T; ++t) {
     FRow<V, M> fA;
     const unsigned char* sA = ring.wait(q0 + t + 1);
-    if (row_of(t + 1) < 0 || row_of(t + 1) >= ny) fA.zero(); else field(sA, fA);
+    if (row_of(t + 1) < 0 || row_of(t + 1) >= ny) fA.zero(); else field(row_of(t + 1), sA, fA);
     if (!rev) finish(row_of(t), sC, fB, fC, fA);
     else finish(row_of(t), sC, fA, fC, fB);
     __syncwarp();
