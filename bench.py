@@ -40,7 +40,9 @@ WORKLOAD = ("4096x4096 interior grid, FP64, b = A u* + 1e-3 N(0,1) (seed 2), x0 
 # bytes = minimum HBM traffic of the variant (each state vector read/written once),
 # ops = FP64-pipe instructions (stencil 4, each axpy 1, each dot 1).
 COST = {
-    "classic": {"bytes": 80, "fp64_ops": 9, "kernel": "k_classic<double,2>"},  # store-z form
+    # store-z form with the x update deferred into the next phase P:
+    # phase P reads r, p_old, x and writes p, z, x; phase R reads r, z and writes r
+    "classic": {"bytes": 72, "fp64_ops": 9, "kernel": "k_classic<double,2>"},
     "newcg": {"bytes": 96, "fp64_ops": 12, "kernel": "k_newcg<double,2>"},
 }
 FP64_PEAK_TFLOPS = 1.25  # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (nominal GB300 FP64)
@@ -258,6 +260,34 @@ def batched_workload(lap5cg, torch, dev, tune=True):
             "max_relres_true": max(r["relres_true"] for r in recs), "tuned_opts": tuned}
 
 
+def paper_size_workload(lap5cg, torch, dev, reps=20):
+    """The paper's largest grid: 100 x 100 FP64, U[-1,1) (seed 1), x0 = 0, to 1e-8;
+    latency-bound.  Through cg_solve (grid barrier over a few CTAs) and through
+    cg_solve_batched with one instance (one thread-block cluster, hardware
+    cluster barrier)."""
+    b = torch.from_numpy(gen.uniform_rhs(100, 100, seed=1)).to(dev)
+    out = {}
+    for variant in ("classic", "newcg"):
+        for path in ("grid", "cluster"):
+            def run():
+                if path == "grid":
+                    return lap5cg.cg_solve(b, tol=1e-8, maxit=10000, variant=variant)[1]
+                return lap5cg.cg_solve_batched([b], tol=1e-8, maxit=10000, variant=variant, precision="f64")[1]
+            run()
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                info = run()
+            e1.record()
+            torch.cuda.synchronize(dev)
+            ms = e0.elapsed_time(e1) / reps
+            rec = lap5cg.decode_info(info)[0]
+            out["%s_%s" % (variant, path)] = {"ms": ms, "iters": rec["iters"], "status": rec["status"],
+                                              "us_per_iter": ms * 1e3 / max(rec["iters"], 1)}
+    return out
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -316,6 +346,8 @@ def main():
     ap.add_argument("--n", type=int, default=NX, help="grid side (profiling only)")
     ap.add_argument("--iters", type=int, default=ITERS, help="iterations per solve (profiling only)")
     ap.add_argument("--variants", default=",".join(VARIANTS), help="comma list (profiling only)")
+    ap.add_argument("--profile-f32", type=int, default=0,
+                    help="profiling only: run the binary32 8192^2 solve for this many iterations and exit")
     args = ap.parse_args()
     _apply_overrides(args)
     if args.warmup < 3:
@@ -325,6 +357,13 @@ def main():
 
     import torch
     import paper_1803_03797_gb300 as lap5cg
+
+    if args.profile_f32:
+        lap5cg.lib()
+        r = fused_f32_roofline(lap5cg, torch, torch.device("cuda", 0), load_peaks()[0], iters=args.profile_f32,
+                               reps=1)
+        print(json.dumps({"profiling_case": r}))
+        return 0
 
     ws, rank, local = dist_env()
     if ws > 1:
@@ -440,6 +479,7 @@ def main():
         extras["fused_f32_8192"] = fused_f32_roofline(lap5cg, torch, dev, hbm_peak)
         extras["time_to_1e-10_4096"] = time_to_solution(lap5cg, torch, dev, 4096, b_host)
         extras["batched_256_ir_f32"] = batched_workload(lap5cg, torch, dev)
+        extras["paper_100x100_to_1e-8"] = paper_size_workload(lap5cg, torch, dev)
         if args.tts:
             extras["time_to_1e-10_8192"] = time_to_solution(lap5cg, torch, dev, 8192,
                                                             gen.uniform_rhs(8192, 8192, seed=3))

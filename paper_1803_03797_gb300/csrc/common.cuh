@@ -308,7 +308,7 @@ __device__ __forceinline__ bool grid_reduce(Ctl* ctl, unsigned long long& epoch,
       const unsigned long long t0 = global_ns();
       unsigned spins = 0;
       while (ld_acquire_u64(&ctl->bar) < target) {
-        if ((++spins & 63u) == 0u) {
+        if ((++spins & 7u) == 0u) {  // each poll is an L2 round trip: check the clock often
           if (ld_relaxed_i32(&ctl->abort)) { go = 0; break; }
           if ((long long)(global_ns() - t0) > timeout_ns) {
             record_error(ctl, LAP5CG_ERR_SYNC_TIMEOUT);

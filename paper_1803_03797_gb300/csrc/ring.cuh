@@ -49,6 +49,9 @@ struct WarpRing {
   int S, slot_bytes;
   unsigned q;          // sequence number of the next row to produce / consume
   unsigned q_issued;   // 1 + the last sequence number produced (lane 0)
+  int pslot;           // slot of the next produce (lane 0)
+  int cslot;           // slot of the next wait
+  uint32_t cpar;       // phase parity the next wait expects
   bool failed;
   long long timeout_ns;
   int* err;
@@ -63,6 +66,9 @@ struct WarpRing {
     slots = smem_u32(slots_ptr);
     q = 0;
     q_issued = 0;
+    pslot = 0;
+    cslot = 0;
+    cpar = 0;
     failed = false;
     timeout_ns = to;
     err = err_word;
@@ -81,7 +87,10 @@ struct WarpRing {
   __device__ __forceinline__ void produce(unsigned seq, int row, int ny, int xs, bool interior,
                                           const RingVec (&v)[K], const int (&off)[K]) {
     if ((threadIdx.x & 31) != 0 || failed) return;  // after a failure nothing more is issued
-    const int s = (int)(seq % (unsigned)S);
+    // produce() is called in strictly increasing sequence order: the slot
+    // advances by one each call (no division by the runtime S)
+    const int s = pslot;
+    pslot = (pslot + 1 == S) ? 0 : pslot + 1;
     const uint32_t bar = bars + 8u * s;
     const uint32_t dst0 = slots + (uint32_t)(s * slot_bytes);
     q_issued = seq + 1u;
@@ -119,11 +128,17 @@ struct WarpRing {
     }
   }
 
-  // Whole warp: wait until the row with sequence number seq has landed.
-  __device__ __forceinline__ const unsigned char* wait(unsigned seq) {
-    const int s = (int)(seq % (unsigned)S);
+  // Whole warp: wait until the next row (in sequence order) has landed.
+  __device__ __forceinline__ const unsigned char* wait(unsigned) {
+    const int s = cslot;
     const uint32_t bar = bars + 8u * s;
-    const uint32_t parity = (seq / (unsigned)S) & 1u;
+    const uint32_t parity = cpar;
+    if (cslot + 1 == S) {
+      cslot = 0;
+      cpar ^= 1u;
+    } else {
+      ++cslot;
+    }
     if (!failed) {
       const unsigned long long t0 = global_ns();
       unsigned spins = 0;
