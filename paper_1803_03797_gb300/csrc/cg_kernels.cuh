@@ -33,6 +33,7 @@ struct SolveCommon {
   int maxit;
   int true_res;
   long long timeout_ns;
+  double m1;       // -1.0, opaque to the compiler (see sub_fma)
   RingGeom rg;     // shared-memory row ring (rg.S == 0: register march)
   int* err;        // error word: ring wait timeouts are recorded here
   int* abort_flag; // grid teams: set with err so every CTA leaves at its next barrier
@@ -117,7 +118,7 @@ __device__ __forceinline__ void pass_residual(const SolveCommon& c, Walker& wk, 
     auto load = [&](int j, D& d) { load_row<V>(b, j, xl, c.nx, d.b); };
     auto finish = [&](int j, const D& d, const FRow<V, M>& S, const FRow<V, M>& C, const FRow<V, M>& N) {
       M ax[V], rv[V];
-      stencil_row<V>(S, C, N, wk.lane, ax);
+      stencil_row<V>(S, C, N, wk.lane, ax, c.m1);
 #pragma unroll
       for (int k = 0; k < V; ++k) {
         rv[k] = d.b[k] - ax[k];
@@ -262,12 +263,10 @@ __device__ void classic_solve(const ClassicArgs<T>& a, Team& tm, double* red, un
             auto finish = [&](int j, const unsigned char*, const FRow<V, M>& S, const FRow<V, M>& C,
                               const FRow<V, M>& N) {
               M ap[V];
-              stencil_row<V>(S, C, N, wk.lane, ap);
+              stencil_row<V>(S, C, N, wk.lane, ap, c.m1);
               store_row<V>(pnew, j, xl, c.nx, C.f);
               if (a.store_z) store_row<V>(a.z, j, xl, c.nx, ap);
-#pragma unroll
-              for (int k = 0; k < V; ++k)
-                if (k < nval) acc.add(C.f[k], ap[k]);
+              acc_dot<V>(acc, C.f, ap, nval);
             };
             march_ring<V, M>(ring, c.ny, xs, y0, y1, wk.rev(), vv, off, field, finish);
           }
@@ -309,7 +308,7 @@ __device__ void classic_solve(const ClassicArgs<T>& a, Team& tm, double* red, un
           auto load = [&](int, D&) {};
           auto finish = [&](int j, const D&, const FRow<V, M>& S, const FRow<V, M>& C, const FRow<V, M>& N) {
             M ap[V];
-            stencil_row<V>(S, C, N, wk.lane, ap);
+            stencil_row<V>(S, C, N, wk.lane, ap, c.m1);
             store_row<V>(pnew, j, xl, c.nx, C.f);
             if (a.store_z) store_row<V>(a.z, j, xl, c.nx, ap);
 #pragma unroll
@@ -345,10 +344,8 @@ __device__ void classic_solve(const ClassicArgs<T>& a, Team& tm, double* red, un
                 ring_lane<V, T>(sl, off[0], false, wk.lane, xl, c.nx, rv);
                 ring_lane<V, T>(sl, off[1], false, wk.lane, xl, c.nx, zv);
 #pragma unroll
-                for (int k = 0; k < V; ++k) {
-                  rv[k] = fmx(-am, zv[k], rv[k]);
-                  if (k < nval) acc.add(rv[k], rv[k]);
-                }
+                for (int k = 0; k < V; ++k) rv[k] = fmx(-am, zv[k], rv[k]);
+                acc_dot<V>(acc, rv, rv, nval);
                 store_row<V>(a.r, j, xl, c.nx, rv);
               };
               stream_ring<V>(ring, c.ny, xs, y0, y1, wk.rev(), vv, off, finish);
@@ -373,15 +370,15 @@ __device__ void classic_solve(const ClassicArgs<T>& a, Team& tm, double* red, un
               auto finish = [&](int j, const unsigned char* sl, const FRow<V, M>& S, const FRow<V, M>& C,
                                 const FRow<V, M>& N) {
                 M ap[V], xv[V], rv[V];
-                stencil_row<V>(S, C, N, wk.lane, ap);
+                stencil_row<V>(S, C, N, wk.lane, ap, c.m1);
                 ring_lane<V, T>(sl, off[1], false, wk.lane, xl, c.nx, xv);
                 ring_lane<V, T>(sl, off[2], false, wk.lane, xl, c.nx, rv);
 #pragma unroll
                 for (int k = 0; k < V; ++k) {
                   xv[k] = fmx(am, C.f[k], xv[k]);
                   rv[k] = fmx(-am, ap[k], rv[k]);
-                  if (k < nval) acc.add(rv[k], rv[k]);
                 }
+                acc_dot<V>(acc, rv, rv, nval);
                 store_row<V>(a.x, j, xl, c.nx, xv);
                 store_row<V>(a.r, j, xl, c.nx, rv);
               };
@@ -419,7 +416,7 @@ __device__ void classic_solve(const ClassicArgs<T>& a, Team& tm, double* red, un
             };
             auto finish = [&](int j, const D& d, const FRow<V, M>& S, const FRow<V, M>& C, const FRow<V, M>& N) {
               M ap[V], xv[V], rv[V];
-              stencil_row<V>(S, C, N, wk.lane, ap);
+              stencil_row<V>(S, C, N, wk.lane, ap, c.m1);
 #pragma unroll
               for (int k = 0; k < V; ++k) {
                 xv[k] = fmx(am, C.f[k], d.x[k]);
@@ -524,7 +521,7 @@ __device__ __forceinline__ void pass_apply(const SolveCommon& c, Walker& wk, con
     auto load = [&](int, D&) {};
     auto finish = [&](int j, const D&, const FRow<V, M>& S, const FRow<V, M>& C, const FRow<V, M>& N) {
       M yv[V];
-      stencil_row<V>(S, C, N, wk.lane, yv);
+      stencil_row<V>(S, C, N, wk.lane, yv, c.m1);
       store_row<V>(y, j, xl, c.nx, yv);
     };
     march<V, M, D>(y0, y1, wk.rev(), field, load, finish);
@@ -548,7 +545,7 @@ __device__ __forceinline__ void pass_w_from_r(const SolveCommon& c, Walker& wk, 
     auto load = [&](int, D&) {};
     auto finish = [&](int j, const D&, const FRow<V, M>& S, const FRow<V, M>& C, const FRow<V, M>& N) {
       M wv[V];
-      stencil_row<V>(S, C, N, wk.lane, wv);
+      stencil_row<V>(S, C, N, wk.lane, wv, c.m1);
       store_row<V>(w, j, xl, c.nx, wv);
 #pragma unroll
       for (int k = 0; k < V; ++k)
@@ -639,7 +636,7 @@ __device__ void newcg_solve(const NewcgArgs<T>& a, Team& tm, double* red, unsign
           auto finish = [&](int j, const unsigned char* sl, const FRow<V, M>& S, const FRow<V, M>& C,
                             const FRow<V, M>& N) {
             M nv[V], zv[V], qv[V], pv[V], xv[V], rv[V], wv[V];
-            stencil_row<V>(S, C, N, wk.lane, nv);  // n = A w
+            stencil_row<V>(S, C, N, wk.lane, nv, c.m1);  // n = A w
             ring_lane<V, T>(sl, off[4], false, wk.lane, xl, c.nx, xv);
             ring_lane<V, T>(sl, off[5], false, wk.lane, xl, c.nx, rv);
             if (!first) {
@@ -661,8 +658,9 @@ __device__ void newcg_solve(const NewcgArgs<T>& a, Team& tm, double* red, unsign
               xv[k] = fmx(am, pv[k], xv[k]);
               rv[k] = fmx(-am, qv[k], rv[k]);
               wv[k] = fmx(-am, zv[k], C.f[k]);
-              if (k < nval) { ag.add(rv[k], rv[k]); ad.add(wv[k], rv[k]); }
             }
+            acc_dot<V>(ag, rv, rv, nval);
+            acc_dot<V>(ad, wv, rv, nval);
             store_row<V>(a.z, j, xl, c.nx, zv);
             store_row<V>(a.q, j, xl, c.nx, qv);
             store_row<V>(a.p, j, xl, c.nx, pv);
@@ -690,7 +688,7 @@ __device__ void newcg_solve(const NewcgArgs<T>& a, Team& tm, double* red, unsign
         };
         auto finish = [&](int j, const D& d, const FRow<V, M>& S, const FRow<V, M>& C, const FRow<V, M>& N) {
           M nv[V], zv[V], qv[V], pv[V], xv[V], rv[V], wv[V];
-          stencil_row<V>(S, C, N, wk.lane, nv);  // n = A w
+          stencil_row<V>(S, C, N, wk.lane, nv, c.m1);  // n = A w
 #pragma unroll
           for (int k = 0; k < V; ++k) {
             if (first) {
