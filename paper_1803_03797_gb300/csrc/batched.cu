@@ -32,7 +32,6 @@ struct BatchCtl {
 };
 
 struct BatchArgs {
-  double m1;  // -1.0 (see sub_fma)
   RingGeom rg;
   int* errs;  // per-instance error words (caller order)
   int count;
@@ -105,7 +104,6 @@ __device__ __forceinline__ void solve_instance(const BatchArgs& a, const BatchEn
   c.maxit = a.maxit;
   c.true_res = a.true_res;
   c.timeout_ns = 2000000000LL;
-  c.m1 = a.m1;
   c.rg = a.rg;
   c.err = a.errs + e.idx;
   c.abort_flag = nullptr;
@@ -285,7 +283,6 @@ int solve_batched(int count, const int* nx, const int* ny, const int* ld, const 
   if (cudaMemsetAsync(errs, 0, (size_t)count * sizeof(int), st) != cudaSuccess) return LAP5CG_ERR_CUDA;
 
   BatchArgs a;
-  a.m1 = -1.0;
   a.errs = errs;
   a.count = count;
   a.tab = dtab;

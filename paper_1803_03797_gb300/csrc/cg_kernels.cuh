@@ -33,7 +33,6 @@ struct SolveCommon {
   int maxit;
   int true_res;
   long long timeout_ns;
-  double m1;       // -1.0, opaque to the compiler (see sub_fma)
   RingGeom rg;     // shared-memory row ring (rg.S == 0: register march)
   int* err;        // error word: ring wait timeouts are recorded here
   int* abort_flag; // grid teams: set with err so every CTA leaves at its next barrier
@@ -118,7 +117,7 @@ __device__ __forceinline__ void pass_residual(const SolveCommon& c, Walker& wk, 
     auto load = [&](int j, D& d) { load_row<V>(b, j, xl, c.nx, d.b); };
     auto finish = [&](int j, const D& d, const FRow<V, M>& S, const FRow<V, M>& C, const FRow<V, M>& N) {
       M ax[V], rv[V];
-      stencil_row<V>(S, C, N, wk.lane, ax, c.m1);
+      stencil_row<V>(S, C, N, wk.lane, ax);
 #pragma unroll
       for (int k = 0; k < V; ++k) {
         rv[k] = d.b[k] - ax[k];
@@ -263,7 +262,7 @@ __device__ void classic_solve(const ClassicArgs<T>& a, Team& tm, double* red, un
             auto finish = [&](int j, const unsigned char*, const FRow<V, M>& S, const FRow<V, M>& C,
                               const FRow<V, M>& N) {
               M ap[V];
-              stencil_row<V>(S, C, N, wk.lane, ap, c.m1);
+              stencil_row<V>(S, C, N, wk.lane, ap);
               store_row<V>(pnew, j, xl, c.nx, C.f);
               if (a.store_z) store_row<V>(a.z, j, xl, c.nx, ap);
               acc_dot<V>(acc, C.f, ap, nval);
@@ -308,7 +307,7 @@ __device__ void classic_solve(const ClassicArgs<T>& a, Team& tm, double* red, un
           auto load = [&](int, D&) {};
           auto finish = [&](int j, const D&, const FRow<V, M>& S, const FRow<V, M>& C, const FRow<V, M>& N) {
             M ap[V];
-            stencil_row<V>(S, C, N, wk.lane, ap, c.m1);
+            stencil_row<V>(S, C, N, wk.lane, ap);
             store_row<V>(pnew, j, xl, c.nx, C.f);
             if (a.store_z) store_row<V>(a.z, j, xl, c.nx, ap);
 #pragma unroll
@@ -370,7 +369,7 @@ __device__ void classic_solve(const ClassicArgs<T>& a, Team& tm, double* red, un
               auto finish = [&](int j, const unsigned char* sl, const FRow<V, M>& S, const FRow<V, M>& C,
                                 const FRow<V, M>& N) {
                 M ap[V], xv[V], rv[V];
-                stencil_row<V>(S, C, N, wk.lane, ap, c.m1);
+                stencil_row<V>(S, C, N, wk.lane, ap);
                 ring_lane<V, T>(sl, off[1], false, wk.lane, xl, c.nx, xv);
                 ring_lane<V, T>(sl, off[2], false, wk.lane, xl, c.nx, rv);
 #pragma unroll
@@ -416,7 +415,7 @@ __device__ void classic_solve(const ClassicArgs<T>& a, Team& tm, double* red, un
             };
             auto finish = [&](int j, const D& d, const FRow<V, M>& S, const FRow<V, M>& C, const FRow<V, M>& N) {
               M ap[V], xv[V], rv[V];
-              stencil_row<V>(S, C, N, wk.lane, ap, c.m1);
+              stencil_row<V>(S, C, N, wk.lane, ap);
 #pragma unroll
               for (int k = 0; k < V; ++k) {
                 xv[k] = fmx(am, C.f[k], d.x[k]);
@@ -521,7 +520,7 @@ __device__ __forceinline__ void pass_apply(const SolveCommon& c, Walker& wk, con
     auto load = [&](int, D&) {};
     auto finish = [&](int j, const D&, const FRow<V, M>& S, const FRow<V, M>& C, const FRow<V, M>& N) {
       M yv[V];
-      stencil_row<V>(S, C, N, wk.lane, yv, c.m1);
+      stencil_row<V>(S, C, N, wk.lane, yv);
       store_row<V>(y, j, xl, c.nx, yv);
     };
     march<V, M, D>(y0, y1, wk.rev(), field, load, finish);
@@ -545,7 +544,7 @@ __device__ __forceinline__ void pass_w_from_r(const SolveCommon& c, Walker& wk, 
     auto load = [&](int, D&) {};
     auto finish = [&](int j, const D&, const FRow<V, M>& S, const FRow<V, M>& C, const FRow<V, M>& N) {
       M wv[V];
-      stencil_row<V>(S, C, N, wk.lane, wv, c.m1);
+      stencil_row<V>(S, C, N, wk.lane, wv);
       store_row<V>(w, j, xl, c.nx, wv);
 #pragma unroll
       for (int k = 0; k < V; ++k)
@@ -636,7 +635,7 @@ __device__ void newcg_solve(const NewcgArgs<T>& a, Team& tm, double* red, unsign
           auto finish = [&](int j, const unsigned char* sl, const FRow<V, M>& S, const FRow<V, M>& C,
                             const FRow<V, M>& N) {
             M nv[V], zv[V], qv[V], pv[V], xv[V], rv[V], wv[V];
-            stencil_row<V>(S, C, N, wk.lane, nv, c.m1);  // n = A w
+            stencil_row<V>(S, C, N, wk.lane, nv);  // n = A w
             ring_lane<V, T>(sl, off[4], false, wk.lane, xl, c.nx, xv);
             ring_lane<V, T>(sl, off[5], false, wk.lane, xl, c.nx, rv);
             if (!first) {
@@ -688,7 +687,7 @@ __device__ void newcg_solve(const NewcgArgs<T>& a, Team& tm, double* red, unsign
         };
         auto finish = [&](int j, const D& d, const FRow<V, M>& S, const FRow<V, M>& C, const FRow<V, M>& N) {
           M nv[V], zv[V], qv[V], pv[V], xv[V], rv[V], wv[V];
-          stencil_row<V>(S, C, N, wk.lane, nv, c.m1);  // n = A w
+          stencil_row<V>(S, C, N, wk.lane, nv);  // n = A w
 #pragma unroll
           for (int k = 0; k < V; ++k) {
             if (first) {

@@ -73,7 +73,6 @@ inline SolveCommon make_common(const SolvePlan& p, const LaunchCfg& cfg, const R
   c.true_res = p.opts.true_residual;
   const double to = p.opts.timeout_s > 0.0 ? p.opts.timeout_s : 2.0;
   c.timeout_ns = (long long)(to * 1e9);
-  c.m1 = -1.0;
   c.rg = rg;
   c.err = &c.ctl->status;
   c.abort_flag = &c.ctl->abort;

@@ -181,17 +181,9 @@ __device__ __forceinline__ float shfl_dn1(float v) { return __shfl_down_sync(0xf
 // y = A f on the centre row: the Sec. II-B mask in the fixed add order
 // 4*C - W - E - S - N.  4*C is exact, so contracting the first subtraction
 // into a fused multiply-add does not change the result.  Whole-warp call.
-// Subtraction as a fused multiply-add by -1: fma(-1, b, a) rounds a - b
-// exactly as a subtraction does, and on GB300 the FP64 pipe issues FMAs faster
-// than adds (measured 2.0 vs 1.7 per SM per clock).  The -1 must not be a
-// literal (the compiler would fold the FMA back into an add): it is read from
-// the opaque value m1, which the host sets to -1.
-__device__ __forceinline__ double sub_fma(double a, double b, double m1) { return __fma_rn(m1, b, a); }
-__device__ __forceinline__ float sub_fma(float a, float b, double) { return a - b; }
-
 template <int V, class M>
 __device__ __forceinline__ void stencil_row(const FRow<V, M>& S, const FRow<V, M>& C, const FRow<V, M>& N,
-                                            int lane, M (&y)[V], double m1 = -1.0) {
+                                            int lane, M (&y)[V]) {
   M left = shfl_up1(C.f[V - 1]);
   M right = shfl_dn1(C.f[0]);
   if (lane == 0) left = C.hl;
@@ -201,10 +193,10 @@ __device__ __forceinline__ void stencil_row(const FRow<V, M>& S, const FRow<V, M
     const M w = (k == 0) ? left : C.f[k - 1];
     const M e = (k == V - 1) ? right : C.f[k + 1];
     M acc = M(4) * C.f[k];
-    acc = sub_fma(acc, w, m1);
-    acc = sub_fma(acc, e, m1);
-    acc = sub_fma(acc, S.f[k], m1);
-    acc = sub_fma(acc, N.f[k], m1);
+    acc -= w;
+    acc -= e;
+    acc -= S.f[k];
+    acc -= N.f[k];
     y[k] = acc;
   }
 }

@@ -89,7 +89,7 @@ __device__ void ir_solve(const IrArgs<TR>& a, Team& tm, double* red, unsigned ch
                           const FRow<V, double>& N) {
           double ax[V];
           float ri[V];
-          stencil_row<V>(S, C, N, wk.lane, ax, c.m1);
+          stencil_row<V>(S, C, N, wk.lane, ax);
 #pragma unroll
           for (int k = 0; k < V; ++k) {
             const double rv = dd.b[k] - ax[k];
@@ -186,7 +186,7 @@ __device__ void ir_solve(const IrArgs<TR>& a, Team& tm, double* red, unsigned ch
               auto finish = [&](int j, const unsigned char*, const FRow<V, float>& S, const FRow<V, float>& C,
                                 const FRow<V, float>& N) {
                 float ap[V];
-                stencil_row<V>(S, C, N, wk.lane, ap, c.m1);
+                stencil_row<V>(S, C, N, wk.lane, ap);
                 store_row<V>(pnew, j, xl, c.nx, C.f);
                 if (a.store_z) store_row<V>(a.z, j, xl, c.nx, ap);
                 acc_dot<V>(acc, C.f, ap, nval);
@@ -225,7 +225,7 @@ __device__ void ir_solve(const IrArgs<TR>& a, Team& tm, double* red, unsigned ch
             auto finish = [&](int j, const D&, const FRow<V, float>& S, const FRow<V, float>& C,
                               const FRow<V, float>& N) {
               float ap[V];
-              stencil_row<V>(S, C, N, wk.lane, ap, c.m1);
+              stencil_row<V>(S, C, N, wk.lane, ap);
               store_row<V>(pnew, j, xl, c.nx, C.f);
               if (a.store_z) store_row<V>(a.z, j, xl, c.nx, ap);
 #pragma unroll
@@ -264,7 +264,7 @@ __device__ void ir_solve(const IrArgs<TR>& a, Team& tm, double* red, unsigned ch
               auto finish = [&](int j, const unsigned char* sl, const FRow<V, float>& S, const FRow<V, float>& C,
                                 const FRow<V, float>& N) {
                 float ap[V], dv[V], rv[V];
-                stencil_row<V>(S, C, N, wk.lane, ap, c.m1);
+                stencil_row<V>(S, C, N, wk.lane, ap);
                 ring_lane<V, TR>(sl, off[2], false, wk.lane, xl, c.nx, rv);
                 if (!first) ring_lane<V, float>(sl, off[1], false, wk.lane, xl, c.nx, dv);
 #pragma unroll
@@ -314,7 +314,7 @@ __device__ void ir_solve(const IrArgs<TR>& a, Team& tm, double* red, unsigned ch
               auto finish = [&](int j, const D& dd, const FRow<V, float>& S, const FRow<V, float>& C,
                                 const FRow<V, float>& N) {
                 float ap[V], dv[V], rv[V];
-                stencil_row<V>(S, C, N, wk.lane, ap, c.m1);
+                stencil_row<V>(S, C, N, wk.lane, ap);
 #pragma unroll
                 for (int q = 0; q < V; ++q) {
                   dv[q] = first ? __fmul_rn(am, C.f[q]) : fmx(am, C.f[q], dd.d[q]);

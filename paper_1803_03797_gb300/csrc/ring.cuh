@@ -19,6 +19,7 @@ namespace lap5 {
 
 constexpr int kRingMaxVecs = 6;
 constexpr int kRingMaxSlots = 8;
+constexpr uint32_t kSuspendHintNs = 64;  // upper bound on one try_wait suspension
 
 enum { RV_HALO = 1, RV_ALWAYS = 2 };  // stencil operand; also needed on the unit's halo rows
 
@@ -48,7 +49,7 @@ struct WarpRing {
   unsigned char* slots_ptr;
   int S, slot_bytes;
   unsigned q;          // sequence number of the next row to produce / consume
-  unsigned q_issued;   // 1 + the last sequence number produced (lane 0)
+  unsigned q_issued;   // rows produced so far (lane 0)
   int pslot;           // slot of the next produce (lane 0)
   int cslot;           // slot of the next wait
   uint32_t cpar;       // phase parity the next wait expects
@@ -81,49 +82,67 @@ struct WarpRing {
     __syncwarp();
   }
 
-  // Lane 0: issue the copies of one row into slot (seq % S).  Out-of-grid rows
-  // only complete the slot's phase.
+  // Per-unit copy plan: for each vector the byte range of the strip (with its
+  // halo chunks) inside a row, where it lands in the slot, and the bytes an
+  // interior / halo row brings.  Computed once per unit so that producing a
+  // row costs one row-offset multiply-add and one copy instruction per vector.
   template <int V, int K>
-  __device__ __forceinline__ void produce(unsigned seq, int row, int ny, int xs, bool interior,
-                                          const RingVec (&v)[K], const int (&off)[K]) {
+  struct Plan {
+    const unsigned char* src[K];  // base + first byte of the strip's range (row 0)
+    size_t row_bytes[K];          // ld * es
+    uint32_t dst[K];              // shared address offset inside a slot
+    int nb[K];                    // bytes per row (0: not streamed)
+    bool always[K];               // also on the unit's halo rows
+    uint32_t tx_interior, tx_halo;
+  };
+
+  template <int V, int K>
+  __device__ __forceinline__ static void plan(Plan<V, K>& P, int xs, const RingVec (&v)[K], const int (&off)[K]) {
+    P.tx_interior = 0;
+    P.tx_halo = 0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int es = v[k].es;
+      const int hb = (v[k].flags & RV_HALO) ? 16 : 0;  // halo chunk bytes
+      const int xb = xs * es;
+      const int c0 = max(xb - hb, 0);
+      const int c1 = min(xb + 32 * V * es + hb, v[k].ld * es);
+      P.nb[k] = v[k].base ? (c1 - c0) : 0;
+      P.src[k] = v[k].base + c0;
+      P.row_bytes[k] = (size_t)v[k].ld * (size_t)es;
+      P.dst[k] = (uint32_t)(off[k] + c0 - (xb - hb));
+      P.always[k] = (v[k].flags & RV_ALWAYS) != 0;
+      P.tx_interior += (uint32_t)P.nb[k];
+      if (P.always[k]) P.tx_halo += (uint32_t)P.nb[k];
+    }
+  }
+
+  // Lane 0: issue the copies of one row into the next slot (rows are produced
+  // in sequence order).  Out-of-grid rows only complete the slot's phase.
+  template <int V, int K>
+  __device__ __forceinline__ void produce(int row, int ny, bool interior, const Plan<V, K>& P) {
     if ((threadIdx.x & 31) != 0 || failed) return;  // after a failure nothing more is issued
-    // produce() is called in strictly increasing sequence order: the slot
-    // advances by one each call (no division by the runtime S)
     const int s = pslot;
     pslot = (pslot + 1 == S) ? 0 : pslot + 1;
+    ++q_issued;
     const uint32_t bar = bars + 8u * s;
     const uint32_t dst0 = slots + (uint32_t)(s * slot_bytes);
-    q_issued = seq + 1u;
     // the slot's previous contents were read through the generic proxy
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if (row < 0 || row >= ny) {
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
       return;
     }
-    uint32_t tx = 0;
-    int cs[K], nb[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      nb[k] = 0;
-      if (!v[k].base) continue;  // vector not streamed in this pass
-      if (!interior && !(v[k].flags & RV_ALWAYS)) continue;
-      const int h = (v[k].flags & RV_HALO) ? 16 / v[k].es : 0;
-      const int c0 = max(xs - h, 0);
-      const int c1 = min(xs + 32 * V + h, v[k].ld);
-      cs[k] = c0;
-      nb[k] = (c1 - c0) * v[k].es;
-      tx += (uint32_t)nb[k];
-    }
+    const uint32_t tx = interior ? P.tx_interior : P.tx_halo;
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(tx) : "memory");
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      if (nb[k] == 0) continue;
-      const int h = (v[k].flags & RV_HALO) ? 16 / v[k].es : 0;
-      const unsigned char* src = v[k].base + ((size_t)row * (size_t)v[k].ld + (size_t)cs[k]) * (size_t)v[k].es;
-      const uint32_t dst = dst0 + (uint32_t)off[k] + (uint32_t)((cs[k] - (xs - h)) * v[k].es);
+      if (P.nb[k] == 0 || (!interior && !P.always[k])) continue;
+      const unsigned char* src = P.src[k] + (size_t)row * P.row_bytes[k];
       asm volatile(
-          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-          "l"(src), "r"(nb[k]), "r"(bar)
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+              dst0 + P.dst[k]),
+          "l"(src), "r"(P.nb[k]), "r"(bar)
           : "memory");
     }
   }
@@ -144,12 +163,14 @@ struct WarpRing {
       unsigned spins = 0;
       for (;;) {
         uint32_t ok;
+        // a short suspend hint: a row in flight usually lands within a
+        // microsecond, and a long default suspension would outlast it
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
             "selp.u32 %0, 1, 0, p;\n\t}"
             : "=r"(ok)
-            : "r"(bar), "r"(parity)
+            : "r"(bar), "r"(parity), "r"(kSuspendHintNs)
             : "memory");
         if (ok) break;
         if ((++spins & 15u) == 0u && (long long)(global_ns() - t0) > timeout_ns) {
@@ -251,13 +272,15 @@ __device__ __forceinline__ void march_ring(WarpRing& ring, int ny, int xs, int y
   auto row_of = [&](int t) { return ystart + (t - 1) * step; };
   const int total = T + 2;
   const int pre = min(ring.S, total);
-  for (int t = 0; t < pre; ++t) ring.produce<V, K>(q0 + t, row_of(t), ny, xs, t >= 1 && t <= T, vecs, off);
+  typename WarpRing::Plan<V, K> P;
+  WarpRing::plan<V, K>(P, xs, vecs, off);
+  for (int t = 0; t < pre; ++t) ring.produce<V, K>(row_of(t), ny, t >= 1 && t <= T, P);
   FRow<V, M> fB, fC;
   {
     const unsigned char* s0 = ring.wait(q0);
     if (row_of(0) < 0 || row_of(0) >= ny) fB.zero(); else field(row_of(0), s0, fB);
     __syncwarp();
-    if (ring.S < total) ring.produce<V, K>(q0 + ring.S, row_of(ring.S), ny, xs, ring.S <= T, vecs, off);
+    if (ring.S < total) ring.produce<V, K>(row_of(ring.S), ny, ring.S <= T, P);
   }
   const unsigned char* sC = ring.wait(q0 + 1);
   field(row_of(1), sC, fC);
@@ -268,7 +291,7 @@ __device__ __forceinline__ void march_ring(WarpRing& ring, int ny, int xs, int y
     if (!rev) finish(row_of(t), sC, fB, fC, fA);
     else finish(row_of(t), sC, fA, fC, fB);
     __syncwarp();
-    if (t + ring.S < total) ring.produce<V, K>(q0 + t + ring.S, row_of(t + ring.S), ny, xs, t + ring.S <= T, vecs, off);
+    if (t + ring.S < total) ring.produce<V, K>(row_of(t + ring.S), ny, t + ring.S <= T, P);
     fB = fC;
     fC = fA;
     sC = sA;
@@ -286,12 +309,14 @@ __device__ __forceinline__ void stream_ring(WarpRing& ring, int ny, int xs, int 
   const int ystart = rev ? y1 - 1 : y0;
   const unsigned q0 = ring.q;
   const int pre = min(ring.S, T);
-  for (int t = 0; t < pre; ++t) ring.produce<V, K>(q0 + t, ystart + t * step, ny, xs, true, vecs, off);
+  typename WarpRing::Plan<V, K> P;
+  WarpRing::plan<V, K>(P, xs, vecs, off);
+  for (int t = 0; t < pre; ++t) ring.produce<V, K>(ystart + t * step, ny, true, P);
   for (int t = 0; t < T; ++t) {
     const unsigned char* sl = ring.wait(q0 + t);
     finish(ystart + t * step, sl);
     __syncwarp();
-    if (t + ring.S < T) ring.produce<V, K>(q0 + t + ring.S, ystart + (t + ring.S) * step, ny, xs, true, vecs, off);
+    if (t + ring.S < T) ring.produce<V, K>(ystart + (t + ring.S) * step, ny, true, P);
   }
   ring.q = q0 + (unsigned)T;
 }

@@ -8,7 +8,7 @@
 namespace lap5 {
 
 template <class T, int V>
-__global__ void __launch_bounds__(256) k_lap5_apply(int nx, int ny, Grid<const T> x, Grid<T> y, Units un, double m1) {
+__global__ void __launch_bounds__(256) k_lap5_apply(int nx, int ny, Grid<const T> x, Grid<T> y, Units un) {
   using M = typename Math<T>::type;
   struct D { int dummy; };
   const int lane = threadIdx.x & 31;
@@ -28,7 +28,7 @@ __global__ void __launch_bounds__(256) k_lap5_apply(int nx, int ny, Grid<const T
     auto load = [&](int, D&) {};
     auto finish = [&](int j, const D&, const FRow<V, M>& S, const FRow<V, M>& C, const FRow<V, M>& N) {
       M yv[V];
-      stencil_row<V>(S, C, N, lane, yv, m1);
+      stencil_row<V>(S, C, N, lane, yv);
       store_row<V>(y, j, xl, nx, yv);
     };
     march<V, M, D>(y0, y1, false, field, load, finish);
@@ -47,7 +47,7 @@ static int launch_apply(int nx, int ny, int ld, const void* x, void* y, cudaStre
   if (blocks > 65535) blocks = 65535;
   Grid<const T> gx{static_cast<const T*>(x), ld};
   Grid<T> gy{static_cast<T*>(y), ld};
-  k_lap5_apply<T, V><<<blocks, threads, 0, st>>>(nx, ny, gx, gy, un, -1.0);  // m1: see sub_fma
+  k_lap5_apply<T, V><<<blocks, threads, 0, st>>>(nx, ny, gx, gy, un);
   return cudaGetLastError() == cudaSuccess ? LAP5CG_OK : LAP5CG_ERR_CUDA;
 }
 
