@@ -97,8 +97,8 @@ typedef struct {
   int32_t store_z;          /* classic: 1 stores z = A p (fewer FP64 ops), 0 recomputes A p
                                in the update pass (fewer bytes), -1 = choose by precision */
   int32_t ctas;             /* persistent CTAs; 0 = choose from size and occupancy */
-  int32_t warps_per_cta;    /* 4, 8 or 16; 0 = default */
-  int32_t min_rows;         /* minimum rows per warp unit; 0 = default */
+  int32_t warps_per_cta;    /* 1..16; 0 = default (4; batched: 8) */
+  int32_t min_rows;         /* minimum rows per warp unit; 0 = default (2) */
   int32_t true_residual;    /* 1 (default) recompute ||b - A x|| at exit, 0 skip */
   int32_t maxit_inner;      /* IR: inner iteration cap per refinement step; 0 = default */
   int32_t max_outer;        /* IR: refinement step cap; 0 = default (60) */
@@ -111,8 +111,9 @@ typedef struct {
                                cluster: 1, 2, 4, 8 or 16); 0 = default (8).  For batched
                                solves `ctas` caps the total CTAs. */
   int32_t ring_slots;       /* rows each warp keeps in flight in its shared-memory ring
-                               (bulk asynchronous copies): 0 = automatic, 3..8 = that many,
-                               < 0 = no ring (rows loaded straight into registers) */
+                               (bulk asynchronous copies): 0 = automatic (on for binary64 /
+                               binary32 solves whose warp units are at least 8 rows tall),
+                               3..8 = that many, < 0 = no ring (rows loaded into registers) */
 } lap5cg_opts;
 
 /* Fill *o with the defaults above. */

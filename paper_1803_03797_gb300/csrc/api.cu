@@ -32,7 +32,7 @@ int plan_units(const void* func, int nx, int ny, int V, const lap5cg_opts& o, si
   DevProps dp;
   int rc = dev_props(&dp);
   if (rc != LAP5CG_OK) return rc;
-  int wpc = o.warps_per_cta > 0 ? o.warps_per_cta : 8;
+  int wpc = o.warps_per_cta > 0 ? o.warps_per_cta : kDefaultWarps;
   if (wpc > 16) wpc = 16;
   const int threads = 32 * wpc;
   int occ = 0;
@@ -43,7 +43,7 @@ int plan_units(const void* func, int nx, int ny, int V, const lap5cg_opts& o, si
   if (maxctas > kMaxCtas) maxctas = kMaxCtas;
   int ctas = o.ctas > 0 ? (o.ctas < maxctas ? o.ctas : maxctas) : maxctas;
   const long long W = (long long)ctas * wpc;
-  const Units un = make_units(nx, ny, V, W, o.min_rows > 0 ? o.min_rows : 8);
+  const Units un = make_units(nx, ny, V, W, o.min_rows > 0 ? o.min_rows : kDefaultMinRows);
   const long long nunits = un.nunits;
   if (o.ctas <= 0 && nunits < W) ctas = (int)((nunits + wpc - 1) / wpc);
   cfg->ctas = ctas;
@@ -62,9 +62,9 @@ int choose_ring(const void* func, int slot_bytes, const lap5cg_opts& o, RingGeom
   g->warp_bytes = 0;
   *dyn_smem = 0;
   if (o.ring_slots < 0 || (o.ring_slots == 0 && !auto_on)) return LAP5CG_OK;
-  int wpc = o.warps_per_cta > 0 ? o.warps_per_cta : 8;
+  int wpc = o.warps_per_cta > 0 ? o.warps_per_cta : kDefaultWarps;
   if (wpc > 16) wpc = 16;
-  const int budget = 100 * 1024;  // two CTAs of this size fit one SM's 228 KB
+  const int budget = wpc * kRingBytesPerWarp;
   int S;
   if (o.ring_slots > 0) {
     S = o.ring_slots < 3 ? 3 : (o.ring_slots > kRingMaxSlots ? kRingMaxSlots : o.ring_slots);

@@ -299,7 +299,7 @@ int solve_batched(int count, const int* nx, const int* ny, const int* ld, const 
   a.maxit_inner = o.maxit_inner;
   a.tol_inner = o.tol_inner > 0.0 ? o.tol_inner : (kind == KIND_IR_BF16 ? 1e-2 : 1e-4);
 
-  int wpc = o.warps_per_cta > 0 ? o.warps_per_cta : 8;
+  int wpc = o.warps_per_cta > 0 ? o.warps_per_cta : 8;  // batched teams measured best with 8
   if (wpc > 16) wpc = 16;
   int team = o.team_ctas > 0 ? o.team_ctas : 8;
   if (team != 1 && team != 2 && team != 4 && team != 8 && team != 16) return LAP5CG_ERR_INVALID_ARG;

@@ -97,6 +97,14 @@ int solve_typed(const SolvePlan& p, cudaStream_t st) {
                           : reinterpret_cast<const void*>(&k_classic<T, V, false>);
     rc = plan_units(fn, p.nx, p.ny, V, p.opts, dyn, &cfg);
     if (rc != LAP5CG_OK) return rc;
+    if (ring && p.opts.ring_slots == 0 && cfg.seg_rows < kRingMinRows) {  // short units: register march
+      ring = false;
+      rg.S = 0;
+      dyn = 0;
+      fn = reinterpret_cast<const void*>(&k_classic<T, V, false>);
+      rc = plan_units(fn, p.nx, p.ny, V, p.opts, dyn, &cfg);
+      if (rc != LAP5CG_OK) return rc;
+    }
     ClassicArgs<T> a;
     a.c = make_common(p, cfg, rg);
     a.b = Grid<const T>{static_cast<const T*>(p.b), p.ld};
@@ -121,6 +129,14 @@ int solve_typed(const SolvePlan& p, cudaStream_t st) {
                           : reinterpret_cast<const void*>(&k_newcg<T, V, false>);
     rc = plan_units(fn, p.nx, p.ny, V, p.opts, dyn, &cfg);
     if (rc != LAP5CG_OK) return rc;
+    if (ring && p.opts.ring_slots == 0 && cfg.seg_rows < kRingMinRows) {  // short units: register march
+      ring = false;
+      rg.S = 0;
+      dyn = 0;
+      fn = reinterpret_cast<const void*>(&k_newcg<T, V, false>);
+      rc = plan_units(fn, p.nx, p.ny, V, p.opts, dyn, &cfg);
+      if (rc != LAP5CG_OK) return rc;
+    }
     NewcgArgs<T> a;
     a.c = make_common(p, cfg, rg);
     a.b = Grid<const T>{static_cast<const T*>(p.b), p.ld};

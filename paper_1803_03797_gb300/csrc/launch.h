@@ -82,6 +82,12 @@ inline int ring_slot_ir(int V, int es_r) {
   return p > r ? p : r;
 }
 
+// Launch defaults (measured on GB300; the autotuner can override them).
+constexpr int kDefaultWarps = 4;          // warps per CTA
+constexpr int kDefaultMinRows = 2;        // shortest warp unit (rows) on small grids
+constexpr int kRingBytesPerWarp = 12800;  // 16 warps per SM fit 228 KB of shared memory
+constexpr int kRingMinRows = 8;           // automatic ring only for units at least this tall
+
 constexpr size_t kCtlBytes = 256 * 1024;  // control block region at the workspace start
 constexpr size_t kAlign = 256;
 __host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }

@@ -85,3 +85,16 @@ def test_ir_2048_time_to_solution_beats_fp64():
         assert rec["status"] == lap5cg.OK and rec["relres_true"] <= 1.5e-10, (precision, rec)
         times[precision] = e0.elapsed_time(e1)
     assert times["ir_f32"] < times["f64"], times
+
+
+def test_ir_8192_full_size_reaches_1e10():
+    # the 8192 x 8192 mixed-precision workload at full size: FP64 true residual
+    # recomputed by the oracle's stencil on the returned solution
+    n = 8192
+    b_np = gen.uniform_rhs(n, n, seed=3)
+    x, info = lap5cg.cg_solve(_dev(b_np), tol=1e-10, maxit=10 ** 7, precision="ir_f32")
+    rec = lap5cg.decode_info(info)[0]
+    assert rec["status"] == lap5cg.OK and rec["relres_true"] <= 1e-10, rec
+    x_np = x.cpu().numpy()
+    res = b_np - oracle.lap5_apply(x_np)
+    assert np.linalg.norm(res) <= 1.05e-10 * np.linalg.norm(b_np)
