@@ -114,6 +114,11 @@ typedef struct {
                                (bulk asynchronous copies): 0 = automatic (on for binary64 /
                                binary32 solves whose warp units are at least 8 rows tall),
                                3..8 = that many, < 0 = no ring (rows loaded into registers) */
+  int32_t resident;         /* F64 / F32 solves of grids that fit in the shared memory of one
+                               thread-block cluster (about 250 x 250 binary64): 0 = solve them
+                               there (default, when ring_slots == 0 and rr_period == 0),
+                               < 0 = always use the streaming kernels */
+  int32_t pad_;
 } lap5cg_opts;
 
 /* Fill *o with the defaults above. */

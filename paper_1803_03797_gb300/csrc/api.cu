@@ -145,6 +145,8 @@ void lap5cg_opts_default(lap5cg_opts* o) {
   o->history = nullptr;
   o->team_ctas = 0;
   o->ring_slots = 0;
+  o->resident = 0;
+  o->pad_ = 0;
 }
 
 const char* lap5cg_status_string(int status) {
@@ -246,10 +248,15 @@ int cg_solve(int nx, int ny, int ld, const void* b, void* x, double tol, int max
       p.ld = ld;
     }
     int rc;
-    switch (precision) {
-      case LAP5CG_PREC_F64: rc = solve_f64(p, st); break;
-      case LAP5CG_PREC_F32: rc = solve_f32(p, st); break;
-      default: rc = solve_ir(p, st); break;
+    bool done = false;
+    rc = try_small(p, st, &done);  // small grids: one cluster, shared-memory resident
+    if (rc != LAP5CG_OK) return rc;
+    if (!done) {
+      switch (precision) {
+        case LAP5CG_PREC_F64: rc = solve_f64(p, st); break;
+        case LAP5CG_PREC_F32: rc = solve_f32(p, st); break;
+        default: rc = solve_ir(p, st); break;
+      }
     }
     if (rc != LAP5CG_OK) return rc;
     if (stage) {

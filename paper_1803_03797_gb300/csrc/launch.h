@@ -47,6 +47,10 @@ int solve_batched(int count, const int* nx, const int* ny, const int* ld, const 
                   double tol, int maxit, int variant, int precision, void* workspace, size_t ws_bytes,
                   lap5cg_info* info, const lap5cg_opts& o, cudaStream_t st);
 
+// Cluster-resident solve of a small grid (F64 / F32): *used = false when the
+// grid does not fit or the options ask for the streaming kernels.
+int try_small(const SolvePlan& p, cudaStream_t st, bool* used);
+
 int solve_f64(const SolvePlan& p, cudaStream_t st);
 int solve_f32(const SolvePlan& p, cudaStream_t st);
 int solve_ir(const SolvePlan& p, cudaStream_t st);

@@ -39,12 +39,15 @@ def _rel(a, b):
 SHAPES = [(1, 1), (1, 7), (7, 1), (2, 2), (3, 5), (16, 16), (33, 70), (100, 100), (130, 67), (255, 257)]
 
 
+@pytest.mark.parametrize("resident", [0, -1])
 @pytest.mark.parametrize("variant", VARIANTS)
 @pytest.mark.parametrize("nx,ny", SHAPES)
-def test_f64_converged_parity(variant, nx, ny):
+def test_f64_converged_parity(variant, nx, ny, resident):
+    # resident 0: small grids are solved inside one cluster's shared memory;
+    # -1: the streaming kernels
     b = gen.uniform_rhs(nx, ny, seed=nx * 1000 + ny, ld=gen.pitch(nx, 8))
     tol = 1e-10
-    x, info = _solve(b, tol=tol, maxit=20000, variant=variant, nx=nx)
+    x, info = _solve(b, tol=tol, maxit=20000, variant=variant, nx=nx, opts=lap5cg.default_opts(resident=resident))
     xo, io = oracle.cg_solve(b, variant=variant, tol=tol, maxit=20000, nx=nx)
     rec = info[0]
     assert rec["status"] == lap5cg.OK, rec
@@ -59,11 +62,12 @@ def test_f64_converged_parity(variant, nx, ny):
     assert _rel(x[:, :nx], xo[:, :nx]) <= max(kappa * max(tol, io["relres_true"]), 1e-12)
 
 
+@pytest.mark.parametrize("resident", [0, -1])
 @pytest.mark.parametrize("variant", VARIANTS)
 @pytest.mark.parametrize("nx,ny,k", [(100, 100, 1), (100, 100, 7), (100, 100, 40), (257, 130, 25), (65, 64, 30)])
-def test_f64_fixed_iteration_trajectory(variant, nx, ny, k):
+def test_f64_fixed_iteration_trajectory(variant, nx, ny, k, resident):
     b = gen.uniform_rhs(nx, ny, seed=k + nx, ld=gen.pitch(nx, 8))
-    x, info = _solve(b, tol=0.0, maxit=k, variant=variant, nx=nx)
+    x, info = _solve(b, tol=0.0, maxit=k, variant=variant, nx=nx, opts=lap5cg.default_opts(resident=resident))
     xo, io = oracle.cg_solve(b, variant=variant, tol=0.0, maxit=k, nx=nx)
     assert info[0]["iters"] == io["iters"] == k
     assert info[0]["status"] == lap5cg.NOT_CONVERGED
@@ -71,12 +75,13 @@ def test_f64_fixed_iteration_trajectory(variant, nx, ny, k):
     assert abs(info[0]["relres_recursive"] - io["relres_recursive"]) <= 1e-9 * io["relres_recursive"]
 
 
+@pytest.mark.parametrize("resident", [0, -1])
 @pytest.mark.parametrize("variant", VARIANTS)
-def test_residual_history_matches_oracle(variant):
+def test_residual_history_matches_oracle(variant, resident):
     n, K = 100, 120
     b = gen.uniform_rhs(n, n, seed=1)
     hist = torch.full((K + 1,), float("nan"), dtype=torch.float64, device="cuda")
-    opts = lap5cg.default_opts(history=hist.data_ptr())
+    opts = lap5cg.default_opts(history=hist.data_ptr(), resident=resident)
     lap5cg.cg_solve(_dev(b), tol=0.0, maxit=K, variant=variant, opts=opts)
     tr = oracle.Trace(n, n, 1, K, newcg=(variant == "newcg"))
     oracle.cg_solve(b, variant=variant, tol=0.0, maxit=K, trace=tr)
@@ -88,7 +93,7 @@ def test_residual_history_matches_oracle(variant):
 def test_classic_store_z_and_recompute_agree(store_z):
     n = 200
     b = gen.uniform_rhs(n, n, seed=5)
-    x, info = _solve(b, tol=0.0, maxit=60, variant="classic", opts=lap5cg.default_opts(store_z=store_z))
+    x, info = _solve(b, tol=0.0, maxit=60, variant="classic", opts=lap5cg.default_opts(store_z=store_z, resident=-1))
     xo, _ = oracle.cg_classic(b, tol=0.0, maxit=60)
     assert _rel(x, xo) <= 1e-10
 
@@ -97,7 +102,7 @@ def test_classic_store_z_and_recompute_agree(store_z):
 def test_launch_geometries_agree(ctas, warps, min_rows):
     nx, ny = 300, 170
     b = gen.uniform_rhs(nx, ny, seed=9, ld=gen.pitch(nx, 8))
-    opts = lap5cg.default_opts(ctas=ctas, warps_per_cta=warps, min_rows=min_rows)
+    opts = lap5cg.default_opts(ctas=ctas, warps_per_cta=warps, min_rows=min_rows, resident=-1)
     for variant in VARIANTS:
         x, info = _solve(b, tol=0.0, maxit=30, variant=variant, nx=nx, opts=opts)
         xo, _ = oracle.cg_solve(b, variant=variant, tol=0.0, maxit=30, nx=nx)
