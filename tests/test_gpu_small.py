@@ -45,7 +45,7 @@ def test_resident_equals_streaming(variant, nx, ny):
     b = gen.uniform_rhs(nx, ny, seed=nx + ny, ld=gen.pitch(nx, 8))
     xa, ra = _solve(b, nx, tol=0.0, maxit=50, variant=variant)
     xb, rb = _solve(b, nx, tol=0.0, maxit=50, variant=variant, opts=lap5cg.default_opts(resident=-1))
-    assert _rel(xa[:, :nx], xb[:, :nx]) <= 1e-12
+    assert _rel(xa[:, :nx], xb[:, :nx]) <= 1e-10  # dot sums differ in order only
 
 
 @pytest.mark.parametrize("variant", VARIANTS)
