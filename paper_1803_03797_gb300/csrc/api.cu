@@ -28,12 +28,16 @@ int dev_props(DevProps* out) {
   return LAP5CG_OK;
 }
 
+int warps_of(const lap5cg_opts& o) {
+  int wpc = o.warps_per_cta > 0 ? o.warps_per_cta : kDefaultWarps;
+  return wpc > 16 ? 16 : wpc;
+}
+
 int plan_units(const void* func, int nx, int ny, int V, const lap5cg_opts& o, size_t dyn_smem, LaunchCfg* cfg) {
   DevProps dp;
   int rc = dev_props(&dp);
   if (rc != LAP5CG_OK) return rc;
-  int wpc = o.warps_per_cta > 0 ? o.warps_per_cta : kDefaultWarps;
-  if (wpc > 16) wpc = 16;
+  const int wpc = warps_of(o);
   const int threads = 32 * wpc;
   int occ = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, func, threads, dyn_smem) != cudaSuccess)
@@ -56,14 +60,14 @@ int plan_units(const void* func, int nx, int ny, int V, const lap5cg_opts& o, si
   return LAP5CG_OK;
 }
 
-int choose_ring(const void* func, int slot_bytes, const lap5cg_opts& o, RingGeom* g, size_t* dyn_smem, bool auto_on) {
+int choose_ring(const void* func, int slot_bytes, const lap5cg_opts& o, int wpc, RingGeom* g, size_t* dyn_smem,
+                bool auto_on) {
   g->S = 0;
   g->slot_bytes = slot_bytes;
   g->warp_bytes = 0;
   *dyn_smem = 0;
   if (o.ring_slots < 0 || (o.ring_slots == 0 && !auto_on)) return LAP5CG_OK;
-  int wpc = o.warps_per_cta > 0 ? o.warps_per_cta : kDefaultWarps;
-  if (wpc > 16) wpc = 16;
+  if (wpc < 1 || wpc > 16) return LAP5CG_ERR_INVALID_ARG;
   const int budget = wpc * kRingBytesPerWarp;
   int S;
   if (o.ring_slots > 0) {

@@ -282,6 +282,8 @@ int solve_batched(int count, const int* nx, const int* ny, const int* ld, const 
   if (cudaMemsetAsync(bctl, 0, sizeof(BatchCtl), st) != cudaSuccess) return LAP5CG_ERR_CUDA;
   if (cudaMemsetAsync(errs, 0, (size_t)count * sizeof(int), st) != cudaSuccess) return LAP5CG_ERR_CUDA;
 
+  int wpc = o.warps_per_cta > 0 ? o.warps_per_cta : 8;  // batched teams measured best with 8
+  if (wpc > 16) wpc = 16;
   BatchArgs a;
   a.errs = errs;
   a.count = count;
@@ -299,14 +301,13 @@ int solve_batched(int count, const int* nx, const int* ny, const int* ld, const 
   a.maxit_inner = o.maxit_inner;
   a.tol_inner = o.tol_inner > 0.0 ? o.tol_inner : (kind == KIND_IR_BF16 ? 1e-2 : 1e-4);
 
-  int wpc = o.warps_per_cta > 0 ? o.warps_per_cta : 8;  // batched teams measured best with 8
-  if (wpc > 16) wpc = 16;
   int team = o.team_ctas > 0 ? o.team_ctas : 8;
   if (team != 1 && team != 2 && team != 4 && team != 8 && team != 16) return LAP5CG_ERR_INVALID_ARG;
   size_t dyn = 0;
   const bool auto_on = !(kind == KIND_IR_F32 || kind == KIND_IR_BF16);  // as for single solves
-  int rc = choose_ring(kernel_of(kind, true), ring_slot_kind(kind), o, &a.rg, &dyn, auto_on);
+  int rc = choose_ring(kernel_of(kind, true), ring_slot_kind(kind), o, wpc, &a.rg, &dyn, auto_on);
   if (rc != LAP5CG_OK) return rc;
+  if (a.rg.S > 0 && dyn < (size_t)wpc * (size_t)a.rg.warp_bytes) return LAP5CG_ERR_INVALID_ARG;
   const void* fn = kernel_of(kind, a.rg.S > 0);
   if (team > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
     return LAP5CG_ERR_CUDA;

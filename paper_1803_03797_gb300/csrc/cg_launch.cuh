@@ -29,7 +29,7 @@ __global__ void __launch_bounds__(512) k_newcg(const NewcgArgs<T> a) {
 // the register kernel when the ring is off or does not fit.
 inline int pick_ring(const void* fn_ring, int slot_bytes, const lap5cg_opts& o, RingGeom* rg, size_t* dyn,
                      bool* use_ring, bool auto_on = true) {
-  int rc = choose_ring(fn_ring, slot_bytes, o, rg, dyn, auto_on);
+  int rc = choose_ring(fn_ring, slot_bytes, o, warps_of(o), rg, dyn, auto_on);
   if (rc != LAP5CG_OK) return rc;
   *use_ring = rg->S > 0;
   return LAP5CG_OK;
@@ -42,7 +42,10 @@ inline size_t ws_bytes_t(int ny, int ldw, int variant) {
   return kCtlBytes + nvec * vec;
 }
 
-inline int cooperative_launch(const void* func, const LaunchCfg& cfg, void** args, cudaStream_t st) {
+inline int cooperative_launch(const void* func, const LaunchCfg& cfg, void** args, cudaStream_t st,
+                              const RingGeom& rg) {
+  // every warp's ring must lie inside the CTA's dynamic shared memory
+  if (rg.S > 0 && cfg.dyn_smem < (size_t)(cfg.threads / 32) * (size_t)rg.warp_bytes) return LAP5CG_ERR_INVALID_ARG;
   cudaLaunchConfig_t lc = {};
   lc.gridDim = dim3(cfg.ctas);
   lc.blockDim = dim3(cfg.threads);
@@ -117,7 +120,7 @@ int solve_typed(const SolvePlan& p, cudaStream_t st) {
     if (sz < 0) sz = (sizeof(T) == 8) ? 1 : 0;  // binary64 is FP64-pipe bound: trade bytes for DP ops
     a.store_z = sz;
     void* args[] = {&a};
-    return cooperative_launch(fn, cfg, args, st);
+    return cooperative_launch(fn, cfg, args, st, rg);
   } else {
     RingGeom rg;
     size_t dyn = 0;
@@ -149,7 +152,7 @@ int solve_typed(const SolvePlan& p, cudaStream_t st) {
     a.p = Grid<T>{vecp(5), p.ldw};
     a.rr_period = p.opts.rr_period;
     void* args[] = {&a};
-    return cooperative_launch(fn, cfg, args, st);
+    return cooperative_launch(fn, cfg, args, st, rg);
   }
 }
 

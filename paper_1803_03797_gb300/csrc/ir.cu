@@ -64,7 +64,7 @@ static int solve_ir_t(const SolvePlan& p, cudaStream_t st) {
   a.maxit_inner = p.opts.maxit_inner > 0 ? p.opts.maxit_inner : 4 * (p.nx + p.ny) + 50;
   a.tol_inner = p.opts.tol_inner > 0.0 ? p.opts.tol_inner : (sizeof(TR) == 2 ? 1e-2 : 1e-4);
   void* args[] = {&a};
-  return cooperative_launch(fn, cfg, args, st);
+  return cooperative_launch(fn, cfg, args, st, rg);
 }
 
 int solve_ir(const SolvePlan& p, cudaStream_t st) {

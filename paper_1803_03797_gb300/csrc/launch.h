@@ -70,8 +70,13 @@ int plan_units(const void* func, int nx, int ny, int V, const lap5cg_opts& o, si
 // the kernel's dynamic shared memory limit and returns the bytes per CTA
 // (S = 0 and 0 bytes when the ring is off or does not fit).  auto_on: whether
 // ring_slots = 0 (automatic) turns the ring on for this kernel family.
-int choose_ring(const void* func, int slot_bytes, const lap5cg_opts& o, RingGeom* g, size_t* dyn_smem,
+// wpc: the warps per CTA the kernel will be launched with (every warp gets a
+// ring of its own in the dynamic shared memory).
+int choose_ring(const void* func, int slot_bytes, const lap5cg_opts& o, int wpc, RingGeom* g, size_t* dyn_smem,
                 bool auto_on);
+
+// Warps per CTA of the single-grid kernels for these options.
+int warps_of(const lap5cg_opts& o);
 
 // Largest ring slot (bytes) of each kernel family, V = lane vector width.
 inline int ring_slot_classic(int V, int es) {

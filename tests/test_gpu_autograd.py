@@ -34,7 +34,9 @@ def test_dense_gradient_32(variant):
     g_ref = sla.cho_solve(cf, x - flat(xt.cpu().numpy(), n))
     g = flat(b.grad.cpu().numpy(), n)
     kappa = gen.condition_number(n, n)
-    assert np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref) <= kappa * 1e-12
+    # pipelined CG's true residual trails its recursive one (attainable accuracy)
+    bound = kappa * (1e-12 if variant == "classic" else 1e-11)
+    assert np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref) <= bound
     assert abs(loss.item() - 0.5 * np.sum((x - flat(xt.cpu().numpy(), n)) ** 2)) <= 1e-9 * loss.item()
 
 
