@@ -276,9 +276,10 @@ def test_ring_and_register_paths_agree(ring_slots):
 @pytest.mark.parametrize("variant", VARIANTS)
 @pytest.mark.parametrize("nx,ny", [(1, 200000), (200000, 1), (3, 70001)])
 def test_extreme_aspect_ratios(variant, nx, ny):
-    # one-row / one-column grids: many strips or many row segments
+    # one-row / one-column grids: many strips or many row segments.  kappa is
+    # about 3 here, so 20 steps stay well above rounding level
     b = gen.uniform_rhs(nx, ny, seed=nx + ny, ld=gen.pitch(nx, 8))
-    x, info = _solve(b, tol=0.0, maxit=40, variant=variant, nx=nx)
-    xo, io = oracle.cg_solve(b, variant=variant, tol=0.0, maxit=40, nx=nx)
+    x, info = _solve(b, tol=0.0, maxit=20, variant=variant, nx=nx)
+    xo, io = oracle.cg_solve(b, variant=variant, tol=0.0, maxit=20, nx=nx)
     assert info[0]["iters"] == io["iters"]
     assert _rel(x[:, :nx], xo[:, :nx]) <= 1e-10
