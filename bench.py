@@ -55,7 +55,7 @@ def captured_traffic(kernel):
     try:
         d = json.load(open(os.path.join(ROOT, "profiles", "traffic_per_launch.json")))[kernel]
         m = hashlib.sha1()
-        for f in d["files"]:
+        for f in d["files"]:  # the kernel sources the counters were taken from
             m.update(open(os.path.join(ROOT, "paper_1803_03797_gb300", "csrc", f), "rb").read())
         return d["bytes_per_launch"] if m.hexdigest() == d["source_sha1"] else None
     except Exception:

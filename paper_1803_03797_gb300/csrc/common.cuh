@@ -206,12 +206,12 @@ __device__ __forceinline__ void stencil_row(const FRow<V, M>& S, const FRow<V, M
 template <int V, class Acc, class M>
 __device__ __forceinline__ void acc_dot(Acc& acc, const M (&a)[V], const M (&b)[V], int nval) {
   if (nval == V) {
+    acc.add_block(a, b);
+  } else if (nval > 0) {
+    M am[V];
 #pragma unroll
-    for (int k = 0; k < V; ++k) acc.add(a[k], b[k]);
-  } else {
-#pragma unroll
-    for (int k = 0; k < V; ++k)
-      if (k < nval) acc.add(a[k], b[k]);
+    for (int k = 0; k < V; ++k) am[k] = k < nval ? a[k] : M(0);
+    acc.add_block(am, b);
   }
 }
 
@@ -224,6 +224,11 @@ __device__ __forceinline__ void acc_dot(Acc& acc, const M (&a)[V], const M (&b)[
 struct Acc64 {
   double s = 0.0;
   __device__ __forceinline__ void add(double a, double b) { s = __fma_rn(a, b, s); }
+  template <int V>
+  __device__ __forceinline__ void add_block(const double (&a)[V], const double (&b)[V]) {
+#pragma unroll
+    for (int k = 0; k < V; ++k) s = __fma_rn(a[k], b[k], s);
+  }
   __device__ __forceinline__ double value() const { return s; }
 };
 struct Acc32 {
@@ -238,6 +243,21 @@ struct Acc32 {
     const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(x, zz)), __fsub_rn(h, zz));
     s = x;
     c = __fadd_rn(c, __fadd_rn(e, l));
+  }
+  // A lane's V products of one row: summed with fused multiply-adds, and the
+  // partial added to (s, c) with TwoSum.  The compensation then acts between
+  // row blocks; within a block the error is at most (V-1) roundings of the
+  // block's partial sums.  About a quarter of Dot2's instructions per element.
+  template <int V>
+  __device__ __forceinline__ void add_block(const float (&a)[V], const float (&b)[V]) {
+    float p = __fmul_rn(a[0], b[0]);
+#pragma unroll
+    for (int k = 1; k < V; ++k) p = __fmaf_rn(a[k], b[k], p);
+    const float x = __fadd_rn(s, p);
+    const float zz = __fsub_rn(x, s);
+    const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(x, zz)), __fsub_rn(p, zz));
+    s = x;
+    c = __fadd_rn(c, e);
   }
   __device__ __forceinline__ double value() const { return (double)s + (double)c; }
 };
