@@ -61,7 +61,26 @@ template <class T> struct Grid {
 };
 
 // ---------------------------------------------------------------------------
-// Lane-vector IO: a lane owns V consecutive columns x .. x+V-1 of a row.
+// Lane layout of a warp strip of 32*V columns starting at xs.  A lane owns V
+// columns in G = V / W groups of W = min(V, 4) consecutive columns; group g of
+// lane l starts at column xs + 32*W*g + W*l.  With V <= 4 this is one group of
+// V consecutive columns; with V = 8 (binary32) a lane holds two 16-byte
+// vectors 128 columns apart, so every lane-vector access of the warp covers
+// 512 contiguous bytes (conflict-free in shared memory, full sectors in HBM).
+// ---------------------------------------------------------------------------
+template <int V> struct Lanes {
+  static constexpr int W = V > 4 ? 4 : V;
+  static constexpr int G = V / W;
+  static constexpr int GS = 32 * W;  // column distance between a lane's groups
+  // column of the lane's element k relative to its first column
+  __host__ __device__ static constexpr int col(int k) { return (k / W) * GS + (k % W); }
+  // one past the lane's last column relative to its first column
+  static constexpr int span = (G - 1) * GS + W;
+  __host__ __device__ static constexpr int first(int xs, int lane) { return xs + lane * W; }
+};
+
+// ---------------------------------------------------------------------------
+// Lane-vector IO: VecIO<W> moves W consecutive columns x .. x+W-1 of a row.
 // The vector path needs the row start 16-byte aligned for binary64 / binary32
 // (8-byte for bf16 with V = 4) and ld a multiple of V: then a vector that
 // straddles nx stays inside the row's ld elements and is masked after the load.
@@ -121,32 +140,68 @@ template <class T> struct VecIO<1, T> {
 
 // Load the lane's V values of row j; columns >= nx read as 0.  x < ld is
 // guaranteed by the caller (x is a lane column inside an ld-aligned row).
-template <int V, class T, class M>
-__device__ __forceinline__ void load_row(const Grid<T>& g, int j, int x, int nx, M (&v)[V]) {
-  using U = typename std::remove_const<T>::type;
+// Load W consecutive values at p (column x); columns >= nx read as 0.
+template <int W, class U, class M>
+__device__ __forceinline__ void load_group(const U* p, int x, int nx, M (&v)[W]) {
   if (x < nx) {
-    VecIO<V, U>::load(g.row(j) + x, v);
-    if (x + V > nx) {
+    VecIO<W, U>::load(p, v);
+    if (x + W > nx) {
 #pragma unroll
-      for (int k = 0; k < V; ++k)
+      for (int k = 0; k < W; ++k)
         if (x + k >= nx) v[k] = M(0);
     }
   } else {
 #pragma unroll
-    for (int k = 0; k < V; ++k) v[k] = M(0);
+    for (int k = 0; k < W; ++k) v[k] = M(0);
+  }
+}
+
+// Load the lane's V values of row j (lane layout above; x = the lane's first
+// column); columns >= nx read as 0.
+template <int V, class T, class M>
+__device__ __forceinline__ void load_row(const Grid<T>& g, int j, int x, int nx, M (&v)[V]) {
+  using U = typename std::remove_const<T>::type;
+  using L = Lanes<V>;
+  if constexpr (L::G == 1) {
+    load_group<V, U, M>(g.row(j) + x, x, nx, v);
+  } else {
+#pragma unroll
+    for (int gi = 0; gi < L::G; ++gi) {
+      M t[L::W];
+      const int xg = x + gi * L::GS;
+      load_group<L::W, U, M>(g.row(j) + xg, xg, nx, t);
+#pragma unroll
+      for (int k = 0; k < L::W; ++k) v[gi * L::W + k] = t[k];
+    }
   }
 }
 
 // Store the lane's V values of row j; columns >= nx are not written.
+template <int W, class T, class M>
+__device__ __forceinline__ void store_group(T* p, int x, int nx, const M (&v)[W]) {
+  if (x + W <= nx) {
+    VecIO<W, T>::store(p, v);
+  } else if (x < nx) {
+#pragma unroll
+    for (int k = 0; k < W; ++k)
+      if (x + k < nx) p[k] = from_math<T, M>(v[k]);
+  }
+}
+
 template <int V, class T, class M>
 __device__ __forceinline__ void store_row(const Grid<T>& g, int j, int x, int nx, const M (&v)[V]) {
-  if (x + V <= nx) {
-    VecIO<V, T>::store(g.row(j) + x, v);
-  } else if (x < nx) {
-    T* p = g.row(j) + x;
+  using L = Lanes<V>;
+  if constexpr (L::G == 1) {
+    store_group<V, T, M>(g.row(j) + x, x, nx, v);
+  } else {
 #pragma unroll
-    for (int k = 0; k < V; ++k)
-      if (x + k < nx) p[k] = from_math<T, M>(v[k]);
+    for (int gi = 0; gi < L::G; ++gi) {
+      M t[L::W];
+#pragma unroll
+      for (int k = 0; k < L::W; ++k) t[k] = v[gi * L::W + k];
+      const int xg = x + gi * L::GS;
+      store_group<L::W, T, M>(g.row(j) + xg, xg, nx, t);
+    }
   }
 }
 
@@ -184,33 +239,50 @@ __device__ __forceinline__ float shfl_dn1(float v) { return __shfl_down_sync(0xf
 template <int V, class M>
 __device__ __forceinline__ void stencil_row(const FRow<V, M>& S, const FRow<V, M>& C, const FRow<V, M>& N,
                                             int lane, M (&y)[V]) {
-  M left = shfl_up1(C.f[V - 1]);
-  M right = shfl_dn1(C.f[0]);
-  if (lane == 0) left = C.hl;
-  if (lane == 31) right = C.hr;
+  using L = Lanes<V>;
+  constexpr int W = L::W;
 #pragma unroll
-  for (int k = 0; k < V; ++k) {
-    const M w = (k == 0) ? left : C.f[k - 1];
-    const M e = (k == V - 1) ? right : C.f[k + 1];
-    M acc = M(4) * C.f[k];
-    acc -= w;
-    acc -= e;
-    acc -= S.f[k];
-    acc -= N.f[k];
-    y[k] = acc;
+  for (int gi = 0; gi < L::G; ++gi) {
+    M left, right;
+    if constexpr (L::G == 1) {
+      left = shfl_up1(C.f[V - 1]);
+      right = shfl_dn1(C.f[0]);
+    } else {
+      // west of lane 0's group gi is lane 31's group gi-1; east of lane 31's
+      // group gi is lane 0's group gi+1 (rotating shuffles)
+      const M wv = (lane == 31 && gi > 0) ? C.f[gi * W - 1] : C.f[gi * W + W - 1];
+      const M ev = (lane == 0 && gi < L::G - 1) ? C.f[(gi + 1) * W] : C.f[gi * W];
+      left = __shfl_sync(0xffffffffu, wv, (lane + 31) & 31);
+      right = __shfl_sync(0xffffffffu, ev, (lane + 1) & 31);
+    }
+    if (gi == 0 && lane == 0) left = C.hl;
+    if (gi == L::G - 1 && lane == 31) right = C.hr;
+#pragma unroll
+    for (int q = 0; q < W; ++q) {
+      const int k = gi * W + q;
+      const M w = (q == 0) ? left : C.f[k - 1];
+      const M e = (q == W - 1) ? right : C.f[k + 1];
+      M acc = M(4) * C.f[k];
+      acc -= w;
+      acc -= e;
+      acc -= S.f[k];
+      acc -= N.f[k];
+      y[k] = acc;
+    }
   }
 }
 
-// Accumulate (a, b) over the lane's valid elements (the first nval); a single
-// uniform branch for lanes whose V columns are all inside the grid.
+// Accumulate (a, b) over the lane's valid elements: element k is valid when
+// its column offset Lanes<V>::col(k) < ncols (ncols = nx - the lane's first
+// column).  A single uniform branch for lanes whose columns are all inside.
 template <int V, class Acc, class M>
-__device__ __forceinline__ void acc_dot(Acc& acc, const M (&a)[V], const M (&b)[V], int nval) {
-  if (nval == V) {
+__device__ __forceinline__ void acc_dot(Acc& acc, const M (&a)[V], const M (&b)[V], int ncols) {
+  if (ncols >= Lanes<V>::span) {
     acc.add_block(a, b);
-  } else if (nval > 0) {
+  } else if (ncols > 0) {
     M am[V];
 #pragma unroll
-    for (int k = 0; k < V; ++k) am[k] = k < nval ? a[k] : M(0);
+    for (int k = 0; k < V; ++k) am[k] = Lanes<V>::col(k) < ncols ? a[k] : M(0);
     acc.add_block(am, b);
   }
 }
@@ -477,18 +549,16 @@ struct GridTeam {
 };
 
 //  ClusterTeam: the CTAs of one thread-block cluster.  The barrier is the
-//  hardware cluster barrier (release/acquire at cluster scope, plus gpu-scope
-//  fences for the global-memory halos); partial sums move through distributed
-//  shared memory.  No spin-wait, so nothing to time out.
+//  hardware cluster barrier, whose arrive has release and whose wait has
+//  acquire semantics at cluster scope: global-memory halo values written by one
+//  CTA before the barrier are visible to the cluster's other CTAs after it.
+//  Partial sums move through distributed shared memory.  No spin-wait, so
+//  nothing to time out.
 struct ClusterTeam {
   unsigned long long epoch;
   __device__ __forceinline__ int rank() const { return (int)cooperative_groups::this_cluster().block_rank(); }
   __device__ __forceinline__ int size() const { return (int)cooperative_groups::this_cluster().num_blocks(); }
-  __device__ __forceinline__ void barrier() {
-    __threadfence();
-    cooperative_groups::this_cluster().sync();
-    __threadfence();
-  }
+  __device__ __forceinline__ void barrier() { cooperative_groups::this_cluster().sync(); }
   template <int NV>
   __device__ __forceinline__ bool reduce(const double (&v)[NV], double (&out)[NV], double* red) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
