@@ -18,6 +18,7 @@ import math
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -82,7 +83,9 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % index)
+        # the raw samples go to LAP5CG_CLOCKS_DIR when set (kept for inspection), else a temporary folder
+        d = os.environ.get("LAP5CG_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(d, "lap5cg_clocks_rank%d.csv" % index)
 
     def start(self):
         try:
@@ -169,29 +172,35 @@ def fused_f32_roofline(lap5cg, torch, dev, hbm_peak, n=8192, iters=200, reps=3):
     x = torch.zeros_like(b)
     ws = torch.empty(lap5cg.workspace_size(n, n, n, "classic", "f32"), dtype=torch.uint8, device=dev)
     info = torch.empty(lap5cg.INFO_BYTES, dtype=torch.uint8, device=dev)
-    opts = lap5cg.default_opts(true_residual=0)
-
-    def run():
-        lap5cg.cg_solve(b, tol=0.0, maxit=iters, precision="f32", workspace=ws, info=info, out=x, opts=opts)
-
-    run()
-    torch.cuda.synchronize(dev)
-    ms = []
-    for _ in range(reps):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        run()
-        e1.record()
-        torch.cuda.synchronize(dev)
-        ms.append(e0.elapsed_time(e1))
-    t = float(np.median(ms)) * 1e-3
     pts_it = n * n * iters
+
+    def timed(lane_vec):
+        opts = lap5cg.default_opts(true_residual=0, lane_vec=lane_vec)
+
+        def run():
+            lap5cg.cg_solve(b, tol=0.0, maxit=iters, precision="f32", workspace=ws, info=info, out=x, opts=opts)
+
+        run()
+        torch.cuda.synchronize(dev)
+        ms = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            run()
+            e1.record()
+            torch.cuda.synchronize(dev)
+            ms.append(e0.elapsed_time(e1))
+        return float(np.median(ms)) * 1e-3
+
+    t = timed(0)  # the default: eight columns a lane at this width
+    t4 = timed(4)
     gbs = 32 * pts_it / t / 1e9
     del b, x, ws
-    return {"kernel": "k_classic<float,4>", "workload": "%dx%d binary32 classic CG, U[-1,1) (seed 3), %d fixed "
+    return {"kernel": "k_classic<float,8>", "workload": "%dx%d binary32 classic CG, U[-1,1) (seed 3), %d fixed "
             "iterations, A p recomputed" % (n, n, iters), "ms_per_launch": t * 1e3, "pts_iters_per_s": pts_it / t,
             "hbm": {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
-                    "bytes_per_pt_iter": 32}}
+                    "bytes_per_pt_iter": 32},
+            "lane_vec_4": {"ms_per_launch": t4 * 1e3, "hbm_frac": 32 * pts_it / t4 / 1e9 / hbm_peak}}
 
 
 def time_to_solution(lap5cg, torch, dev, n, rhs, tol=1e-10):

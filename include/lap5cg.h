@@ -111,14 +111,20 @@ typedef struct {
                                cluster: 1, 2, 4, 8 or 16); 0 = default (8).  For batched
                                solves `ctas` caps the total CTAs. */
   int32_t ring_slots;       /* rows each warp keeps in flight in its shared-memory ring
-                               (bulk asynchronous copies): 0 = automatic (on for binary64 /
-                               binary32 solves whose warp units are at least 8 rows tall),
+                               (bulk asynchronous copies): 0 = automatic (on when the warp
+                               units are at least 8 rows tall),
                                3..8 = that many, < 0 = no ring (rows loaded into registers) */
   int32_t resident;         /* F64 / F32 solves of grids that fit in the shared memory of one
                                thread-block cluster (about 250 x 250 binary64): 0 = solve them
                                there (default, when ring_slots == 0 and rr_period == 0),
                                < 0 = always use the streaming kernels */
-  int32_t pad_;
+  int32_t lane_vec;         /* cg_solve with binary32 passes (F32 classic; the inner passes of
+                               IR_F32 / IR_BF16PR): columns each lane owns in its warp's strip,
+                               4 or 8; 0 = automatic (8 when nx >= 1024 and the ring is used).
+                               8 needs the classic variant and the shared-memory ring
+                               (ring_slots > 0, or automatic with units at least 8 rows tall),
+                               and store_z <= 0 for IR; otherwise LAP5CG_ERR_UNSUPPORTED.
+                               F64 solves and batched solves ignore it. */
 } lap5cg_opts;
 
 /* Fill *o with the defaults above. */

@@ -17,7 +17,7 @@
  *   ld >= nx; the Dirichlet boundary is implicit zeros, never stored.
  *   A = the paper's 3x3 mask [0 -1 0; -1 4 -1; 0 -1 0] (Sec. II-B), no 1/h^2.
  *
- * Readings of the paper taken here (each one is listed in the design doc):
+ * Readings of the paper taken here:
  *   - stencil add order: acc = 4*xC; acc -= xW; acc -= xE; acc -= xS; acc -= xN
  *     (W = i-1, E = i+1, S = j-1, N = j+1).  The paper fixes only the mask.
  *   - Alg. 2 garbles: "r = r + alpha*s" read as r = r - alpha*q;

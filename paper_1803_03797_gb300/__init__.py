@@ -48,7 +48,7 @@ class Opts(ctypes.Structure):
                 ("true_residual", ctypes.c_int32), ("maxit_inner", ctypes.c_int32),
                 ("max_outer", ctypes.c_int32), ("tol_inner", ctypes.c_double), ("timeout_s", ctypes.c_double),
                 ("history", ctypes.c_void_p), ("team_ctas", ctypes.c_int32), ("ring_slots", ctypes.c_int32),
-                ("resident", ctypes.c_int32), ("pad_", ctypes.c_int32)]
+                ("resident", ctypes.c_int32), ("lane_vec", ctypes.c_int32)]
 
 
 _lib = None
@@ -281,7 +281,7 @@ def cg_solve_classic_f64_noalloc(b: torch.Tensor, x0: torch.Tensor = None, tol: 
 # results are cached in a JSON file keyed by GPU name, precision, variant and
 # a size class (powers of two of the grid sides).
 # ---------------------------------------------------------------------------
-_OPT_FIELDS = ("warps_per_cta", "ring_slots", "min_rows", "store_z", "team_ctas", "ctas", "resident")
+_OPT_FIELDS = ("warps_per_cta", "ring_slots", "min_rows", "store_z", "team_ctas", "ctas", "resident", "lane_vec")
 
 
 def _cache_path():

@@ -150,7 +150,7 @@ void lap5cg_opts_default(lap5cg_opts* o) {
   o->team_ctas = 0;
   o->ring_slots = 0;
   o->resident = 0;
-  o->pad_ = 0;
+  o->lane_vec = 0;
 }
 
 const char* lap5cg_status_string(int status) {
@@ -199,7 +199,8 @@ int cg_solve(int nx, int ny, int ld, const void* b, void* x, double tol, int max
   if (opts) o = *opts;
   else lap5cg_opts_default(&o);
   if (o.rr_period < 0 || o.warps_per_cta < 0 || o.warps_per_cta > 16 || o.ctas < 0 || o.min_rows < 0 ||
-      o.maxit_inner < 0 || o.max_outer < 0 || o.ring_slots > kRingMaxSlots)
+      o.maxit_inner < 0 || o.max_outer < 0 || o.ring_slots > kRingMaxSlots ||
+      (o.lane_vec != 0 && o.lane_vec != 4 && o.lane_vec != 8))
     return LAP5CG_ERR_INVALID_ARG;
   if (o.rr_period > 0 && variant != LAP5CG_NEWCG) return LAP5CG_ERR_INVALID_ARG;
   const size_t need = cg_workspace_size(nx, ny, ld, variant, precision, nrhs);

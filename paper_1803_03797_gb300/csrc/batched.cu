@@ -151,7 +151,8 @@ __device__ __forceinline__ void solve_instance(const BatchArgs& a, const BatchEn
     s.max_outer = a.max_outer;
     s.maxit_inner = a.maxit_inner > 0 ? a.maxit_inner : 4 * (e.nx + e.ny) + 50;
     s.tol_inner = a.tol_inner;
-    ir_solve<T, V, R>(s, tm, red, dsm);
+    s.uo = c.un;
+    ir_solve<T, V, V, R>(s, tm, red, dsm);
   }
 }
 

@@ -111,8 +111,8 @@ __device__ __forceinline__ void pass_residual(const SolveCommon& c, Walker& wk, 
   for (int u = wk.gw; u < c.un.nunits; u += wk.nw) {
     int s, y0, y1;
     unit_bounds(c.un, u, c.ny, s, y0, y1);
-    const int xs = s * 32 * V, xl = xs + wk.lane * V;
-    const int nval = min(max(c.nx - xl, 0), V);
+    const int xs = s * 32 * V, xl = Lanes<V>::first(xs, wk.lane);
+    const int nval = c.nx - xl;  // columns from xl to the grid edge
     auto field = [&](int j, FRow<V, M>& f) { field_plain<V>(x, c.nx, c.ny, j, xl, xs, wk.lane, f); };
     auto load = [&](int j, D& d) { load_row<V>(b, j, xl, c.nx, d.b); };
     auto finish = [&](int j, const D& d, const FRow<V, M>& S, const FRow<V, M>& C, const FRow<V, M>& N) {
@@ -121,7 +121,7 @@ __device__ __forceinline__ void pass_residual(const SolveCommon& c, Walker& wk, 
 #pragma unroll
       for (int k = 0; k < V; ++k) {
         rv[k] = d.b[k] - ax[k];
-        if (k < nval) { abb.add(d.b[k], d.b[k]); arr.add(rv[k], rv[k]); }
+        if (Lanes<V>::col(k) < nval) { abb.add(d.b[k], d.b[k]); arr.add(rv[k], rv[k]); }
       }
       if (r.ptr) store_row<V>(r, j, xl, c.nx, rv);
     };
@@ -132,12 +132,12 @@ __device__ __forceinline__ void pass_residual(const SolveCommon& c, Walker& wk, 
 
 // x = 0 over the interior (b = 0 case).
 template <int V, class TX>
-__device__ __forceinline__ void pass_zero(const SolveCommon& c, Walker& wk, const Grid<TX>& x) {
+__device__ __forceinline__ void pass_zero(const SolveCommon& c, const Units& un, Walker& wk, const Grid<TX>& x) {
   using M = typename Math<TX>::type;
-  for (int u = wk.gw; u < c.un.nunits; u += wk.nw) {
+  for (int u = wk.gw; u < un.nunits; u += wk.nw) {
     int s, y0, y1;
-    unit_bounds(c.un, u, c.ny, s, y0, y1);
-    const int xl = s * 32 * V + wk.lane * V;
+    unit_bounds(un, u, c.ny, s, y0, y1);
+    const int xl = Lanes<V>::first(s * 32 * V, wk.lane);
     M zv[V];
 #pragma unroll
     for (int k = 0; k < V; ++k) zv[k] = M(0);
@@ -191,7 +191,7 @@ __device__ void classic_solve(const ClassicArgs<T>& a, Team& tm, double* red, un
   }
   if (!isfinite(bb)) { status = LAP5CG_ERR_NONFINITE; relres_true = nan(""); goto done; }
   if (bb == 0.0) {
-    pass_zero<V>(c, wk, a.x);
+    pass_zero<V>(c, c.un, wk, a.x);
     status = LAP5CG_OK;
     gamma = 0.0;
     relres_true = 0.0;
@@ -232,8 +232,8 @@ __device__ void classic_solve(const ClassicArgs<T>& a, Team& tm, double* red, un
           for (int u = wk.gw; u < c.un.nunits; u += wk.nw) {
             int s, y0, y1;
             unit_bounds(c.un, u, c.ny, s, y0, y1);
-            const int xs = s * 32 * V, xl = xs + wk.lane * V;
-            const int nval = min(max(c.nx - xl, 0), V);
+            const int xs = s * 32 * V, xl = Lanes<V>::first(xs, wk.lane);
+            const int nval = c.nx - xl;  // columns from xl to the grid edge
             auto field = [&](int j, const unsigned char* sl, FRow<V, M>& f) {
               M rv[V];
               ring_lane<V, T>(sl, off[0], true, wk.lane, xl, c.nx, rv);
@@ -273,8 +273,8 @@ __device__ void classic_solve(const ClassicArgs<T>& a, Team& tm, double* red, un
         for (int u = wk.gw; u < c.un.nunits; u += wk.nw) {
           int s, y0, y1;
           unit_bounds(c.un, u, c.ny, s, y0, y1);
-          const int xs = s * 32 * V, xl = xs + wk.lane * V;
-          const int nval = min(max(c.nx - xl, 0), V);
+          const int xs = s * 32 * V, xl = Lanes<V>::first(xs, wk.lane);
+          const int nval = c.nx - xl;  // columns from xl to the grid edge
           auto field = [&](int j, FRow<V, M>& f) {
             if (j < 0 || j >= c.ny) { f.zero(); return; }
             M rv[V];
@@ -310,9 +310,7 @@ __device__ void classic_solve(const ClassicArgs<T>& a, Team& tm, double* red, un
             stencil_row<V>(S, C, N, wk.lane, ap);
             store_row<V>(pnew, j, xl, c.nx, C.f);
             if (a.store_z) store_row<V>(a.z, j, xl, c.nx, ap);
-#pragma unroll
-            for (int k = 0; k < V; ++k)
-              if (k < nval) acc.add(C.f[k], ap[k]);
+            acc_dot<V>(acc, C.f, ap, nval);
           };
           march<V, M, D>(y0, y1, wk.rev(), field, load, finish);
         }
@@ -336,8 +334,8 @@ __device__ void classic_solve(const ClassicArgs<T>& a, Team& tm, double* red, un
             for (int u = wk.gw; u < c.un.nunits; u += wk.nw) {
               int s, y0, y1;
               unit_bounds(c.un, u, c.ny, s, y0, y1);
-              const int xs = s * 32 * V, xl = xs + wk.lane * V;
-              const int nval = min(max(c.nx - xl, 0), V);
+              const int xs = s * 32 * V, xl = Lanes<V>::first(xs, wk.lane);
+              const int nval = c.nx - xl;  // columns from xl to the grid edge
               auto finish = [&](int j, const unsigned char* sl) {
                 M rv[V], zv[V];
                 ring_lane<V, T>(sl, off[0], false, wk.lane, xl, c.nx, rv);
@@ -359,8 +357,8 @@ __device__ void classic_solve(const ClassicArgs<T>& a, Team& tm, double* red, un
             for (int u = wk.gw; u < c.un.nunits; u += wk.nw) {
               int s, y0, y1;
               unit_bounds(c.un, u, c.ny, s, y0, y1);
-              const int xs = s * 32 * V, xl = xs + wk.lane * V;
-              const int nval = min(max(c.nx - xl, 0), V);
+              const int xs = s * 32 * V, xl = Lanes<V>::first(xs, wk.lane);
+              const int nval = c.nx - xl;  // columns from xl to the grid edge
               auto field = [&](int, const unsigned char* sl, FRow<V, M>& f) {
                 ring_lane<V, T>(sl, off[0], true, wk.lane, xl, c.nx, f.f);
                 f.hl = ring_halo<V, T, M>(sl, off[0], wk.lane, xs, c.nx);
@@ -388,8 +386,8 @@ __device__ void classic_solve(const ClassicArgs<T>& a, Team& tm, double* red, un
         for (int u = wk.gw; u < c.un.nunits; u += wk.nw) {
           int s, y0, y1;
           unit_bounds(c.un, u, c.ny, s, y0, y1);
-          const int xs = s * 32 * V, xl = xs + wk.lane * V;
-          const int nval = min(max(c.nx - xl, 0), V);
+          const int xs = s * 32 * V, xl = Lanes<V>::first(xs, wk.lane);
+          const int nval = c.nx - xl;  // columns from xl to the grid edge
           if (a.store_z) {
             struct D { M r[V], z[V]; };
             auto load = [&](int j, D& d) {
@@ -399,10 +397,8 @@ __device__ void classic_solve(const ClassicArgs<T>& a, Team& tm, double* red, un
             auto finish = [&](int j, const D& d) {
               M rv[V];
 #pragma unroll
-              for (int k = 0; k < V; ++k) {
-                rv[k] = fmx(-am, d.z[k], d.r[k]);
-                if (k < nval) acc.add(rv[k], rv[k]);
-              }
+              for (int k = 0; k < V; ++k) rv[k] = fmx(-am, d.z[k], d.r[k]);
+              acc_dot<V>(acc, rv, rv, nval);
               store_row<V>(a.r, j, xl, c.nx, rv);
             };
             stream_rows<D>(y0, y1, wk.rev(), load, finish);
@@ -420,8 +416,8 @@ __device__ void classic_solve(const ClassicArgs<T>& a, Team& tm, double* red, un
               for (int k = 0; k < V; ++k) {
                 xv[k] = fmx(am, C.f[k], d.x[k]);
                 rv[k] = fmx(-am, ap[k], d.r[k]);
-                if (k < nval) acc.add(rv[k], rv[k]);
               }
+              acc_dot<V>(acc, rv, rv, nval);
               store_row<V>(a.x, j, xl, c.nx, xv);
               store_row<V>(a.r, j, xl, c.nx, rv);
             };
@@ -453,7 +449,7 @@ finalx:
     for (int u = wk.gw; u < c.un.nunits; u += wk.nw) {
       int s, y0, y1;
       unit_bounds(c.un, u, c.ny, s, y0, y1);
-      const int xl = s * 32 * V + wk.lane * V;
+      const int xl = Lanes<V>::first(s * 32 * V, wk.lane);
       struct D { M x[V], p[V]; };
       auto load = [&](int j, D& d) {
         load_row<V>(a.x, j, xl, c.nx, d.x);
@@ -515,7 +511,7 @@ __device__ __forceinline__ void pass_apply(const SolveCommon& c, Walker& wk, con
   for (int u = wk.gw; u < c.un.nunits; u += wk.nw) {
     int s, y0, y1;
     unit_bounds(c.un, u, c.ny, s, y0, y1);
-    const int xs = s * 32 * V, xl = xs + wk.lane * V;
+    const int xs = s * 32 * V, xl = Lanes<V>::first(xs, wk.lane);
     auto field = [&](int j, FRow<V, M>& f) { field_plain<V>(g, c.nx, c.ny, j, xl, xs, wk.lane, f); };
     auto load = [&](int, D&) {};
     auto finish = [&](int j, const D&, const FRow<V, M>& S, const FRow<V, M>& C, const FRow<V, M>& N) {
@@ -538,17 +534,16 @@ __device__ __forceinline__ void pass_w_from_r(const SolveCommon& c, Walker& wk, 
   for (int u = wk.gw; u < c.un.nunits; u += wk.nw) {
     int s, y0, y1;
     unit_bounds(c.un, u, c.ny, s, y0, y1);
-    const int xs = s * 32 * V, xl = xs + wk.lane * V;
-    const int nval = min(max(c.nx - xl, 0), V);
+    const int xs = s * 32 * V, xl = Lanes<V>::first(xs, wk.lane);
+    const int nval = c.nx - xl;  // columns from xl to the grid edge
     auto field = [&](int j, FRow<V, M>& f) { field_plain<V>(r, c.nx, c.ny, j, xl, xs, wk.lane, f); };
     auto load = [&](int, D&) {};
     auto finish = [&](int j, const D&, const FRow<V, M>& S, const FRow<V, M>& C, const FRow<V, M>& N) {
       M wv[V];
       stencil_row<V>(S, C, N, wk.lane, wv);
       store_row<V>(w, j, xl, c.nx, wv);
-#pragma unroll
-      for (int k = 0; k < V; ++k)
-        if (k < nval) { ag.add(C.f[k], C.f[k]); ad.add(wv[k], C.f[k]); }
+      acc_dot<V>(ag, C.f, C.f, nval);
+      acc_dot<V>(ad, wv, C.f, nval);
     };
     march<V, M, D>(y0, y1, wk.rev(), field, load, finish);
   }
@@ -579,7 +574,7 @@ __device__ void newcg_solve(const NewcgArgs<T>& a, Team& tm, double* red, unsign
   }
   if (!isfinite(bb)) { status = LAP5CG_ERR_NONFINITE; goto done; }
   if (bb == 0.0) {
-    pass_zero<V>(c, wk, a.x);
+    pass_zero<V>(c, c.un, wk, a.x);
     status = LAP5CG_OK;
     relres_true = 0.0;
     goto done;
@@ -625,8 +620,8 @@ __device__ void newcg_solve(const NewcgArgs<T>& a, Team& tm, double* red, unsign
         for (int u = wk.gw; u < c.un.nunits; u += wk.nw) {
           int s, y0, y1;
           unit_bounds(c.un, u, c.ny, s, y0, y1);
-          const int xs = s * 32 * V, xl = xs + wk.lane * V;
-          const int nval = min(max(c.nx - xl, 0), V);
+          const int xs = s * 32 * V, xl = Lanes<V>::first(xs, wk.lane);
+          const int nval = c.nx - xl;  // columns from xl to the grid edge
           auto field = [&](int, const unsigned char* sl, FRow<V, M>& f) {
             ring_lane<V, T>(sl, off[0], true, wk.lane, xl, c.nx, f.f);
             f.hl = ring_halo<V, T, M>(sl, off[0], wk.lane, xs, c.nx);
@@ -673,8 +668,8 @@ __device__ void newcg_solve(const NewcgArgs<T>& a, Team& tm, double* red, unsign
       for (int u = wk.gw; u < c.un.nunits; u += wk.nw) {
         int s, y0, y1;
         unit_bounds(c.un, u, c.ny, s, y0, y1);
-        const int xs = s * 32 * V, xl = xs + wk.lane * V;
-        const int nval = min(max(c.nx - xl, 0), V);
+        const int xs = s * 32 * V, xl = Lanes<V>::first(xs, wk.lane);
+        const int nval = c.nx - xl;  // columns from xl to the grid edge
         auto field = [&](int j, FRow<V, M>& f) { field_plain<V>(w, c.nx, c.ny, j, xl, xs, wk.lane, f); };
         auto load = [&](int j, D& d) {
           if (!first) {
@@ -702,8 +697,9 @@ __device__ void newcg_solve(const NewcgArgs<T>& a, Team& tm, double* red, unsign
             xv[k] = fmx(am, pv[k], d.x[k]);
             rv[k] = fmx(-am, qv[k], d.r[k]);
             wv[k] = fmx(-am, zv[k], C.f[k]);
-            if (k < nval) { ag.add(rv[k], rv[k]); ad.add(wv[k], rv[k]); }
           }
+          acc_dot<V>(ag, rv, rv, nval);
+          acc_dot<V>(ad, wv, rv, nval);
           store_row<V>(a.z, j, xl, c.nx, zv);
           store_row<V>(a.q, j, xl, c.nx, qv);
           store_row<V>(a.p, j, xl, c.nx, pv);

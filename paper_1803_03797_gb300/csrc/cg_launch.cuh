@@ -101,6 +101,7 @@ int solve_typed(const SolvePlan& p, cudaStream_t st) {
     rc = plan_units(fn, p.nx, p.ny, V, p.opts, dyn, &cfg);
     if (rc != LAP5CG_OK) return rc;
     if (ring && p.opts.ring_slots == 0 && cfg.seg_rows < kRingMinRows) {  // short units: register march
+      if constexpr (Lanes<V>::G > 1) return LAP5CG_ERR_UNSUPPORTED;  // the caller narrows the lane vector
       ring = false;
       rg.S = 0;
       dyn = 0;
@@ -121,6 +122,8 @@ int solve_typed(const SolvePlan& p, cudaStream_t st) {
     a.store_z = sz;
     void* args[] = {&a};
     return cooperative_launch(fn, cfg, args, st, rg);
+  } else if constexpr (Lanes<V>::G > 1) {
+    return LAP5CG_ERR_UNSUPPORTED;  // NewCG keeps six vectors live: one group per lane
   } else {
     RingGeom rg;
     size_t dyn = 0;

@@ -96,6 +96,24 @@ template <> struct VecIO<2, double> {
     *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
   }
 };
+template <> struct VecIO<2, float> {
+  __device__ __forceinline__ static void load(const float* p, float (&v)[2]) {
+    float2 t = *reinterpret_cast<const float2*>(p);
+    v[0] = t.x; v[1] = t.y;
+  }
+  __device__ __forceinline__ static void store(float* p, const float (&v)[2]) {
+    *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+  }
+};
+template <> struct VecIO<2, bf16s> {
+  __device__ __forceinline__ static void load(const bf16s* p, float (&v)[2]) {
+    const uint32_t t = *reinterpret_cast<const uint32_t*>(p);
+    v[0] = __uint_as_float(t << 16); v[1] = __uint_as_float(t & 0xffff0000u);
+  }
+  __device__ __forceinline__ static void store(bf16s* p, const float (&v)[2]) {
+    *reinterpret_cast<uint32_t*>(p) = (uint32_t)bf_narrow(v[0]) | ((uint32_t)bf_narrow(v[1]) << 16);
+  }
+};
 template <> struct VecIO<4, float> {
   __device__ __forceinline__ static void load(const float* p, float (&v)[4]) {
     float4 t = *reinterpret_cast<const float4*>(p);

@@ -6,12 +6,16 @@
 
 namespace lap5 {
 
+// Outer (binary64) passes move two columns a lane: their b, x and field rows
+// then fit the register budget that the inner passes need.
+constexpr int kOuterVec = 2;
+
 template <class TR, int V, bool R>
 __global__ void __launch_bounds__(512) k_ir(const IrArgs<TR> a) {
   __shared__ double red[kRedDoubles];
   extern __shared__ __align__(128) unsigned char dsm[];
   GridTeam tm{a.c.ctl, a.c.timeout_ns, 0ull};
-  ir_solve<TR, V, R>(a, tm, red, dsm);
+  ir_solve<TR, V, kOuterVec, R>(a, tm, red, dsm);
 }
 
 static int inner_ld(int nx) { return (nx + 7) / 8 * 8; }
@@ -29,9 +33,8 @@ size_t ws_bytes_ir(int nx, int ny, int variant, int precision) {
   return 0;
 }
 
-template <class TR>
+template <class TR, int V>
 static int solve_ir_t(const SolvePlan& p, cudaStream_t st) {
-  constexpr int V = 4;
   const int ldi = inner_ld(p.nx);
   const size_t vr = align_up((size_t)p.ny * ldi * sizeof(TR), kAlign);
   const size_t vf = align_up((size_t)p.ny * ldi * 4, kAlign);
@@ -41,17 +44,29 @@ static int solve_ir_t(const SolvePlan& p, cudaStream_t st) {
   RingGeom rg;
   size_t dyn = 0;
   bool ring = false;
-  // automatic choice: register march (measured faster for these kernels,
-  // whose FP64 outer passes set the register budget); ring_slots > 0 forces the ring
   int rc = pick_ring(reinterpret_cast<const void*>(&k_ir<TR, V, true>), ring_slot_ir(V, (int)sizeof(TR)), p.opts,
-                     &rg, &dyn, &ring, false);
+                     &rg, &dyn, &ring);
   if (rc != LAP5CG_OK) return rc;
+  if constexpr (Lanes<V>::G > 1) {
+    if (!ring) return LAP5CG_ERR_UNSUPPORTED;  // eight columns a lane exist with the ring only
+  }
   const void* fn = ring ? reinterpret_cast<const void*>(&k_ir<TR, V, true>)
                         : reinterpret_cast<const void*>(&k_ir<TR, V, false>);
   rc = plan_units(fn, p.nx, p.ny, V, p.opts, dyn, &cfg);
   if (rc != LAP5CG_OK) return rc;
+  if (ring && p.opts.ring_slots == 0 && cfg.seg_rows < kRingMinRows) {  // short units: register march
+    if constexpr (Lanes<V>::G > 1) return LAP5CG_ERR_UNSUPPORTED;      // the caller narrows the lane vector
+    ring = false;
+    rg.S = 0;
+    dyn = 0;
+    fn = reinterpret_cast<const void*>(&k_ir<TR, V, false>);
+    rc = plan_units(fn, p.nx, p.ny, V, p.opts, dyn, &cfg);
+    if (rc != LAP5CG_OK) return rc;
+  }
   IrArgs<TR> a;
   a.c = make_common(p, cfg, rg);
+  a.uo = make_units(p.nx, p.ny, kOuterVec, (long long)cfg.ctas * (cfg.threads / 32),
+                    p.opts.min_rows > 0 ? p.opts.min_rows : kDefaultMinRows);
   a.b = Grid<const double>{static_cast<const double*>(p.b), p.ld};
   a.x = Grid<double>{static_cast<double*>(p.x), p.ld};
   a.r = Grid<TR>{reinterpret_cast<TR*>(base), ldi};
@@ -67,10 +82,23 @@ static int solve_ir_t(const SolvePlan& p, cudaStream_t st) {
   return cooperative_launch(fn, cfg, args, st, rg);
 }
 
+// Inner lane vector: eight columns (ring kernel) on wide grids, as for the
+// binary32 solve; four with the register march.
+template <class TR>
+static int solve_ir_lanes(const SolvePlan& p, cudaStream_t st) {
+  const bool v8_ok = p.opts.ring_slots >= 0 && p.opts.store_z <= 0;
+  if (p.opts.lane_vec == 8) return v8_ok ? solve_ir_t<TR, 8>(p, st) : LAP5CG_ERR_UNSUPPORTED;
+  if (p.opts.lane_vec == 0 && v8_ok && p.nx >= 1024) {
+    const int rc = solve_ir_t<TR, 8>(p, st);
+    if (rc != LAP5CG_ERR_UNSUPPORTED) return rc;
+  }
+  return solve_ir_t<TR, 4>(p, st);
+}
+
 int solve_ir(const SolvePlan& p, cudaStream_t st) {
   if (p.variant != LAP5CG_CLASSIC) return LAP5CG_ERR_UNSUPPORTED;
-  if (p.precision == LAP5CG_PREC_IR_F32) return solve_ir_t<float>(p, st);
-  if (p.precision == LAP5CG_PREC_IR_BF16PR) return solve_ir_t<bf16s>(p, st);
+  if (p.precision == LAP5CG_PREC_IR_F32) return solve_ir_lanes<float>(p, st);
+  if (p.precision == LAP5CG_PREC_IR_BF16PR) return solve_ir_lanes<bf16s>(p, st);
   return LAP5CG_ERR_INVALID_ARG;
 }
 

@@ -24,13 +24,17 @@ struct IrArgs {
   Grid<double> x;
   Grid<TR> r, p0, p1;            // inner r and p (binary32 or bf16)
   Grid<float> z, d;              // inner A p (stored form) and correction d
+  Units uo;                      // warp units of the outer passes (lane vector VO)
   int store_z;
   int max_outer;
   int maxit_inner;
   double tol_inner;
 };
 
-template <class TR, int V, bool R, class Team>
+// V: lane vector of the inner passes (c.un); VO: lane vector of the binary64
+// outer passes (a.uo).  Grid barriers separate every pass, so the two unit
+// decompositions never touch the same data concurrently.
+template <class TR, int V, int VO, bool R, class Team>
 __device__ void ir_solve(const IrArgs<TR>& a, Team& tm, double* red, unsigned char* dsm) {
   using Acc = Acc32;
   const SolveCommon& c = a.c;
@@ -39,6 +43,9 @@ __device__ void ir_solve(const IrArgs<TR>& a, Team& tm, double* red, unsigned ch
   WarpRing ring;
   ring_setup(ring, c, dsm);
   constexpr int ES = (int)sizeof(TR);
+  // A p stored (zs) only with four columns a lane: the stored form's register
+  // march would not fit the register budget with eight
+  const int zs = Lanes<V>::G > 1 ? 0 : a.store_z;
 
   int status = LAP5CG_NOT_CONVERGED, total = 0, outer = 0;
   double bb = 0.0, rr = 0.0, rr_prev = 0.0, relres_true = nan("");
@@ -47,26 +54,27 @@ __device__ void ir_solve(const IrArgs<TR>& a, Team& tm, double* red, unsigned ch
 
   for (;;) {
     // ---------------- outer passes (binary64) ----------------
-    // x <- x + d touches only a warp's own points (d there was written by the
-    // same warp), but the residual pass reads x at halo points, so the update
-    // is a pass of its own followed by a grid barrier: updating x inside the
-    // stencil pass would let a neighbour read an already-updated halo value.
+    // x <- x + d is element-wise, but the residual pass reads x at halo
+    // points, so the update is a pass of its own followed by a grid barrier:
+    // updating x inside the stencil pass would let a neighbour read an
+    // already-updated halo value.  (d was published by the barrier that ended
+    // the last inner pass.)
     if (have_d) {
       const double sgn = reverting ? -1.0 : 1.0;  // x - d undoes a rejected correction
-      struct DU { double x[V]; float d[V]; };
-      for (int u = wk.gw; u < c.un.nunits; u += wk.nw) {
+      struct DU { double x[VO]; float d[VO]; };
+      for (int u = wk.gw; u < a.uo.nunits; u += wk.nw) {
         int s, y0, y1;
-        unit_bounds(c.un, u, c.ny, s, y0, y1);
-        const int xl = s * 32 * V + wk.lane * V;
+        unit_bounds(a.uo, u, c.ny, s, y0, y1);
+        const int xl = Lanes<VO>::first(s * 32 * VO, wk.lane);
         auto load = [&](int j, DU& dd) {
-          load_row<V>(a.x, j, xl, c.nx, dd.x);
-          load_row<V>(a.d, j, xl, c.nx, dd.d);
+          load_row<VO>(a.x, j, xl, c.nx, dd.x);
+          load_row<VO>(a.d, j, xl, c.nx, dd.d);
         };
         auto finish = [&](int j, const DU& dd) {
-          double xv[V];
+          double xv[VO];
 #pragma unroll
-          for (int k = 0; k < V; ++k) xv[k] = dd.x[k] + sgn * (double)dd.d[k];
-          store_row<V>(a.x, j, xl, c.nx, xv);
+          for (int k = 0; k < VO; ++k) xv[k] = dd.x[k] + sgn * (double)dd.d[k];
+          store_row<VO>(a.x, j, xl, c.nx, xv);
         };
         stream_rows<DU>(y0, y1, wk.rev(), load, finish);
       }
@@ -77,32 +85,32 @@ __device__ void ir_solve(const IrArgs<TR>& a, Team& tm, double* red, unsigned ch
     {
       Acc64 abb, arr;
       Acc32 agi;
-      struct D { double b[V]; };
-      for (int u = wk.gw; u < c.un.nunits; u += wk.nw) {
+      struct D { double b[VO]; };
+      for (int u = wk.gw; u < a.uo.nunits; u += wk.nw) {
         int s, y0, y1;
-        unit_bounds(c.un, u, c.ny, s, y0, y1);
-        const int xs = s * 32 * V, xl = xs + wk.lane * V;
-        const int nval = min(max(c.nx - xl, 0), V);
-        auto field = [&](int j, FRow<V, double>& f) { field_plain<V>(a.x, c.nx, c.ny, j, xl, xs, wk.lane, f); };
-        auto load = [&](int j, D& dd) { load_row<V>(a.b, j, xl, c.nx, dd.b); };
-        auto finish = [&](int j, const D& dd, const FRow<V, double>& S, const FRow<V, double>& C,
-                          const FRow<V, double>& N) {
-          double ax[V];
-          float ri[V];
-          stencil_row<V>(S, C, N, wk.lane, ax);
+        unit_bounds(a.uo, u, c.ny, s, y0, y1);
+        const int xs = s * 32 * VO, xl = Lanes<VO>::first(xs, wk.lane);
+        const int nval = c.nx - xl;  // columns from xl to the grid edge
+        auto field = [&](int j, FRow<VO, double>& f) { field_plain<VO>(a.x, c.nx, c.ny, j, xl, xs, wk.lane, f); };
+        auto load = [&](int j, D& dd) { load_row<VO>(a.b, j, xl, c.nx, dd.b); };
+        auto finish = [&](int j, const D& dd, const FRow<VO, double>& S, const FRow<VO, double>& C,
+                          const FRow<VO, double>& N) {
+          double ax[VO];
+          float ri[VO];
+          stencil_row<VO>(S, C, N, wk.lane, ax);
 #pragma unroll
-          for (int k = 0; k < V; ++k) {
+          for (int k = 0; k < VO; ++k) {
             const double rv = dd.b[k] - ax[k];
             ri[k] = quantize<TR>(__double2float_rn(rv));
-            if (k < nval) {
+            if (Lanes<VO>::col(k) < nval) {
               if (outer == 0) abb.add(dd.b[k], dd.b[k]);
               arr.add(rv, rv);
               agi.add(ri[k], ri[k]);
             }
           }
-          store_row<V>(a.r, j, xl, c.nx, ri);
+          store_row<VO>(a.r, j, xl, c.nx, ri);
         };
-        march<V, double, D>(y0, y1, wk.rev(), field, load, finish);
+        march<VO, double, D>(y0, y1, wk.rev(), field, load, finish);
       }
       ++wk.pc;
       double v[3] = {abb.value(), arr.value(), agi.value()}, o[3];
@@ -111,7 +119,7 @@ __device__ void ir_solve(const IrArgs<TR>& a, Team& tm, double* red, unsigned ch
         bb = o[0];
         if (!isfinite(bb)) { status = LAP5CG_ERR_NONFINITE; goto done; }
         if (bb == 0.0) {
-          pass_zero<V>(c, wk, a.x);
+          pass_zero<VO>(c, a.uo, wk, a.x);
           status = LAP5CG_OK;
           rr = 0.0;
           relres_true = 0.0;
@@ -163,8 +171,8 @@ __device__ void ir_solve(const IrArgs<TR>& a, Team& tm, double* red, unsigned ch
             for (int u = wk.gw; u < c.un.nunits; u += wk.nw) {
               int s, y0, y1;
               unit_bounds(c.un, u, c.ny, s, y0, y1);
-              const int xs = s * 32 * V, xl = xs + wk.lane * V;
-              const int nval = min(max(c.nx - xl, 0), V);
+              const int xs = s * 32 * V, xl = Lanes<V>::first(xs, wk.lane);
+              const int nval = c.nx - xl;  // columns from xl to the grid edge
               auto field = [&](int, const unsigned char* sl, FRow<V, float>& f) {
                 float rv[V];
                 ring_lane<V, TR>(sl, off[0], true, wk.lane, xl, c.nx, rv);
@@ -188,7 +196,7 @@ __device__ void ir_solve(const IrArgs<TR>& a, Team& tm, double* red, unsigned ch
                 float ap[V];
                 stencil_row<V>(S, C, N, wk.lane, ap);
                 store_row<V>(pnew, j, xl, c.nx, C.f);
-                if (a.store_z) store_row<V>(a.z, j, xl, c.nx, ap);
+                if (zs) store_row<V>(a.z, j, xl, c.nx, ap);
                 acc_dot<V>(acc, C.f, ap, nval);
               };
               march_ring<V, float>(ring, c.ny, xs, y0, y1, wk.rev(), vv, off, field, finish);
@@ -197,8 +205,8 @@ __device__ void ir_solve(const IrArgs<TR>& a, Team& tm, double* red, unsigned ch
           for (int u = wk.gw; u < c.un.nunits; u += wk.nw) {
             int s, y0, y1;
             unit_bounds(c.un, u, c.ny, s, y0, y1);
-            const int xs = s * 32 * V, xl = xs + wk.lane * V;
-            const int nval = min(max(c.nx - xl, 0), V);
+            const int xs = s * 32 * V, xl = Lanes<V>::first(xs, wk.lane);
+            const int nval = c.nx - xl;  // columns from xl to the grid edge
             auto field = [&](int j, FRow<V, float>& f) {
               if (j < 0 || j >= c.ny) { f.zero(); return; }
               float rv[V];
@@ -227,10 +235,8 @@ __device__ void ir_solve(const IrArgs<TR>& a, Team& tm, double* red, unsigned ch
               float ap[V];
               stencil_row<V>(S, C, N, wk.lane, ap);
               store_row<V>(pnew, j, xl, c.nx, C.f);
-              if (a.store_z) store_row<V>(a.z, j, xl, c.nx, ap);
-#pragma unroll
-              for (int q = 0; q < V; ++q)
-                if (q < nval) acc.add(C.f[q], ap[q]);
+              if (zs) store_row<V>(a.z, j, xl, c.nx, ap);
+              acc_dot<V>(acc, C.f, ap, nval);
             };
             march<V, float, D>(y0, y1, wk.rev(), field, load, finish);
           }
@@ -243,7 +249,7 @@ __device__ void ir_solve(const IrArgs<TR>& a, Team& tm, double* red, unsigned ch
         {  // phase R
           const float am = (float)(gamma / pz);
           Acc acc;
-          if (R && !a.store_z) {
+          if (R && !zs) {
             const RingVec vv[3] = {
                 {reinterpret_cast<const unsigned char*>(pnew.ptr), pnew.ld, ES, RV_HALO | RV_ALWAYS},
                 {first ? nullptr : reinterpret_cast<const unsigned char*>(a.d.ptr), a.d.ld, 4, 0},
@@ -254,8 +260,8 @@ __device__ void ir_solve(const IrArgs<TR>& a, Team& tm, double* red, unsigned ch
             for (int u = wk.gw; u < c.un.nunits; u += wk.nw) {
               int s, y0, y1;
               unit_bounds(c.un, u, c.ny, s, y0, y1);
-              const int xs = s * 32 * V, xl = xs + wk.lane * V;
-              const int nval = min(max(c.nx - xl, 0), V);
+              const int xs = s * 32 * V, xl = Lanes<V>::first(xs, wk.lane);
+              const int nval = c.nx - xl;  // columns from xl to the grid edge
               auto field = [&](int, const unsigned char* sl, FRow<V, float>& f) {
                 ring_lane<V, TR>(sl, off[0], true, wk.lane, xl, c.nx, f.f);
                 f.hl = ring_halo<V, TR, float>(sl, off[0], wk.lane, xs, c.nx);
@@ -271,8 +277,8 @@ __device__ void ir_solve(const IrArgs<TR>& a, Team& tm, double* red, unsigned ch
                 for (int q = 0; q < V; ++q) {
                   dv[q] = first ? __fmul_rn(am, C.f[q]) : fmx(am, C.f[q], dv[q]);
                   rv[q] = quantize<TR>(fmx(-am, ap[q], rv[q]));
-                  if (q < nval) acc.add(rv[q], rv[q]);
                 }
+                acc_dot<V>(acc, rv, rv, nval);
                 store_row<V>(a.d, j, xl, c.nx, dv);
                 store_row<V>(a.r, j, xl, c.nx, rv);
               };
@@ -282,9 +288,9 @@ __device__ void ir_solve(const IrArgs<TR>& a, Team& tm, double* red, unsigned ch
           for (int u = wk.gw; u < c.un.nunits; u += wk.nw) {
             int s, y0, y1;
             unit_bounds(c.un, u, c.ny, s, y0, y1);
-            const int xs = s * 32 * V, xl = xs + wk.lane * V;
-            const int nval = min(max(c.nx - xl, 0), V);
-            if (a.store_z) {
+            const int xs = s * 32 * V, xl = Lanes<V>::first(xs, wk.lane);
+            const int nval = c.nx - xl;  // columns from xl to the grid edge
+            if (zs) {
               struct D { float p[V], d[V], r[V], z[V]; };
               auto load = [&](int j, D& dd) {
                 load_row<V>(pnew, j, xl, c.nx, dd.p);
@@ -298,8 +304,8 @@ __device__ void ir_solve(const IrArgs<TR>& a, Team& tm, double* red, unsigned ch
                 for (int q = 0; q < V; ++q) {
                   dv[q] = first ? __fmul_rn(am, dd.p[q]) : fmx(am, dd.p[q], dd.d[q]);
                   rv[q] = quantize<TR>(fmx(-am, dd.z[q], dd.r[q]));
-                  if (q < nval) acc.add(rv[q], rv[q]);
                 }
+                acc_dot<V>(acc, rv, rv, nval);
                 store_row<V>(a.d, j, xl, c.nx, dv);
                 store_row<V>(a.r, j, xl, c.nx, rv);
               };
@@ -319,8 +325,8 @@ __device__ void ir_solve(const IrArgs<TR>& a, Team& tm, double* red, unsigned ch
                 for (int q = 0; q < V; ++q) {
                   dv[q] = first ? __fmul_rn(am, C.f[q]) : fmx(am, C.f[q], dd.d[q]);
                   rv[q] = quantize<TR>(fmx(-am, ap[q], dd.r[q]));
-                  if (q < nval) acc.add(rv[q], rv[q]);
                 }
+                acc_dot<V>(acc, rv, rv, nval);
                 store_row<V>(a.d, j, xl, c.nx, dv);
                 store_row<V>(a.r, j, xl, c.nx, rv);
               };

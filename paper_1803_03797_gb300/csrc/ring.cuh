@@ -159,6 +159,17 @@ struct WarpRing {
       ++cslot;
     }
     if (!failed) {
+      // fast path: the row has usually landed already (it was issued S rows
+      // ago); the timer is read only when the first probe fails
+      uint32_t ready;
+      asm volatile(
+          "{\n\t.reg .pred p;\n\t"
+          "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+          "selp.u32 %0, 1, 0, p;\n\t}"
+          : "=r"(ready)
+          : "r"(bar), "r"(parity)
+          : "memory");
+      if (__all_sync(0xffffffffu, ready != 0u)) return slots_ptr + (size_t)s * slot_bytes;
       const unsigned long long t0 = global_ns();
       unsigned spins = 0;
       for (;;) {
@@ -231,17 +242,18 @@ template <int V, class T, class M>
 __device__ __forceinline__ void ring_lane(const unsigned char* slot, int off, bool halo, int lane, int x, int nx,
                                           M (&v)[V]) {
   using U = typename std::remove_const<T>::type;
-  const U* p = reinterpret_cast<const U*>(slot + off + (halo ? 16 : 0)) + lane * V;
-  if (x < nx) {
-    VecIO<V, U>::load(p, v);
-    if (x + V > nx) {
-#pragma unroll
-      for (int k = 0; k < V; ++k)
-        if (x + k >= nx) v[k] = M(0);
-    }
+  using L = Lanes<V>;
+  const U* p = reinterpret_cast<const U*>(slot + off + (halo ? 16 : 0)) + lane * L::W;
+  if constexpr (L::G == 1) {
+    load_group<V, U, M>(p, x, nx, v);
   } else {
 #pragma unroll
-    for (int k = 0; k < V; ++k) v[k] = M(0);
+    for (int gi = 0; gi < L::G; ++gi) {
+      M t[L::W];
+      load_group<L::W, U, M>(p + gi * L::GS, x + gi * L::GS, nx, t);
+#pragma unroll
+      for (int k = 0; k < L::W; ++k) v[gi * L::W + k] = t[k];
+    }
   }
 }
 

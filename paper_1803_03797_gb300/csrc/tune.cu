@@ -125,12 +125,14 @@ extern "C" LAP5CG_API int lap5cg_tune(int nx, int ny, int ld, const void* b, voi
   if (!opts || iters < 1 || !b || !x) return LAP5CG_ERR_INVALID_ARG;
   SingleCtx c{nx, ny, ld, variant, precision, iters, b, x, workspace, ws_bytes, info,
               static_cast<cudaStream_t>(stream), (size_t)(precision == LAP5CG_PREC_F32 ? 4 : 8)};
-  Param params[4] = {{&lap5cg_opts::warps_per_cta, {4, 8, 16}, 3},
+  Param params[5] = {{&lap5cg_opts::warps_per_cta, {4, 8, 16}, 3},
                      {&lap5cg_opts::ring_slots, {-1, 3, 4, 6, 8}, 5},
-                     {&lap5cg_opts::min_rows, {4, 8, 16, 32, 64}, 5},
-                     {&lap5cg_opts::store_z, {0, 1}, 2}};
-  const int np = (variant == LAP5CG_CLASSIC && precision != LAP5CG_PREC_IR_F32 &&
-                  precision != LAP5CG_PREC_IR_BF16PR) ? 4 : 3;
+                     {&lap5cg_opts::min_rows, {4, 8, 16, 32, 64}, 5}};
+  int np = 3;
+  if (variant == LAP5CG_CLASSIC && precision != LAP5CG_PREC_IR_F32 && precision != LAP5CG_PREC_IR_BF16PR)
+    params[np++] = {&lap5cg_opts::store_z, {0, 1}, 2};
+  if (variant == LAP5CG_CLASSIC && precision != LAP5CG_PREC_F64)  // binary32 passes: lane vector width
+    params[np++] = {&lap5cg_opts::lane_vec, {4, 8}, 2};
   return coordinate_descent(opts, params, np, run_single, &c, c.st, best_ms);
 }
 

@@ -205,6 +205,62 @@ def test_f32_fixed_iterations_track_fp64_oracle(variant, nx, ny, k):
     assert _rel(x[:, :nx].astype(np.float64), xo[:, :nx]) <= (1e-4 if variant == "classic" else 1e-3)
 
 
+@pytest.mark.parametrize("nx,ny", [(1, 9), (5, 40), (127, 33), (128, 30), (129, 41), (255, 64), (256, 64),
+                                   (257, 70), (300, 77), (513, 100), (1100, 64)])
+def test_f32_lane_vec_8_tracks_oracle_and_lane_vec_4(nx, ny):
+    # eight columns a lane (two 16-byte groups 128 columns apart): ragged
+    # strips where the second group is partly or wholly outside the grid
+    b = gen.uniform_rhs(nx, ny, seed=5 * nx + ny, ld=gen.pitch(nx, 4)).astype(np.float32)
+    k = 25
+    xs = {}
+    for lv in (4, 8):
+        opts = lap5cg.default_opts(lane_vec=lv, ring_slots=4)
+        x, info = _solve(b, tol=0.0, maxit=k, variant="classic", precision="f32", nx=nx, opts=opts)
+        xs[lv] = x[:, :nx].astype(np.float64)
+        assert info[0]["iters"] <= k and info[0]["status"] in (lap5cg.OK, lap5cg.NOT_CONVERGED)
+    xo, io = oracle.cg_classic(b.astype(np.float64), tol=0.0, maxit=k, nx=nx)
+    assert _rel(xs[8], xo[:, :nx]) <= 1e-4
+    # the two layouts differ only in the order of dot-product partial sums
+    assert _rel(xs[8], xs[4]) <= 1e-4
+    assert np.isfinite(xs[8]).all()
+
+
+def test_f32_lane_vec_8_converged_and_rejected_forms():
+    nx, ny = 1030, 300
+    b = gen.uniform_rhs(nx, ny, seed=91, ld=gen.pitch(nx, 4)).astype(np.float32)
+    tol = 1e-5
+    # explicit ring: at this size the automatic choice would take the register
+    # march (units shorter than 8 rows), which has no eight-column form
+    x, info = _solve(b, tol=tol, maxit=20000, variant="classic", precision="f32", nx=nx,
+                     opts=lap5cg.default_opts(lane_vec=8, ring_slots=4))
+    rec = info[0]
+    assert rec["status"] == lap5cg.OK, rec
+    xo, io = oracle.cg_solve(b.astype(np.float64), variant="classic", tol=1e-13, maxit=20000, nx=nx)
+    kappa = gen.condition_number(nx, ny)
+    assert _rel(x[:, :nx].astype(np.float64), xo[:, :nx]) <= kappa * (2 * tol + 4 * 2.0 ** -24)
+    # eight columns a lane exist for the ring kernel of classic CG only
+    for kw in (dict(variant="newcg"), dict(variant="classic", opts_extra=dict(ring_slots=-1))):
+        extra = kw.pop("opts_extra", {})
+        with pytest.raises(RuntimeError):
+            _solve(b, tol=tol, maxit=10, precision="f32", nx=nx, opts=lap5cg.default_opts(lane_vec=8, **extra), **kw)
+    with pytest.raises(RuntimeError):
+        _solve(b, tol=tol, maxit=10, precision="f32", nx=nx, opts=lap5cg.default_opts(lane_vec=6))
+
+
+def test_f32_full_size_8192_fused_launch_tracks_oracle():
+    # the 8192 x 8192 binary32 fused-iteration workload in its timed launch
+    # configuration (automatic lane vector: 8), fixed iterations, against the
+    # binary64 oracle
+    n, k = 8192, 6
+    b = gen.uniform_rhs(n, n, seed=3).astype(np.float32)
+    x, info = _solve(b, tol=0.0, maxit=k, variant="classic", precision="f32",
+                     opts=lap5cg.default_opts(true_residual=0))
+    assert info[0]["iters"] == k
+    xo, io = oracle.cg_classic(b.astype(np.float64), tol=0.0, maxit=k)
+    assert _rel(x.astype(np.float64), xo) <= 1e-5
+    assert abs(info[0]["relres_recursive"] - io["relres_recursive"]) <= 1e-4 * io["relres_recursive"]
+
+
 def test_f32_newcg_limited_accuracy_reports_breakdown():
     # Binary32 pipelined CG loses the accuracy of its w/q/z recurrences: an
     # independent numpy binary32 restatement of Algorithm 2 breaks down at

@@ -62,6 +62,33 @@ def test_ir_edge_cases(precision):
     assert rec["status"] == lap5cg.NOT_CONVERGED and rec["iters"] == 10
 
 
+@pytest.mark.parametrize("precision", ["ir_f32", "ir_bf16pr"])
+@pytest.mark.parametrize("nx,ny", [(1, 40), (100, 90), (129, 64), (257, 70), (300, 77), (1030, 120)])
+def test_ir_inner_lane_vec_8(precision, nx, ny):
+    # inner passes with eight columns a lane (two 16-byte groups 128 columns
+    # apart, ring kernel), outer binary64 passes with two: ragged strips
+    tol = 1e-10
+    b = gen.uniform_rhs(nx, ny, seed=nx * 17 + ny, ld=gen.pitch(nx, 32))
+    recs, xs = {}, {}
+    for lv in (4, 8):
+        opts = lap5cg.default_opts(lane_vec=lv, ring_slots=4)
+        x, info = lap5cg.cg_solve(_dev(b), tol=tol, maxit=10 ** 6, precision=precision, nx=nx, opts=opts)
+        recs[lv] = lap5cg.decode_info(info)[0]
+        xs[lv] = x.cpu().numpy()[:, :nx]
+        assert recs[lv]["status"] == lap5cg.OK and recs[lv]["relres_true"] <= tol, (lv, recs[lv])
+    xo, io = oracle.cg_classic(b, tol=1e-13, maxit=10 ** 6, nx=nx)
+    kappa = gen.condition_number(nx, ny)
+    assert _rel(xs[8], xo[:, :nx]) <= max(kappa * 2 * tol, 1e-13)
+    assert abs(recs[8]["outer_iters"] - recs[4]["outer_iters"]) <= 1
+
+
+def test_ir_lane_vec_8_rejected_forms():
+    b = _dev(gen.uniform_rhs(64, 64, seed=2))
+    for opts in (dict(lane_vec=8, ring_slots=-1), dict(lane_vec=8, store_z=1, ring_slots=4)):
+        with pytest.raises(lap5cg.Lap5cgError):
+            lap5cg.cg_solve(b, tol=1e-10, precision="ir_f32", opts=lap5cg.default_opts(**opts))
+
+
 def test_ir_newcg_inner_is_unsupported():
     b = _dev(gen.uniform_rhs(16, 16, seed=1))
     with pytest.raises(lap5cg.Lap5cgError):
