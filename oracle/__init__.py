@@ -19,8 +19,17 @@ Functions and the passages they follow (arxiv 1803.03797):
   cg_ir             -- FP64 iterative refinement around a binary32 (or bf16
                        p/r) inner Algorithm 1 with Dot2 inner dot products.
   dot2_f32          -- Dot2 (Ogita, Rump & Oishi 2005).
+  dot_repro, cg_classic_repro, cg_newcg_repro
+                    -- the reproducible mode: a dot product whose value does
+                       not depend on how the work is split (the paper
+                       accumulates in fixed point because floating-point
+                       addition is not associative, Sec. III; the dot product
+                       is a multiplier-adder tree, Sec. II-C-1), and
+                       Algorithms 1 / 2 with those dots and single-rounding
+                       vector updates.
 """
 import ctypes
+import math
 import numpy as np
 
 from . import build as _build
@@ -62,6 +71,12 @@ def lib():
         L.ora_cg_ir.argtypes = [i, i, i, vp, vp, d, i, i, d, i, ctypes.POINTER(Info)]
         for name in ("ora_cg_classic", "ora_cg_newcg", "ora_cg_ir"):
             getattr(L, name).restype = i
+        L.ora_repro_blocks.argtypes = [i, i, i, vp, vp, vp]
+        L.ora_repro_blocks.restype = None
+        L.ora_fma_axpy.argtypes = [i, i, i, vp, d, vp]
+        L.ora_fma_axpy.restype = None
+        L.ora_fma_xpby.argtypes = [i, i, i, vp, d, vp]
+        L.ora_fma_xpby.restype = None
         L.ora_f32_to_bf16.argtypes = [ctypes.c_float]
         L.ora_f32_to_bf16.restype = ctypes.c_uint16
         _lib = L
@@ -200,3 +215,198 @@ def cg_solve(b, variant="classic", **kw):
     if variant == "newcg":
         return cg_newcg(b, **kw)
     raise ValueError(variant)
+
+
+# ---------------------------------------------------------------------------
+# Reproducible mode.  Definition of (a, b) (steps 1-3 in lap5_oracle.c):
+#   1. blocks of 2 columns x 16 rows aligned at column 2c, row 16t (points
+#      outside the grid: a = b = 0);
+#   2. row value fma(a1, b1, a0*b0);
+#   3. block value: fixed pairwise tree over the 16 row values;
+#   4. the exact sum of the block values, rounded once to nearest (ties to
+#      even); exact zero -> +0; a non-finite block value -> NaN.
+# Step 4 uses math.fsum, which returns the correctly rounded exact sum.
+# ---------------------------------------------------------------------------
+def repro_blocks(a, b, nx=None):
+    """Block values of steps 1-3, shape (ceil(ny/16), ceil(nx/2))."""
+    ny, ld = a.shape
+    nx = ld if nx is None else nx
+    a = _grid(a, np.float64, nx)
+    b = _grid(b, np.float64, nx)
+    out = np.empty(((ny + 15) // 16, (nx + 1) // 2))
+    lib().ora_repro_blocks(nx, ny, ld, _ptr(a), _ptr(b), _ptr(out))
+    return out
+
+
+def exact_sum(values):
+    """Correctly rounded exact sum (step 4)."""
+    v = np.asarray(values, dtype=np.float64).reshape(-1)
+    if not np.all(np.isfinite(v)):
+        return math.nan
+    try:
+        s = math.fsum(v.tolist())
+    except OverflowError:
+        return math.nan
+    return s + 0.0  # an exact zero is +0
+
+
+def dot_repro(a, b, nx=None):
+    return exact_sum(repro_blocks(a, b, nx))
+
+
+def _fma_axpy(y, alpha, x, nx):
+    ny, ld = y.shape
+    lib().ora_fma_axpy(nx, ny, ld, _ptr(y), float(alpha), _ptr(x))
+
+
+def _fma_xpby(x, beta, y, nx):
+    ny, ld = y.shape
+    lib().ora_fma_xpby(nx, ny, ld, _ptr(x), float(beta), _ptr(y))
+
+
+def _apply(x, nx):
+    return lap5_apply(x, nx=nx)
+
+
+def _residual(b, x, nx):
+    r = np.zeros_like(b)
+    r[:, :nx] = b[:, :nx] - _apply(x, nx)[:, :nx]  # one rounding per element
+    return r
+
+
+def _finish(status, k, gamma, bb, b, x, nx):
+    res = _residual(b, x, nx)
+    rt = dot_repro(res, res, nx)
+    return x, {"status": status, "iters": k, "outer_iters": 0, "relres_recursive": math.sqrt(gamma / bb),
+               "relres_true": math.sqrt(rt / bb)}
+
+
+def cg_classic_repro(b, x0=None, tol=1e-10, maxit=1000, nx=None, history=None):
+    """Algorithm 1 with reproducible dot products and fused updates
+    (x = fma(alpha, p, x), r = fma(-alpha, z, r), p = fma(beta, p, r)).
+    history, if a list, receives sqrt(gamma_k / (b, b)) for k = 0, 1, ..."""
+    ny, ld = b.shape
+    nx = ld if nx is None else nx
+    b = _grid(b, np.float64, nx).copy()
+    b[:, nx:] = 0.0
+    x = np.zeros_like(b) if x0 is None else _grid(x0, np.float64, nx).copy()
+    x[:, nx:] = 0.0
+    bb = dot_repro(b, b, nx)
+    if not math.isfinite(bb):
+        return x, {"status": ERR_NONFINITE, "iters": 0, "outer_iters": 0, "relres_recursive": math.nan,
+                   "relres_true": math.nan}
+    if bb == 0.0:
+        x[:] = 0.0
+        return x, {"status": OK, "iters": 0, "outer_iters": 0, "relres_recursive": 0.0, "relres_true": 0.0}
+    thr = tol * tol * bb if tol > 0 else 0.0
+    r = _residual(b, x, nx)                      # line 1: r = b - A x0
+    gamma = dot_repro(r, r, nx)                  # (r, r)
+    p = r.copy()                                 # p = r
+    if history is not None:
+        history.append(math.sqrt(gamma / bb))
+    status, k = NOT_CONVERGED, 0
+    if not math.isfinite(gamma):
+        status = ERR_NONFINITE
+    elif gamma <= thr:
+        status = OK
+    while status == NOT_CONVERGED and k < maxit:
+        z = _apply(p, nx)                        # z = A p
+        pz = dot_repro(p, z, nx)                 # (p, z)
+        if not (pz > 0.0) or not math.isfinite(pz):
+            status = ERR_BREAKDOWN
+            break
+        alpha = gamma / pz
+        _fma_axpy(x, alpha, p, nx)               # x = x + alpha p
+        _fma_axpy(r, -alpha, z, nx)              # r = r - alpha z
+        gnew = dot_repro(r, r, nx)
+        k += 1
+        if history is not None:
+            history.append(math.sqrt(gnew / bb))
+        if not math.isfinite(gnew):
+            status, gamma = ERR_NONFINITE, gnew
+            break
+        beta = gnew / gamma
+        gamma = gnew
+        if gnew <= thr:
+            status = OK
+            break
+        _fma_xpby(r, beta, p, nx)                # p = r + beta p
+    return _finish(status, k, gamma, bb, b, x, nx)
+
+
+def cg_newcg_repro(b, x0=None, tol=1e-10, maxit=1000, nx=None, rr_period=0, history=None):
+    """Algorithm 2 (de-garbled as cg_newcg) with reproducible dot products
+    and fused updates (z = fma(beta, z, n), q = fma(beta, q, w),
+    p = fma(beta, p, r), x = fma(alpha, p, x), r = fma(-alpha, q, r),
+    w = fma(-alpha, z, w))."""
+    ny, ld = b.shape
+    nx = ld if nx is None else nx
+    b = _grid(b, np.float64, nx).copy()
+    b[:, nx:] = 0.0
+    x = np.zeros_like(b) if x0 is None else _grid(x0, np.float64, nx).copy()
+    x[:, nx:] = 0.0
+    bb = dot_repro(b, b, nx)
+    if not math.isfinite(bb):
+        return x, {"status": ERR_NONFINITE, "iters": 0, "outer_iters": 0, "relres_recursive": math.nan,
+                   "relres_true": math.nan}
+    if bb == 0.0:
+        x[:] = 0.0
+        return x, {"status": OK, "iters": 0, "outer_iters": 0, "relres_recursive": 0.0, "relres_true": 0.0}
+    thr = tol * tol * bb if tol > 0 else 0.0
+    status, k = NOT_CONVERGED, 0
+    r = _residual(b, x, nx)                      # line 1
+    w = _apply(r, nx)                            # line 2
+    gamma = dot_repro(r, r, nx)                  # line 3
+    if history is not None:
+        history.append(math.sqrt(gamma / bb))
+    alpha = 0.0
+    if not math.isfinite(gamma):
+        status = ERR_NONFINITE
+    elif gamma <= thr:
+        status = OK
+    elif maxit > 0:
+        delta = dot_repro(w, r, nx)              # line 4
+        n = _apply(w, nx)                        # line 5
+        if not (delta > 0.0) or not math.isfinite(delta):
+            status = ERR_BREAKDOWN
+        else:
+            alpha = gamma / delta                # line 6
+            z, q, p = n.copy(), w.copy(), r.copy()   # line 7
+            _fma_axpy(x, alpha, p, nx)           # line 8
+            _fma_axpy(r, -alpha, q, nx)          # line 9
+            _fma_axpy(w, -alpha, z, nx)          # line 10
+            k = 1
+    while status == NOT_CONVERGED and k >= 1:
+        if rr_period > 0 and k % rr_period == 0:  # residual replacement
+            r = _residual(b, x, nx)
+            w = _apply(r, nx)
+            q = _apply(p, nx)
+            z = _apply(q, nx)
+        gamma_old = gamma                        # line 12
+        gamma = dot_repro(r, r, nx)              # line 13
+        if history is not None:
+            history.append(math.sqrt(gamma / bb))
+        if not math.isfinite(gamma):
+            status = ERR_NONFINITE
+            break
+        if gamma <= thr:
+            status = OK
+            break
+        if k >= maxit:
+            break
+        delta = dot_repro(w, r, nx)              # line 14
+        n = _apply(w, nx)                        # line 15
+        beta = gamma / gamma_old                 # line 16
+        denom = delta / gamma - beta / alpha     # line 17 (de-garbled)
+        if not (denom > 0.0) or not math.isfinite(denom):
+            status = ERR_BREAKDOWN
+            break
+        alpha = 1.0 / denom
+        _fma_xpby(n, beta, z, nx)                # line 18: z = n + beta z
+        _fma_xpby(w, beta, q, nx)                # line 19: q = w + beta q
+        _fma_xpby(r, beta, p, nx)                # line 20: p = r + beta p
+        _fma_axpy(x, alpha, p, nx)               # line 21
+        _fma_axpy(r, -alpha, q, nx)              # line 22
+        _fma_axpy(w, -alpha, z, nx)              # line 23
+        k += 1
+    return _finish(status, k, gamma, bb, b, x, nx)

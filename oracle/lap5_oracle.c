@@ -331,6 +331,57 @@ int ora_cg_newcg(int nx, int ny, int ld, const double* b, double* x, double tol,
 }
 
 /* ------------------------------------------------------------------ */
+/* Reproducible dot product: the building blocks.  The paper accumulates  */
+/* in fixed point because floating-point addition is not associative and  */
+/* so would tie the result to one order of operations (Sec. III, Sec.     */
+/* II-C-1: the multiplier-adder tree).  Reading taken here: the value of  */
+/* (a, b) is defined independently of how the grid is split:              */
+/*  1. blocks of 2 columns x 16 rows aligned at column 2c and row 16t;     */
+/*     points outside the grid have a = b = 0;                            */
+/*  2. the row value of a block is fma(a1, b1, a0*b0) (columns 2c, 2c+1;   */
+/*     a0*b0 rounded to binary64 first);                                  */
+/*  3. the block value is a fixed pairwise tree over its 16 row values     */
+/*     (rows 2m + 2m+1, then pairs of those, ...);                        */
+/*  4. (a, b) is the exact sum of all block values rounded once to the     */
+/*     nearest binary64 (ties to even); an exact zero is +0; a non-finite  */
+/*     block value makes the result NaN.                                  */
+/* Steps 1-3 are here; step 4 is a correctly rounded exact sum, done by    */
+/* the Python side with math.fsum.  In the reproducible CG the vector      */
+/* updates are single-rounding fused multiply-adds (fma_axpy, fma_xpby).   */
+/* ------------------------------------------------------------------ */
+void ora_repro_blocks(int nx, int ny, int ld, const double* a, const double* b, double* out) {
+  const int nbx = (nx + 1) / 2, nby = (ny + 15) / 16;
+  for (int t = 0; t < nby; ++t)
+    for (int c = 0; c < nbx; ++c) {
+      double v[16];
+      for (int m = 0; m < 16; ++m) {
+        const int j = 16 * t + m, i0 = 2 * c, i1 = 2 * c + 1;
+        if (j >= ny) { v[m] = 0.0; continue; }
+        const double a0 = a[(size_t)j * ld + i0], b0 = b[(size_t)j * ld + i0];
+        const double a1 = i1 < nx ? a[(size_t)j * ld + i1] : 0.0;
+        const double b1 = i1 < nx ? b[(size_t)j * ld + i1] : 0.0;
+        const double p0 = a0 * b0;
+        v[m] = fma(a1, b1, p0);
+      }
+      for (int w = 1; w < 16; w *= 2)
+        for (int m = 0; m < 16; m += 2 * w) v[m] = v[m] + v[m + w];
+      out[(size_t)t * nbx + c] = v[0];
+    }
+}
+
+/* y = fma(alpha, x, y) over the interior */
+void ora_fma_axpy(int nx, int ny, int ld, double* y, double alpha, const double* x) {
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) y[(size_t)j * ld + i] = fma(alpha, x[(size_t)j * ld + i], y[(size_t)j * ld + i]);
+}
+
+/* y = fma(beta, y, x) over the interior (y = x + beta y, one rounding) */
+void ora_fma_xpby(int nx, int ny, int ld, const double* x, double beta, double* y) {
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) y[(size_t)j * ld + i] = fma(beta, y[(size_t)j * ld + i], x[(size_t)j * ld + i]);
+}
+
+/* ------------------------------------------------------------------ */
 /* Compensated binary32 dot product, Dot2 of Ogita, Rump & Oishi,        */
 /* "Accurate sum and dot product", SIAM J. Sci. Comput. 26 (2005):       */
 /* TwoProduct by an exact fused multiply-add, TwoSum by Knuth.  Returns   */
