@@ -297,6 +297,38 @@ def paper_size_workload(lap5cg, torch, dev, reps=20):
     return out
 
 
+def reproducible_workload(lap5cg, torch, dev, b, iters=500, reps=2):
+    """The benchmark's 4096 x 4096 FP64 step in reproducible mode (exact dot
+    products, fused updates): grid-point iterations per second per variant,
+    next to the default mode timed the same way."""
+    n = b.shape[0]
+    out = {}
+    for variant in VARIANTS:
+        for rep in (0, 1):
+            opts = lap5cg.default_opts(reproducible=rep, true_residual=0)
+
+            def run():
+                lap5cg.cg_solve(b, tol=0.0, maxit=iters, variant=variant, opts=opts)
+
+            run()
+            torch.cuda.synchronize(dev)
+            ms = []
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                run()
+                e1.record()
+                torch.cuda.synchronize(dev)
+                ms.append(e0.elapsed_time(e1))
+            t = min(ms) * 1e-3
+            out["%s_%s" % (variant, "reproducible" if rep else "default")] = {"ms": t * 1e3,
+                                                                              "pts_iters_per_s": n * n * iters / t}
+    for variant in VARIANTS:
+        out["%s_cost" % variant] = (out["%s_default" % variant]["pts_iters_per_s"] /
+                                    out["%s_reproducible" % variant]["pts_iters_per_s"])
+    return out
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -489,6 +521,7 @@ def main():
         extras["time_to_1e-10_4096"] = time_to_solution(lap5cg, torch, dev, 4096, b_host)
         extras["batched_256_ir_f32"] = batched_workload(lap5cg, torch, dev)
         extras["paper_100x100_to_1e-8"] = paper_size_workload(lap5cg, torch, dev)
+        extras["reproducible_4096"] = reproducible_workload(lap5cg, torch, dev, b)
         if args.tts:
             extras["time_to_1e-10_8192"] = time_to_solution(lap5cg, torch, dev, 8192,
                                                             gen.uniform_rhs(8192, 8192, seed=3))

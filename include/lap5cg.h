@@ -125,6 +125,16 @@ typedef struct {
                                (ring_slots > 0, or automatic with units at least 8 rows tall),
                                and store_z <= 0 for IR; otherwise LAP5CG_ERR_UNSUPPORTED.
                                F64 solves and batched solves ignore it. */
+  int32_t reproducible;     /* cg_solve, F64 (classic and NewCG): 1 = dot products whose value
+                               does not depend on the launch configuration (CTAs, warps, ring,
+                               unit sizes): each is the exact sum of fixed 2-column x 16-row
+                               block values (row value fma(a1, b1, a0*b0), a pairwise tree over
+                               the 16 rows), rounded once; vector updates are single-rounding
+                               fused multiply-adds.  Equal inputs and options other than the
+                               launch parameters give bit-identical results.  0 = the default
+                               fixed-order partial sums.  Other precisions:
+                               LAP5CG_ERR_UNSUPPORTED; batched solves reject 1 as well. */
+  int32_t pad_;
 } lap5cg_opts;
 
 /* Fill *o with the defaults above. */

@@ -48,7 +48,8 @@ class Opts(ctypes.Structure):
                 ("true_residual", ctypes.c_int32), ("maxit_inner", ctypes.c_int32),
                 ("max_outer", ctypes.c_int32), ("tol_inner", ctypes.c_double), ("timeout_s", ctypes.c_double),
                 ("history", ctypes.c_void_p), ("team_ctas", ctypes.c_int32), ("ring_slots", ctypes.c_int32),
-                ("resident", ctypes.c_int32), ("lane_vec", ctypes.c_int32)]
+                ("resident", ctypes.c_int32), ("lane_vec", ctypes.c_int32),
+                ("reproducible", ctypes.c_int32), ("pad_", ctypes.c_int32)]
 
 
 _lib = None

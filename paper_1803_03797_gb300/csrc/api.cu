@@ -33,7 +33,8 @@ int warps_of(const lap5cg_opts& o) {
   return wpc > 16 ? 16 : wpc;
 }
 
-int plan_units(const void* func, int nx, int ny, int V, const lap5cg_opts& o, size_t dyn_smem, LaunchCfg* cfg) {
+int plan_units(const void* func, int nx, int ny, int V, const lap5cg_opts& o, size_t dyn_smem, LaunchCfg* cfg,
+               int row_align) {
   DevProps dp;
   int rc = dev_props(&dp);
   if (rc != LAP5CG_OK) return rc;
@@ -47,7 +48,7 @@ int plan_units(const void* func, int nx, int ny, int V, const lap5cg_opts& o, si
   if (maxctas > kMaxCtas) maxctas = kMaxCtas;
   int ctas = o.ctas > 0 ? (o.ctas < maxctas ? o.ctas : maxctas) : maxctas;
   const long long W = (long long)ctas * wpc;
-  const Units un = make_units(nx, ny, V, W, o.min_rows > 0 ? o.min_rows : kDefaultMinRows);
+  const Units un = make_units(nx, ny, V, W, o.min_rows > 0 ? o.min_rows : kDefaultMinRows, row_align);
   const long long nunits = un.nunits;
   if (o.ctas <= 0 && nunits < W) ctas = (int)((nunits + wpc - 1) / wpc);
   cfg->ctas = ctas;
@@ -151,6 +152,8 @@ void lap5cg_opts_default(lap5cg_opts* o) {
   o->ring_slots = 0;
   o->resident = 0;
   o->lane_vec = 0;
+  o->reproducible = 0;
+  o->pad_ = 0;
 }
 
 const char* lap5cg_status_string(int status) {
@@ -200,8 +203,9 @@ int cg_solve(int nx, int ny, int ld, const void* b, void* x, double tol, int max
   else lap5cg_opts_default(&o);
   if (o.rr_period < 0 || o.warps_per_cta < 0 || o.warps_per_cta > 16 || o.ctas < 0 || o.min_rows < 0 ||
       o.maxit_inner < 0 || o.max_outer < 0 || o.ring_slots > kRingMaxSlots ||
-      (o.lane_vec != 0 && o.lane_vec != 4 && o.lane_vec != 8))
+      (o.lane_vec != 0 && o.lane_vec != 4 && o.lane_vec != 8) || o.reproducible < 0 || o.reproducible > 1)
     return LAP5CG_ERR_INVALID_ARG;
+  if (o.reproducible && precision != LAP5CG_PREC_F64) return LAP5CG_ERR_UNSUPPORTED;
   if (o.rr_period > 0 && variant != LAP5CG_NEWCG) return LAP5CG_ERR_INVALID_ARG;
   const size_t need = cg_workspace_size(nx, ny, ld, variant, precision, nrhs);
   if (need == 0) return LAP5CG_ERR_UNSUPPORTED;
@@ -294,6 +298,7 @@ int cg_solve_batched(int count, const int* nx, const int* ny, const int* ld, con
       o.maxit_inner < 0 || o.max_outer < 0 || o.team_ctas < 0)
     return LAP5CG_ERR_INVALID_ARG;
   if (o.rr_period > 0 && variant != LAP5CG_NEWCG) return LAP5CG_ERR_INVALID_ARG;
+  if (o.reproducible) return LAP5CG_ERR_UNSUPPORTED;  // exact dot products: single solves only
   return solve_batched(count, nx, ny, ld, b, x, tol, maxit, variant, precision, workspace, ws_bytes, info, o,
                        static_cast<cudaStream_t>(stream));
 }

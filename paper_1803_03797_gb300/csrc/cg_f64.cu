@@ -8,6 +8,9 @@ size_t ws_bytes_f64(int nx, int ny, int ldw, int variant) {
   return ws_bytes_t<double>(ny, ldw, variant);
 }
 
-int solve_f64(const SolvePlan& p, cudaStream_t st) { return solve_typed<double, 2>(p, st); }
+int solve_f64(const SolvePlan& p, cudaStream_t st) {
+  if (p.opts.reproducible) return solve_typed<double, 2, true>(p, st);
+  return solve_typed<double, 2>(p, st);
+}
 
 }  // namespace lap5

@@ -19,6 +19,7 @@
 
 #include "common.cuh"
 #include "ring.cuh"
+#include "repro.cuh"
 
 namespace lap5 {
 
@@ -101,11 +102,9 @@ __device__ __forceinline__ void write_info(const SolveCommon& c, int team_rank, 
 
 // r = b - A x (x is the stencil operand); accumulates (b,b) and (r,r).
 // When r is null only the dot products are formed (true-residual check).
-template <int V, class TB, class TX, class TR>
+template <int V, class TB, class TX, class TR, class Acc>
 __device__ __forceinline__ void pass_residual(const SolveCommon& c, Walker& wk, const Grid<const TB>& b,
-                                              const Grid<TX>& x, const Grid<TR>& r,
-                                              typename AccOf<typename Math<TX>::type>::type& abb,
-                                              typename AccOf<typename Math<TX>::type>::type& arr) {
+                                              const Grid<TX>& x, const Grid<TR>& r, Acc& abb, Acc& arr) {
   using M = typename Math<TX>::type;
   struct D { M b[V]; };
   for (int u = wk.gw; u < c.un.nunits; u += wk.nw) {
@@ -119,10 +118,9 @@ __device__ __forceinline__ void pass_residual(const SolveCommon& c, Walker& wk, 
       M ax[V], rv[V];
       stencil_row<V>(S, C, N, wk.lane, ax);
 #pragma unroll
-      for (int k = 0; k < V; ++k) {
-        rv[k] = d.b[k] - ax[k];
-        if (Lanes<V>::col(k) < nval) { abb.add(d.b[k], d.b[k]); arr.add(rv[k], rv[k]); }
-      }
+      for (int k = 0; k < V; ++k) rv[k] = d.b[k] - ax[k];
+      acc_dot<V>(abb, j, d.b, d.b, nval);
+      acc_dot<V>(arr, j, rv, rv, nval);
       if (r.ptr) store_row<V>(r, j, xl, c.nx, rv);
     };
     march<V, M, D>(y0, y1, wk.rev(), field, load, finish);
@@ -164,10 +162,11 @@ struct ClassicArgs {
   int store_z;
 };
 
-template <class T, int V, bool R, class Team>
+template <class T, int V, bool R, bool EX = false, class Team>
 __device__ void classic_solve(const ClassicArgs<T>& a, Team& tm, double* red, unsigned char* dsm) {
   using M = typename Math<T>::type;
-  using Acc = typename AccOf<M>::type;
+  // EX: reproducible (exact) dot products
+  using Acc = typename std::conditional<EX, AccExact, typename AccOf<M>::type>::type;
   const SolveCommon& c = a.c;
   Walker wk;
   wk.init(tm.rank(), tm.size());
@@ -182,10 +181,10 @@ __device__ void classic_solve(const ClassicArgs<T>& a, Team& tm, double* red, un
   Grid<T> plast = a.p0;
 
   {  // r = b - A x0, (b, b), (r, r)
-    Acc abb, arr;
+    Acc abb = make_acc<Acc>(tm, 0, c.ny, wk.rev()), arr = make_acc<Acc>(tm, 1, c.ny, wk.rev());
     pass_residual<V>(c, wk, a.b, a.x, a.r, abb, arr);
-    double v[2] = {abb.value(), arr.value()}, o[2];
-    if (!tm.template reduce<2>(v, o, red)) { aborted = true; goto done; }
+    double o[2];
+    if (!acc_reduce<2>(tm, {&abb, &arr}, o, red)) { aborted = true; goto done; }
     bb = o[0];
     gamma = o[1];
   }
@@ -217,7 +216,7 @@ __device__ void classic_solve(const ClassicArgs<T>& a, Team& tm, double* red, un
       // ---------------- phase P ----------------
       double pap;
       {
-        Acc acc;
+        Acc acc = make_acc<Acc>(tm, 0, c.ny, wk.rev());
         const M bm = (M)beta;
         struct D { int dummy; };
         if constexpr (R) {
@@ -265,7 +264,7 @@ __device__ void classic_solve(const ClassicArgs<T>& a, Team& tm, double* red, un
               stencil_row<V>(S, C, N, wk.lane, ap);
               store_row<V>(pnew, j, xl, c.nx, C.f);
               if (a.store_z) store_row<V>(a.z, j, xl, c.nx, ap);
-              acc_dot<V>(acc, C.f, ap, nval);
+              acc_dot<V>(acc, j, C.f, ap, nval);
             };
             march_ring<V, M>(ring, c.ny, xs, y0, y1, wk.rev(), vv, off, field, finish);
           }
@@ -310,20 +309,20 @@ __device__ void classic_solve(const ClassicArgs<T>& a, Team& tm, double* red, un
             stencil_row<V>(S, C, N, wk.lane, ap);
             store_row<V>(pnew, j, xl, c.nx, C.f);
             if (a.store_z) store_row<V>(a.z, j, xl, c.nx, ap);
-            acc_dot<V>(acc, C.f, ap, nval);
+            acc_dot<V>(acc, j, C.f, ap, nval);
           };
           march<V, M, D>(y0, y1, wk.rev(), field, load, finish);
         }
         ++wk.pc;
-        double v[1] = {acc.value()}, o[1];
-        if (!tm.template reduce<1>(v, o, red)) { aborted = true; goto done; }
+        double o[1];
+        if (!acc_reduce<1>(tm, {&acc}, o, red)) { aborted = true; goto done; }
         pap = o[0];
       }
       if (!(pap > 0.0) || !isfinite(pap)) { status = LAP5CG_ERR_BREAKDOWN; goto truecheck; }
       {
         const double alpha = gamma / pap;
         const M am = (M)alpha;
-        Acc acc;
+        Acc acc = make_acc<Acc>(tm, 0, c.ny, wk.rev());
         if constexpr (R) {
           ring.fence_global_to_async();
           if (a.store_z) {
@@ -342,7 +341,7 @@ __device__ void classic_solve(const ClassicArgs<T>& a, Team& tm, double* red, un
                 ring_lane<V, T>(sl, off[1], false, wk.lane, xl, c.nx, zv);
 #pragma unroll
                 for (int k = 0; k < V; ++k) rv[k] = fmx(-am, zv[k], rv[k]);
-                acc_dot<V>(acc, rv, rv, nval);
+                acc_dot<V>(acc, j, rv, rv, nval);
                 store_row<V>(a.r, j, xl, c.nx, rv);
               };
               stream_ring<V>(ring, c.ny, xs, y0, y1, wk.rev(), vv, off, finish);
@@ -375,7 +374,7 @@ __device__ void classic_solve(const ClassicArgs<T>& a, Team& tm, double* red, un
                   xv[k] = fmx(am, C.f[k], xv[k]);
                   rv[k] = fmx(-am, ap[k], rv[k]);
                 }
-                acc_dot<V>(acc, rv, rv, nval);
+                acc_dot<V>(acc, j, rv, rv, nval);
                 store_row<V>(a.x, j, xl, c.nx, xv);
                 store_row<V>(a.r, j, xl, c.nx, rv);
               };
@@ -398,7 +397,7 @@ __device__ void classic_solve(const ClassicArgs<T>& a, Team& tm, double* red, un
               M rv[V];
 #pragma unroll
               for (int k = 0; k < V; ++k) rv[k] = fmx(-am, d.z[k], d.r[k]);
-              acc_dot<V>(acc, rv, rv, nval);
+              acc_dot<V>(acc, j, rv, rv, nval);
               store_row<V>(a.r, j, xl, c.nx, rv);
             };
             stream_rows<D>(y0, y1, wk.rev(), load, finish);
@@ -417,7 +416,7 @@ __device__ void classic_solve(const ClassicArgs<T>& a, Team& tm, double* red, un
                 xv[k] = fmx(am, C.f[k], d.x[k]);
                 rv[k] = fmx(-am, ap[k], d.r[k]);
               }
-              acc_dot<V>(acc, rv, rv, nval);
+              acc_dot<V>(acc, j, rv, rv, nval);
               store_row<V>(a.x, j, xl, c.nx, xv);
               store_row<V>(a.r, j, xl, c.nx, rv);
             };
@@ -425,8 +424,8 @@ __device__ void classic_solve(const ClassicArgs<T>& a, Team& tm, double* red, un
           }
         }
         ++wk.pc;
-        double v[1] = {acc.value()}, o[1];
-        if (!tm.template reduce<1>(v, o, red)) { aborted = true; goto done; }
+        double o[1];
+        if (!acc_reduce<1>(tm, {&acc}, o, red)) { aborted = true; goto done; }
         const double gnew = o[0];
         ++iters;
         if (defer) {
@@ -469,11 +468,11 @@ finalx:
   }
 truecheck:
   if (c.true_res) {
-    Acc abb, arr;
+    Acc abb = make_acc<Acc>(tm, -1, c.ny, wk.rev()), arr = make_acc<Acc>(tm, 0, c.ny, wk.rev());
     const Grid<T> none{nullptr, 0};
     pass_residual<V>(c, wk, a.b, a.x, none, abb, arr);
-    double v[1] = {arr.value()}, o[1];
-    if (!tm.template reduce<1>(v, o, red)) { aborted = true; goto done; }
+    double o[1];
+    if (!acc_reduce<1>(tm, {&arr}, o, red)) { aborted = true; goto done; }
     relres_true = sqrt(o[0] / bb);
   }
 done:
@@ -525,10 +524,9 @@ __device__ __forceinline__ void pass_apply(const SolveCommon& c, Walker& wk, con
 }
 
 // w = A r with gamma = (r, r), delta = (w, r).
-template <int V, class T>
+template <int V, class T, class Acc>
 __device__ __forceinline__ void pass_w_from_r(const SolveCommon& c, Walker& wk, const Grid<T>& r, const Grid<T>& w,
-                                              typename AccOf<typename Math<T>::type>::type& ag,
-                                              typename AccOf<typename Math<T>::type>::type& ad) {
+                                              Acc& ag, Acc& ad) {
   using M = typename Math<T>::type;
   struct D { int dummy; };
   for (int u = wk.gw; u < c.un.nunits; u += wk.nw) {
@@ -542,18 +540,19 @@ __device__ __forceinline__ void pass_w_from_r(const SolveCommon& c, Walker& wk, 
       M wv[V];
       stencil_row<V>(S, C, N, wk.lane, wv);
       store_row<V>(w, j, xl, c.nx, wv);
-      acc_dot<V>(ag, C.f, C.f, nval);
-      acc_dot<V>(ad, wv, C.f, nval);
+      acc_dot<V>(ag, j, C.f, C.f, nval);
+      acc_dot<V>(ad, j, wv, C.f, nval);
     };
     march<V, M, D>(y0, y1, wk.rev(), field, load, finish);
   }
   ++wk.pc;
 }
 
-template <class T, int V, bool R, class Team>
+template <class T, int V, bool R, bool EX = false, class Team>
 __device__ void newcg_solve(const NewcgArgs<T>& a, Team& tm, double* red, unsigned char* dsm) {
   using M = typename Math<T>::type;
-  using Acc = typename AccOf<M>::type;
+  // EX: reproducible (exact) dot products
+  using Acc = typename std::conditional<EX, AccExact, typename AccOf<M>::type>::type;
   const SolveCommon& c = a.c;
   Walker wk;
   wk.init(tm.rank(), tm.size());
@@ -566,10 +565,10 @@ __device__ void newcg_solve(const NewcgArgs<T>& a, Team& tm, double* red, unsign
   int cur = 0;  // current w lives in w[cur]
 
   {  // line 1: r = b - A x
-    Acc abb, arr;
+    Acc abb = make_acc<Acc>(tm, 0, c.ny, wk.rev()), arr = make_acc<Acc>(tm, -1, c.ny, wk.rev());
     pass_residual<V>(c, wk, a.b, a.x, a.r, abb, arr);
-    double v[1] = {abb.value()}, o[1];
-    if (!tm.template reduce<1>(v, o, red)) { aborted = true; goto done; }
+    double o[1];
+    if (!acc_reduce<1>(tm, {&abb}, o, red)) { aborted = true; goto done; }
     bb = o[0];
   }
   if (!isfinite(bb)) { status = LAP5CG_ERR_NONFINITE; goto done; }
@@ -582,10 +581,10 @@ __device__ void newcg_solve(const NewcgArgs<T>& a, Team& tm, double* red, unsign
   {
     const double thr = c.tol > 0.0 ? c.tol * c.tol * bb : 0.0;
     {  // lines 2-4: w = A r, gamma = (r, r), delta = (w, r)
-      Acc ag, ad;
+      Acc ag = make_acc<Acc>(tm, 0, c.ny, wk.rev()), ad = make_acc<Acc>(tm, 1, c.ny, wk.rev());
       pass_w_from_r<V>(c, wk, a.r, a.w0, ag, ad);
-      double v[2] = {ag.value(), ad.value()}, o[2];
-      if (!tm.template reduce<2>(v, o, red)) { aborted = true; goto done; }
+      double o[2];
+      if (!acc_reduce<2>(tm, {&ag, &ad}, o, red)) { aborted = true; goto done; }
       gamma = o[0];
       delta = o[1];
     }
@@ -601,7 +600,7 @@ __device__ void newcg_solve(const NewcgArgs<T>& a, Team& tm, double* red, unsign
       const Grid<T> w = cur ? a.w1 : a.w0;
       const Grid<T> wn = cur ? a.w0 : a.w1;
       const M am = (M)alpha, bm = (M)beta;
-      Acc ag, ad;
+      Acc ag = make_acc<Acc>(tm, 0, c.ny, wk.rev()), ad = make_acc<Acc>(tm, 1, c.ny, wk.rev());
       struct D { M z[V], q[V], p[V], x[V], r[V]; };
       if constexpr (R) {
         ring.fence_global_to_async();
@@ -653,8 +652,8 @@ __device__ void newcg_solve(const NewcgArgs<T>& a, Team& tm, double* red, unsign
               rv[k] = fmx(-am, qv[k], rv[k]);
               wv[k] = fmx(-am, zv[k], C.f[k]);
             }
-            acc_dot<V>(ag, rv, rv, nval);
-            acc_dot<V>(ad, wv, rv, nval);
+            acc_dot<V>(ag, j, rv, rv, nval);
+            acc_dot<V>(ad, j, wv, rv, nval);
             store_row<V>(a.z, j, xl, c.nx, zv);
             store_row<V>(a.q, j, xl, c.nx, qv);
             store_row<V>(a.p, j, xl, c.nx, pv);
@@ -698,8 +697,8 @@ __device__ void newcg_solve(const NewcgArgs<T>& a, Team& tm, double* red, unsign
             rv[k] = fmx(-am, qv[k], d.r[k]);
             wv[k] = fmx(-am, zv[k], C.f[k]);
           }
-          acc_dot<V>(ag, rv, rv, nval);
-          acc_dot<V>(ad, wv, rv, nval);
+          acc_dot<V>(ag, j, rv, rv, nval);
+          acc_dot<V>(ad, j, wv, rv, nval);
           store_row<V>(a.z, j, xl, c.nx, zv);
           store_row<V>(a.q, j, xl, c.nx, qv);
           store_row<V>(a.p, j, xl, c.nx, pv);
@@ -715,23 +714,24 @@ __device__ void newcg_solve(const NewcgArgs<T>& a, Team& tm, double* red, unsign
       double gnew, dnew;
       if (a.rr_period > 0 && iters % a.rr_period == 0) {
         // residual replacement: r = b - A x; w = A r; q = A p; z = A q
-        Acc abb, arr;
         if (!tm.sync(red)) { aborted = true; goto done; }
+        acc_discard<Acc>(tm);  // the fused pass's (r, r), (w, r) are replaced below
+        Acc abb = make_acc<Acc>(tm, -1, c.ny, wk.rev()), arr = make_acc<Acc>(tm, -1, c.ny, wk.rev());
         pass_residual<V>(c, wk, a.b, a.x, a.r, abb, arr);
         if (!tm.sync(red)) { aborted = true; goto done; }
         const Grid<T> wr = cur ? a.w1 : a.w0;
-        Acc ag2, ad2;
+        Acc ag2 = make_acc<Acc>(tm, 0, c.ny, wk.rev()), ad2 = make_acc<Acc>(tm, 1, c.ny, wk.rev());
         pass_w_from_r<V>(c, wk, a.r, wr, ag2, ad2);
         pass_apply<V>(c, wk, a.p, a.q);
-        double v[2] = {ag2.value(), ad2.value()}, o[2];
-        if (!tm.template reduce<2>(v, o, red)) { aborted = true; goto done; }
+        double o[2];
+        if (!acc_reduce<2>(tm, {&ag2, &ad2}, o, red)) { aborted = true; goto done; }
         pass_apply<V>(c, wk, a.q, a.z);
         if (!tm.sync(red)) { aborted = true; goto done; }
         gnew = o[0];
         dnew = o[1];
       } else {
-        double v[2] = {ag.value(), ad.value()}, o[2];
-        if (!tm.template reduce<2>(v, o, red)) { aborted = true; goto done; }
+        double o[2];
+        if (!acc_reduce<2>(tm, {&ag, &ad}, o, red)) { aborted = true; goto done; }
         gnew = o[0];
         dnew = o[1];
       }
@@ -750,11 +750,11 @@ __device__ void newcg_solve(const NewcgArgs<T>& a, Team& tm, double* red, unsign
   }
 truecheck:
   if (c.true_res) {
-    Acc abb, arr;
+    Acc abb = make_acc<Acc>(tm, -1, c.ny, wk.rev()), arr = make_acc<Acc>(tm, 0, c.ny, wk.rev());
     const Grid<T> none{nullptr, 0};
     pass_residual<V>(c, wk, a.b, a.x, none, abb, arr);
-    double v[1] = {arr.value()}, o[1];
-    if (!tm.template reduce<1>(v, o, red)) { aborted = true; goto done; }
+    double o[1];
+    if (!acc_reduce<1>(tm, {&arr}, o, red)) { aborted = true; goto done; }
     relres_true = sqrt(o[0] / bb);
   }
 done:

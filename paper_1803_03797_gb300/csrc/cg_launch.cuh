@@ -9,20 +9,39 @@ namespace lap5 {
 
 // R: rows staged through the shared-memory ring (bulk asynchronous copies)
 // or loaded straight into registers.
-template <class T, int V, bool R>
+// EX: reproducible dot products (exact accumulation; the CTA's accumulators
+// live in static shared memory and start at zero).
+template <bool EX> struct ExactSmem {
+  __device__ __forceinline__ void attach(GridTeam&) {}
+};
+template <> struct ExactSmem<true> {
+  __device__ __forceinline__ void attach(GridTeam& tm) {
+    __shared__ unsigned long long xs[kExactSlots * kExactLimbs];
+    __shared__ unsigned xsb[kExactSlots];
+    for (int t = threadIdx.x; t < kExactSlots * kExactLimbs; t += blockDim.x) xs[t] = 0ull;
+    if (threadIdx.x < kExactSlots) xsb[threadIdx.x] = 0u;
+    __syncthreads();
+    tm.xs = xs;
+    tm.xsb = xsb;
+  }
+};
+
+template <class T, int V, bool R, bool EX = false>
 __global__ void __launch_bounds__(512) k_classic(const ClassicArgs<T> a) {
   __shared__ double red[kRedDoubles];
   extern __shared__ __align__(128) unsigned char dsm[];
   GridTeam tm{a.c.ctl, a.c.timeout_ns, 0ull};
-  classic_solve<T, V, R>(a, tm, red, dsm);
+  ExactSmem<EX>().attach(tm);
+  classic_solve<T, V, R, EX>(a, tm, red, dsm);
 }
 
-template <class T, int V, bool R>
+template <class T, int V, bool R, bool EX = false>
 __global__ void __launch_bounds__(512) k_newcg(const NewcgArgs<T> a) {
   __shared__ double red[kRedDoubles];
   extern __shared__ __align__(128) unsigned char dsm[];
   GridTeam tm{a.c.ctl, a.c.timeout_ns, 0ull};
-  newcg_solve<T, V, R>(a, tm, red, dsm);
+  ExactSmem<EX>().attach(tm);
+  newcg_solve<T, V, R, EX>(a, tm, red, dsm);
 }
 
 // Ring geometry for a kernel pair: tries the ring kernel first; falls back to
@@ -82,31 +101,35 @@ inline SolveCommon make_common(const SolvePlan& p, const LaunchCfg& cfg, const R
   return c;
 }
 
-template <class T, int V>
+// EX: reproducible dot products.  Their units start at multiples of 16 rows
+// and the first of the control block's three exact accumulators starts at zero.
+template <class T, int V, bool EX = false>
 int solve_typed(const SolvePlan& p, cudaStream_t st) {
   const size_t vec = align_up((size_t)p.ny * (size_t)p.ldw * sizeof(T), kAlign);
   unsigned char* base = p.ws + kCtlBytes;
   auto vecp = [&](int k) { return reinterpret_cast<T*>(base + (size_t)k * vec); };
-  if (cudaMemsetAsync(p.ws, 0, 256, st) != cudaSuccess) return LAP5CG_ERR_CUDA;
+  const size_t ctl_zero = EX ? offsetof(Ctl, part) : 256;
+  if (cudaMemsetAsync(p.ws, 0, ctl_zero, st) != cudaSuccess) return LAP5CG_ERR_CUDA;
+  const int row_align = EX ? kExactRows : 1;
   LaunchCfg cfg;
   if (p.variant == LAP5CG_CLASSIC) {
     RingGeom rg;
     size_t dyn = 0;
     bool ring = false;
-    int rc = pick_ring(reinterpret_cast<const void*>(&k_classic<T, V, true>), ring_slot_classic(V, (int)sizeof(T)),
+    int rc = pick_ring(reinterpret_cast<const void*>(&k_classic<T, V, true, EX>), ring_slot_classic(V, (int)sizeof(T)),
                        p.opts, &rg, &dyn, &ring);
     if (rc != LAP5CG_OK) return rc;
-    const void* fn = ring ? reinterpret_cast<const void*>(&k_classic<T, V, true>)
-                          : reinterpret_cast<const void*>(&k_classic<T, V, false>);
-    rc = plan_units(fn, p.nx, p.ny, V, p.opts, dyn, &cfg);
+    const void* fn = ring ? reinterpret_cast<const void*>(&k_classic<T, V, true, EX>)
+                          : reinterpret_cast<const void*>(&k_classic<T, V, false, EX>);
+    rc = plan_units(fn, p.nx, p.ny, V, p.opts, dyn, &cfg, row_align);
     if (rc != LAP5CG_OK) return rc;
     if (ring && p.opts.ring_slots == 0 && cfg.seg_rows < kRingMinRows) {  // short units: register march
       if constexpr (Lanes<V>::G > 1) return LAP5CG_ERR_UNSUPPORTED;  // the caller narrows the lane vector
       ring = false;
       rg.S = 0;
       dyn = 0;
-      fn = reinterpret_cast<const void*>(&k_classic<T, V, false>);
-      rc = plan_units(fn, p.nx, p.ny, V, p.opts, dyn, &cfg);
+      fn = reinterpret_cast<const void*>(&k_classic<T, V, false, EX>);
+      rc = plan_units(fn, p.nx, p.ny, V, p.opts, dyn, &cfg, row_align);
       if (rc != LAP5CG_OK) return rc;
     }
     ClassicArgs<T> a;
@@ -128,19 +151,19 @@ int solve_typed(const SolvePlan& p, cudaStream_t st) {
     RingGeom rg;
     size_t dyn = 0;
     bool ring = false;
-    int rc = pick_ring(reinterpret_cast<const void*>(&k_newcg<T, V, true>), ring_slot_newcg(V, (int)sizeof(T)),
+    int rc = pick_ring(reinterpret_cast<const void*>(&k_newcg<T, V, true, EX>), ring_slot_newcg(V, (int)sizeof(T)),
                        p.opts, &rg, &dyn, &ring);
     if (rc != LAP5CG_OK) return rc;
-    const void* fn = ring ? reinterpret_cast<const void*>(&k_newcg<T, V, true>)
-                          : reinterpret_cast<const void*>(&k_newcg<T, V, false>);
-    rc = plan_units(fn, p.nx, p.ny, V, p.opts, dyn, &cfg);
+    const void* fn = ring ? reinterpret_cast<const void*>(&k_newcg<T, V, true, EX>)
+                          : reinterpret_cast<const void*>(&k_newcg<T, V, false, EX>);
+    rc = plan_units(fn, p.nx, p.ny, V, p.opts, dyn, &cfg, row_align);
     if (rc != LAP5CG_OK) return rc;
     if (ring && p.opts.ring_slots == 0 && cfg.seg_rows < kRingMinRows) {  // short units: register march
       ring = false;
       rg.S = 0;
       dyn = 0;
-      fn = reinterpret_cast<const void*>(&k_newcg<T, V, false>);
-      rc = plan_units(fn, p.nx, p.ny, V, p.opts, dyn, &cfg);
+      fn = reinterpret_cast<const void*>(&k_newcg<T, V, false, EX>);
+      rc = plan_units(fn, p.nx, p.ny, V, p.opts, dyn, &cfg, row_align);
       if (rc != LAP5CG_OK) return rc;
     }
     NewcgArgs<T> a;

@@ -294,7 +294,8 @@ __device__ __forceinline__ void stencil_row(const FRow<V, M>& S, const FRow<V, M
 // its column offset Lanes<V>::col(k) < ncols (ncols = nx - the lane's first
 // column).  A single uniform branch for lanes whose columns are all inside.
 template <int V, class Acc, class M>
-__device__ __forceinline__ void acc_dot(Acc& acc, const M (&a)[V], const M (&b)[V], int ncols) {
+__device__ __forceinline__ void acc_dot(Acc& acc, int j, const M (&a)[V], const M (&b)[V], int ncols) {
+  (void)j;  // the row index matters to the exact accumulator only
   if (ncols >= Lanes<V>::span) {
     acc.add_block(a, b);
   } else if (ncols > 0) {
@@ -361,11 +362,19 @@ template <> struct AccOf<float> { using type = Acc32; };
 constexpr int kMaxCtas = 2048;     // partial-sum slots per parity
 constexpr int kMaxVals = 4;        // reduced values per barrier
 
+constexpr int kExactLimbs = 67;  // exact accumulator: 32-bit digits over 2^-1074 .. 2^1024, plus carry room
+constexpr int kExactSlots = 2;   // exact dot products per reduction
+
 struct Ctl {
   unsigned long long bar;          // monotonic arrival counter
   int abort;                       // nonzero: every CTA leaves at its next check
   int status;                      // first error recorded (0 = none)
   int pad[12];
+  // exact (reproducible) dot products: the solve's accumulators, three
+  // buffers used in turn by successive exact reductions
+  unsigned long long xacc[3][kExactSlots][kExactLimbs];
+  unsigned xbad[3][kExactSlots];
+  unsigned xpad[2];
   double part[2][kMaxCtas][kMaxVals];  // per-CTA partials, double-buffered by barrier parity
 };
 
@@ -529,7 +538,9 @@ struct Units {
 // Units for W warps: as many row segments per strip as there are warps per
 // strip, but no segment shorter than min_rows (halo rows cost two extra row
 // loads per segment); segments rebalanced to equal height.
-__host__ __device__ inline Units make_units(int nx, int ny, int V, long long W, int min_rows) {
+// row_align > 1: segment heights are multiples of row_align (segments start at
+// multiples of it).
+__host__ __device__ inline Units make_units(int nx, int ny, int V, long long W, int min_rows, int row_align = 1) {
   Units u;
   u.ns = (nx + 32 * V - 1) / (32 * V);
   long long nseg = W / u.ns;
@@ -539,6 +550,10 @@ __host__ __device__ inline Units make_units(int nx, int ny, int V, long long W, 
   if (L < min_rows) L = min_rows < ny ? min_rows : ny;
   nseg = (ny + L - 1) / L;
   L = (int)((ny + nseg - 1) / nseg);
+  if (row_align > 1) {
+    L = (L + row_align - 1) / row_align * row_align;
+    nseg = (ny + L - 1) / L;
+  }
   u.nseg = (int)nseg;
   u.seg_rows = L;
   u.nunits = (int)((long long)u.ns * nseg);
@@ -557,6 +572,9 @@ struct GridTeam {
   Ctl* ctl;
   long long timeout_ns;
   unsigned long long epoch;
+  unsigned long long* xs = nullptr;  // CTA exact accumulators [kExactSlots][kExactLimbs] (shared memory)
+  unsigned* xsb = nullptr;           // their non-finite flags
+  unsigned xepoch = 0;               // exact reductions so far
   __device__ __forceinline__ int rank() const { return (int)blockIdx.x; }
   __device__ __forceinline__ int size() const { return (int)gridDim.x; }
   template <int NV>

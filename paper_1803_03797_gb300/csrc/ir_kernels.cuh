@@ -197,7 +197,7 @@ __device__ void ir_solve(const IrArgs<TR>& a, Team& tm, double* red, unsigned ch
                 stencil_row<V>(S, C, N, wk.lane, ap);
                 store_row<V>(pnew, j, xl, c.nx, C.f);
                 if (zs) store_row<V>(a.z, j, xl, c.nx, ap);
-                acc_dot<V>(acc, C.f, ap, nval);
+                acc_dot<V>(acc, j, C.f, ap, nval);
               };
               march_ring<V, float>(ring, c.ny, xs, y0, y1, wk.rev(), vv, off, field, finish);
             }
@@ -236,7 +236,7 @@ __device__ void ir_solve(const IrArgs<TR>& a, Team& tm, double* red, unsigned ch
               stencil_row<V>(S, C, N, wk.lane, ap);
               store_row<V>(pnew, j, xl, c.nx, C.f);
               if (zs) store_row<V>(a.z, j, xl, c.nx, ap);
-              acc_dot<V>(acc, C.f, ap, nval);
+              acc_dot<V>(acc, j, C.f, ap, nval);
             };
             march<V, float, D>(y0, y1, wk.rev(), field, load, finish);
           }
@@ -278,7 +278,7 @@ __device__ void ir_solve(const IrArgs<TR>& a, Team& tm, double* red, unsigned ch
                   dv[q] = first ? __fmul_rn(am, C.f[q]) : fmx(am, C.f[q], dv[q]);
                   rv[q] = quantize<TR>(fmx(-am, ap[q], rv[q]));
                 }
-                acc_dot<V>(acc, rv, rv, nval);
+                acc_dot<V>(acc, j, rv, rv, nval);
                 store_row<V>(a.d, j, xl, c.nx, dv);
                 store_row<V>(a.r, j, xl, c.nx, rv);
               };
@@ -305,7 +305,7 @@ __device__ void ir_solve(const IrArgs<TR>& a, Team& tm, double* red, unsigned ch
                   dv[q] = first ? __fmul_rn(am, dd.p[q]) : fmx(am, dd.p[q], dd.d[q]);
                   rv[q] = quantize<TR>(fmx(-am, dd.z[q], dd.r[q]));
                 }
-                acc_dot<V>(acc, rv, rv, nval);
+                acc_dot<V>(acc, j, rv, rv, nval);
                 store_row<V>(a.d, j, xl, c.nx, dv);
                 store_row<V>(a.r, j, xl, c.nx, rv);
               };
@@ -326,7 +326,7 @@ __device__ void ir_solve(const IrArgs<TR>& a, Team& tm, double* red, unsigned ch
                   dv[q] = first ? __fmul_rn(am, C.f[q]) : fmx(am, C.f[q], dd.d[q]);
                   rv[q] = quantize<TR>(fmx(-am, ap[q], dd.r[q]));
                 }
-                acc_dot<V>(acc, rv, rv, nval);
+                acc_dot<V>(acc, j, rv, rv, nval);
                 store_row<V>(a.d, j, xl, c.nx, dv);
                 store_row<V>(a.r, j, xl, c.nx, rv);
               };

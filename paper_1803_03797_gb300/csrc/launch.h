@@ -64,7 +64,8 @@ int dev_props(DevProps* out);
 
 // Grid sizing shared by the persistent kernels: fills cfg from the occupancy
 // of kernel func at the requested warps per CTA.
-int plan_units(const void* func, int nx, int ny, int V, const lap5cg_opts& o, size_t dyn_smem, LaunchCfg* cfg);
+int plan_units(const void* func, int nx, int ny, int V, const lap5cg_opts& o, size_t dyn_smem, LaunchCfg* cfg,
+               int row_align = 1);
 
 // Row-ring geometry for a kernel whose largest ring slot is slot_bytes: sets
 // the kernel's dynamic shared memory limit and returns the bytes per CTA
