@@ -132,8 +132,8 @@ typedef struct {
                                the 16 rows), rounded once; vector updates are single-rounding
                                fused multiply-adds.  Equal inputs and options other than the
                                launch parameters give bit-identical results.  0 = the default
-                               fixed-order partial sums.  Other precisions:
-                               LAP5CG_ERR_UNSUPPORTED; batched solves reject 1 as well. */
+                               fixed-order partial sums.  Other precisions, grids of 2^36
+                               points or more and batched solves: LAP5CG_ERR_UNSUPPORTED. */
   int32_t pad_;
 } lap5cg_opts;
 

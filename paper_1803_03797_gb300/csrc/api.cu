@@ -206,6 +206,7 @@ int cg_solve(int nx, int ny, int ld, const void* b, void* x, double tol, int max
       (o.lane_vec != 0 && o.lane_vec != 4 && o.lane_vec != 8) || o.reproducible < 0 || o.reproducible > 1)
     return LAP5CG_ERR_INVALID_ARG;
   if (o.reproducible && precision != LAP5CG_PREC_F64) return LAP5CG_ERR_UNSUPPORTED;
+  if (o.reproducible && (long long)nx * (long long)ny >= (1ll << 36)) return LAP5CG_ERR_UNSUPPORTED;  // limb range
   if (o.rr_period > 0 && variant != LAP5CG_NEWCG) return LAP5CG_ERR_INVALID_ARG;
   const size_t need = cg_workspace_size(nx, ny, ld, variant, precision, nrhs);
   if (need == 0) return LAP5CG_ERR_UNSUPPORTED;

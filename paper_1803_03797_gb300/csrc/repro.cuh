@@ -19,8 +19,10 @@
 // shared memory, then one per solve in global memory, and rounds the total.
 //
 // The accumulator: kExactLimbs signed 64-bit limbs, limb k weighing
-// 2^(32k - 1074); each block value adds three 32-bit digits, so a limb absorbs
-// 2^31 additions before it could overflow (2^36 grid points per dot).
+// 2^(32k - 1074); a block value adds three 32-bit digits, which a warp
+// combines over its lanes into sums below 2^37 before adding, so a limb absorbs
+// 2^26 warp additions -- one per 1024 grid points: 2^36 points per dot --
+// before it could overflow; larger grids are rejected on the host.
 #pragma once
 
 #include "common.cuh"
@@ -29,16 +31,19 @@ namespace lap5 {
 
 constexpr int kExactRows = 16;   // block height (kExactLimbs, kExactSlots: common.cuh)
 
-// Add v exactly to the accumulator L (shared or global; atomics, so any
-// number of threads may add at once).  Non-finite v sets *bad.
-__device__ __forceinline__ void exact_add(unsigned long long* L, unsigned* bad, double v) {
-  if (v == 0.0) return;
+// Whole warp: add every lane's v exactly to L.  Lanes whose lowest digit
+// falls within four limbs of the warp's lowest combine their digits first --
+// integer sums of 16-bit halves, exact -- so the warp issues at most six
+// atomics for them instead of three per lane; other lanes add their own digits.
+// Non-finite values set *bad.
+__device__ __forceinline__ void exact_add_warp(unsigned long long* L, unsigned* bad, double v) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
   const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
   const unsigned ex = (unsigned)(bits >> 52) & 0x7ffu;
-  if (ex == 0x7ffu) {
-    atomicOr(bad, 1u);
-    return;
-  }
+  const bool nonfinite = ex == 0x7ffu;
+  if (__any_sync(full, nonfinite) && lane == 0) atomicOr(bad, 1u);
+  const bool use = !nonfinite && v != 0.0;
   unsigned long long m = bits & 0xfffffffffffffull;
   int o = 0;  // weight of m's lowest bit: 2^(o - 1074)
   if (ex != 0) {
@@ -48,47 +53,69 @@ __device__ __forceinline__ void exact_add(unsigned long long* L, unsigned* bad, 
   const int k = o >> 5, sh = o & 31;
   const unsigned long long lo = m << sh;
   const unsigned long long hi = sh ? (m >> (64 - sh)) : 0ull;
-  unsigned long long d0 = lo & 0xffffffffull, d1 = lo >> 32, d2 = hi;
-  if (bits >> 63) {  // subtract: two's complement digits (the limbs are signed)
-    d0 = 0ull - d0;
-    d1 = 0ull - d1;
-    d2 = 0ull - d2;
+  const unsigned d0 = (unsigned)(lo & 0xffffffffull), d1 = (unsigned)(lo >> 32), d2 = (unsigned)hi;
+  const bool neg = (bits >> 63) != 0ull;
+  const int kmin = __reduce_min_sync(full, use ? k : 0x7fffffff);
+  if (kmin == 0x7fffffff) return;  // no lane holds a nonzero value
+  const int off = k - kmin;
+  const bool near = use && off < 4;
+  if (use && !near) {  // two's complement digits (the limbs are signed)
+    const unsigned long long s0 = neg ? 0ull - d0 : d0, s1 = neg ? 0ull - d1 : d1, s2 = neg ? 0ull - d2 : d2;
+    if (s0) atomicAdd(&L[k], s0);
+    if (s1) atomicAdd(&L[k + 1], s1);
+    if (s2) atomicAdd(&L[k + 2], s2);
   }
-  if (d0) atomicAdd(&L[k], d0);
-  if (d1) atomicAdd(&L[k + 1], d1);
-  if (d2) atomicAdd(&L[k + 2], d2);
+  long long mine = 0;
+#pragma unroll
+  for (int p = 0; p < 6; ++p) {
+    const int q = p - off;
+    const unsigned dig = !near ? 0u : (q == 0) ? d0 : (q == 1) ? d1 : (q == 2) ? d2 : 0u;
+    const int l16 = (int)(dig & 0xffffu), h16 = (int)(dig >> 16);
+    const int sl = __reduce_add_sync(full, neg ? -l16 : l16);
+    const int sh16 = __reduce_add_sync(full, neg ? -h16 : h16);
+    if (lane == p) mine = (long long)sl + (long long)sh16 * 65536ll;
+  }
+  if (lane < 6 && mine != 0 && kmin + lane < kExactLimbs) atomicAdd(&L[kmin + lane], (unsigned long long)mine);
+}
+
+// Whole warp: lowest and highest nonzero limb of L (lo = kExactLimbs if none).
+__device__ __forceinline__ void exact_range(const long long* L, int& lo, int& hi) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const unsigned b0 = __ballot_sync(full, L[lane] != 0);
+  const unsigned b1 = __ballot_sync(full, L[lane + 32] != 0);
+  const unsigned b2 = __ballot_sync(full, lane + 64 < kExactLimbs && L[lane + 64] != 0);
+  lo = b0 ? __ffs(b0) - 1 : b1 ? 32 + __ffs(b1) - 1 : b2 ? 64 + __ffs(b2) - 1 : kExactLimbs;
+  hi = b2 ? 64 + 31 - __clz(b2) : b1 ? 32 + 31 - __clz(b1) : b0 ? 31 - __clz(b0) : -1;
 }
 
 // Round the exact total to binary64 (nearest, ties to even).  L holds the
-// limbs (shared memory) and is normalised in place; one thread.
-__device__ inline double exact_round(long long* L, bool bad) {
+// limbs (shared memory), nonzero only within [lo, hi]; normalised in place.
+// One thread.
+__device__ inline double exact_round(long long* L, bool bad, int lo, int hi) {
   if (bad) return __longlong_as_double(0x7ff8000000000000ll);
-  int lo = 0, hi = kExactLimbs - 1;
-  while (lo < kExactLimbs && L[lo] == 0) ++lo;
-  if (lo == kExactLimbs) return 0.0;
-  while (L[hi] == 0) --hi;
-  // digits in [0, 2^32), the top limb carries the sign; carries stop a few
-  // limbs above the highest nonzero one
-  auto normalise = [&]() {
+  if (lo >= kExactLimbs) return 0.0;
+  // digits in [0, 2^32) from lo upwards; a negative total borrows up to the
+  // top limb, which then holds its sign.  Returns the highest limb touched.
+  auto normalise = [&](int from, int until) -> int {
     long long c = 0;
-    for (int k = lo; k + 1 < kExactLimbs; ++k) {
+    int k = from;
+    for (; k + 1 < kExactLimbs; ++k) {
       const long long t = L[k] + c;
       c = t >> 32;  // arithmetic shift: floor division
       L[k] = t - c * (1ll << 32);
-      if (k >= hi && c == 0) break;
+      if (k >= until && c == 0) return k;
     }
-    if (c != 0) L[kExactLimbs - 1] += c;
+    L[kExactLimbs - 1] += c;
+    return kExactLimbs - 1;
   };
-  normalise();
-  int top = kExactLimbs - 1;
-  while (top > lo && L[top] == 0) --top;
+  int top = normalise(lo, hi);
   const bool neg = L[top] < 0;
   if (neg) {
     for (int k = lo; k <= top; ++k) L[k] = -L[k];
-    hi = top;
-    normalise();
+    top = normalise(lo, top);
   }
-  int h = kExactLimbs - 1;
+  int h = top;
   while (h >= lo && L[h] == 0) --h;
   if (h < lo) return 0.0;
   auto D = [&](int k) -> unsigned long long { return k >= lo ? (unsigned long long)L[k] : 0ull; };
@@ -137,7 +164,7 @@ struct AccExact {
           c = p2 + c;
           if (n & 8) {
             c = p3 + c;
-            if (L) exact_add(L, bad, c);
+            if (L) exact_add_warp(L, bad, c);
           } else {
             p3 = c;
           }
@@ -232,10 +259,18 @@ __device__ __forceinline__ bool grid_reduce_exact(GridTeam& tm, double (&out)[NV
   for (int t = threadIdx.x; t < NV * kExactLimbs; t += blockDim.x)
     tm.xs[t] = __ldcg(&ctl->xacc[e][0][0] + t);
   __syncthreads();
-  if (threadIdx.x < NV) {
-    const bool bad = __ldcg(&ctl->xbad[e][threadIdx.x]) != 0u;
-    red[32 * kMaxVals + threadIdx.x] =
-        exact_round(reinterpret_cast<long long*>(tm.xs + threadIdx.x * kExactLimbs), bad);
+  {
+    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (int k = warp; k < NV; k += nwarps) {
+      long long* Lk = reinterpret_cast<long long*>(tm.xs + k * kExactLimbs);
+      int lo, hi;
+      exact_range(Lk, lo, hi);
+      if ((threadIdx.x & 31) == 0) {
+        const bool bad = __ldcg(&ctl->xbad[e][k]) != 0u;
+        red[32 * kMaxVals + k] = exact_round(Lk, bad, lo, hi);
+      }
+      __syncwarp();
+    }
   }
   __syncthreads();
   for (int t = threadIdx.x; t < NV * kExactLimbs; t += blockDim.x) tm.xs[t] = 0ull;
