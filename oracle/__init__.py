@@ -19,6 +19,9 @@ Functions and the passages they follow (arxiv 1803.03797):
   cg_ir             -- FP64 iterative refinement around a binary32 (or bf16
                        p/r) inner Algorithm 1 with Dot2 inner dot products.
   dot2_f32          -- Dot2 (Ogita, Rump & Oishi 2005).
+  mg_precond, cg_pcg -- preconditioned CG (Algorithm 1 with M) with a
+                       geometric multigrid V-cycle as M^-1 (the cited
+                       pipelined CG's general form; the paper fixes M = I).
   dot_repro, cg_classic_repro, cg_newcg_repro
                     -- the reproducible mode: a dot product whose value does
                        not depend on how the work is split (the paper
@@ -77,6 +80,14 @@ def lib():
         L.ora_fma_axpy.restype = None
         L.ora_fma_xpby.argtypes = [i, i, i, vp, d, vp]
         L.ora_fma_xpby.restype = None
+        L.ora_mg_restrict.argtypes = [i, i, vp, vp]
+        L.ora_mg_restrict.restype = None
+        L.ora_mg_prolong_add.argtypes = [i, i, vp, vp]
+        L.ora_mg_prolong_add.restype = None
+        L.ora_mg_precond.argtypes = [i, i, i, vp, vp, i, i, i]
+        L.ora_mg_precond.restype = i
+        L.ora_cg_pcg.argtypes = [i, i, i, vp, vp, d, i, i, i, i, vp, ctypes.POINTER(Info)]
+        L.ora_cg_pcg.restype = i
         L.ora_f32_to_bf16.argtypes = [ctypes.c_float]
         L.ora_f32_to_bf16.restype = ctypes.c_uint16
         _lib = L
@@ -410,3 +421,62 @@ def cg_newcg_repro(b, x0=None, tol=1e-10, maxit=1000, nx=None, rr_period=0, hist
         _fma_axpy(w, -alpha, z, nx)              # line 23
         k += 1
     return _finish(status, k, gamma, bb, b, x, nx)
+
+
+# ---------------------------------------------------------------------------
+# Multigrid-preconditioned CG (readings in lap5_oracle.c).  Level grids are
+# dense (pitch = nx); the solver's grids are pitched like the other solvers.
+# ---------------------------------------------------------------------------
+MG_LEVELS, MG_NU, MG_NU_COARSE = 30, 2, 8
+
+
+def mg_coarse_shape(ny, nx):
+    return (ny - 1) // 2, (nx - 1) // 2
+
+
+def mg_restrict(r):
+    """P^T r for a dense (ny, nx) fine grid."""
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    ny, nx = r.shape
+    out = np.zeros(mg_coarse_shape(ny, nx))
+    lib().ora_mg_restrict(nx, ny, _ptr(r), _ptr(out))
+    return out
+
+
+def mg_prolong_add(ec, x):
+    """x + P ec for a dense coarse grid ec and fine grid x (returns a copy)."""
+    x = np.ascontiguousarray(x, dtype=np.float64).copy()
+    ec = np.ascontiguousarray(ec, dtype=np.float64)
+    ny, nx = x.shape
+    assert ec.shape == mg_coarse_shape(ny, nx)
+    lib().ora_mg_prolong_add(nx, ny, _ptr(ec), _ptr(x))
+    return x
+
+
+def mg_precond(r, nx=None, levels=MG_LEVELS, nu=MG_NU, nu_coarse=MG_NU_COARSE):
+    """z = M^-1 r: one V(nu, nu) cycle from z = 0 (levels = 0: z = r)."""
+    ny, ld = r.shape
+    nx = ld if nx is None else nx
+    r = _grid(r, np.float64, nx)
+    z = np.zeros_like(r)
+    rc = lib().ora_mg_precond(nx, ny, ld, _ptr(r), _ptr(z), levels, nu, nu_coarse)
+    if rc != OK:
+        raise RuntimeError("ora_mg_precond: %d" % rc)
+    return z
+
+
+def cg_pcg(b, x0=None, tol=1e-10, maxit=1000, nx=None, levels=MG_LEVELS, nu=MG_NU, nu_coarse=MG_NU_COARSE,
+           history=False):
+    """Algorithm 1 with M^-1 = one multigrid V-cycle.  Returns (x, info dict)
+    and, with history=True, also the relative residuals after each update."""
+    ny, ld = b.shape
+    nx = ld if nx is None else nx
+    b = _grid(b, np.float64, nx)
+    x = np.zeros_like(b) if x0 is None else _grid(x0, np.float64, nx).copy()
+    hist = np.full(maxit + 1, np.nan)
+    info = Info()
+    lib().ora_cg_pcg(nx, ny, ld, _ptr(b), _ptr(x), tol, maxit, levels, nu, nu_coarse, _ptr(hist),
+                     ctypes.byref(info))
+    if history:
+        return x, info.as_dict(), hist[:info.iters + 1]
+    return x, info.as_dict()

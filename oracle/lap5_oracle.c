@@ -507,3 +507,188 @@ int ora_cg_ir(int nx, int ny, int ld, const double* b, double* x, double tol, in
   if (info) *info = inf;
   return status;
 }
+
+/* ------------------------------------------------------------------ */
+/* Preconditioned CG with a geometric multigrid V-cycle as M^-1.  Not in  */
+/* the paper: the preconditioned form of the cited pipelined CG (Ghysels  */
+/* and Vanroose, with a general M; the paper fixes M = I).  Readings:     */
+/*  - levels: grid (nx, ny) -> ((nx-1)/2, (ny-1)/2), coarse point (I, J)   */
+/*    at fine (2I+1, 2J+1) (0-based); coarsening stops when either side    */
+/*    of the next grid would be 0, or after max_levels grids;             */
+/*  - every level's operator is the same 5-point mask (Sec. II-B): with    */
+/*    the unscaled mask A_h = h^2 L_h the coarse-grid correction is        */
+/*    e = P A_c^-1 P^T r, P bilinear interpolation, restriction P^T       */
+/*    (weights [1 2 1; 2 4 2; 1 2 1] / 4); coarse points outside the       */
+/*    coarse grid count as 0;                                              */
+/*  - smoother: damped Jacobi x <- x + c (b - A x), c = omega / 4 with     */
+/*    omega = 4/5 (c = 0.2), nu sweeps before and nu after the coarse      */
+/*    correction (symmetric, so M is symmetric positive definite);         */
+/*  - coarsest grid: nu_c damped Jacobi sweeps from 0;                     */
+/*  - PCG (Algorithm 1 with M): z = M^-1 r, gamma = (r, z), p = z + beta p,*/
+/*    stop when (r, r) <= tol^2 (b, b) as in the unpreconditioned solve.   */
+/* Fixed operation orders (the GPU kernels follow them):                   */
+/*    Jacobi:   x + c * (b - A x)                                          */
+/*    restrict: 0.25 * ((4 rC + 2 ((rW + rE) + rS + rN))                   */
+/*                      + ((rSW + rSE) + rNW + rNE))                        */
+/*    prolong:  odd-odd e; even-odd 0.5 (eW + eE); odd-even 0.5 (eS + eN); */
+/*              even-even 0.25 ((eSW + eSE) + (eNW + eNE))                 */
+/* ------------------------------------------------------------------ */
+#define ORA_MG_C 0.2
+
+static double mg_at(const double* v, int nx, int ny, int i, int j) {
+  return (i < 0 || i >= nx || j < 0 || j >= ny) ? 0.0 : v[(size_t)j * nx + i];
+}
+
+/* y = A x on a dense (pitch = nx) level grid, fixed add order */
+static void mg_apply(int nx, int ny, const double* x, double* y) {
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      double acc = 4.0 * x[(size_t)j * nx + i];
+      acc -= mg_at(x, nx, ny, i - 1, j);
+      acc -= mg_at(x, nx, ny, i + 1, j);
+      acc -= mg_at(x, nx, ny, i, j - 1);
+      acc -= mg_at(x, nx, ny, i, j + 1);
+      y[(size_t)j * nx + i] = acc;
+    }
+}
+
+/* one damped Jacobi sweep: xo = xi + c (b - A xi) */
+static void mg_jacobi(int nx, int ny, const double* b, const double* xi, double* xo, double* tmp) {
+  mg_apply(nx, ny, xi, tmp);
+  for (size_t t = 0; t < (size_t)nx * ny; ++t) xo[t] = xi[t] + ORA_MG_C * (b[t] - tmp[t]);
+}
+
+/* bc = P^T r (fine nx x ny -> coarse (nx-1)/2 x (ny-1)/2) */
+void ora_mg_restrict(int nx, int ny, const double* r, double* bc) {
+  const int nxc = (nx - 1) / 2, nyc = (ny - 1) / 2;
+  for (int J = 0; J < nyc; ++J)
+    for (int I = 0; I < nxc; ++I) {
+      const int i = 2 * I + 1, j = 2 * J + 1;
+      const double rC = mg_at(r, nx, ny, i, j);
+      const double s1 = ((mg_at(r, nx, ny, i - 1, j) + mg_at(r, nx, ny, i + 1, j)) + mg_at(r, nx, ny, i, j - 1)) +
+                        mg_at(r, nx, ny, i, j + 1);
+      const double s2 = ((mg_at(r, nx, ny, i - 1, j - 1) + mg_at(r, nx, ny, i + 1, j - 1)) +
+                         mg_at(r, nx, ny, i - 1, j + 1)) + mg_at(r, nx, ny, i + 1, j + 1);
+      bc[(size_t)J * nxc + I] = 0.25 * ((4.0 * rC + 2.0 * s1) + s2);
+    }
+}
+
+/* x += P ec (coarse (nx-1)/2 x (ny-1)/2 -> fine nx x ny) */
+void ora_mg_prolong_add(int nx, int ny, const double* ec, double* x) {
+  const int nxc = (nx - 1) / 2, nyc = (ny - 1) / 2;
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      double v;
+      const int I = i >> 1, J = j >> 1;  /* odd i: I = (i-1)/2; even i: neighbours I-1, I */
+      if ((i & 1) && (j & 1)) {
+        v = mg_at(ec, nxc, nyc, I, J);
+      } else if (!(i & 1) && (j & 1)) {
+        v = 0.5 * (mg_at(ec, nxc, nyc, I - 1, J) + mg_at(ec, nxc, nyc, I, J));
+      } else if ((i & 1) && !(j & 1)) {
+        v = 0.5 * (mg_at(ec, nxc, nyc, I, J - 1) + mg_at(ec, nxc, nyc, I, J));
+      } else {
+        v = 0.25 * ((mg_at(ec, nxc, nyc, I - 1, J - 1) + mg_at(ec, nxc, nyc, I, J - 1)) +
+                    (mg_at(ec, nxc, nyc, I - 1, J) + mg_at(ec, nxc, nyc, I, J)));
+      }
+      x[(size_t)j * nx + i] += v;
+    }
+}
+
+/* x = V-cycle(b) from x = 0 on a dense level grid; returns 0, -1 on allocation failure */
+static int mg_vcycle(int nx, int ny, const double* b, double* x, int nu, int nu_c, int levels_left) {
+  const size_t n = (size_t)nx * ny;
+  const int nxc = (nx - 1) / 2, nyc = (ny - 1) / 2;
+  double* t = (double*)malloc(n * sizeof(double));
+  double* w = (double*)malloc(n * sizeof(double));
+  if (!t || !w) { free(t); free(w); return -1; }
+  memset(x, 0, n * sizeof(double));
+  if (nxc < 1 || nyc < 1 || levels_left <= 1) {          /* coarsest grid */
+    for (int s = 0; s < nu_c; ++s) { mg_jacobi(nx, ny, b, x, w, t); memcpy(x, w, n * sizeof(double)); }
+    free(t); free(w);
+    return 0;
+  }
+  for (int s = 0; s < nu; ++s) { mg_jacobi(nx, ny, b, x, w, t); memcpy(x, w, n * sizeof(double)); }
+  mg_apply(nx, ny, x, t);
+  for (size_t k = 0; k < n; ++k) w[k] = b[k] - t[k];      /* residual */
+  const size_t nc = (size_t)nxc * nyc;
+  double* bc = (double*)malloc(nc * sizeof(double));
+  double* ec = (double*)malloc(nc * sizeof(double));
+  if (!bc || !ec) { free(t); free(w); free(bc); free(ec); return -1; }
+  ora_mg_restrict(nx, ny, w, bc);
+  int rc = mg_vcycle(nxc, nyc, bc, ec, nu, nu_c, levels_left - 1);
+  if (rc == 0) {
+    ora_mg_prolong_add(nx, ny, ec, x);
+    for (int s = 0; s < nu; ++s) { mg_jacobi(nx, ny, b, x, w, t); memcpy(x, w, n * sizeof(double)); }
+  }
+  free(t); free(w); free(bc); free(ec);
+  return rc;
+}
+
+/* z = M^-1 r on a pitched grid (one V-cycle; levels = 0 gives z = r) */
+int ora_mg_precond(int nx, int ny, int ld, const double* r, double* z, int levels, int nu, int nu_c) {
+  if (nx < 1 || ny < 1 || ld < nx || levels < 0 || nu < 0 || nu_c < 0) return ORA_ERR_INVALID_ARG;
+  if (levels == 0) { copy64(nx, ny, ld, z, r); return ORA_OK; }
+  const size_t n = (size_t)nx * ny;
+  double* b = (double*)malloc(n * sizeof(double));
+  double* x = (double*)malloc(n * sizeof(double));
+  if (!b || !x) { free(b); free(x); return ORA_ERR_INVALID_ARG; }
+  for (int j = 0; j < ny; ++j) memcpy(b + (size_t)j * nx, r + (size_t)j * ld, (size_t)nx * sizeof(double));
+  int rc = mg_vcycle(nx, ny, b, x, nu, nu_c, levels);
+  if (rc == 0)
+    for (int j = 0; j < ny; ++j) memcpy(z + (size_t)j * ld, x + (size_t)j * nx, (size_t)nx * sizeof(double));
+  free(b); free(x);
+  return rc == 0 ? ORA_OK : ORA_ERR_INVALID_ARG;
+}
+
+int ora_cg_pcg(int nx, int ny, int ld, const double* b, double* x, double tol, int maxit, int levels, int nu,
+               int nu_c, double* relres_hist, ora_info* info) {
+  ora_info inf; memset(&inf, 0, sizeof inf);
+  if (!arg_ok(nx, ny, ld, maxit) || !b || !x || levels < 0 || nu < 0 || nu_c < 0) {
+    inf.status = ORA_ERR_INVALID_ARG; if (info) *info = inf; return inf.status;
+  }
+  const size_t n = (size_t)ny * ld;
+  double bb = ora_dot_f64(nx, ny, ld, b, b);
+  if (!isfinite(bb)) { inf.status = ORA_ERR_NONFINITE; inf.relres_recursive = NAN; inf.relres_true = NAN; if (info) *info = inf; return inf.status; }
+  if (bb == 0.0) { zero64(nx, ny, ld, x); inf.status = ORA_OK; if (info) *info = inf; return inf.status; }
+  const double thr = tol > 0.0 ? tol * tol * bb : 0.0;
+  double *r = calloc(n, 8), *z = calloc(n, 8), *p = calloc(n, 8), *q = calloc(n, 8);
+  if (!r || !z || !p || !q) { free(r); free(z); free(p); free(q); inf.status = ORA_ERR_INVALID_ARG; if (info) *info = inf; return inf.status; }
+  int status = ORA_NOT_CONVERGED, k = 0;
+  residual64(nx, ny, ld, b, x, r);                       /* r = b - A x0 */
+  double rr = ora_dot_f64(nx, ny, ld, r, r);
+  if (relres_hist) relres_hist[0] = sqrt(rr / bb);
+  if (!isfinite(rr)) status = ORA_ERR_NONFINITE;
+  else if (rr <= thr) status = ORA_OK;
+  double gamma = 0.0;
+  if (status == ORA_NOT_CONVERGED) {
+    if (ora_mg_precond(nx, ny, ld, r, z, levels, nu, nu_c) != ORA_OK) status = ORA_ERR_INVALID_ARG;
+    copy64(nx, ny, ld, p, z);                            /* p = z */
+    gamma = ora_dot_f64(nx, ny, ld, r, z);               /* (r, z) */
+    if (!(gamma > 0.0) || !isfinite(gamma)) status = ORA_ERR_BREAKDOWN;
+  }
+  while (status == ORA_NOT_CONVERGED && k < maxit) {
+    ora_lap5_apply_f64(nx, ny, ld, p, q);                /* q = A p */
+    double pq = ora_dot_f64(nx, ny, ld, p, q);
+    if (!(pq > 0.0) || !isfinite(pq)) { status = ORA_ERR_BREAKDOWN; break; }
+    double alpha = gamma / pq;
+    axpy64(nx, ny, ld, x, alpha, p);                     /* x = x + alpha p */
+    axpy64(nx, ny, ld, r, -alpha, q);                    /* r = r - alpha q */
+    ++k;
+    rr = ora_dot_f64(nx, ny, ld, r, r);
+    if (relres_hist) relres_hist[k] = sqrt(rr / bb);
+    if (!isfinite(rr)) { status = ORA_ERR_NONFINITE; break; }
+    if (rr <= thr) { status = ORA_OK; break; }
+    if (ora_mg_precond(nx, ny, ld, r, z, levels, nu, nu_c) != ORA_OK) { status = ORA_ERR_INVALID_ARG; break; }
+    double gnew = ora_dot_f64(nx, ny, ld, r, z);         /* (r, z) */
+    if (!(gnew > 0.0) || !isfinite(gnew)) { status = ORA_ERR_BREAKDOWN; break; }
+    double beta = gnew / gamma;
+    gamma = gnew;
+    xpby64(nx, ny, ld, z, beta, p);                      /* p = z + beta p */
+  }
+  inf.status = status; inf.iters = k;
+  inf.relres_recursive = sqrt(rr / bb);
+  inf.relres_true = true_relres(nx, ny, ld, b, x, bb);
+  free(r); free(z); free(p); free(q);
+  if (info) *info = inf;
+  return status;
+}
