@@ -74,9 +74,17 @@ typedef enum { LAP5CG_CLASSIC = 0, LAP5CG_NEWCG = 1 } lap5cg_variant;
  *              b - A x, update x += d and their dot products in binary64)
  *              around an inner classic CG stored and computed in binary32.
  *   IR_BF16PR: as IR_F32 but the inner p and r are stored as bf16 (round to
- *              nearest even); inner arithmetic binary32. */
+ *              nearest even); inner arithmetic binary32.
+ *   MG_F32:    preconditioned CG (Algorithm 1 with M; the cited pipelined CG
+ *              takes a general M, the paper uses M = I) in binary64, M^-1 one
+ *              geometric multigrid V(nu, nu) cycle in binary32: levels
+ *              (nx, ny) -> ((nx-1)/2, (ny-1)/2), bilinear prolongation P,
+ *              restriction P^T, the 5-point mask on every level, damped Jacobi
+ *              (omega = 4/5) smoothing.  b and x binary64; classic variant only.
+ *   MG_F64:    the same with the V-cycle in binary64. */
 typedef enum {
-  LAP5CG_PREC_F64 = 0, LAP5CG_PREC_F32 = 1, LAP5CG_PREC_IR_F32 = 2, LAP5CG_PREC_IR_BF16PR = 3
+  LAP5CG_PREC_F64 = 0, LAP5CG_PREC_F32 = 1, LAP5CG_PREC_IR_F32 = 2, LAP5CG_PREC_IR_BF16PR = 3,
+  LAP5CG_PREC_MG_F32 = 4, LAP5CG_PREC_MG_F64 = 5
 } lap5cg_precision;
 
 /* Per-solve outcome, written on the device (one entry per right-hand side or
@@ -134,7 +142,12 @@ typedef struct {
                                launch parameters give bit-identical results.  0 = the default
                                fixed-order partial sums.  Other precisions, grids of 2^36
                                points or more and batched solves: LAP5CG_ERR_UNSUPPORTED. */
-  int32_t pad_;
+  int32_t mg_nu;            /* MG_F32 / MG_F64: smoothing sweeps before and after the coarse
+                               correction; 0 = default (2) */
+  int32_t mg_levels;        /* MG_F32 / MG_F64: at most this many grids; 0 = as many as the
+                               sides allow */
+  int32_t mg_coarse_sweeps; /* MG_F32 / MG_F64: damped Jacobi sweeps on the coarsest grid;
+                               0 = default (8) */
 } lap5cg_opts;
 
 /* Fill *o with the defaults above. */

@@ -28,13 +28,15 @@ ERR_INVALID_ARG, ERR_CUDA, ERR_BREAKDOWN, ERR_SYNC_TIMEOUT = -1, -2, -3, -4
 ERR_NONFINITE, ERR_UNSUPPORTED, ERR_WORKSPACE = -5, -6, -7
 
 CLASSIC, NEWCG = 0, 1
-PREC_F64, PREC_F32, PREC_IR_F32, PREC_IR_BF16PR = 0, 1, 2, 3
+PREC_F64, PREC_F32, PREC_IR_F32, PREC_IR_BF16PR, PREC_MG_F32, PREC_MG_F64 = 0, 1, 2, 3, 4, 5
 DT_F64, DT_F32, DT_BF16 = 0, 1, 2
 MAX_BATCH = 1024
 
 _VARIANTS = {"classic": CLASSIC, "newcg": NEWCG, CLASSIC: CLASSIC, NEWCG: NEWCG}
 _PRECISIONS = {"f64": PREC_F64, "f32": PREC_F32, "ir_f32": PREC_IR_F32, "ir_bf16pr": PREC_IR_BF16PR,
-               PREC_F64: PREC_F64, PREC_F32: PREC_F32, PREC_IR_F32: PREC_IR_F32, PREC_IR_BF16PR: PREC_IR_BF16PR}
+               "mg_f32": PREC_MG_F32, "mg_f64": PREC_MG_F64,
+               PREC_F64: PREC_F64, PREC_F32: PREC_F32, PREC_IR_F32: PREC_IR_F32, PREC_IR_BF16PR: PREC_IR_BF16PR,
+               PREC_MG_F32: PREC_MG_F32, PREC_MG_F64: PREC_MG_F64}
 
 INFO_DTYPE = np.dtype([("status", "<i4"), ("iters", "<i4"), ("outer_iters", "<i4"), ("pad", "<i4"),
                        ("relres_recursive", "<f8"), ("relres_true", "<f8")])
@@ -49,7 +51,8 @@ class Opts(ctypes.Structure):
                 ("max_outer", ctypes.c_int32), ("tol_inner", ctypes.c_double), ("timeout_s", ctypes.c_double),
                 ("history", ctypes.c_void_p), ("team_ctas", ctypes.c_int32), ("ring_slots", ctypes.c_int32),
                 ("resident", ctypes.c_int32), ("lane_vec", ctypes.c_int32),
-                ("reproducible", ctypes.c_int32), ("pad_", ctypes.c_int32)]
+                ("reproducible", ctypes.c_int32), ("mg_nu", ctypes.c_int32), ("mg_levels", ctypes.c_int32),
+                ("mg_coarse_sweeps", ctypes.c_int32)]
 
 
 _lib = None

@@ -98,10 +98,11 @@ int choose_ring(const void* func, int slot_bytes, const lap5cg_opts& o, int wpc,
 static bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
 static size_t elem_of_precision(int precision) { return precision == LAP5CG_PREC_F32 ? 4 : 8; }
+static bool is_mg(int precision) { return precision == LAP5CG_PREC_MG_F32 || precision == LAP5CG_PREC_MG_F64; }
 
 // Lane vector width of the solver kernels for a precision: binary64 2,
 // binary32 4, mixed-precision kernels 4 (binary64 b and x read 32 bytes a lane).
-static int vec_of_precision(int precision) { return precision == LAP5CG_PREC_F64 ? 2 : 4; }
+static int vec_of_precision(int precision) { return (precision == LAP5CG_PREC_F64 || is_mg(precision)) ? 2 : 4; }
 
 static int internal_ld(int nx, int ld, int precision) {
   const int v = vec_of_precision(precision);
@@ -113,6 +114,8 @@ static size_t solver_ws(int nx, int ny, int ldw, int variant, int precision) {
   switch (precision) {
     case LAP5CG_PREC_F64: return ws_bytes_f64(nx, ny, ldw, variant);
     case LAP5CG_PREC_F32: return ws_bytes_f32(nx, ny, ldw, variant);
+    case LAP5CG_PREC_MG_F32:
+    case LAP5CG_PREC_MG_F64: return ws_bytes_mg(nx, ny, ldw, variant, precision);
     default: return ws_bytes_ir(nx, ny, variant, precision);
   }
 }
@@ -153,7 +156,9 @@ void lap5cg_opts_default(lap5cg_opts* o) {
   o->resident = 0;
   o->lane_vec = 0;
   o->reproducible = 0;
-  o->pad_ = 0;
+  o->mg_nu = 0;
+  o->mg_levels = 0;
+  o->mg_coarse_sweeps = 0;
 }
 
 const char* lap5cg_status_string(int status) {
@@ -183,7 +188,7 @@ int lap5_apply(int nx, int ny, int ld, int dtype, const void* x, void* y, void* 
 size_t cg_workspace_size(int nx, int ny, int ld, int variant, int precision, int nrhs) {
   if (!valid_shape(nx, ny, ld) || nrhs < 1) return 0;
   if (variant != LAP5CG_CLASSIC && variant != LAP5CG_NEWCG) return 0;
-  if (precision < LAP5CG_PREC_F64 || precision > LAP5CG_PREC_IR_BF16PR) return 0;
+  if (precision < LAP5CG_PREC_F64 || precision > LAP5CG_PREC_MG_F64) return 0;
   const int ldw = internal_ld(nx, ld, precision);
   size_t s = solver_ws(nx, ny, ldw, variant, precision);
   if (s == 0) return 0;
@@ -196,13 +201,14 @@ int cg_solve(int nx, int ny, int ld, const void* b, void* x, double tol, int max
              void* stream) {
   if (!valid_shape(nx, ny, ld) || !b || !x || !info || maxit < 0 || nrhs < 1) return LAP5CG_ERR_INVALID_ARG;
   if (variant != LAP5CG_CLASSIC && variant != LAP5CG_NEWCG) return LAP5CG_ERR_INVALID_ARG;
-  if (precision < LAP5CG_PREC_F64 || precision > LAP5CG_PREC_IR_BF16PR) return LAP5CG_ERR_INVALID_ARG;
+  if (precision < LAP5CG_PREC_F64 || precision > LAP5CG_PREC_MG_F64) return LAP5CG_ERR_INVALID_ARG;
   if (tol != tol) return LAP5CG_ERR_INVALID_ARG;  // NaN tolerance
   lap5cg_opts o;
   if (opts) o = *opts;
   else lap5cg_opts_default(&o);
   if (o.rr_period < 0 || o.warps_per_cta < 0 || o.warps_per_cta > 16 || o.ctas < 0 || o.min_rows < 0 ||
-      o.maxit_inner < 0 || o.max_outer < 0 || o.ring_slots > kRingMaxSlots ||
+      o.maxit_inner < 0 || o.max_outer < 0 || o.ring_slots > kRingMaxSlots || o.mg_nu < 0 || o.mg_levels < 0 ||
+      o.mg_coarse_sweeps < 0 ||
       (o.lane_vec != 0 && o.lane_vec != 4 && o.lane_vec != 8) || o.reproducible < 0 || o.reproducible > 1)
     return LAP5CG_ERR_INVALID_ARG;
   if (o.reproducible && precision != LAP5CG_PREC_F64) return LAP5CG_ERR_UNSUPPORTED;
@@ -265,6 +271,8 @@ int cg_solve(int nx, int ny, int ld, const void* b, void* x, double tol, int max
       switch (precision) {
         case LAP5CG_PREC_F64: rc = solve_f64(p, st); break;
         case LAP5CG_PREC_F32: rc = solve_f32(p, st); break;
+        case LAP5CG_PREC_MG_F32:
+        case LAP5CG_PREC_MG_F64: rc = solve_mg(p, st); break;
         default: rc = solve_ir(p, st); break;
       }
     }

@@ -41,6 +41,7 @@ int apply_dispatch(int nx, int ny, int ld, int dtype, const void* x, void* y, cu
 size_t ws_bytes_f64(int nx, int ny, int ldw, int variant);
 size_t ws_bytes_f32(int nx, int ny, int ldw, int variant);
 size_t ws_bytes_ir(int nx, int ny, int variant, int precision);
+size_t ws_bytes_mg(int nx, int ny, int ldw, int variant, int precision);
 
 size_t batched_ws(int count, const int* nx, const int* ny, const int* ld, int variant, int precision);
 int solve_batched(int count, const int* nx, const int* ny, const int* ld, const void* const* b, void* const* x,
@@ -54,6 +55,7 @@ int try_small(const SolvePlan& p, cudaStream_t st, bool* used);
 int solve_f64(const SolvePlan& p, cudaStream_t st);
 int solve_f32(const SolvePlan& p, cudaStream_t st);
 int solve_ir(const SolvePlan& p, cudaStream_t st);
+int solve_mg(const SolvePlan& p, cudaStream_t st);
 
 // Device properties cached per device.
 struct DevProps {

@@ -1,0 +1,107 @@
+"""GPU multigrid-preconditioned CG (precision "mg_f64" / "mg_f32": binary64
+PCG with a binary64 / binary32 V-cycle as M^-1) against the oracle's cg_pcg.
+
+Tolerances.  With the V-cycle in binary64 the GPU and the oracle take the same
+steps in the same association order; they differ in fused multiply-adds
+(Jacobi sweeps, vector updates) and in the order of dot-product partial sums,
+so fixed-iteration iterates agree to rounding level (asserted 1e-11 relative).
+A binary32 V-cycle is a slightly different (rounded) preconditioner: converged
+solves reach the same tolerance in about the same number of iterations."""
+import numpy as np
+import pytest
+import torch
+
+import lap5_inputs as gen
+import oracle
+import paper_1803_03797_gb300 as lap5cg
+
+pytestmark = pytest.mark.gpu
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+
+
+def _solve(b, nx, precision, tol, maxit, **opt):
+    x, info = lap5cg.cg_solve(_dev(b), tol=tol, maxit=maxit, precision=precision, nx=nx,
+                              opts=lap5cg.default_opts(**opt))
+    return x.cpu().numpy()[:, :nx], lap5cg.decode_info(info)[0]
+
+
+def _rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+# (1, 1) .. (16, 16): the whole hierarchy on one CTA; (300, 200): level 0 grid-wide,
+# the rest on one CTA; (1, 200), (200, 1): no coarse grid at all
+SHAPES = [(1, 1), (2, 2), (3, 5), (15, 15), (16, 16), (63, 63), (100, 100), (130, 67), (300, 200), (255, 257),
+          (1, 200), (200, 1), (513, 130)]
+
+
+@pytest.mark.parametrize("nx,ny", SHAPES)
+def test_fixed_iterations_track_oracle_f64_vcycle(nx, ny):
+    b = gen.uniform_rhs(nx, ny, seed=nx * 3 + ny, ld=gen.pitch(nx, 8))
+    for k in (1, 3, 6):
+        x, rec = _solve(b, nx, "mg_f64", 0.0, k)
+        xo, io = oracle.cg_pcg(b, tol=0.0, maxit=k, nx=nx)
+        assert rec["iters"] == io["iters"], (k, rec, io)
+        assert rec["status"] == io["status"], (k, rec, io)
+        assert _rel(x, xo[:, :nx]) <= 1e-11, (k, _rel(x, xo[:, :nx]))
+
+
+@pytest.mark.parametrize("precision", ["mg_f64", "mg_f32"])
+@pytest.mark.parametrize("nx,ny", [(63, 63), (100, 100), (300, 200), (513, 130), (1, 200)])
+def test_converged_solve_matches_oracle(precision, nx, ny):
+    tol = 1e-10
+    b = gen.uniform_rhs(nx, ny, seed=nx + 5 * ny, ld=gen.pitch(nx, 8))
+    x, rec = _solve(b, nx, precision, tol, 500)
+    xo, io = oracle.cg_pcg(b, tol=tol, maxit=500, nx=nx)
+    assert rec["status"] == lap5cg.OK, rec
+    assert rec["relres_true"] <= 1.5 * tol
+    slack = 2 if precision == "mg_f64" else 4
+    assert abs(rec["iters"] - io["iters"]) <= slack, (rec, io)
+    xt, _ = oracle.cg_pcg(b, tol=1e-13, maxit=500, nx=nx)
+    assert _rel(x, xt[:, :nx]) <= gen.condition_number(nx, ny) * 2 * tol
+
+
+@pytest.mark.parametrize("opt", [dict(mg_nu=1), dict(mg_nu=3), dict(mg_levels=1), dict(mg_levels=2),
+                                 dict(mg_coarse_sweeps=3), dict(warps_per_cta=4), dict(ctas=40)])
+def test_options_track_oracle(opt):
+    nx, ny = 300, 200
+    b = gen.uniform_rhs(nx, ny, seed=17, ld=gen.pitch(nx, 8))
+    k = 5
+    x, rec = _solve(b, nx, "mg_f64", 0.0, k, **opt)
+    ok = {"levels": opt.get("mg_levels", oracle.MG_LEVELS) or oracle.MG_LEVELS, "nu": opt.get("mg_nu", 2),
+          "nu_coarse": opt.get("mg_coarse_sweeps", 8)}
+    xo, io = oracle.cg_pcg(b, tol=0.0, maxit=k, nx=nx, **ok)
+    assert rec["iters"] == io["iters"] == k
+    assert _rel(x, xo[:, :nx]) <= 1e-11
+
+
+def test_edge_cases_and_rejections():
+    n = 48
+    z = np.zeros((n, n))
+    x, rec = _solve(z, n, "mg_f32", 1e-10, 100)
+    assert rec["status"] == lap5cg.OK and rec["iters"] == 0 and not x.any()
+    b = gen.uniform_rhs(n, n, seed=1)
+    b[5, 5] = np.inf
+    x, rec = _solve(b, n, "mg_f32", 1e-10, 100)
+    assert rec["status"] == lap5cg.ERR_NONFINITE
+    bd = _dev(gen.uniform_rhs(n, n, seed=1))
+    with pytest.raises(lap5cg.Lap5cgError):  # the outer solver is Algorithm 1
+        lap5cg.cg_solve(bd, tol=1e-10, precision="mg_f32", variant="newcg")
+    with pytest.raises(lap5cg.Lap5cgError):
+        lap5cg.cg_solve(bd, tol=1e-10, precision="mg_f32", opts=lap5cg.default_opts(mg_nu=-1))
+
+
+@pytest.mark.parametrize("precision", ["mg_f32", "mg_f64"])
+def test_full_size_4096_reaches_1e10(precision):
+    # the 4096 x 4096 benchmark grid and right-hand side, to 1e-10; the true
+    # residual recomputed by the oracle's stencil
+    n = 4096
+    b = gen.manufactured_rhs(n, n, seed=2)
+    x, rec = _solve(b, n, precision, 1e-10, 200)
+    assert rec["status"] == lap5cg.OK and rec["iters"] <= 30, rec
+    res = b - oracle.lap5_apply(x)
+    assert np.linalg.norm(res) <= 1.05e-10 * np.linalg.norm(b)

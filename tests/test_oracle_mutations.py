@@ -19,7 +19,8 @@ SRC = os.path.join(os.path.dirname(oracle.__file__), "lap5_oracle.c")
 MUTATIONS = {
     "stencil_sign_west": ("acc -= at64(x, nx, ny, ld, i - 1, j);", "acc += at64(x, nx, ny, ld, i - 1, j);"),
     "stencil_index_north": ("acc -= at64(x, nx, ny, ld, i, j + 1);", "acc -= at64(x, nx, ny, ld, i + 1, j + 1);"),
-    "classic_beta_inverted": ("double beta = gnew / gamma;", "double beta = gamma / gnew;"),
+    "classic_beta_inverted": ("double beta = gnew / gamma;                      /* (r,r)/(r_old,r_old) */",
+                              "double beta = gamma / gnew;                      /* (r,r)/(r_old,r_old) */"),
     "classic_alpha_transposed": ("double alpha = gamma / pz;", "double alpha = pz / gamma;"),
     "newcg_r_sign": ("axpy64(nx, ny, ld, r, -alpha, q);                 /* line 22 */",
                      "axpy64(nx, ny, ld, r, alpha, q);                 /* line 22 */"),
