@@ -205,13 +205,15 @@ def fused_f32_roofline(lap5cg, torch, dev, hbm_peak, n=8192, iters=200, reps=3):
 
 def time_to_solution(lap5cg, torch, dev, n, rhs, tol=1e-10):
     """Wall time on the GPU (CUDA events, one solve after a warm-up) to reach
-    relative residual tol: FP64 classic and NewCG vs mixed precision."""
+    relative residual tol: FP64 classic and NewCG vs mixed precision and the
+    multigrid-preconditioned CG (binary64 PCG, binary32 / binary64 V-cycle)."""
     b = torch.from_numpy(rhs).to(dev)
     out = {}
     # NewCG to 1e-10 at these condition numbers needs residual replacement
     # (without it Algorithm 2 breaks down in binary64, on the oracle as well)
     for name, variant, prec, rr in (("f64_classic", "classic", "f64", 0), ("f64_newcg_rr100", "newcg", "f64", 100),
-                                    ("ir_f32", "classic", "ir_f32", 0), ("ir_bf16pr", "classic", "ir_bf16pr", 0)):
+                                    ("ir_f32", "classic", "ir_f32", 0), ("ir_bf16pr", "classic", "ir_bf16pr", 0),
+                                    ("pcg_mg_f32", "classic", "mg_f32", 0), ("pcg_mg_f64", "classic", "mg_f64", 0)):
         opts = lap5cg.default_opts(rr_period=rr)
         lap5cg.cg_solve(b, tol=tol, maxit=10 ** 6, variant=variant, precision=prec, opts=opts)  # warm-up
         torch.cuda.synchronize(dev)
@@ -226,6 +228,7 @@ def time_to_solution(lap5cg, torch, dev, n, rhs, tol=1e-10):
         del x
     out["speedup_ir_f32_vs_f64_classic"] = out["f64_classic"]["ms"] / out["ir_f32"]["ms"]
     out["speedup_ir_bf16pr_vs_f64_classic"] = out["f64_classic"]["ms"] / out["ir_bf16pr"]["ms"]
+    out["speedup_pcg_mg_f32_vs_f64_classic"] = out["f64_classic"]["ms"] / out["pcg_mg_f32"]["ms"]
     return out
 
 
