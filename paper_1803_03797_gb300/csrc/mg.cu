@@ -33,106 +33,182 @@ constexpr double kMgC = 0.2;         // omega / 4 with omega = 4/5
 
 template <class TM>
 struct MgLevel {
-  int nx, ny;    // dense grid, pitch nx
-  TM *b, *u, *v;  // right-hand side and two iterate buffers
+  int nx, ny, ld;  // ld a multiple of 4, rows 16-byte aligned
+  TM *b, *u, *v;   // right-hand side and two iterate buffers
 };
 
 template <class TM>
 struct PcgArgs {
   SolveCommon c;
   Grid<const double> b;
-  Grid<double> x, r, p, q;
+  Grid<double> x, r, p0, p1, q;  // p double-buffered: its halo is read while it is rewritten
   MgLevel<TM> lv[kMgMaxLevels];
   int nlev;    // levels (>= 1); level nlev-1 is the coarsest
   int lsmall;  // first level run by CTA 0 alone (nlev: none)
   int nu, nu_c;
 };
 
-// rows over warps, columns over lanes
+// The warps taking part in a pass (all of the grid's, or CTA 0's) and the
+// march direction (alternating from pass to pass keeps rows in L2).
 struct Sched {
   int w, nw, lane;
+  bool rev;
 };
 
-template <class F>
-__device__ __forceinline__ void for_points(const Sched& s, int nx, int ny, F&& f) {
-  for (int j = s.w; j < ny; j += s.nw)
-    for (int i = s.lane; i < nx; i += 32) f(i, j);
-}
-
-template <class T>
-__device__ __forceinline__ T mg_at(const T* a, int nx, int ny, int i, int j) {
-  return (i < 0 || i >= nx || j < 0 || j >= ny) ? T(0) : a[(size_t)j * nx + i];
-}
-
-// (A a)(i, j) in the Sec. II-B add order
-template <class T>
-__device__ __forceinline__ T mg_apply(const T* a, int nx, int ny, int i, int j) {
-  T acc = T(4) * a[(size_t)j * nx + i];
-  acc -= mg_at(a, nx, ny, i - 1, j);
-  acc -= mg_at(a, nx, ny, i + 1, j);
-  acc -= mg_at(a, nx, ny, i, j - 1);
-  acc -= mg_at(a, nx, ny, i, j + 1);
-  return acc;
-}
+template <class TM> struct MgVec { static constexpr int V = 16 / (int)sizeof(TM); };  // one 16-byte vector a lane
 
 __device__ __forceinline__ float mg_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double mg_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
 
-// out = in + c (b - A in)
-template <class TM>
-__device__ void mg_jacobi(const Sched& s, const MgLevel<TM>& L, const TM* in, TM* out) {
+// Damped Jacobi sweep (JAC) out = in + c (b - A in), or residual out = b - A in;
+// with DOT also accumulates (r, out) against the binary64 grid r (level 0).
+template <class TM, bool JAC, bool DOT>
+__device__ void mg_stencil_pass(const Sched& s, const MgLevel<TM>& L, const TM* in, TM* out,
+                                const Grid<const double>& r, Acc64& acc) {
+  constexpr int V = MgVec<TM>::V;
+  const Units un = make_units(L.nx, L.ny, V, s.nw, 2);
+  const Grid<const TM> gi{in, L.ld}, gb{L.b, L.ld};
+  const Grid<TM> go{out, L.ld};
   const TM c = (TM)kMgC;
-  for_points(s, L.nx, L.ny, [&](int i, int j) {
-    const size_t k = (size_t)j * L.nx + i;
-    out[k] = mg_fma(c, L.b[k] - mg_apply(in, L.nx, L.ny, i, j), in[k]);
-  });
+  struct D { TM b[V]; };
+  for (int u = s.w; u < un.nunits; u += s.nw) {
+    int st, y0, y1;
+    unit_bounds(un, u, L.ny, st, y0, y1);
+    const int xs = st * 32 * V, xl = Lanes<V>::first(xs, s.lane);
+    const int nval = L.nx - xl;
+    auto field = [&](int j, FRow<V, TM>& f) { field_plain<V>(gi, L.nx, L.ny, j, xl, xs, s.lane, f); };
+    auto load = [&](int j, D& d) { load_row<V>(gb, j, xl, L.nx, d.b); };
+    auto finish = [&](int j, const D& d, const FRow<V, TM>& S, const FRow<V, TM>& C, const FRow<V, TM>& N) {
+      TM ax[V], o[V];
+      stencil_row<V>(S, C, N, s.lane, ax);
+#pragma unroll
+      for (int k = 0; k < V; ++k) o[k] = JAC ? mg_fma(c, d.b[k] - ax[k], C.f[k]) : d.b[k] - ax[k];
+      store_row<V>(go, j, xl, L.nx, o);
+      if constexpr (DOT) {
+        double rv[V], zv[V];
+        load_row<V>(r, j, xl, L.nx, rv);
+#pragma unroll
+        for (int k = 0; k < V; ++k) zv[k] = (double)o[k];
+        acc_dot<V>(acc, j, rv, zv, nval);
+      }
+    };
+    march<V, TM, D>(y0, y1, s.rev, field, load, finish);
+  }
 }
 
-// out = b - A in
+// Fine values 2I0 .. 2I0+4 of row j for a lane whose coarse columns are I0,
+// I0+1 (2I0 a multiple of 4): one vector load, the fifth from the next lane.
 template <class TM>
-__device__ void mg_residual(const Sched& s, const MgLevel<TM>& L, const TM* in, TM* out) {
-  for_points(s, L.nx, L.ny, [&](int i, int j) {
-    const size_t k = (size_t)j * L.nx + i;
-    out[k] = L.b[k] - mg_apply(in, L.nx, L.ny, i, j);
-  });
+__device__ __forceinline__ void mg_fine5(const Grid<const TM>& g, int nx, int ny, int j, int f0, int lane, TM (&v)[5]) {
+  TM t[4];
+  if (j < ny) {
+    load_row<4>(g, j, f0, nx, t);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) t[k] = TM(0);
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) v[k] = t[k];
+  TM e = __shfl_down_sync(0xffffffffu, t[0], 1);
+  if (lane == 31) e = (j < ny && f0 + 4 < nx) ? g.row(j)[f0 + 4] : TM(0);
+  v[4] = e;
 }
 
-// C.b = P^T res (fine F), and the first sweep from zero: C.u = c C.b
+// C.b = P^T res (fine F), and the first sweep from zero: C.u = c C.b.  Two
+// coarse columns a lane; coarse rows march upwards re-using the shared fine row.
 template <class TM>
 __device__ void mg_restrict(const Sched& s, const MgLevel<TM>& F, const TM* res, const MgLevel<TM>& C) {
+  const Units un = make_units(C.nx, C.ny, 2, s.nw, 2);
+  const Grid<const TM> gf{res, F.ld};
+  const Grid<TM> gcb{C.b, C.ld}, gcu{C.u, C.ld};
   const TM c = (TM)kMgC;
-  for_points(s, C.nx, C.ny, [&](int I, int J) {
-    const int i = 2 * I + 1, j = 2 * J + 1;
-    const TM rC = res[(size_t)j * F.nx + i];
-    const TM s1 = ((mg_at(res, F.nx, F.ny, i - 1, j) + mg_at(res, F.nx, F.ny, i + 1, j)) +
-                   mg_at(res, F.nx, F.ny, i, j - 1)) + mg_at(res, F.nx, F.ny, i, j + 1);
-    const TM s2 = ((mg_at(res, F.nx, F.ny, i - 1, j - 1) + mg_at(res, F.nx, F.ny, i + 1, j - 1)) +
-                   mg_at(res, F.nx, F.ny, i - 1, j + 1)) + mg_at(res, F.nx, F.ny, i + 1, j + 1);
-    const TM bc = TM(0.25) * ((TM(4) * rC + TM(2) * s1) + s2);
-    const size_t k = (size_t)J * C.nx + I;
-    C.b[k] = bc;
-    C.u[k] = c * bc;
-  });
+  for (int u = s.w; u < un.nunits; u += s.nw) {
+    int st, y0, y1;
+    unit_bounds(un, u, C.ny, st, y0, y1);
+    const int I0 = st * 64 + 2 * s.lane, f0 = 2 * I0;
+    TM lo[5], mid[5], hi[5];
+    mg_fine5(gf, F.nx, F.ny, 2 * y0, f0, s.lane, lo);
+    for (int J = y0; J < y1; ++J) {
+      mg_fine5(gf, F.nx, F.ny, 2 * J + 1, f0, s.lane, mid);
+      mg_fine5(gf, F.nx, F.ny, 2 * J + 2, f0, s.lane, hi);
+      TM bc[2], uc[2];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {  // coarse column I0 + q: fine columns f0 + 2q + {0, 1, 2}
+        const int w = 2 * q, m = w + 1, e = w + 2;
+        const TM s1 = ((mid[w] + mid[e]) + lo[m]) + hi[m];
+        const TM s2 = ((lo[w] + lo[e]) + hi[w]) + hi[e];
+        bc[q] = TM(0.25) * ((TM(4) * mid[m] + TM(2) * s1) + s2);
+        uc[q] = c * bc[q];
+      }
+      store_row<2>(gcb, J, I0, C.nx, bc);
+      store_row<2>(gcu, J, I0, C.nx, uc);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) lo[k] = hi[k];
+    }
+  }
 }
 
-// f += P e (coarse C)
+// Coarse values I0-1, I0, I0+1 of coarse row J for a lane whose fine columns
+// are 2*I0 .. 2*I0+3 (I0 even): a 2-vector load, the first from the previous lane.
+template <class TM>
+__device__ __forceinline__ void mg_coarse3(const Grid<const TM>& g, int nx, int ny, int J, int I0, int lane,
+                                           TM (&v)[3]) {
+  TM t[2];
+  if (J >= 0 && J < ny) {
+    load_row<2>(g, J, I0, nx, t);
+  } else {
+    t[0] = TM(0);
+    t[1] = TM(0);
+  }
+  TM w = __shfl_up_sync(0xffffffffu, t[1], 1);
+  if (lane == 0) w = (J >= 0 && J < ny && I0 >= 1 && I0 - 1 < nx) ? g.row(J)[I0 - 1] : TM(0);
+  v[0] = w;
+  v[1] = t[0];
+  v[2] = t[1];
+}
+
+// f += P e (coarse C, four fine columns a lane), rows marching upwards.
 template <class TM>
 __device__ void mg_prolong(const Sched& s, const MgLevel<TM>& F, TM* f, const MgLevel<TM>& C, const TM* e) {
-  for_points(s, F.nx, F.ny, [&](int i, int j) {
-    const int I = i >> 1, J = j >> 1;
-    TM v;
-    if ((i & 1) && (j & 1)) {
-      v = mg_at(e, C.nx, C.ny, I, J);
-    } else if (!(i & 1) && (j & 1)) {
-      v = TM(0.5) * (mg_at(e, C.nx, C.ny, I - 1, J) + mg_at(e, C.nx, C.ny, I, J));
-    } else if ((i & 1) && !(j & 1)) {
-      v = TM(0.5) * (mg_at(e, C.nx, C.ny, I, J - 1) + mg_at(e, C.nx, C.ny, I, J));
-    } else {
-      v = TM(0.25) * ((mg_at(e, C.nx, C.ny, I - 1, J - 1) + mg_at(e, C.nx, C.ny, I, J - 1)) +
-                      (mg_at(e, C.nx, C.ny, I - 1, J) + mg_at(e, C.nx, C.ny, I, J)));
+  const Units un = make_units(F.nx, F.ny, 4, s.nw, 2);
+  const Grid<const TM> gc{e, C.ld};
+  const Grid<TM> gf{f, F.ld};
+  for (int u = s.w; u < un.nunits; u += s.nw) {
+    int st, y0, y1;
+    unit_bounds(un, u, F.ny, st, y0, y1);
+    const int f0 = st * 128 + 4 * s.lane, I0 = f0 / 2;
+    // coarse rows J-1 (below) and J (at or above) of the current fine row
+    int Jb = (y0 >> 1) - 1;
+    TM cb[3], ca[3];
+    mg_coarse3(gc, C.nx, C.ny, Jb, I0, s.lane, cb);
+    mg_coarse3(gc, C.nx, C.ny, Jb + 1, I0, s.lane, ca);
+    for (int j = y0; j < y1; ++j) {
+      const int J = j >> 1;  // odd j: coarse row (j-1)/2 = J; even j: rows J-1 and J
+      if (J - 1 != Jb) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) cb[k] = ca[k];
+        Jb = J - 1;
+        mg_coarse3(gc, C.nx, C.ny, J, I0, s.lane, ca);
+      }
+      TM v[4];
+      if (j & 1) {  // odd fine row: coarse row J only
+        v[0] = TM(0.5) * (ca[0] + ca[1]);
+        v[1] = ca[1];
+        v[2] = TM(0.5) * (ca[1] + ca[2]);
+        v[3] = ca[2];
+      } else {      // even fine row: coarse rows J-1 and J
+        v[0] = TM(0.25) * ((cb[0] + cb[1]) + (ca[0] + ca[1]));
+        v[1] = TM(0.5) * (cb[1] + ca[1]);
+        v[2] = TM(0.25) * ((cb[1] + cb[2]) + (ca[1] + ca[2]));
+        v[3] = TM(0.5) * (cb[2] + ca[2]);
+      }
+      TM cur[4];
+      load_row<4>(Grid<const TM>{f, F.ld}, j, f0, F.nx, cur);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) cur[k] += v[k];
+      store_row<4>(gf, j, f0, F.nx, cur);
     }
-    f[(size_t)j * F.nx + i] += v;
-  });
+  }
 }
 
 template <class TM>
@@ -142,13 +218,21 @@ struct Vcycle {
   GridTeam& tm;
   double* red;
   Sched grid, cta;
+  Grid<const double> r;        // for the fused (r, z) of level 0's last sweep
+  Acc64* dot;
   int cur[kMgMaxLevels];  // 0: the level's iterate is in u, 1: in v
   bool exec;              // this CTA runs the passes it meets (small levels: CTA 0 only)
+  bool dot_done;          // (r, z) was accumulated (and the last barrier left to the caller)
+  unsigned pc;            // pass counter: march direction
 
   __device__ TM* it(int l) const { return cur[l] ? lv[l].v : lv[l].u; }
   __device__ TM* other(int l) const { return cur[l] ? lv[l].u : lv[l].v; }
   __device__ bool small(int l) const { return l >= lsmall; }
-  __device__ const Sched& sched(int l) const { return small(l) ? cta : grid; }
+  __device__ Sched sched(int l) {
+    Sched s = small(l) ? cta : grid;
+    s.rev = (pc++ & 1u) != 0u;
+    return s;
+  }
   // barrier after a pass at level l: grid-wide for big levels, CTA-wide for
   // small ones (which only CTA 0 runs)
   __device__ bool sync(int l) {
@@ -158,35 +242,52 @@ struct Vcycle {
     }
     return tm.sync(red);
   }
-  // One pass at level l, then its barrier.  A CTA that does not run small
-  // levels only follows the iterate buffers.
-  template <class F>
-  __device__ bool pass(int l, F&& f) {
-    if (!exec) return true;
-    f(sched(l));
+  // a Jacobi sweep at level l; level 0's final sweep (last) accumulates
+  // (r, z) and leaves its grid barrier to the caller's reduction
+  __device__ bool jacobi(int l, bool last) {
+    if (!exec) {
+      cur[l] ^= 1;
+      if (l == 0 && last) dot_done = true;
+      return true;
+    }
+    const Sched s = sched(l);
+    Acc64 dummy;
+    if (l == 0 && last) {
+      mg_stencil_pass<TM, true, true>(s, lv[l], it(l), other(l), r, *dot);
+      dot_done = true;
+      cur[l] ^= 1;
+      if (small(l)) __syncthreads();
+      return true;
+    }
+    mg_stencil_pass<TM, true, false>(s, lv[l], it(l), other(l), r, dummy);
+    cur[l] ^= 1;
     return sync(l);
   }
   // sweeps 2..n of damped Jacobi (the first sweep, u = c b, came with b)
-  __device__ bool sweeps(int l, int n) {
-    for (int k = 1; k < n; ++k) {
-      if (!pass(l, [&](const Sched& s) { mg_jacobi(s, lv[l], it(l), other(l)); })) return false;
-      cur[l] ^= 1;
-    }
+  __device__ bool sweeps(int l, int n, bool final_level0) {
+    for (int k = 1; k < n; ++k)
+      if (!jacobi(l, final_level0 && k == n - 1)) return false;
     return true;
   }
   __device__ bool down(int l) {  // pre-smoothing, residual, restriction into l+1
-    if (!sweeps(l, nu)) return false;
-    if (!pass(l, [&](const Sched& s) { mg_residual(s, lv[l], it(l), other(l)); })) return false;
-    if (!pass(l, [&](const Sched& s) { mg_restrict(s, lv[l], other(l), lv[l + 1]); })) return false;
+    if (!sweeps(l, nu, false)) return false;
+    if (exec) {
+      Acc64 dummy;
+      mg_stencil_pass<TM, false, false>(sched(l), lv[l], it(l), other(l), r, dummy);
+      if (!sync(l)) return false;
+      mg_restrict(sched(l), lv[l], other(l), lv[l + 1]);
+      if (!sync(l)) return false;
+    }
     cur[l + 1] = 0;
     return true;
   }
   __device__ bool up(int l) {  // prolongation from l+1, then nu post-smoothing sweeps
-    if (!pass(l, [&](const Sched& s) { mg_prolong(s, lv[l], it(l), lv[l + 1], it(l + 1)); })) return false;
-    for (int k = 0; k < nu; ++k) {
-      if (!pass(l, [&](const Sched& s) { mg_jacobi(s, lv[l], it(l), other(l)); })) return false;
-      cur[l] ^= 1;
+    if (exec) {
+      mg_prolong(sched(l), lv[l], it(l), lv[l + 1], it(l + 1));
+      if (!sync(l)) return false;
     }
+    for (int k = 0; k < nu; ++k)
+      if (!jacobi(l, l == 0 && k == nu - 1)) return false;
     return true;
   }
   // One V-cycle; level 0's b and u = c b are in place.  Returns false when
@@ -194,17 +295,20 @@ struct Vcycle {
   __device__ bool run() {
     const int L = nlev;
     cur[0] = 0;
+    dot_done = false;
     const int big_end = min(lsmall, L - 1);  // levels [0, big_end) restrict grid-wide
     exec = true;
     for (int l = 0; l < big_end; ++l)
       if (!down(l)) return false;
     if (lsmall >= L) {  // the coarsest level is big
-      if (!sweeps(L - 1, nu_c)) return false;
+      if (!sweeps(L - 1, nu_c, L == 1)) return false;
     } else {
       exec = blockIdx.x == 0;  // CTA 0 alone; the others follow the buffers
+      const unsigned pc0 = pc;
       for (int l = big_end; l < L - 1; ++l) down(l);
-      sweeps(L - 1, nu_c);
+      sweeps(L - 1, nu_c, L == 1);
       for (int l = L - 2; l >= big_end; --l) up(l);
+      pc = pc0;  // CTA 0 counted its passes; every CTA resumes from the same count
       exec = true;
       if (!tm.sync(red)) return false;  // publishes CTA 0's levels
     }
@@ -216,42 +320,55 @@ struct Vcycle {
 
 template <class TM>
 __device__ __forceinline__ void pcg_solve(const PcgArgs<TM>& a, const MgLevel<TM>* lv, GridTeam& tm, double* red) {
+  constexpr int V = 2;  // binary64 passes: two columns a lane
   const SolveCommon& c = a.c;
   const int lane = threadIdx.x & 31;
   const int wpc = blockDim.x >> 5;
-  const Sched grid{(int)blockIdx.x * wpc + (int)(threadIdx.x >> 5), (int)gridDim.x * wpc, lane};
-  const Sched cta{(int)(threadIdx.x >> 5), wpc, lane};
+  const Sched grid{(int)blockIdx.x * wpc + (int)(threadIdx.x >> 5), (int)gridDim.x * wpc, lane, false};
+  const Sched cta{(int)(threadIdx.x >> 5), wpc, lane, false};
   const MgLevel<TM> L0 = lv[0];
+  const Grid<TM> g0b{L0.b, L0.ld}, g0u{L0.u, L0.ld};
   const TM cm = (TM)kMgC;
   int status = LAP5CG_NOT_CONVERGED, iters = 0;
   double bb = 0.0, rr = 0.0, gamma = 0.0, relres_true = nan("");
   bool aborted = false;
-  Vcycle<TM> vc{a.nlev, a.lsmall, a.nu, a.nu_c, lv, tm, red, grid, cta, {}, true};
-
-  // the iterate of level 0 after a V-cycle, as binary64 (z = M^-1 r)
-  auto z_at = [&](size_t k) -> double { return (double)vc.it(0)[k]; };
+  Acc64 arz;
+  Vcycle<TM> vc{a.nlev, a.lsmall, a.nu, a.nu_c, lv, tm, red, grid, cta,
+                Grid<const double>{a.r.ptr, a.r.ld}, &arz, {}, true, false, 0u};
+  Walker wk;
+  wk.init(tm.rank(), tm.size());
+  int cur = 0;  // p lives in p[cur]
 
   {  // r = b - A x; (b, b), (r, r); level 0: b = r, u = c b
     Acc64 abb, arr;
-    for_points(grid, c.nx, c.ny, [&](int i, int j) {
-      const double* xr = a.x.ptr;
-      const int ld = a.x.ld;
-      auto X = [&](int ii, int jj) -> double {
-        return (ii < 0 || ii >= c.nx || jj < 0 || jj >= c.ny) ? 0.0 : xr[(size_t)jj * ld + ii];
+    struct D { double b[V]; };
+    for (int u = wk.gw; u < c.un.nunits; u += wk.nw) {
+      int s, y0, y1;
+      unit_bounds(c.un, u, c.ny, s, y0, y1);
+      const int xs = s * 32 * V, xl = Lanes<V>::first(xs, wk.lane);
+      const int nval = c.nx - xl;
+      auto field = [&](int j, FRow<V, double>& f) { field_plain<V>(a.x, c.nx, c.ny, j, xl, xs, wk.lane, f); };
+      auto load = [&](int j, D& d) { load_row<V>(a.b, j, xl, c.nx, d.b); };
+      auto finish = [&](int j, const D& d, const FRow<V, double>& S, const FRow<V, double>& C,
+                        const FRow<V, double>& N) {
+        double ax[V], rv[V];
+        TM rb[V], ru[V];
+        stencil_row<V>(S, C, N, wk.lane, ax);
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+          rv[k] = d.b[k] - ax[k];
+          rb[k] = (TM)rv[k];
+          ru[k] = cm * rb[k];
+        }
+        acc_dot<V>(abb, j, d.b, d.b, nval);
+        acc_dot<V>(arr, j, rv, rv, nval);
+        store_row<V>(a.r, j, xl, c.nx, rv);
+        store_row<V>(g0b, j, xl, c.nx, rb);
+        store_row<V>(g0u, j, xl, c.nx, ru);
       };
-      double acc = 4.0 * X(i, j);
-      acc -= X(i - 1, j);
-      acc -= X(i + 1, j);
-      acc -= X(i, j - 1);
-      acc -= X(i, j + 1);
-      const double bv = a.b.row(j)[i], rv = bv - acc;
-      a.r.row(j)[i] = rv;
-      abb.add(bv, bv);
-      arr.add(rv, rv);
-      const size_t k = (size_t)j * L0.nx + i;
-      L0.b[k] = (TM)rv;
-      L0.u[k] = cm * (TM)rv;
-    });
+      march<V, double, D>(y0, y1, wk.rev(), field, load, finish);
+    }
+    ++wk.pc;
     double v[2] = {abb.value(), arr.value()}, o[2];
     if (!tm.template reduce<2>(v, o, red)) { aborted = true; goto done; }
     bb = o[0];
@@ -259,7 +376,7 @@ __device__ __forceinline__ void pcg_solve(const PcgArgs<TM>& a, const MgLevel<TM
   }
   if (!isfinite(bb)) { status = LAP5CG_ERR_NONFINITE; goto done; }
   if (bb == 0.0) {
-    for_points(grid, c.nx, c.ny, [&](int i, int j) { a.x.row(j)[i] = 0.0; });
+    pass_zero<V>(c, c.un, wk, a.x);
     status = LAP5CG_OK;
     rr = 0.0;
     relres_true = 0.0;
@@ -270,67 +387,122 @@ __device__ __forceinline__ void pcg_solve(const PcgArgs<TM>& a, const MgLevel<TM
     if (c.history && tm.rank() == 0 && threadIdx.x == 0) c.history[0] = sqrt(rr / bb);
     if (!isfinite(rr)) { status = LAP5CG_ERR_NONFINITE; goto truecheck; }
     if (rr <= thr) { status = LAP5CG_OK; goto truecheck; }
-    double beta = 0.0;
     for (;;) {
-      // z = M^-1 r, gamma_new = (r, z)
+      // z = M^-1 r and (r, z)
+      arz = Acc64{};
       if (!vc.run()) { aborted = true; goto done; }
+      if (!vc.dot_done) {  // no sweep wrote level 0 (a single level, one sweep): z = u = c b
+        for (int u = wk.gw; u < c.un.nunits; u += wk.nw) {
+          int s, y0, y1;
+          unit_bounds(c.un, u, c.ny, s, y0, y1);
+          const int xl = Lanes<V>::first(s * 32 * V, wk.lane);
+          for (int j = y0; j < y1; ++j) {
+            double rv[V], zv[V];
+            TM zt[V];
+            load_row<V>(a.r, j, xl, c.nx, rv);
+            load_row<V>(Grid<const TM>{vc.it(0), L0.ld}, j, xl, c.nx, zt);
+#pragma unroll
+            for (int k = 0; k < V; ++k) zv[k] = (double)zt[k];
+            acc_dot<V>(arz, j, rv, zv, c.nx - xl);
+          }
+        }
+      }
+      double beta;
       {
-        Acc64 arz;
-        for_points(grid, c.nx, c.ny, [&](int i, int j) {
-          arz.add(a.r.row(j)[i], z_at((size_t)j * L0.nx + i));
-        });
         double v[1] = {arz.value()}, o[1];
         if (!tm.template reduce<1>(v, o, red)) { aborted = true; goto done; }
         if (!(o[0] > 0.0) || !isfinite(o[0])) { status = LAP5CG_ERR_BREAKDOWN; goto truecheck; }
         beta = (iters == 0) ? 0.0 : o[0] / gamma;
         gamma = o[0];
       }
-      // p = z + beta p
-      for_points(grid, c.nx, c.ny, [&](int i, int j) {
-        double* pr = a.p.row(j) + i;
-        const double zv = z_at((size_t)j * L0.nx + i);
-        *pr = (iters == 0) ? zv : __fma_rn(beta, *pr, zv);
-      });
-      if (!tm.sync(red)) { aborted = true; goto done; }
-      // q = A p, (p, q)
+      // p = z + beta p (halo included), q = A p, (p, q)
+      const Grid<double> pold = cur ? a.p1 : a.p0;
+      const Grid<double> pnew = cur ? a.p0 : a.p1;
+      const Grid<const TM> gz{vc.it(0), L0.ld};
+      const bool first = (iters == 0);
       double alpha;
       {
         Acc64 apq;
-        for_points(grid, c.nx, c.ny, [&](int i, int j) {
-          const double* pp = a.p.ptr;
-          const int ld = a.p.ld;
-          auto P = [&](int ii, int jj) -> double {
-            return (ii < 0 || ii >= c.nx || jj < 0 || jj >= c.ny) ? 0.0 : pp[(size_t)jj * ld + ii];
+        struct D { int dummy; };
+        for (int u = wk.gw; u < c.un.nunits; u += wk.nw) {
+          int s, y0, y1;
+          unit_bounds(c.un, u, c.ny, s, y0, y1);
+          const int xs = s * 32 * V, xl = Lanes<V>::first(xs, wk.lane);
+          const int nval = c.nx - xl;
+          auto zone = [&](int j, int x) -> double {
+            return (x < 0 || x >= c.nx) ? 0.0 : (double)gz.row(j)[x];
           };
-          double acc = 4.0 * P(i, j);
-          acc -= P(i - 1, j);
-          acc -= P(i + 1, j);
-          acc -= P(i, j - 1);
-          acc -= P(i, j + 1);
-          a.q.row(j)[i] = acc;
-          apq.add(P(i, j), acc);
-        });
+          auto pone = [&](int j, int x) -> double { return (x < 0 || x >= c.nx) ? 0.0 : pold.row(j)[x]; };
+          auto field = [&](int j, FRow<V, double>& f) {
+            if (j < 0 || j >= c.ny) { f.zero(); return; }
+            TM zt[V];
+            load_row<V>(gz, j, xl, c.nx, zt);
+            if (first) {
+#pragma unroll
+              for (int k = 0; k < V; ++k) f.f[k] = (double)zt[k];
+              f.hl = (wk.lane == 0) ? zone(j, xs - 1) : 0.0;
+              f.hr = (wk.lane == 31) ? zone(j, xs + 32 * V) : 0.0;
+            } else {
+              double pv[V];
+              load_row<V>(pold, j, xl, c.nx, pv);
+#pragma unroll
+              for (int k = 0; k < V; ++k) f.f[k] = __fma_rn(beta, pv[k], (double)zt[k]);
+              f.hl = (wk.lane == 0) ? __fma_rn(beta, pone(j, xs - 1), zone(j, xs - 1)) : 0.0;
+              f.hr = (wk.lane == 31) ? __fma_rn(beta, pone(j, xs + 32 * V), zone(j, xs + 32 * V)) : 0.0;
+            }
+          };
+          auto load = [&](int, D&) {};
+          auto finish = [&](int j, const D&, const FRow<V, double>& S, const FRow<V, double>& C,
+                            const FRow<V, double>& N) {
+            double qv[V];
+            stencil_row<V>(S, C, N, wk.lane, qv);
+            store_row<V>(pnew, j, xl, c.nx, C.f);
+            store_row<V>(a.q, j, xl, c.nx, qv);
+            acc_dot<V>(apq, j, C.f, qv, nval);
+          };
+          march<V, double, D>(y0, y1, wk.rev(), field, load, finish);
+        }
+        ++wk.pc;
         double v[1] = {apq.value()}, o[1];
         if (!tm.template reduce<1>(v, o, red)) { aborted = true; goto done; }
         if (!(o[0] > 0.0) || !isfinite(o[0])) { status = LAP5CG_ERR_BREAKDOWN; goto truecheck; }
         alpha = gamma / o[0];
       }
+      cur ^= 1;
       // x += alpha p, r -= alpha q, (r, r); level 0: b = r, u = c b
       {
         Acc64 arr;
-        const TM cmm = cm;
-        for_points(grid, c.nx, c.ny, [&](int i, int j) {
-          double* xr = a.x.row(j) + i;
-          double* rp = a.r.row(j) + i;
-          const double pv = a.p.row(j)[i], qv = a.q.row(j)[i];
-          *xr = __fma_rn(alpha, pv, *xr);
-          const double rv = __fma_rn(-alpha, qv, *rp);
-          *rp = rv;
-          arr.add(rv, rv);
-          const size_t k = (size_t)j * L0.nx + i;
-          L0.b[k] = (TM)rv;
-          L0.u[k] = cmm * (TM)rv;
-        });
+        struct D { double x[V], r[V], p[V], q[V]; };
+        for (int u = wk.gw; u < c.un.nunits; u += wk.nw) {
+          int s, y0, y1;
+          unit_bounds(c.un, u, c.ny, s, y0, y1);
+          const int xl = Lanes<V>::first(s * 32 * V, wk.lane);
+          const int nval = c.nx - xl;
+          auto load = [&](int j, D& d) {
+            load_row<V>(a.x, j, xl, c.nx, d.x);
+            load_row<V>(a.r, j, xl, c.nx, d.r);
+            load_row<V>(pnew, j, xl, c.nx, d.p);
+            load_row<V>(a.q, j, xl, c.nx, d.q);
+          };
+          auto finish = [&](int j, const D& d) {
+            double xv[V], rv[V];
+            TM rb[V], ru[V];
+#pragma unroll
+            for (int k = 0; k < V; ++k) {
+              xv[k] = __fma_rn(alpha, d.p[k], d.x[k]);
+              rv[k] = __fma_rn(-alpha, d.q[k], d.r[k]);
+              rb[k] = (TM)rv[k];
+              ru[k] = cm * rb[k];
+            }
+            acc_dot<V>(arr, j, rv, rv, nval);
+            store_row<V>(a.x, j, xl, c.nx, xv);
+            store_row<V>(a.r, j, xl, c.nx, rv);
+            store_row<V>(g0b, j, xl, c.nx, rb);
+            store_row<V>(g0u, j, xl, c.nx, ru);
+          };
+          stream_rows<D>(y0, y1, wk.rev(), load, finish);
+        }
+        ++wk.pc;
         double v[1] = {arr.value()}, o[1];
         if (!tm.template reduce<1>(v, o, red)) { aborted = true; goto done; }
         rr = o[0];
@@ -344,21 +516,9 @@ __device__ __forceinline__ void pcg_solve(const PcgArgs<TM>& a, const MgLevel<TM
   }
 truecheck:
   if (c.true_res) {
-    Acc64 arr;
-    for_points(grid, c.nx, c.ny, [&](int i, int j) {
-      const double* xr = a.x.ptr;
-      const int ld = a.x.ld;
-      auto X = [&](int ii, int jj) -> double {
-        return (ii < 0 || ii >= c.nx || jj < 0 || jj >= c.ny) ? 0.0 : xr[(size_t)jj * ld + ii];
-      };
-      double acc = 4.0 * X(i, j);
-      acc -= X(i - 1, j);
-      acc -= X(i + 1, j);
-      acc -= X(i, j - 1);
-      acc -= X(i, j + 1);
-      const double rv = a.b.row(j)[i] - acc;
-      arr.add(rv, rv);
-    });
+    Acc64 abb, arr;
+    const Grid<double> none{nullptr, 0};
+    pass_residual<V>(c, wk, a.b, a.x, none, abb, arr);
     double v[1] = {arr.value()}, o[1];
     if (!tm.template reduce<1>(v, o, red)) { aborted = true; goto done; }
     relres_true = sqrt(o[0] / bb);
@@ -392,12 +552,14 @@ static int mg_levels(int nx, int ny, int max_levels, int* lnx, int* lny) {
   return L;
 }
 
+static int mg_pitch(int nx) { return (nx + 3) / 4 * 4; }
+
 template <class TM>
 static size_t mg_level_bytes(int nx, int ny) {
   int lnx[kMgMaxLevels], lny[kMgMaxLevels];
   const int L = mg_levels(nx, ny, 0, lnx, lny);
   size_t s = 0;
-  for (int l = 0; l < L; ++l) s += 3 * align_up((size_t)lnx[l] * (size_t)lny[l] * sizeof(TM), kAlign);
+  for (int l = 0; l < L; ++l) s += 3 * align_up((size_t)mg_pitch(lnx[l]) * (size_t)lny[l] * sizeof(TM), kAlign);
   return s;
 }
 
@@ -405,7 +567,7 @@ size_t ws_bytes_mg(int nx, int ny, int ldw, int variant, int precision) {
   if (variant != LAP5CG_CLASSIC) return 0;  // the outer solver is Algorithm 1
   const size_t vec = align_up((size_t)ny * (size_t)ldw * sizeof(double), kAlign);
   const size_t lv = precision == LAP5CG_PREC_MG_F32 ? mg_level_bytes<float>(nx, ny) : mg_level_bytes<double>(nx, ny);
-  return kCtlBytes + 3 * vec + lv;
+  return kCtlBytes + 4 * vec + lv;
 }
 
 template <class TM>
@@ -416,12 +578,13 @@ static int solve_mg_t(const SolvePlan& p, cudaStream_t st) {
   PcgArgs<TM> a;
   int lnx[kMgMaxLevels], lny[kMgMaxLevels];
   a.nlev = mg_levels(p.nx, p.ny, p.opts.mg_levels, lnx, lny);
-  unsigned char* lv = base + 3 * vec;
+  unsigned char* lv = base + 4 * vec;
   a.lsmall = a.nlev;
   for (int l = 0; l < a.nlev; ++l) {
-    const size_t bytes = align_up((size_t)lnx[l] * (size_t)lny[l] * sizeof(TM), kAlign);
+    const size_t bytes = align_up((size_t)mg_pitch(lnx[l]) * (size_t)lny[l] * sizeof(TM), kAlign);
     a.lv[l].nx = lnx[l];
     a.lv[l].ny = lny[l];
+    a.lv[l].ld = mg_pitch(lnx[l]);
     a.lv[l].b = reinterpret_cast<TM*>(lv);
     a.lv[l].u = reinterpret_cast<TM*>(lv + bytes);
     a.lv[l].v = reinterpret_cast<TM*>(lv + 2 * bytes);
@@ -441,8 +604,9 @@ static int solve_mg_t(const SolvePlan& p, cudaStream_t st) {
   a.b = Grid<const double>{static_cast<const double*>(p.b), p.ld};
   a.x = Grid<double>{static_cast<double*>(p.x), p.ld};
   a.r = Grid<double>{reinterpret_cast<double*>(base), p.ldw};
-  a.p = Grid<double>{reinterpret_cast<double*>(base + vec), p.ldw};
-  a.q = Grid<double>{reinterpret_cast<double*>(base + 2 * vec), p.ldw};
+  a.p0 = Grid<double>{reinterpret_cast<double*>(base + vec), p.ldw};
+  a.p1 = Grid<double>{reinterpret_cast<double*>(base + 2 * vec), p.ldw};
+  a.q = Grid<double>{reinterpret_cast<double*>(base + 3 * vec), p.ldw};
   void* args[] = {&a};
   return cooperative_launch(fn, cfg, args, st, rg);
 }
