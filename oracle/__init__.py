@@ -88,6 +88,8 @@ def lib():
         L.ora_mg_precond.restype = i
         L.ora_cg_pcg.argtypes = [i, i, i, vp, vp, d, i, i, i, i, vp, ctypes.POINTER(Info)]
         L.ora_cg_pcg.restype = i
+        L.ora_cg_ppcg.argtypes = [i, i, i, vp, vp, d, i, i, i, i, ctypes.POINTER(Info)]
+        L.ora_cg_ppcg.restype = i
         L.ora_f32_to_bf16.argtypes = [ctypes.c_float]
         L.ora_f32_to_bf16.restype = ctypes.c_uint16
         _lib = L
@@ -479,4 +481,16 @@ def cg_pcg(b, x0=None, tol=1e-10, maxit=1000, nx=None, levels=MG_LEVELS, nu=MG_N
                      ctypes.byref(info))
     if history:
         return x, info.as_dict(), hist[:info.iters + 1]
+    return x, info.as_dict()
+
+
+def cg_ppcg(b, x0=None, tol=1e-10, maxit=1000, nx=None, levels=MG_LEVELS, nu=MG_NU, nu_coarse=MG_NU_COARSE):
+    """Pipelined preconditioned CG (Algorithm 2 with M^-1 = one V-cycle;
+    levels = 0 gives M = I).  Returns (x, info dict)."""
+    ny, ld = b.shape
+    nx = ld if nx is None else nx
+    b = _grid(b, np.float64, nx)
+    x = np.zeros_like(b) if x0 is None else _grid(x0, np.float64, nx).copy()
+    info = Info()
+    lib().ora_cg_ppcg(nx, ny, ld, _ptr(b), _ptr(x), tol, maxit, levels, nu, nu_coarse, ctypes.byref(info))
     return x, info.as_dict()

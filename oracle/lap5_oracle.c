@@ -692,3 +692,81 @@ int ora_cg_pcg(int nx, int ny, int ld, const double* b, double* x, double tol, i
   if (info) *info = inf;
   return status;
 }
+
+/* ------------------------------------------------------------------ */
+/* Pipelined preconditioned CG: Algorithm 2 with a preconditioner, in the  */
+/* general form of the cited Ghysels-Vanroose method (the paper fixes     */
+/* M = I, where u = r, m = w and s = q below and the recurrences reduce to */
+/* Algorithm 2 line by line).  With M^-1 the multigrid V-cycle above:     */
+/*   r = b - A x, u = M^-1 r, w = A u;                                     */
+/*   per iteration: gamma = (r, u), delta = (w, u), m = M^-1 w, n = A m;   */
+/*   beta = gamma / gamma_old, alpha = 1 / (delta / gamma - beta / alpha)  */
+/*   (first: beta = 0, alpha = gamma / delta);                             */
+/*   z = n + beta z, q = m + beta q, s = w + beta s, p = u + beta p;       */
+/*   x += alpha p, r -= alpha s, u -= alpha q, w -= alpha z.               */
+/* Stops when (r, r) <= tol^2 (b, b), tested where gamma is formed.        */
+/* ------------------------------------------------------------------ */
+int ora_cg_ppcg(int nx, int ny, int ld, const double* b, double* x, double tol, int maxit, int levels, int nu,
+                int nu_c, ora_info* info) {
+  ora_info inf; memset(&inf, 0, sizeof inf);
+  if (!arg_ok(nx, ny, ld, maxit) || !b || !x || levels < 0 || nu < 0 || nu_c < 0) {
+    inf.status = ORA_ERR_INVALID_ARG; if (info) *info = inf; return inf.status;
+  }
+  const size_t n = (size_t)ny * ld;
+  double bb = ora_dot_f64(nx, ny, ld, b, b);
+  if (!isfinite(bb)) { inf.status = ORA_ERR_NONFINITE; inf.relres_recursive = NAN; inf.relres_true = NAN; if (info) *info = inf; return inf.status; }
+  if (bb == 0.0) { zero64(nx, ny, ld, x); inf.status = ORA_OK; if (info) *info = inf; return inf.status; }
+  const double thr = tol > 0.0 ? tol * tol * bb : 0.0;
+  double *r = calloc(n, 8), *u = calloc(n, 8), *w = calloc(n, 8), *m = calloc(n, 8), *nv = calloc(n, 8);
+  double *z = calloc(n, 8), *q = calloc(n, 8), *s = calloc(n, 8), *p = calloc(n, 8);
+  if (!r || !u || !w || !m || !nv || !z || !q || !s || !p) {
+    free(r); free(u); free(w); free(m); free(nv); free(z); free(q); free(s); free(p);
+    inf.status = ORA_ERR_INVALID_ARG; if (info) *info = inf; return inf.status;
+  }
+  int status = ORA_NOT_CONVERGED, k = 0;
+  double rr = 0.0, gamma = 0.0, alpha = 0.0;
+  residual64(nx, ny, ld, b, x, r);                       /* r = b - A x */
+  if (ora_mg_precond(nx, ny, ld, r, u, levels, nu, nu_c) != ORA_OK) status = ORA_ERR_INVALID_ARG;
+  ora_lap5_apply_f64(nx, ny, ld, u, w);                  /* w = A u */
+  while (status == ORA_NOT_CONVERGED) {
+    const double gamma_old = gamma;
+    rr = ora_dot_f64(nx, ny, ld, r, r);
+    if (!isfinite(rr)) { status = ORA_ERR_NONFINITE; break; }
+    if (rr <= thr) { status = ORA_OK; break; }
+    if (k >= maxit) break;
+    gamma = ora_dot_f64(nx, ny, ld, r, u);               /* gamma = (r, u) */
+    const double delta = ora_dot_f64(nx, ny, ld, w, u);  /* delta = (w, u) */
+    if (ora_mg_precond(nx, ny, ld, w, m, levels, nu, nu_c) != ORA_OK) { status = ORA_ERR_INVALID_ARG; break; }
+    ora_lap5_apply_f64(nx, ny, ld, m, nv);               /* n = A m */
+    double beta;
+    if (k == 0) {
+      if (!(delta > 0.0) || !isfinite(delta) || !(gamma > 0.0)) { status = ORA_ERR_BREAKDOWN; break; }
+      beta = 0.0;
+      alpha = gamma / delta;
+      copy64(nx, ny, ld, z, nv);                         /* z = n, q = m, s = w, p = u */
+      copy64(nx, ny, ld, q, m);
+      copy64(nx, ny, ld, s, w);
+      copy64(nx, ny, ld, p, u);
+    } else {
+      beta = gamma / gamma_old;
+      const double denom = delta / gamma - beta / alpha;
+      if (!(denom > 0.0) || !isfinite(denom) || !(gamma > 0.0)) { status = ORA_ERR_BREAKDOWN; break; }
+      alpha = 1.0 / denom;
+      xpby64(nx, ny, ld, nv, beta, z);                   /* z = n + beta z */
+      xpby64(nx, ny, ld, m, beta, q);                    /* q = m + beta q */
+      xpby64(nx, ny, ld, w, beta, s);                    /* s = w + beta s */
+      xpby64(nx, ny, ld, u, beta, p);                    /* p = u + beta p */
+    }
+    axpy64(nx, ny, ld, x, alpha, p);                     /* x = x + alpha p */
+    axpy64(nx, ny, ld, r, -alpha, s);                    /* r = r - alpha s */
+    axpy64(nx, ny, ld, u, -alpha, q);                    /* u = u - alpha q */
+    axpy64(nx, ny, ld, w, -alpha, z);                    /* w = w - alpha z */
+    ++k;
+  }
+  inf.status = status; inf.iters = k;
+  inf.relres_recursive = sqrt(rr / bb);
+  inf.relres_true = true_relres(nx, ny, ld, b, x, bb);
+  free(r); free(u); free(w); free(m); free(nv); free(z); free(q); free(s); free(p);
+  if (info) *info = inf;
+  return status;
+}

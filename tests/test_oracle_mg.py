@@ -1,5 +1,5 @@
 """Pins for the oracle's multigrid-preconditioned CG (Algorithm 1 with
-M^-1 = one geometric V-cycle).
+M^-1 = one geometric V-cycle) and its pipelined form (Algorithm 2 with M).
 
 References independent of the oracle: dense transfer matrices built column by
 column (restriction = transpose of prolongation), exact interpolation of
@@ -7,7 +7,8 @@ bilinear functions, dense Cholesky and sparse direct solves, symmetry and
 positive definiteness of M^-1 probed with random vectors, the V-cycle's
 contraction as a stationary iteration (textbook range for damped-Jacobi
 V(2,2) on the model problem), size-independent iteration counts, and the
-identity preconditioner reproducing classic CG bit for bit.  Planted mistakes
+identity preconditioner reproducing classic CG (and, pipelined, Algorithm 2)
+bit for bit, the pipelined form tracking the classic one.  Planted mistakes
 in a temporary copy of the oracle are each caught.
 """
 import os
@@ -138,6 +139,38 @@ def test_identity_preconditioner_reproduces_classic_cg():
     assert np.array_equal(x1, x2) and i1["iters"] == i2["iters"] == 25
 
 
+def test_pipelined_pcg_with_identity_is_algorithm_2():
+    # M = I turns the preconditioned recurrences into Algorithm 2 line by line
+    b = gen.uniform_rhs(40, 33, seed=2)
+    x1, i1 = oracle.cg_ppcg(b, tol=0.0, maxit=25, levels=0)
+    x2, i2 = oracle.cg_newcg(b, tol=0.0, maxit=25)
+    assert np.array_equal(x1, x2) and i1["iters"] == i2["iters"] == 25
+
+
+@pytest.mark.parametrize("nx,ny", [(63, 63), (100, 83), (300, 200)])
+def test_pipelined_pcg_tracks_pcg(nx, ny):
+    # the same Krylov iterates in exact arithmetic; early iterations agree to rounding
+    b = gen.uniform_rhs(nx, ny, seed=nx + ny)
+    for k in (1, 4, 8):
+        x1, i1 = oracle.cg_ppcg(b, tol=0.0, maxit=k)
+        x2, i2 = oracle.cg_pcg(b, tol=0.0, maxit=k)
+        assert i1["iters"] == i2["iters"] == k
+        assert np.linalg.norm(x1 - x2) <= 1e-10 * np.linalg.norm(x2)
+    x, info = oracle.cg_ppcg(b, tol=1e-10, maxit=200)
+    _, ic = oracle.cg_pcg(b, tol=1e-10, maxit=200)
+    assert info["status"] == oracle.OK and abs(info["iters"] - ic["iters"]) <= 1
+
+
+@pytest.mark.parametrize("nx,ny", [(3, 5), (16, 7)])
+def test_pipelined_pcg_matches_dense_cholesky(nx, ny):
+    A = kron_laplacian(nx, ny).toarray()
+    b = gen.uniform_rhs(nx, ny, seed=nx * 100 + ny)
+    x_ref = sla.cho_solve(sla.cho_factor(A), flat(b, nx))
+    x, info = oracle.cg_ppcg(b, tol=1e-13, maxit=200)
+    assert info["status"] == oracle.OK
+    assert np.linalg.norm(flat(x, nx) - x_ref) <= gen.condition_number(nx, ny) * 4e-13 * np.linalg.norm(x_ref)
+
+
 def test_pcg_a_norm_error_is_monotone():
     n = 40
     A = kron_laplacian(n, n)
@@ -165,6 +198,10 @@ MUTATIONS = {
     "jacobi_sign": ("xo[t] = xi[t] + ORA_MG_C * (b[t] - tmp[t]);", "xo[t] = xi[t] - ORA_MG_C * (b[t] - tmp[t]);"),
     "pcg_beta_uses_rr": ("double beta = gnew / gamma;\n    gamma = gnew;\n    xpby64(nx, ny, ld, z, beta, p);",
                          "double beta = rr / gamma;\n    gamma = gnew;\n    xpby64(nx, ny, ld, z, beta, p);"),
+    "ppcg_r_uses_q": ("axpy64(nx, ny, ld, r, -alpha, s);                    /* r = r - alpha s */",
+                      "axpy64(nx, ny, ld, r, -alpha, q);                    /* r = r - alpha s */"),
+    "ppcg_q_drops_beta": ("xpby64(nx, ny, ld, m, beta, q);                    /* q = m + beta q */",
+                          "xpby64(nx, ny, ld, m, 0.0, q);                    /* q = m + beta q */"),
     "pcg_p_from_r": ("xpby64(nx, ny, ld, z, beta, p);                      /* p = z + beta p */",
                      "xpby64(nx, ny, ld, r, beta, p);                      /* p = z + beta p */"),
 }
@@ -195,7 +232,12 @@ def _mg_pins_pass():
         if info["status"] != oracle.OK or np.linalg.norm(flat(x, 16) - x_ref) > 1e-9 * np.linalg.norm(x_ref):
             return False
         _, info = oracle.cg_pcg(gen.uniform_rhs(63, 63, seed=6), tol=1e-10, maxit=200)
-        return info["status"] == oracle.OK and info["iters"] <= 10
+        if not (info["status"] == oracle.OK and info["iters"] <= 10):
+            return False
+        b = gen.uniform_rhs(63, 63, seed=7)
+        x1, _ = oracle.cg_ppcg(b, tol=0.0, maxit=6)
+        x2, _ = oracle.cg_pcg(b, tol=0.0, maxit=6)
+        return bool(np.all(np.isfinite(x1))) and np.linalg.norm(x1 - x2) <= 1e-10 * np.linalg.norm(x2)
     except Exception:
         return False
 
