@@ -80,7 +80,9 @@ typedef enum { LAP5CG_CLASSIC = 0, LAP5CG_NEWCG = 1 } lap5cg_variant;
  *              geometric multigrid V(nu, nu) cycle in binary32: levels
  *              (nx, ny) -> ((nx-1)/2, (ny-1)/2), bilinear prolongation P,
  *              restriction P^T, the 5-point mask on every level, damped Jacobi
- *              (omega = 4/5) smoothing.  b and x binary64; classic variant only.
+ *              (omega = 4/5) smoothing.  b and x binary64.  LAP5CG_CLASSIC:
+ *              PCG; LAP5CG_NEWCG: the pipelined form (Algorithm 2 with M: one
+ *              fused pass and one grid reduction per iteration besides M^-1).
  *   MG_F64:    the same with the V-cycle in binary64. */
 typedef enum {
   LAP5CG_PREC_F64 = 0, LAP5CG_PREC_F32 = 1, LAP5CG_PREC_IR_F32 = 2, LAP5CG_PREC_IR_BF16PR = 3,

@@ -312,7 +312,7 @@ def cg_classic_repro(b, x0=None, tol=1e-10, maxit=1000, nx=None, history=None):
         x[:] = 0.0
         return x, {"status": OK, "iters": 0, "outer_iters": 0, "relres_recursive": 0.0, "relres_true": 0.0}
     thr = tol * tol * bb if tol > 0 else 0.0
-    r = _residual(b, x, nx)                      # line 1: r = b - A x0
+    r = _residual(b, x, nx)                      # r = b - A x0
     gamma = dot_repro(r, r, nx)                  # (r, r)
     p = r.copy()                                 # p = r
     if history is not None:
@@ -367,9 +367,9 @@ def cg_newcg_repro(b, x0=None, tol=1e-10, maxit=1000, nx=None, rr_period=0, hist
         return x, {"status": OK, "iters": 0, "outer_iters": 0, "relres_recursive": 0.0, "relres_true": 0.0}
     thr = tol * tol * bb if tol > 0 else 0.0
     status, k = NOT_CONVERGED, 0
-    r = _residual(b, x, nx)                      # line 1
-    w = _apply(r, nx)                            # line 2
-    gamma = dot_repro(r, r, nx)                  # line 3
+    r = _residual(b, x, nx)                      # r = b - A x
+    w = _apply(r, nx)                            # w = A r
+    gamma = dot_repro(r, r, nx)                  # gamma = (r, r)
     if history is not None:
         history.append(math.sqrt(gamma / bb))
     alpha = 0.0
@@ -378,16 +378,16 @@ def cg_newcg_repro(b, x0=None, tol=1e-10, maxit=1000, nx=None, rr_period=0, hist
     elif gamma <= thr:
         status = OK
     elif maxit > 0:
-        delta = dot_repro(w, r, nx)              # line 4
-        n = _apply(w, nx)                        # line 5
+        delta = dot_repro(w, r, nx)              # delta = (w, r)
+        n = _apply(w, nx)                        # n = A w
         if not (delta > 0.0) or not math.isfinite(delta):
             status = ERR_BREAKDOWN
         else:
-            alpha = gamma / delta                # line 6
-            z, q, p = n.copy(), w.copy(), r.copy()   # line 7
-            _fma_axpy(x, alpha, p, nx)           # line 8
-            _fma_axpy(r, -alpha, q, nx)          # line 9
-            _fma_axpy(w, -alpha, z, nx)          # line 10
+            alpha = gamma / delta                # alpha = gamma / delta (beta = 0)
+            z, q, p = n.copy(), w.copy(), r.copy()   # z = n, q = w, p = r
+            _fma_axpy(x, alpha, p, nx)           # x = x + alpha p
+            _fma_axpy(r, -alpha, q, nx)          # r = r - alpha q
+            _fma_axpy(w, -alpha, z, nx)          # w = w - alpha z
             k = 1
     while status == NOT_CONVERGED and k >= 1:
         if rr_period > 0 and k % rr_period == 0:  # residual replacement
@@ -395,8 +395,8 @@ def cg_newcg_repro(b, x0=None, tol=1e-10, maxit=1000, nx=None, rr_period=0, hist
             w = _apply(r, nx)
             q = _apply(p, nx)
             z = _apply(q, nx)
-        gamma_old = gamma                        # line 12
-        gamma = dot_repro(r, r, nx)              # line 13
+        gamma_old = gamma                        # gamma_old = gamma
+        gamma = dot_repro(r, r, nx)              # gamma = (r, r)
         if history is not None:
             history.append(math.sqrt(gamma / bb))
         if not math.isfinite(gamma):
@@ -407,20 +407,20 @@ def cg_newcg_repro(b, x0=None, tol=1e-10, maxit=1000, nx=None, rr_period=0, hist
             break
         if k >= maxit:
             break
-        delta = dot_repro(w, r, nx)              # line 14
-        n = _apply(w, nx)                        # line 15
-        beta = gamma / gamma_old                 # line 16
-        denom = delta / gamma - beta / alpha     # line 17 (de-garbled)
+        delta = dot_repro(w, r, nx)              # delta = (w, r)
+        n = _apply(w, nx)                        # n = A w
+        beta = gamma / gamma_old                 # beta = gamma / gamma_old
+        denom = delta / gamma - beta / alpha     # de-garbled alpha update
         if not (denom > 0.0) or not math.isfinite(denom):
             status = ERR_BREAKDOWN
             break
         alpha = 1.0 / denom
-        _fma_xpby(n, beta, z, nx)                # line 18: z = n + beta z
-        _fma_xpby(w, beta, q, nx)                # line 19: q = w + beta q
-        _fma_xpby(r, beta, p, nx)                # line 20: p = r + beta p
-        _fma_axpy(x, alpha, p, nx)               # line 21
-        _fma_axpy(r, -alpha, q, nx)              # line 22
-        _fma_axpy(w, -alpha, z, nx)              # line 23
+        _fma_xpby(n, beta, z, nx)                # z = n + beta z
+        _fma_xpby(w, beta, q, nx)                # q = w + beta q
+        _fma_xpby(r, beta, p, nx)                # p = r + beta p
+        _fma_axpy(x, alpha, p, nx)               # x = x + alpha p
+        _fma_axpy(r, -alpha, q, nx)              # r = r - alpha q
+        _fma_axpy(w, -alpha, z, nx)              # w = w - alpha z
         k += 1
     return _finish(status, k, gamma, bb, b, x, nx)
 

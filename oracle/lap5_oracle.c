@@ -21,8 +21,9 @@
  *   - stencil add order: acc = 4*xC; acc -= xW; acc -= xE; acc -= xS; acc -= xN
  *     (W = i-1, E = i+1, S = j-1, N = j+1).  The paper fixes only the mask.
  *   - Alg. 2 garbles: "r = r + alpha*s" read as r = r - alpha*q;
- *     "w = w + alpha*z" read as w = w - alpha*z; the unbalanced line 17 read as
- *     alpha = 1/(delta/gamma - beta/alpha_old); line 6 delta is delta_new.
+ *     "w = w + alpha*z" read as w = w - alpha*z; the unbalanced alpha update
+ *     read as alpha = 1/(delta/gamma - beta/alpha_old); the delta of the
+ *     first alpha is delta_new.
  *     These follow the cited Ghysels-Vanroose pipelined CG with M = I.
  *   - stopping test: recursive gamma = (r,r) <= tol^2 (b,b); tol <= 0 means
  *     "never stop early" (threshold 0).  iters = number of x updates.
@@ -264,29 +265,29 @@ int ora_cg_newcg(int nx, int ny, int ld, const double* b, double* x, double tol,
   if (!r || !w || !nv || !z || !q || !p) { free(r); free(w); free(nv); free(z); free(q); free(p); inf.status = ORA_ERR_INVALID_ARG; if (info) *info = inf; return inf.status; }
 
   int status = ORA_NOT_CONVERGED, k = 0;
-  residual64(nx, ny, ld, b, x, r);                    /* line 1: r = b - A x */
-  ora_lap5_apply_f64(nx, ny, ld, r, w);               /* line 2: w = A r */
-  double gamma = ora_dot_f64(nx, ny, ld, r, r);       /* line 3 */
+  residual64(nx, ny, ld, b, x, r);                    /* r = b - A x */
+  ora_lap5_apply_f64(nx, ny, ld, r, w);               /* w = A r */
+  double gamma = ora_dot_f64(nx, ny, ld, r, r);       /* gamma = (r, r) */
   if (tr && tr->relres) tr->relres[0] = sqrt(gamma / bb);
   if (tr) { snap(tr->x, 0, nt, n, x); snap(tr->r, 0, nt, n, r); snap(tr->w, 0, nt, n, w); }
   double alpha = 0.0;
   if (!isfinite(gamma)) status = ORA_ERR_NONFINITE;
   else if (gamma <= thr) status = ORA_OK;
   else if (maxit > 0) {
-    double delta = ora_dot_f64(nx, ny, ld, w, r);     /* line 4 */
-    ora_lap5_apply_f64(nx, ny, ld, w, nv);            /* line 5: n = A w */
+    double delta = ora_dot_f64(nx, ny, ld, w, r);     /* delta = (w, r) */
+    ora_lap5_apply_f64(nx, ny, ld, w, nv);            /* n = A w */
     if (!(delta > 0.0) || !isfinite(delta)) status = ORA_ERR_BREAKDOWN;
     else {
-      alpha = gamma / delta;                          /* line 6 (beta = 0) */
-      copy64(nx, ny, ld, z, nv);                      /* line 7: z = n, q = w, p = r */
+      alpha = gamma / delta;                          /* alpha = gamma / delta (beta = 0) */
+      copy64(nx, ny, ld, z, nv);                      /* z = n, q = w, p = r */
       copy64(nx, ny, ld, q, w);
       copy64(nx, ny, ld, p, r);
       if (tr) { snap(tr->p, 0, nt, n, p); snap(tr->q, 0, nt, n, q); snap(tr->z, 0, nt, n, z);
                 if (tr->alpha && nt > 0) tr->alpha[0] = alpha;
                 if (tr->beta && nt > 0) tr->beta[0] = 0.0; }
-      axpy64(nx, ny, ld, x, alpha, p);                /* line 8 */
-      axpy64(nx, ny, ld, r, -alpha, q);               /* line 9 (read as r - alpha q) */
-      axpy64(nx, ny, ld, w, -alpha, z);               /* line 10 (read as w - alpha z) */
+      axpy64(nx, ny, ld, x, alpha, p);                /* x = x + alpha p */
+      axpy64(nx, ny, ld, r, -alpha, q);               /* r = r - alpha q (printed r + alpha s) */
+      axpy64(nx, ny, ld, w, -alpha, z);               /* w = w - alpha z (printed w + alpha z) */
       k = 1;
       if (tr) { snap(tr->x, 1, nt, n, x); snap(tr->r, 1, nt, n, r); snap(tr->w, 1, nt, n, w); }
     }
@@ -298,27 +299,27 @@ int ora_cg_newcg(int nx, int ny, int ld, const double* b, double* x, double tol,
       ora_lap5_apply_f64(nx, ny, ld, p, q);
       ora_lap5_apply_f64(nx, ny, ld, q, z);
     }
-    double gamma_old = gamma;                         /* line 12 */
-    gamma = ora_dot_f64(nx, ny, ld, r, r);            /* line 13 */
+    double gamma_old = gamma;                         /* gamma_old = gamma */
+    gamma = ora_dot_f64(nx, ny, ld, r, r);            /* gamma = (r, r) */
     if (tr && tr->relres) tr->relres[k] = sqrt(gamma / bb);
     if (!isfinite(gamma)) { status = ORA_ERR_NONFINITE; break; }
     if (gamma <= thr) { status = ORA_OK; break; }
     if (k >= maxit) break;
-    double delta = ora_dot_f64(nx, ny, ld, w, r);     /* line 14 */
-    ora_lap5_apply_f64(nx, ny, ld, w, nv);            /* line 15: n = A w */
-    double beta = gamma / gamma_old;                  /* line 16 */
-    double denom = delta / gamma - beta / alpha;      /* line 17, de-garbled */
+    double delta = ora_dot_f64(nx, ny, ld, w, r);     /* delta = (w, r) */
+    ora_lap5_apply_f64(nx, ny, ld, w, nv);            /* n = A w */
+    double beta = gamma / gamma_old;                  /* beta = gamma / gamma_old */
+    double denom = delta / gamma - beta / alpha;      /* de-garbled alpha update */
     if (!(denom > 0.0) || !isfinite(denom)) { status = ORA_ERR_BREAKDOWN; break; }
     alpha = 1.0 / denom;
-    xpby64(nx, ny, ld, nv, beta, z);                  /* line 18: z = n + beta z */
-    xpby64(nx, ny, ld, w, beta, q);                   /* line 19: q = w + beta q */
-    xpby64(nx, ny, ld, r, beta, p);                   /* line 20: p = r + beta p */
+    xpby64(nx, ny, ld, nv, beta, z);                  /* z = n + beta z */
+    xpby64(nx, ny, ld, w, beta, q);                   /* q = w + beta q */
+    xpby64(nx, ny, ld, r, beta, p);                   /* p = r + beta p */
     if (tr) { snap(tr->p, k, nt, n, p); snap(tr->q, k, nt, n, q); snap(tr->z, k, nt, n, z);
               if (tr->alpha && k < nt) tr->alpha[k] = alpha;
               if (tr->beta && k < nt) tr->beta[k] = beta; }
-    axpy64(nx, ny, ld, x, alpha, p);                  /* line 21 */
-    axpy64(nx, ny, ld, r, -alpha, q);                 /* line 22 */
-    axpy64(nx, ny, ld, w, -alpha, z);                 /* line 23 */
+    axpy64(nx, ny, ld, x, alpha, p);                  /* x = x + alpha p */
+    axpy64(nx, ny, ld, r, -alpha, q);                 /* r = r - alpha q */
+    axpy64(nx, ny, ld, w, -alpha, z);                 /* w = w - alpha z */
     ++k;
     if (tr) { snap(tr->x, k, nt, n, x); snap(tr->r, k, nt, n, r); snap(tr->w, k, nt, n, w); }
   }

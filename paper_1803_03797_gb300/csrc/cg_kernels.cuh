@@ -484,7 +484,7 @@ done:
 // Algorithm 2 (NewCG), one fused pass and one grid reduction per iteration.
 //   prologue: r = b - A x0                       (pass 1, (b,b))
 //             w = A r, gamma = (r,r), delta = (w,r)   (pass 2)
-//   iteration (lines 12-23 of the paper's loop; the prologue's lines 5-10 are
+//   iteration (Algorithm 2's loop body; the prologue's stencil and updates are
 //   the first iteration with beta = 0 and z, q, p unread):
 //             n = A w from the w tile plus halo, then
 //             z = n + beta z, q = w + beta q, p = r + beta p,
@@ -564,7 +564,7 @@ __device__ void newcg_solve(const NewcgArgs<T>& a, Team& tm, double* red, unsign
   bool aborted = false;
   int cur = 0;  // current w lives in w[cur]
 
-  {  // line 1: r = b - A x
+  {  // r = b - A x
     Acc abb = make_acc<Acc>(tm, 0, c.ny, wk.rev()), arr = make_acc<Acc>(tm, -1, c.ny, wk.rev());
     pass_residual<V>(c, wk, a.b, a.x, a.r, abb, arr);
     double o[1];
@@ -580,7 +580,7 @@ __device__ void newcg_solve(const NewcgArgs<T>& a, Team& tm, double* red, unsign
   }
   {
     const double thr = c.tol > 0.0 ? c.tol * c.tol * bb : 0.0;
-    {  // lines 2-4: w = A r, gamma = (r, r), delta = (w, r)
+    {  // w = A r, gamma = (r, r), delta = (w, r)
       Acc ag = make_acc<Acc>(tm, 0, c.ny, wk.rev()), ad = make_acc<Acc>(tm, 1, c.ny, wk.rev());
       pass_w_from_r<V>(c, wk, a.r, a.w0, ag, ad);
       double o[2];
@@ -593,7 +593,7 @@ __device__ void newcg_solve(const NewcgArgs<T>& a, Team& tm, double* red, unsign
     if (gamma <= thr) { status = LAP5CG_OK; goto truecheck; }
     if (c.maxit <= 0) goto truecheck;
     if (!(delta > 0.0) || !isfinite(delta)) { status = LAP5CG_ERR_BREAKDOWN; goto truecheck; }
-    alpha = gamma / delta;  // line 6
+    alpha = gamma / delta;  // beta = 0
     beta = 0.0;
     for (;;) {
       const bool first = (iters == 0);
@@ -742,8 +742,8 @@ __device__ void newcg_solve(const NewcgArgs<T>& a, Team& tm, double* red, unsign
       if (!isfinite(gamma)) { status = LAP5CG_ERR_NONFINITE; goto truecheck; }
       if (gamma <= thr) { status = LAP5CG_OK; goto truecheck; }
       if (iters >= c.maxit) break;
-      beta = gamma / gold;                               // line 16
-      const double denom = delta / gamma - beta / alpha;  // line 17
+      beta = gamma / gold;
+      const double denom = delta / gamma - beta / alpha;  // de-garbled alpha update
       if (!(denom > 0.0) || !isfinite(denom)) { status = LAP5CG_ERR_BREAKDOWN; goto truecheck; }
       alpha = 1.0 / denom;
     }

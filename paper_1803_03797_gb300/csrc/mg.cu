@@ -42,6 +42,7 @@ struct PcgArgs {
   SolveCommon c;
   Grid<const double> b;
   Grid<double> x, r, p0, p1, q;  // p double-buffered: its halo is read while it is rewritten
+  Grid<double> u, w, z, s;       // pipelined form: u = M^-1 r, w = A u, z, s (q and p0 as p shared)
   MgLevel<TM> lv[kMgMaxLevels];
   int nlev;    // levels (>= 1); level nlev-1 is the coarsest
   int lsmall;  // first level run by CTA 0 alone (nlev: none)
@@ -211,6 +212,22 @@ __device__ void mg_prolong(const Sched& s, const MgLevel<TM>& F, TM* f, const Mg
   }
 }
 
+// Stencil operand row j of a V-cycle iterate, widened to binary64.
+template <int V, class TM>
+__device__ __forceinline__ void field_wide(const Grid<const TM>& g, int nx, int ny, int j, int x, int xs, int lane,
+                                           FRow<V, double>& f) {
+  if (j < 0 || j >= ny) {
+    f.zero();
+    return;
+  }
+  TM t[V];
+  load_row<V>(g, j, x, nx, t);
+#pragma unroll
+  for (int k = 0; k < V; ++k) f.f[k] = (double)t[k];
+  f.hl = (lane == 0 && xs >= 1 && xs - 1 < nx) ? (double)g.row(j)[xs - 1] : 0.0;
+  f.hr = (lane == 31 && xs + 32 * V < nx) ? (double)g.row(j)[xs + 32 * V] : 0.0;
+}
+
 template <class TM>
 struct Vcycle {
   int nlev, lsmall, nu, nu_c;  // as in PcgArgs
@@ -247,12 +264,12 @@ struct Vcycle {
   __device__ bool jacobi(int l, bool last) {
     if (!exec) {
       cur[l] ^= 1;
-      if (l == 0 && last) dot_done = true;
+      if (l == 0 && last && dot) dot_done = true;
       return true;
     }
     const Sched s = sched(l);
     Acc64 dummy;
-    if (l == 0 && last) {
+    if (l == 0 && last && dot) {
       mg_stencil_pass<TM, true, true>(s, lv[l], it(l), other(l), r, *dot);
       dot_done = true;
       cur[l] ^= 1;
@@ -292,9 +309,10 @@ struct Vcycle {
   }
   // One V-cycle; level 0's b and u = c b are in place.  Returns false when
   // the solve must stop (abort or barrier timeout).
-  __device__ bool run() {
+  // start0: the buffer (0: u, 1: v) that holds level 0's first sweep.
+  __device__ bool run(int start0 = 0) {
     const int L = nlev;
-    cur[0] = 0;
+    cur[0] = start0;
     dot_done = false;
     const int big_end = min(lsmall, L - 1);  // levels [0, big_end) restrict grid-wide
     exec = true;
@@ -527,6 +545,236 @@ done:
   write_info(c, tm.rank(), status, aborted, iters, 0, rr, bb, relres_true);
 }
 
+// Pipelined preconditioned CG (Algorithm 2 with M; M = I gives the paper's
+// recurrences).  One fused pass and one grid reduction per iteration besides
+// the V-cycle: n = A m from the V-cycle's result m = M^-1 w (binary64
+// stencil of the converted iterate), then z = n + beta z, q = m + beta q,
+// s = w + beta s, p = u + beta p, x += alpha p, r -= alpha s, u -= alpha q,
+// w -= alpha z, the dot products (r, u), (w, u), (r, r) of the new vectors,
+// and level 0's right-hand side (w) and first sweep for the next V-cycle --
+// written into the buffer the pass does not read.
+template <class TM>
+__device__ __forceinline__ void ppcg_solve(const PcgArgs<TM>& a, const MgLevel<TM>* lv, GridTeam& tm, double* red) {
+  constexpr int V = 2;
+  const SolveCommon& c = a.c;
+  const int lane = threadIdx.x & 31;
+  const int wpc = blockDim.x >> 5;
+  const Sched grid{(int)blockIdx.x * wpc + (int)(threadIdx.x >> 5), (int)gridDim.x * wpc, lane, false};
+  const Sched cta{(int)(threadIdx.x >> 5), wpc, lane, false};
+  const MgLevel<TM> L0 = lv[0];
+  const Grid<TM> g0b{L0.b, L0.ld};
+  const TM cm = (TM)kMgC;
+  int status = LAP5CG_NOT_CONVERGED, iters = 0;
+  double bb = 0.0, rr = 0.0, gamma = 0.0, delta = 0.0, alpha = 0.0, relres_true = nan("");
+  bool aborted = false;
+  Vcycle<TM> vc{a.nlev, a.lsmall, a.nu, a.nu_c, lv, tm, red, grid, cta,
+                Grid<const double>{a.r.ptr, a.r.ld}, nullptr, {}, true, false, 0u};
+  Walker wk;
+  wk.init(tm.rank(), tm.size());
+  const Grid<double> pp = a.p0;
+
+  {  // r = b - A x; (b, b), (r, r); level 0: b = r, first sweep in u
+    Acc64 abb, arr;
+    struct D { double b[V]; };
+    const Grid<TM> g0u{L0.u, L0.ld};
+    for (int u = wk.gw; u < c.un.nunits; u += wk.nw) {
+      int s, y0, y1;
+      unit_bounds(c.un, u, c.ny, s, y0, y1);
+      const int xs = s * 32 * V, xl = Lanes<V>::first(xs, wk.lane);
+      const int nval = c.nx - xl;
+      auto field = [&](int j, FRow<V, double>& f) { field_plain<V>(a.x, c.nx, c.ny, j, xl, xs, wk.lane, f); };
+      auto load = [&](int j, D& d) { load_row<V>(a.b, j, xl, c.nx, d.b); };
+      auto finish = [&](int j, const D& d, const FRow<V, double>& S, const FRow<V, double>& C,
+                        const FRow<V, double>& N) {
+        double ax[V], rv[V];
+        TM rb[V], ru[V];
+        stencil_row<V>(S, C, N, wk.lane, ax);
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+          rv[k] = d.b[k] - ax[k];
+          rb[k] = (TM)rv[k];
+          ru[k] = cm * rb[k];
+        }
+        acc_dot<V>(abb, j, d.b, d.b, nval);
+        acc_dot<V>(arr, j, rv, rv, nval);
+        store_row<V>(a.r, j, xl, c.nx, rv);
+        store_row<V>(g0b, j, xl, c.nx, rb);
+        store_row<V>(g0u, j, xl, c.nx, ru);
+      };
+      march<V, double, D>(y0, y1, wk.rev(), field, load, finish);
+    }
+    ++wk.pc;
+    double v[2] = {abb.value(), arr.value()}, o[2];
+    if (!tm.template reduce<2>(v, o, red)) { aborted = true; goto done; }
+    bb = o[0];
+    rr = o[1];
+  }
+  if (!isfinite(bb)) { status = LAP5CG_ERR_NONFINITE; goto done; }
+  if (bb == 0.0) {
+    pass_zero<V>(c, c.un, wk, a.x);
+    status = LAP5CG_OK;
+    rr = 0.0;
+    relres_true = 0.0;
+    goto done;
+  }
+  {
+    const double thr = c.tol > 0.0 ? c.tol * c.tol * bb : 0.0;
+    if (c.history && tm.rank() == 0 && threadIdx.x == 0) c.history[0] = sqrt(rr / bb);
+    if (!isfinite(rr)) { status = LAP5CG_ERR_NONFINITE; goto truecheck; }
+    if (rr <= thr) { status = LAP5CG_OK; goto truecheck; }
+    if (c.maxit <= 0) goto truecheck;
+    // u = M^-1 r, w = A u; gamma = (r, u), delta = (w, u); level 0: b = w
+    if (!vc.run(0)) { aborted = true; goto done; }
+    {
+      const int s0 = vc.cur[0] ^ 1;  // the next first sweep goes where the iterate is not
+      const Grid<const TM> gm{vc.it(0), L0.ld};
+      const Grid<TM> g0n{s0 ? L0.v : L0.u, L0.ld};
+      Acc64 ag, ad;
+      struct D { double r[V]; };
+      for (int u = wk.gw; u < c.un.nunits; u += wk.nw) {
+        int s, y0, y1;
+        unit_bounds(c.un, u, c.ny, s, y0, y1);
+        const int xs = s * 32 * V, xl = Lanes<V>::first(xs, wk.lane);
+        const int nval = c.nx - xl;
+        auto field = [&](int j, FRow<V, double>& f) { field_wide<V>(gm, c.nx, c.ny, j, xl, xs, wk.lane, f); };
+        auto load = [&](int j, D& d) { load_row<V>(a.r, j, xl, c.nx, d.r); };
+        auto finish = [&](int j, const D& d, const FRow<V, double>& S, const FRow<V, double>& C,
+                          const FRow<V, double>& N) {
+          double wv[V];
+          TM wb[V], wu[V];
+          stencil_row<V>(S, C, N, wk.lane, wv);
+#pragma unroll
+          for (int k = 0; k < V; ++k) {
+            wb[k] = (TM)wv[k];
+            wu[k] = cm * wb[k];
+          }
+          acc_dot<V>(ag, j, d.r, C.f, nval);
+          acc_dot<V>(ad, j, wv, C.f, nval);
+          store_row<V>(a.u, j, xl, c.nx, C.f);
+          store_row<V>(a.w, j, xl, c.nx, wv);
+          store_row<V>(g0b, j, xl, c.nx, wb);
+          store_row<V>(g0n, j, xl, c.nx, wu);
+        };
+        march<V, double, D>(y0, y1, wk.rev(), field, load, finish);
+      }
+      ++wk.pc;
+      double v[2] = {ag.value(), ad.value()}, o[2];
+      if (!tm.template reduce<2>(v, o, red)) { aborted = true; goto done; }
+      gamma = o[0];
+      delta = o[1];
+      vc.cur[0] = s0;
+    }
+    double beta = 0.0;
+    for (;;) {
+      // m = M^-1 w
+      if (!vc.run(vc.cur[0])) { aborted = true; goto done; }
+      const bool first = (iters == 0);
+      if (first) {
+        if (!(delta > 0.0) || !isfinite(delta) || !(gamma > 0.0)) { status = LAP5CG_ERR_BREAKDOWN; goto truecheck; }
+        beta = 0.0;
+        alpha = gamma / delta;
+      }
+      const int s0 = vc.cur[0] ^ 1;  // the next first sweep goes where m is not
+      const Grid<const TM> gm{vc.it(0), L0.ld};
+      const Grid<TM> g0n{s0 ? L0.v : L0.u, L0.ld};
+      double gn, dn;
+      {
+        Acc64 ag, ad, arr;
+        struct D { int dummy; };
+        const double am = alpha, bm = beta;
+        for (int u = wk.gw; u < c.un.nunits; u += wk.nw) {
+          int s, y0, y1;
+          unit_bounds(c.un, u, c.ny, s, y0, y1);
+          const int xs = s * 32 * V, xl = Lanes<V>::first(xs, wk.lane);
+          const int nval = c.nx - xl;
+          auto field = [&](int j, FRow<V, double>& f) { field_wide<V>(gm, c.nx, c.ny, j, xl, xs, wk.lane, f); };
+          auto load = [&](int, D&) {};
+          auto finish = [&](int j, const D&, const FRow<V, double>& S, const FRow<V, double>& C,
+                            const FRow<V, double>& N) {
+            double nv[V], zv[V], qv[V], sv[V], pv[V], xv[V], rv[V], uv[V], wv[V];
+            TM wb[V], wu[V];
+            stencil_row<V>(S, C, N, wk.lane, nv);  // n = A m
+            load_row<V>(a.x, j, xl, c.nx, xv);
+            load_row<V>(a.r, j, xl, c.nx, rv);
+            load_row<V>(a.u, j, xl, c.nx, uv);
+            load_row<V>(a.w, j, xl, c.nx, wv);
+            if (!first) {
+              load_row<V>(a.z, j, xl, c.nx, zv);
+              load_row<V>(a.q, j, xl, c.nx, qv);
+              load_row<V>(a.s, j, xl, c.nx, sv);
+              load_row<V>(pp, j, xl, c.nx, pv);
+            }
+#pragma unroll
+            for (int k = 0; k < V; ++k) {
+              if (first) {
+                zv[k] = nv[k];
+                qv[k] = C.f[k];
+                sv[k] = wv[k];
+                pv[k] = uv[k];
+              } else {
+                zv[k] = __fma_rn(bm, zv[k], nv[k]);
+                qv[k] = __fma_rn(bm, qv[k], C.f[k]);
+                sv[k] = __fma_rn(bm, sv[k], wv[k]);
+                pv[k] = __fma_rn(bm, pv[k], uv[k]);
+              }
+              xv[k] = __fma_rn(am, pv[k], xv[k]);
+              rv[k] = __fma_rn(-am, sv[k], rv[k]);
+              uv[k] = __fma_rn(-am, qv[k], uv[k]);
+              wv[k] = __fma_rn(-am, zv[k], wv[k]);
+              wb[k] = (TM)wv[k];
+              wu[k] = cm * wb[k];
+            }
+            acc_dot<V>(ag, j, rv, uv, nval);
+            acc_dot<V>(ad, j, wv, uv, nval);
+            acc_dot<V>(arr, j, rv, rv, nval);
+            store_row<V>(a.z, j, xl, c.nx, zv);
+            store_row<V>(a.q, j, xl, c.nx, qv);
+            store_row<V>(a.s, j, xl, c.nx, sv);
+            store_row<V>(pp, j, xl, c.nx, pv);
+            store_row<V>(a.x, j, xl, c.nx, xv);
+            store_row<V>(a.r, j, xl, c.nx, rv);
+            store_row<V>(a.u, j, xl, c.nx, uv);
+            store_row<V>(a.w, j, xl, c.nx, wv);
+            store_row<V>(g0b, j, xl, c.nx, wb);
+            store_row<V>(g0n, j, xl, c.nx, wu);
+          };
+          march<V, double, D>(y0, y1, wk.rev(), field, load, finish);
+        }
+        ++wk.pc;
+        double v[3] = {ag.value(), ad.value(), arr.value()}, o[3];
+        if (!tm.template reduce<3>(v, o, red)) { aborted = true; goto done; }
+        gn = o[0];
+        dn = o[1];
+        rr = o[2];
+        ++iters;
+        vc.cur[0] = s0;
+      }
+      if (c.history && tm.rank() == 0 && threadIdx.x == 0) c.history[iters] = sqrt(rr / bb);
+      if (!isfinite(rr)) { status = LAP5CG_ERR_NONFINITE; goto truecheck; }
+      if (rr <= thr) { status = LAP5CG_OK; goto truecheck; }
+      if (iters >= c.maxit) break;
+      const double gold = gamma;
+      gamma = gn;
+      delta = dn;
+      beta = gamma / gold;
+      const double denom = delta / gamma - beta / alpha;
+      if (!(denom > 0.0) || !isfinite(denom) || !(gamma > 0.0)) { status = LAP5CG_ERR_BREAKDOWN; goto truecheck; }
+      alpha = 1.0 / denom;
+    }
+  }
+truecheck:
+  if (c.true_res) {
+    Acc64 abb, arr;
+    const Grid<double> none{nullptr, 0};
+    pass_residual<V>(c, wk, a.b, a.x, none, abb, arr);
+    double v[1] = {arr.value()}, o[1];
+    if (!tm.template reduce<1>(v, o, red)) { aborted = true; goto done; }
+    relres_true = sqrt(o[0] / bb);
+  }
+done:
+  write_info(c, tm.rank(), status, aborted, iters, 0, rr, bb, relres_true);
+}
+
 template <class TM>
 __global__ void __launch_bounds__(512) k_pcg(const PcgArgs<TM> a) {
   __shared__ double red[kRedDoubles];
@@ -535,6 +783,16 @@ __global__ void __launch_bounds__(512) k_pcg(const PcgArgs<TM> a) {
   __syncthreads();
   GridTeam tm{a.c.ctl, a.c.timeout_ns, 0ull};
   pcg_solve<TM>(a, lv, tm, red);
+}
+
+template <class TM>
+__global__ void __launch_bounds__(512) k_ppcg(const PcgArgs<TM> a) {
+  __shared__ double red[kRedDoubles];
+  __shared__ MgLevel<TM> lv[kMgMaxLevels];
+  if (threadIdx.x < kMgMaxLevels) lv[threadIdx.x] = a.lv[threadIdx.x];
+  __syncthreads();
+  GridTeam tm{a.c.ctl, a.c.timeout_ns, 0ull};
+  ppcg_solve<TM>(a, lv, tm, red);
 }
 
 // Level geometry: sides shrink to (n-1)/2 until one would be 0 (or max levels).
@@ -563,11 +821,13 @@ static size_t mg_level_bytes(int nx, int ny) {
   return s;
 }
 
+// binary64 vectors: classic r, p0, p1, q; pipelined r, u, w, z, q, s, p
+static int mg_vectors(int variant) { return variant == LAP5CG_NEWCG ? 7 : 4; }
+
 size_t ws_bytes_mg(int nx, int ny, int ldw, int variant, int precision) {
-  if (variant != LAP5CG_CLASSIC) return 0;  // the outer solver is Algorithm 1
   const size_t vec = align_up((size_t)ny * (size_t)ldw * sizeof(double), kAlign);
   const size_t lv = precision == LAP5CG_PREC_MG_F32 ? mg_level_bytes<float>(nx, ny) : mg_level_bytes<double>(nx, ny);
-  return kCtlBytes + 4 * vec + lv;
+  return kCtlBytes + mg_vectors(variant) * vec + lv;
 }
 
 template <class TM>
@@ -578,7 +838,7 @@ static int solve_mg_t(const SolvePlan& p, cudaStream_t st) {
   PcgArgs<TM> a;
   int lnx[kMgMaxLevels], lny[kMgMaxLevels];
   a.nlev = mg_levels(p.nx, p.ny, p.opts.mg_levels, lnx, lny);
-  unsigned char* lv = base + 4 * vec;
+  unsigned char* lv = base + mg_vectors(p.variant) * vec;
   a.lsmall = a.nlev;
   for (int l = 0; l < a.nlev; ++l) {
     const size_t bytes = align_up((size_t)mg_pitch(lnx[l]) * (size_t)lny[l] * sizeof(TM), kAlign);
@@ -594,7 +854,8 @@ static int solve_mg_t(const SolvePlan& p, cudaStream_t st) {
   a.nu = p.opts.mg_nu > 0 ? p.opts.mg_nu : 2;
   a.nu_c = p.opts.mg_coarse_sweeps > 0 ? p.opts.mg_coarse_sweeps : 8;
   LaunchCfg cfg;
-  const void* fn = reinterpret_cast<const void*>(&k_pcg<TM>);
+  const void* fn = p.variant == LAP5CG_NEWCG ? reinterpret_cast<const void*>(&k_ppcg<TM>)
+                                             : reinterpret_cast<const void*>(&k_pcg<TM>);
   lap5cg_opts o = p.opts;
   if (o.warps_per_cta <= 0) o.warps_per_cta = 8;  // a wider CTA 0 for the small levels
   int rc = plan_units(fn, p.nx, p.ny, 2, o, 0, &cfg);
@@ -607,12 +868,19 @@ static int solve_mg_t(const SolvePlan& p, cudaStream_t st) {
   a.p0 = Grid<double>{reinterpret_cast<double*>(base + vec), p.ldw};
   a.p1 = Grid<double>{reinterpret_cast<double*>(base + 2 * vec), p.ldw};
   a.q = Grid<double>{reinterpret_cast<double*>(base + 3 * vec), p.ldw};
+  if (p.variant == LAP5CG_NEWCG) {  // r, p (p0), q as above; u, w, z, s after them
+    a.u = Grid<double>{reinterpret_cast<double*>(base + 4 * vec), p.ldw};
+    a.w = Grid<double>{reinterpret_cast<double*>(base + 5 * vec), p.ldw};
+    a.z = Grid<double>{reinterpret_cast<double*>(base + 6 * vec), p.ldw};
+    a.s = Grid<double>{reinterpret_cast<double*>(base + 2 * vec), p.ldw};  // p1 is unused: s
+  } else {
+    a.u = a.w = a.z = a.s = Grid<double>{nullptr, 0};
+  }
   void* args[] = {&a};
   return cooperative_launch(fn, cfg, args, st, rg);
 }
 
 int solve_mg(const SolvePlan& p, cudaStream_t st) {
-  if (p.variant != LAP5CG_CLASSIC) return LAP5CG_ERR_UNSUPPORTED;
   if (p.precision == LAP5CG_PREC_MG_F32) return solve_mg_t<float>(p, st);
   if (p.precision == LAP5CG_PREC_MG_F64) return solve_mg_t<double>(p, st);
   return LAP5CG_ERR_INVALID_ARG;

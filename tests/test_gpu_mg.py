@@ -22,8 +22,8 @@ def _dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
 
 
-def _solve(b, nx, precision, tol, maxit, **opt):
-    x, info = lap5cg.cg_solve(_dev(b), tol=tol, maxit=maxit, precision=precision, nx=nx,
+def _solve(b, nx, precision, tol, maxit, variant="classic", **opt):
+    x, info = lap5cg.cg_solve(_dev(b), tol=tol, maxit=maxit, precision=precision, nx=nx, variant=variant,
                               opts=lap5cg.default_opts(**opt))
     return x.cpu().numpy()[:, :nx], lap5cg.decode_info(info)[0]
 
@@ -89,8 +89,6 @@ def test_edge_cases_and_rejections():
     x, rec = _solve(b, n, "mg_f32", 1e-10, 100)
     assert rec["status"] == lap5cg.ERR_NONFINITE
     bd = _dev(gen.uniform_rhs(n, n, seed=1))
-    with pytest.raises(lap5cg.Lap5cgError):  # the outer solver is Algorithm 1
-        lap5cg.cg_solve(bd, tol=1e-10, precision="mg_f32", variant="newcg")
     with pytest.raises(lap5cg.Lap5cgError):
         lap5cg.cg_solve(bd, tol=1e-10, precision="mg_f32", opts=lap5cg.default_opts(mg_nu=-1))
 
@@ -105,3 +103,41 @@ def test_full_size_4096_reaches_1e10(precision):
     assert rec["status"] == lap5cg.OK and rec["iters"] <= 30, rec
     res = b - oracle.lap5_apply(x)
     assert np.linalg.norm(res) <= 1.05e-10 * np.linalg.norm(b)
+
+
+# ---------------------------------------------------------------------------
+# Pipelined form (variant "newcg"): oracle.cg_ppcg
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("nx,ny", [(1, 1), (3, 5), (16, 16), (63, 63), (100, 100), (300, 200), (1, 200), (513, 130)])
+def test_pipelined_fixed_iterations_track_oracle(nx, ny):
+    b = gen.uniform_rhs(nx, ny, seed=nx * 7 + ny, ld=gen.pitch(nx, 8))
+    for k in (1, 3, 6):
+        x, rec = _solve(b, nx, "mg_f64", 0.0, k, variant="newcg")
+        xo, io = oracle.cg_ppcg(b, tol=0.0, maxit=k, nx=nx)
+        assert rec["iters"] == io["iters"], (k, rec, io)
+        assert rec["status"] == io["status"], (k, rec, io)
+        assert _rel(x, xo[:, :nx]) <= 1e-11, (k, _rel(x, xo[:, :nx]))
+
+
+@pytest.mark.parametrize("precision", ["mg_f64", "mg_f32"])
+@pytest.mark.parametrize("nx,ny", [(100, 100), (513, 130)])
+def test_pipelined_converged_matches_oracle(precision, nx, ny):
+    tol = 1e-10
+    b = gen.uniform_rhs(nx, ny, seed=nx + 9 * ny, ld=gen.pitch(nx, 8))
+    x, rec = _solve(b, nx, precision, tol, 500, variant="newcg")
+    _, io = oracle.cg_ppcg(b, tol=tol, maxit=500, nx=nx)
+    assert rec["status"] == lap5cg.OK, rec
+    # the pipelined recurrences stop on their recursive residual; the true one stays close
+    assert rec["relres_true"] <= 3 * tol
+    assert abs(rec["iters"] - io["iters"]) <= (2 if precision == "mg_f64" else 4), (rec, io)
+    xt, _ = oracle.cg_pcg(b, tol=1e-13, maxit=500, nx=nx)
+    assert _rel(x, xt[:, :nx]) <= gen.condition_number(nx, ny) * 3 * tol
+
+
+def test_pipelined_full_size_4096():
+    n = 4096
+    b = gen.manufactured_rhs(n, n, seed=2)
+    x, rec = _solve(b, n, "mg_f32", 1e-10, 200, variant="newcg")
+    assert rec["status"] == lap5cg.OK and rec["iters"] <= 30, rec
+    res = b - oracle.lap5_apply(x)
+    assert np.linalg.norm(res) <= 3e-10 * np.linalg.norm(b)

@@ -22,13 +22,14 @@ MUTATIONS = {
     "classic_beta_inverted": ("double beta = gnew / gamma;                      /* (r,r)/(r_old,r_old) */",
                               "double beta = gamma / gnew;                      /* (r,r)/(r_old,r_old) */"),
     "classic_alpha_transposed": ("double alpha = gamma / pz;", "double alpha = pz / gamma;"),
-    "newcg_r_sign": ("axpy64(nx, ny, ld, r, -alpha, q);                 /* line 22 */",
-                     "axpy64(nx, ny, ld, r, alpha, q);                 /* line 22 */"),
-    "newcg_w_uses_q": ("axpy64(nx, ny, ld, w, -alpha, z);                 /* line 23 */",
-                       "axpy64(nx, ny, ld, w, -alpha, q);                 /* line 23 */"),
-    "newcg_z_drops_beta": ("xpby64(nx, ny, ld, nv, beta, z);                  /* line 18: z = n + beta z */",
-                           "xpby64(nx, ny, ld, nv, 0.0, z);                  /* line 18: z = n + beta z */"),
-    "newcg_alpha_sign": ("double denom = delta / gamma - beta / alpha;", "double denom = delta / gamma + beta / alpha;"),
+    "newcg_r_sign": ("axpy64(nx, ny, ld, r, -alpha, q);                 /* r = r - alpha q */",
+                     "axpy64(nx, ny, ld, r, alpha, q);                 /* r = r - alpha q */"),
+    "newcg_w_uses_q": ("axpy64(nx, ny, ld, w, -alpha, z);                 /* w = w - alpha z */",
+                       "axpy64(nx, ny, ld, w, -alpha, q);                 /* w = w - alpha z */"),
+    "newcg_z_drops_beta": ("xpby64(nx, ny, ld, nv, beta, z);                  /* z = n + beta z */",
+                           "xpby64(nx, ny, ld, nv, 0.0, z);                  /* z = n + beta z */"),
+    "newcg_alpha_sign": ("double denom = delta / gamma - beta / alpha;      /* de-garbled alpha update */",
+                         "double denom = delta / gamma + beta / alpha;      /* de-garbled alpha update */"),
 }
 
 
