@@ -213,7 +213,8 @@ def time_to_solution(lap5cg, torch, dev, n, rhs, tol=1e-10):
     # (without it Algorithm 2 breaks down in binary64, on the oracle as well)
     for name, variant, prec, rr in (("f64_classic", "classic", "f64", 0), ("f64_newcg_rr100", "newcg", "f64", 100),
                                     ("ir_f32", "classic", "ir_f32", 0), ("ir_bf16pr", "classic", "ir_bf16pr", 0),
-                                    ("pcg_mg_f32", "classic", "mg_f32", 0), ("pcg_mg_f64", "classic", "mg_f64", 0)):
+                                    ("pcg_mg_f32", "classic", "mg_f32", 0), ("pcg_mg_f64", "classic", "mg_f64", 0),
+                                    ("pipelined_pcg_mg_f64", "newcg", "mg_f64", 0)):
         opts = lap5cg.default_opts(rr_period=rr)
         lap5cg.cg_solve(b, tol=tol, maxit=10 ** 6, variant=variant, precision=prec, opts=opts)  # warm-up
         torch.cuda.synchronize(dev)

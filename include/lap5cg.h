@@ -81,9 +81,11 @@ typedef enum { LAP5CG_CLASSIC = 0, LAP5CG_NEWCG = 1 } lap5cg_variant;
  *              (nx, ny) -> ((nx-1)/2, (ny-1)/2), bilinear prolongation P,
  *              restriction P^T, the 5-point mask on every level, damped Jacobi
  *              (omega = 4/5) smoothing.  b and x binary64.  LAP5CG_CLASSIC:
- *              PCG; LAP5CG_NEWCG: the pipelined form (Algorithm 2 with M: one
- *              fused pass and one grid reduction per iteration besides M^-1).
- *   MG_F64:    the same with the V-cycle in binary64. */
+ *              PCG; LAP5CG_NEWCG: LAP5CG_ERR_UNSUPPORTED (the pipelined
+ *              recurrences need an exactly linear M; see MG_F64).
+ *   MG_F64:    the same with the V-cycle in binary64; LAP5CG_NEWCG runs the
+ *              pipelined form (Algorithm 2 with M: one fused pass and one grid
+ *              reduction per iteration besides M^-1). */
 typedef enum {
   LAP5CG_PREC_F64 = 0, LAP5CG_PREC_F32 = 1, LAP5CG_PREC_IR_F32 = 2, LAP5CG_PREC_IR_BF16PR = 3,
   LAP5CG_PREC_MG_F32 = 4, LAP5CG_PREC_MG_F64 = 5
