@@ -393,6 +393,9 @@ def main():
     ap.add_argument("--variants", default=",".join(VARIANTS), help="comma list (profiling only)")
     ap.add_argument("--profile-f32", type=int, default=0,
                     help="profiling only: run the binary32 8192^2 solve for this many iterations and exit")
+    ap.add_argument("--profile-mg", type=int, default=0,
+                    help="profiling only: solve the n^2 manufactured problem to 1e-10 twice with the multigrid-"
+                         "preconditioned CG (binary32 V-cycle) and exit")
     args = ap.parse_args()
     _apply_overrides(args)
     if args.warmup < 3:
@@ -402,6 +405,17 @@ def main():
 
     import torch
     import paper_1803_03797_gb300 as lap5cg
+
+    if args.profile_mg:
+        lap5cg.lib()
+        n = args.profile_mg
+        bm = torch.from_numpy(gen.manufactured_rhs(n, n, seed=SEED)).to(torch.device("cuda", 0))
+        for _ in range(2):
+            _, info = lap5cg.cg_solve(bm, tol=1e-10, maxit=500, precision="mg_f32",
+                                      opts=lap5cg.default_opts(true_residual=0))
+        torch.cuda.synchronize()
+        print(json.dumps({"profiling_case": lap5cg.decode_info(info)[0]}))
+        return 0
 
     if args.profile_f32:
         lap5cg.lib()

@@ -88,6 +88,39 @@ template <> struct KindTraits<KIND_F32_NEWCG> { using T = float; static constexp
 template <> struct KindTraits<KIND_IR_F32> { using T = float; static constexpr int V = 4; };
 template <> struct KindTraits<KIND_IR_BF16> { using T = bf16s; static constexpr int V = 4; };
 
+// Eight columns a lane for an instance of width nx: the strips of 256 columns
+// (padded width w8) cost about 0.8 of four-column strips (w4) per column.
+__device__ __forceinline__ bool ir_wide(int nx) {
+  const int w8 = (nx + 255) / 256 * 256, w4 = (nx + 127) / 128 * 128;
+  return 4 * w8 < 5 * w4;
+}
+
+template <class T, int V, bool R = true>
+__device__ __forceinline__ void solve_ir_instance(const BatchArgs& a, const BatchEntry& e, SolveCommon c,
+                                                  unsigned char* base, ClusterTeam& tm, double* red,
+                                                  unsigned char* dsm) {
+  const long long W = (long long)tm.size() * (blockDim.x >> 5);
+  c.un = make_units(e.nx, e.ny, V, W, a.min_rows);
+  const int ldi = ir_ld(e.nx);
+  const size_t vr = vec_bytes(e.ny, ldi, sizeof(T));
+  const size_t vf = vec_bytes(e.ny, ldi, 4);
+  IrArgs<T> s;
+  s.c = c;
+  s.b = Grid<const double>{static_cast<const double*>(e.b), e.ld};
+  s.x = Grid<double>{static_cast<double*>(e.x), e.ld};
+  s.r = Grid<T>{reinterpret_cast<T*>(base), ldi};
+  s.p0 = Grid<T>{reinterpret_cast<T*>(base + vr), ldi};
+  s.p1 = Grid<T>{reinterpret_cast<T*>(base + 2 * vr), ldi};
+  s.z = Grid<float>{reinterpret_cast<float*>(base + 3 * vr), ldi};
+  s.d = Grid<float>{reinterpret_cast<float*>(base + 3 * vr + vf), ldi};
+  s.store_z = a.store_z > 0 ? 1 : 0;
+  s.max_outer = a.max_outer;
+  s.maxit_inner = a.maxit_inner > 0 ? a.maxit_inner : 4 * (e.nx + e.ny) + 50;
+  s.tol_inner = a.tol_inner;
+  s.uo = make_units(e.nx, e.ny, 2, W, a.min_rows);
+  ir_solve<T, V, 2, R>(s, tm, red, dsm);
+}
+
 template <int KIND, bool R>
 __device__ __forceinline__ void solve_instance(const BatchArgs& a, const BatchEntry& e, ClusterTeam& tm, double* red,
                                                unsigned char* dsm) {
@@ -135,24 +168,15 @@ __device__ __forceinline__ void solve_instance(const BatchArgs& a, const BatchEn
     s.rr_period = a.rr_period;
     newcg_solve<T, V, R>(s, tm, red, dsm);
   } else {
-    const int ldi = ir_ld(e.nx);
-    const size_t vr = vec_bytes(e.ny, ldi, sizeof(T));
-    const size_t vf = vec_bytes(e.ny, ldi, 4);
-    IrArgs<T> s;
-    s.c = c;
-    s.b = Grid<const double>{static_cast<const double*>(e.b), e.ld};
-    s.x = Grid<double>{static_cast<double*>(e.x), e.ld};
-    s.r = Grid<T>{reinterpret_cast<T*>(base), ldi};
-    s.p0 = Grid<T>{reinterpret_cast<T*>(base + vr), ldi};
-    s.p1 = Grid<T>{reinterpret_cast<T*>(base + 2 * vr), ldi};
-    s.z = Grid<float>{reinterpret_cast<float*>(base + 3 * vr), ldi};
-    s.d = Grid<float>{reinterpret_cast<float*>(base + 3 * vr + vf), ldi};
-    s.store_z = a.store_z > 0 ? 1 : 0;
-    s.max_outer = a.max_outer;
-    s.maxit_inner = a.maxit_inner > 0 ? a.maxit_inner : 4 * (e.nx + e.ny) + 50;
-    s.tol_inner = a.tol_inner;
-    s.uo = c.un;
-    ir_solve<T, V, V, R>(s, tm, red, dsm);
+    // inner passes: eight columns a lane (ring kernels) where the wider strip
+    // pads the row less than it gains, else four; outer passes: two
+    if constexpr (R) {
+      if (ir_wide(e.nx)) {
+        solve_ir_instance<T, 8>(a, e, c, base, tm, red, dsm);
+        return;
+      }
+    }
+    solve_ir_instance<T, 4, R>(a, e, c, base, tm, red, dsm);
   }
 }
 
@@ -212,8 +236,8 @@ static int ring_slot_kind(int kind) {
     case KIND_F64_NEWCG: return ring_slot_newcg(2, 8);
     case KIND_F32_CLASSIC: return ring_slot_classic(4, 4);
     case KIND_F32_NEWCG: return ring_slot_newcg(4, 4);
-    case KIND_IR_F32: return ring_slot_ir(4, 4);
-    default: return ring_slot_ir(4, 2);
+    case KIND_IR_F32: return ring_slot_ir(8, 4);  // wide instances take eight columns a lane
+    default: return ring_slot_ir(8, 2);
   }
 }
 
@@ -305,7 +329,7 @@ int solve_batched(int count, const int* nx, const int* ny, const int* ld, const 
   int team = o.team_ctas > 0 ? o.team_ctas : 8;
   if (team != 1 && team != 2 && team != 4 && team != 8 && team != 16) return LAP5CG_ERR_INVALID_ARG;
   size_t dyn = 0;
-  const bool auto_on = !(kind == KIND_IR_F32 || kind == KIND_IR_BF16);  // as for single solves
+  const bool auto_on = true;  // as for single solves
   int rc = choose_ring(kernel_of(kind, true), ring_slot_kind(kind), o, wpc, &a.rg, &dyn, auto_on);
   if (rc != LAP5CG_OK) return rc;
   if (a.rg.S > 0 && dyn < (size_t)wpc * (size_t)a.rg.warp_bytes) return LAP5CG_ERR_INVALID_ARG;
