@@ -244,33 +244,35 @@ def batched_workload(lap5cg, torch, dev, tune=True):
     need = lap5cg.batched_workspace_size(nxs, nys, lds, "classic", "ir_f32")
     ws = torch.empty(need, dtype=torch.uint8, device=dev)
     info = torch.empty(256 * lap5cg.INFO_BYTES, dtype=torch.uint8, device=dev)
-    opts = lap5cg.default_opts()
-    tuned = None
-    if tune:
-        opts, tms = lap5cg.autotune_batched(bs, precision="ir_f32", iters=200, nx_list=nxs, cache=False)
+    def timed(opts):
+        def run():
+            for x in xs:
+                x.zero_()
+            lap5cg.cg_solve_batched(bs, xs=xs, tol=1e-10, maxit=10 ** 7, precision="ir_f32", nx_list=nxs, opts=opts,
+                                    workspace=ws, info=info)
+
+        run()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        run()
+        e1.record()
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1), lap5cg.decode_info(info)
+
+    ms_default, recs_default = timed(lap5cg.default_opts())
+    ms, recs, tuned = ms_default, recs_default, None
+    if tune:  # trials solve every instance to 1e-4, so the queue's tail weighs as in the real solve
+        opts, tms = lap5cg.autotune_batched(bs, precision="ir_f32", iters=0, nx_list=nxs, cache=False)
         tuned = {k: int(getattr(opts, k)) for k in ("team_ctas", "warps_per_cta", "ring_slots", "min_rows")}
-
-    def run():
-        for x in xs:
-            x.zero_()
-        lap5cg.cg_solve_batched(bs, xs=xs, tol=1e-10, maxit=10 ** 7, precision="ir_f32", nx_list=nxs, opts=opts,
-                                workspace=ws, info=info)
-
-    run()
-    torch.cuda.synchronize(dev)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    run()
-    e1.record()
-    torch.cuda.synchronize(dev)
-    ms = e0.elapsed_time(e1)
-    recs = lap5cg.decode_info(info)
+        ms, recs = timed(opts)
     pts_it = sum(nx * ny * r["iters"] for nx, ny, r in zip(nxs, nys, recs))
     return {"workload": "256 grids, sides U{64..1024} (seed 4), U[-1,1) RHS, IR: binary32 inner classic CG + FP64 "
-                        "refinement to 1e-10, one persistent launch", "ms": ms,
+                        "refinement to 1e-10, one persistent launch", "ms": ms, "ms_default_opts": ms_default,
             "total_points": int(sum(nx * ny for nx, ny in zip(nxs, nys))),
-            "inner_pts_iters_per_s": pts_it / (ms * 1e-3), "all_converged": all(r["status"] == 0 for r in recs),
-            "max_relres_true": max(r["relres_true"] for r in recs), "tuned_opts": tuned}
+            "inner_pts_iters_per_s": pts_it / (ms * 1e-3),
+            "all_converged": all(r["status"] == 0 for r in recs + recs_default),
+            "max_relres_true": max(r["relres_true"] for r in recs + recs_default), "tuned_opts": tuned}
 
 
 def paper_size_workload(lap5cg, torch, dev, reps=20):

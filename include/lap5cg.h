@@ -250,7 +250,9 @@ LAP5CG_API int lap5cg_tune(int nx, int ny, int ld, const void* b, void* x, int v
                            double* best_ms, void* stream);
 
 /* The same for cg_solve_batched, over team_ctas, warps_per_cta, ring_slots and
- * min_rows; every x[k] is overwritten. */
+ * min_rows; every x[k] is overwritten.  iters = 0: each trial solves every
+ * instance to a relative residual of 1e-4 instead of a fixed iteration count,
+ * so that larger instances weigh more, as in a real solve. */
 LAP5CG_API int lap5cg_tune_batched(int count, const int* nx, const int* ny, const int* ld, const void* const* b,
                                    void* const* x, int variant, int precision, int iters, void* workspace,
                                    size_t ws_bytes, lap5cg_info* info, lap5cg_opts* opts, double* best_ms,

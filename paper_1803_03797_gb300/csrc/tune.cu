@@ -111,7 +111,13 @@ static int run_batched(const lap5cg_opts& o, void* p) {
   lap5cg_opts t = o;
   t.true_residual = 0;
   t.history = nullptr;
-  return cg_solve_batched(c->count, c->nx, c->ny, c->ld, c->b, c->x, 0.0, c->iters, c->variant, c->precision, c->ws,
+  // iters > 0: every instance runs that many iterations; iters == 0: every
+  // instance solves to a relative residual of 1e-4, so that the work per
+  // instance grows with its size as in a real solve (the queue's tail then
+  // weighs as it will)
+  const double tol = c->iters > 0 ? 0.0 : 1e-4;
+  const int maxit = c->iters > 0 ? c->iters : 10000000;
+  return cg_solve_batched(c->count, c->nx, c->ny, c->ld, c->b, c->x, tol, maxit, c->variant, c->precision, c->ws,
                           c->ws_bytes, c->info, &t, c->st);
 }
 
@@ -140,7 +146,7 @@ extern "C" LAP5CG_API int lap5cg_tune_batched(int count, const int* nx, const in
                                               const void* const* b, void* const* x, int variant, int precision,
                                               int iters, void* workspace, size_t ws_bytes, lap5cg_info* info,
                                               lap5cg_opts* opts, double* best_ms, void* stream) {
-  if (!opts || iters < 1 || count < 1 || !nx || !ny || !ld || !b || !x) return LAP5CG_ERR_INVALID_ARG;
+  if (!opts || iters < 0 || count < 1 || !nx || !ny || !ld || !b || !x) return LAP5CG_ERR_INVALID_ARG;
   BatchCtx c{count, variant, precision, iters, nx, ny, ld, b, x, workspace, ws_bytes, info,
              static_cast<cudaStream_t>(stream), (size_t)(precision == LAP5CG_PREC_F32 ? 4 : 8)};
   Param params[4] = {{&lap5cg_opts::team_ctas, {1, 2, 4, 8, 16}, 5},

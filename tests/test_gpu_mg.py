@@ -151,3 +151,17 @@ def test_pipelined_full_size_4096():
     assert rec["status"] == lap5cg.OK and rec["iters"] <= 30, rec
     res = b - oracle.lap5_apply(x)
     assert np.linalg.norm(res) <= 3e-10 * np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("variant", ["classic", "newcg"])
+def test_unaligned_pitch_is_staged(variant):
+    # an odd pitch goes through the aligned staging copies; same solve
+    nx, ny = 100, 70
+    b = gen.uniform_rhs(nx, ny, seed=23, ld=nx + 1)
+    x1, r1 = _solve(b, nx, "mg_f64", 1e-10, 200, variant=variant)
+    b2 = np.zeros((ny, 104))
+    b2[:, :nx] = b[:, :nx]
+    x2, r2 = _solve(b2, nx, "mg_f64", 1e-10, 200, variant=variant)
+    assert r1["status"] == r2["status"] == lap5cg.OK
+    assert r1["iters"] == r2["iters"]
+    assert _rel(x1, x2) <= 1e-13
