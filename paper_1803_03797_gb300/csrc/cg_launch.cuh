@@ -119,18 +119,25 @@ int solve_typed(const SolvePlan& p, cudaStream_t st) {
     int rc = pick_ring(reinterpret_cast<const void*>(&k_classic<T, V, true, EX>), ring_slot_classic(V, (int)sizeof(T)),
                        p.opts, &rg, &dyn, &ring);
     if (rc != LAP5CG_OK) return rc;
-    const void* fn = ring ? reinterpret_cast<const void*>(&k_classic<T, V, true, EX>)
-                          : reinterpret_cast<const void*>(&k_classic<T, V, false, EX>);
+    const void* fn = reinterpret_cast<const void*>(&k_classic<T, V, true, EX>);
+    if constexpr (Lanes<V>::G > 1) {  // eight columns a lane exist with the ring only
+      if (!ring) return LAP5CG_ERR_UNSUPPORTED;
+    } else if (!ring) {
+      fn = reinterpret_cast<const void*>(&k_classic<T, V, false, EX>);
+    }
     rc = plan_units(fn, p.nx, p.ny, V, p.opts, dyn, &cfg, row_align);
     if (rc != LAP5CG_OK) return rc;
     if (ring && p.opts.ring_slots == 0 && cfg.seg_rows < kRingMinRows) {  // short units: register march
-      if constexpr (Lanes<V>::G > 1) return LAP5CG_ERR_UNSUPPORTED;  // the caller narrows the lane vector
-      ring = false;
-      rg.S = 0;
-      dyn = 0;
-      fn = reinterpret_cast<const void*>(&k_classic<T, V, false, EX>);
-      rc = plan_units(fn, p.nx, p.ny, V, p.opts, dyn, &cfg, row_align);
-      if (rc != LAP5CG_OK) return rc;
+      if constexpr (Lanes<V>::G > 1) {
+        return LAP5CG_ERR_UNSUPPORTED;  // the caller narrows the lane vector
+      } else {
+        ring = false;
+        rg.S = 0;
+        dyn = 0;
+        fn = reinterpret_cast<const void*>(&k_classic<T, V, false, EX>);
+        rc = plan_units(fn, p.nx, p.ny, V, p.opts, dyn, &cfg, row_align);
+        if (rc != LAP5CG_OK) return rc;
+      }
     }
     ClassicArgs<T> a;
     a.c = make_common(p, cfg, rg);

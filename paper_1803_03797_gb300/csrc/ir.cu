@@ -47,21 +47,25 @@ static int solve_ir_t(const SolvePlan& p, cudaStream_t st) {
   int rc = pick_ring(reinterpret_cast<const void*>(&k_ir<TR, V, true>), ring_slot_ir(V, (int)sizeof(TR)), p.opts,
                      &rg, &dyn, &ring);
   if (rc != LAP5CG_OK) return rc;
-  if constexpr (Lanes<V>::G > 1) {
-    if (!ring) return LAP5CG_ERR_UNSUPPORTED;  // eight columns a lane exist with the ring only
+  const void* fn = reinterpret_cast<const void*>(&k_ir<TR, V, true>);
+  if constexpr (Lanes<V>::G > 1) {  // eight columns a lane exist with the ring only
+    if (!ring) return LAP5CG_ERR_UNSUPPORTED;
+  } else if (!ring) {
+    fn = reinterpret_cast<const void*>(&k_ir<TR, V, false>);
   }
-  const void* fn = ring ? reinterpret_cast<const void*>(&k_ir<TR, V, true>)
-                        : reinterpret_cast<const void*>(&k_ir<TR, V, false>);
   rc = plan_units(fn, p.nx, p.ny, V, p.opts, dyn, &cfg);
   if (rc != LAP5CG_OK) return rc;
   if (ring && p.opts.ring_slots == 0 && cfg.seg_rows < kRingMinRows) {  // short units: register march
-    if constexpr (Lanes<V>::G > 1) return LAP5CG_ERR_UNSUPPORTED;      // the caller narrows the lane vector
-    ring = false;
-    rg.S = 0;
-    dyn = 0;
-    fn = reinterpret_cast<const void*>(&k_ir<TR, V, false>);
-    rc = plan_units(fn, p.nx, p.ny, V, p.opts, dyn, &cfg);
-    if (rc != LAP5CG_OK) return rc;
+    if constexpr (Lanes<V>::G > 1) {
+      return LAP5CG_ERR_UNSUPPORTED;  // the caller narrows the lane vector
+    } else {
+      ring = false;
+      rg.S = 0;
+      dyn = 0;
+      fn = reinterpret_cast<const void*>(&k_ir<TR, V, false>);
+      rc = plan_units(fn, p.nx, p.ny, V, p.opts, dyn, &cfg);
+      if (rc != LAP5CG_OK) return rc;
+    }
   }
   IrArgs<TR> a;
   a.c = make_common(p, cfg, rg);
