@@ -109,7 +109,8 @@ typedef struct {
   int32_t store_z;          /* classic: 1 stores z = A p (fewer FP64 ops), 0 recomputes A p
                                in the update pass (fewer bytes), -1 = choose by precision */
   int32_t ctas;             /* persistent CTAs; 0 = choose from size and occupancy */
-  int32_t warps_per_cta;    /* 1..16; 0 = default (4; batched: 8) */
+  int32_t warps_per_cta;    /* 1..16; 0 = default (4; batched, cluster-resident and multigrid
+                               solves: 8) */
   int32_t min_rows;         /* minimum rows per warp unit; 0 = default (2) */
   int32_t true_residual;    /* 1 (default) recompute ||b - A x|| at exit, 0 skip */
   int32_t maxit_inner;      /* IR: inner iteration cap per refinement step; 0 = default */
@@ -121,7 +122,10 @@ typedef struct {
                                (single solves only) */
   int32_t team_ctas;        /* cg_solve_batched: CTAs per instance team (one thread-block
                                cluster: 1, 2, 4, 8 or 16); 0 = default (8).  For batched
-                               solves `ctas` caps the total CTAs. */
+                               solves `ctas` caps the total CTAs.  cg_solve of a grid that
+                               fits in one cluster's shared memory (`resident`): the cluster
+                               size (1, 2, 4, 8 or 16; other values: 16), at most one CTA a
+                               row. */
   int32_t ring_slots;       /* rows each warp keeps in flight in its shared-memory ring
                                (bulk asynchronous copies): 0 = automatic (on when the warp
                                units are at least 8 rows tall),

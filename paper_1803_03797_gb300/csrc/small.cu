@@ -389,7 +389,10 @@ static int try_small_t(const SolvePlan& p, cudaStream_t st, bool* used) {
   DevProps dp;
   int rc = dev_props(&dp);
   if (rc != LAP5CG_OK) return rc;
-  const int C = p.ny >= 16 ? 16 : p.ny;  // one to sixteen CTAs, each at least one row
+  // one to sixteen CTAs (team_ctas, default 16), each at least one row
+  int C = p.opts.team_ctas;
+  if (C != 1 && C != 2 && C != 4 && C != 8 && C != 16) C = 16;
+  if (C > p.ny) C = p.ny;
   int R, ldp;
   const size_t smem = small_smem<T>(p.nx, p.ny, p.variant, C, &R, &ldp);
   if (smem + sizeof(double) * kRedDoubles + 1024 > (size_t)dp.max_smem_optin) return LAP5CG_OK;  // too large
@@ -419,7 +422,7 @@ static int try_small_t(const SolvePlan& p, cudaStream_t st, bool* used) {
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   lc.gridDim = dim3(C);
-  lc.blockDim = dim3(256);
+  lc.blockDim = dim3(32 * (p.opts.warps_per_cta > 0 ? p.opts.warps_per_cta : 8));
   lc.dynamicSmemBytes = smem;
   lc.stream = st;
   lc.attrs = attr;
