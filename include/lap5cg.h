@@ -109,8 +109,8 @@ typedef struct {
   int32_t store_z;          /* classic: 1 stores z = A p (fewer FP64 ops), 0 recomputes A p
                                in the update pass (fewer bytes), -1 = choose by precision */
   int32_t ctas;             /* persistent CTAs; 0 = choose from size and occupancy */
-  int32_t warps_per_cta;    /* 1..16; 0 = default (4; batched, cluster-resident and multigrid
-                               solves: 8) */
+  int32_t warps_per_cta;    /* 1..16; 0 = default (4; batched and cluster-resident solves: 8;
+                               multigrid solves: 16) */
   int32_t min_rows;         /* minimum rows per warp unit; 0 = default (2) */
   int32_t true_residual;    /* 1 (default) recompute ||b - A x|| at exit, 0 skip */
   int32_t maxit_inner;      /* IR: inner iteration cap per refinement step; 0 = default */

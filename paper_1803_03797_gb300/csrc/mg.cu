@@ -28,7 +28,7 @@
 namespace lap5 {
 
 constexpr int kMgMaxLevels = 24;
-constexpr int kMgCtaPoints = 16384;  // levels this small run on one CTA
+constexpr int kMgCtaPoints = 4096;  // levels this small run on one CTA
 constexpr double kMgC = 0.2;         // omega / 4 with omega = 4/5
 
 template <class TM>
@@ -857,7 +857,7 @@ static int solve_mg_t(const SolvePlan& p, cudaStream_t st) {
   const void* fn = p.variant == LAP5CG_NEWCG ? reinterpret_cast<const void*>(&k_ppcg<TM>)
                                              : reinterpret_cast<const void*>(&k_pcg<TM>);
   lap5cg_opts o = p.opts;
-  if (o.warps_per_cta <= 0) o.warps_per_cta = 8;  // a wider CTA 0 for the small levels
+  if (o.warps_per_cta <= 0) o.warps_per_cta = 16;  // a wide CTA 0 for the small levels
   int rc = plan_units(fn, p.nx, p.ny, 2, o, 0, &cfg);
   if (rc != LAP5CG_OK) return rc;
   RingGeom rg{0, 0, 0};

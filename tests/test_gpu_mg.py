@@ -33,8 +33,8 @@ def _rel(a, b):
     return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
 
 
-# (1, 1) .. (16, 16): the whole hierarchy on one CTA; (300, 200): level 0 grid-wide,
-# the rest on one CTA; (1, 200), (200, 1): no coarse grid at all
+# (1, 1) .. (63, 63): the whole hierarchy on one CTA; (300, 200): levels 0 and 1
+# grid-wide, the rest on one CTA; (1, 200), (200, 1): no coarse grid at all
 SHAPES = [(1, 1), (2, 2), (3, 5), (15, 15), (16, 16), (63, 63), (100, 100), (130, 67), (300, 200), (255, 257),
           (1, 200), (200, 1), (513, 130)]
 
