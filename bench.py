@@ -203,6 +203,39 @@ def fused_f32_roofline(lap5cg, torch, dev, hbm_peak, n=8192, iters=200, reps=3):
             "lane_vec_4": {"ms_per_launch": t4 * 1e3, "hbm_frac": 32 * pts_it / t4 / 1e9 / hbm_peak}}
 
 
+def stencil_roofline(lap5cg, torch, dev, hbm_peak, n=8192, reps=11):
+    """lap5_apply (y = A x) on an n x n grid per storage type, timed alone after
+    an L2 flush (median of reps): HBM roofline at 2 * element-size algorithmic
+    bytes per point (x read once, y written once), and for binary64 the FP64
+    pipe at 4 operations per point."""
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=dev)  # larger than L2
+    out = {}
+    for name, dt in (("f64", torch.float64), ("f32", torch.float32), ("bf16", torch.bfloat16)):
+        x = torch.from_numpy(gen.uniform_rhs(n, n, seed=5)).to(dev).to(dt)
+        y = torch.empty_like(x)
+        lap5cg.lap5_apply(x, out=y)
+        ms = []
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            lap5cg.lap5_apply(x, out=y)
+            e1.record()
+            torch.cuda.synchronize(dev)
+            ms.append(e0.elapsed_time(e1))
+        t = float(np.median(ms)) * 1e-3
+        gbs = 2 * x.element_size() * n * n / t / 1e9
+        out[name] = {"ms": t * 1e3, "hbm": {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                                            "bytes_per_pt": 2 * x.element_size()}}
+        if name == "f64":
+            tfl = 2 * 4 * n * n / t / 1e12
+            out[name]["fp64"] = {"achieved": tfl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                 "frac": tfl / FP64_PEAK_TFLOPS, "ops_per_pt": 4}
+        del x, y
+    out["workload"] = "%dx%d grid, U[-1,1) (seed 5), one lap5_apply per storage type" % (n, n)
+    return out
+
+
 def time_to_solution(lap5cg, torch, dev, n, rhs, tol=1e-10):
     """Wall time on the GPU (CUDA events, one solve after a warm-up) to reach
     relative residual tol: FP64 classic and NewCG vs mixed precision and the
@@ -561,6 +594,7 @@ def main():
     extras = {}
     if not args.no_extras and ws == 1 and (NX, ITERS) == (4096, 500):
         extras["fused_f32_8192"] = fused_f32_roofline(lap5cg, torch, dev, hbm_peak)
+        extras["lap5_apply_8192"] = stencil_roofline(lap5cg, torch, dev, hbm_peak)
         extras["time_to_1e-10_4096"] = time_to_solution(lap5cg, torch, dev, 4096, b_host)
         extras["batched_256_ir_f32"] = batched_workload(lap5cg, torch, dev)
         extras["paper_100x100_to_1e-8"] = paper_size_workload(lap5cg, torch, dev)

@@ -15,7 +15,7 @@ import paper_1803_03797_gb300 as lap5cg
 pytestmark = pytest.mark.gpu
 
 SHAPES = [(1, 1), (1, 9), (9, 1), (2, 2), (3, 5), (63, 65), (64, 64), (65, 33), (127, 130), (129, 7), (1000, 37),
-          (257, 300)]
+          (257, 300), (513, 19), (2049, 17)]
 
 
 def _dev(a):
@@ -69,6 +69,22 @@ def test_full_size_f64(n):
     x = gen.uniform_rhs(n, n, seed=3)
     y = lap5cg.lap5_apply(_dev(x)).cpu().numpy()
     ref = oracle.lap5_apply(x)
+    np.testing.assert_array_equal(y, ref)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_full_size_8192_narrow_types(dtype):
+    # binary32 runs eight columns a lane (two 16-byte groups), bf16 four
+    n = 8192
+    xf = gen.uniform_rhs(n, n, seed=4, dtype=np.float32)
+    if dtype == "f32":
+        y = lap5cg.lap5_apply(_dev(xf)).cpu().numpy()
+        ref = oracle.lap5_apply(xf, dtype=np.float32)
+    else:
+        xb = oracle.f32_to_bf16_bits(xf)
+        xt = torch.from_numpy(xb.view(np.int16)).to("cuda").view(torch.bfloat16)
+        y = lap5cg.lap5_apply(xt).view(torch.int16).cpu().numpy().view(np.uint16)
+        ref = oracle.lap5_apply(xb, dtype="bf16")
     np.testing.assert_array_equal(y, ref)
 
 
