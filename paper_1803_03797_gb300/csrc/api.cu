@@ -98,11 +98,13 @@ int choose_ring(const void* func, int slot_bytes, const lap5cg_opts& o, int wpc,
 static bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
 static size_t elem_of_precision(int precision) { return precision == LAP5CG_PREC_F32 ? 4 : 8; }
-static bool is_mg(int precision) { return precision == LAP5CG_PREC_MG_F32 || precision == LAP5CG_PREC_MG_F64; }
 
 // Lane vector width of the solver kernels for a precision: binary64 2,
 // binary32 4, mixed-precision kernels 4 (binary64 b and x read 32 bytes a lane).
-static int vec_of_precision(int precision) { return (precision == LAP5CG_PREC_F64 || is_mg(precision)) ? 2 : 4; }
+// Pitch granule (elements) of the arrays a solve reads with vector loads.  The
+// multigrid solve reads its binary64 r four columns a lane in the V-cycle's
+// binary32 layout, so its internal pitch is a multiple of 4 as well.
+static int vec_of_precision(int precision) { return precision == LAP5CG_PREC_F64 ? 2 : 4; }
 
 static int internal_ld(int nx, int ld, int precision) {
   const int v = vec_of_precision(precision);
