@@ -43,7 +43,7 @@ WORKLOAD = ("4096x4096 interior grid, FP64, b = A u* + 1e-3 N(0,1) (seed 2), x0 
 COST = {
     # store-z form with the x update deferred into the next phase P:
     # phase P reads r, p_old, x and writes p, z, x; phase R reads r, z and writes r
-    "classic": {"bytes": 72, "fp64_ops": 9, "kernel": "k_classic<double,2>"},
+    "classic": {"bytes": 72, "fp64_ops": 9, "kernel": "k_classic<double,4>"},  # four columns a lane
     "newcg": {"bytes": 96, "fp64_ops": 12, "kernel": "k_newcg<double,2>"},
 }
 FP64_PEAK_TFLOPS = 1.25  # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (nominal GB300 FP64)

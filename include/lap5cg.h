@@ -134,13 +134,17 @@ typedef struct {
                                thread-block cluster (about 250 x 250 binary64): 0 = solve them
                                there (default, when ring_slots == 0 and rr_period == 0),
                                < 0 = always use the streaming kernels */
-  int32_t lane_vec;         /* cg_solve with binary32 passes (F32 classic; the inner passes of
-                               IR_F32 / IR_BF16PR): columns each lane owns in its warp's strip,
-                               4 or 8; 0 = automatic (8 when nx >= 1024 and the ring is used).
-                               8 needs the classic variant and the shared-memory ring
-                               (ring_slots > 0, or automatic with units at least 8 rows tall),
-                               and store_z <= 0 for IR; otherwise LAP5CG_ERR_UNSUPPORTED.
-                               F64 solves and batched solves ignore it. */
+  int32_t lane_vec;         /* columns each lane owns in its warp's strip.
+                               Binary32 passes (F32 classic; the inner passes of IR_F32 /
+                               IR_BF16PR): 4 or 8; 0 = automatic (8 when nx >= 1024 and the
+                               ring is used).  8 needs the classic variant and the
+                               shared-memory ring (ring_slots > 0, or automatic with units at
+                               least 8 rows tall), and store_z <= 0 for IR.
+                               F64: 2 or 4; 0 = automatic (4 for classic CG with the ring when
+                               ld is a multiple of 4, else 2).  4 needs the classic variant,
+                               the ring and ld a multiple of 4; the reproducible mode takes 2.
+                               Other combinations: LAP5CG_ERR_UNSUPPORTED.  Multigrid and
+                               batched solves ignore it. */
   int32_t reproducible;     /* cg_solve, F64 (classic and NewCG): 1 = dot products whose value
                                does not depend on the launch configuration (CTAs, warps, ring,
                                unit sizes): each is the exact sum of fixed 2-column x 16-row

@@ -211,7 +211,7 @@ int cg_solve(int nx, int ny, int ld, const void* b, void* x, double tol, int max
   if (o.rr_period < 0 || o.warps_per_cta < 0 || o.warps_per_cta > 16 || o.ctas < 0 || o.min_rows < 0 ||
       o.maxit_inner < 0 || o.max_outer < 0 || o.ring_slots > kRingMaxSlots || o.mg_nu < 0 || o.mg_levels < 0 ||
       o.mg_coarse_sweeps < 0 ||
-      (o.lane_vec != 0 && o.lane_vec != 4 && o.lane_vec != 8) || o.reproducible < 0 || o.reproducible > 1)
+      (o.lane_vec != 0 && o.lane_vec != 2 && o.lane_vec != 4 && o.lane_vec != 8) || o.reproducible < 0 || o.reproducible > 1)
     return LAP5CG_ERR_INVALID_ARG;
   if (o.reproducible && precision != LAP5CG_PREC_F64) return LAP5CG_ERR_UNSUPPORTED;
   if (o.reproducible && (long long)nx * (long long)ny >= (1ll << 36)) return LAP5CG_ERR_UNSUPPORTED;  // limb range

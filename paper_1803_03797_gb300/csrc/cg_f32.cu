@@ -15,6 +15,7 @@ size_t ws_bytes_f32(int nx, int ny, int ldw, int variant) {
 // Classic CG with the shared-memory ring only: NewCG and the register march
 // keep too many rows live for eight columns a lane.
 int solve_f32(const SolvePlan& p, cudaStream_t st) {
+  if (p.opts.lane_vec == 2) return LAP5CG_ERR_UNSUPPORTED;
   const bool v8_ok = p.variant == LAP5CG_CLASSIC && p.opts.ring_slots >= 0;
   if (p.opts.lane_vec == 8) return v8_ok ? solve_typed<float, 8>(p, st) : LAP5CG_ERR_UNSUPPORTED;
   if (p.opts.lane_vec == 0 && v8_ok && p.nx >= 1024) {

@@ -101,6 +101,14 @@ inline SolveCommon make_common(const SolvePlan& p, const LaunchCfg& cfg, const R
   return c;
 }
 
+// Lane vectors that exist with the shared-memory ring only: eight columns (two
+// groups), and four binary64 columns (32 bytes a lane: the register march
+// would keep too many rows live).  NewCG runs neither: it keeps six vectors live.
+template <class T, int V>
+struct RingOnly {
+  static constexpr bool value = Lanes<V>::G > 1 || (sizeof(T) == 8 && V == 4);
+};
+
 // EX: reproducible dot products.  Their units start at multiples of 16 rows
 // and the first of the control block's three exact accumulators starts at zero.
 template <class T, int V, bool EX = false>
@@ -120,7 +128,7 @@ int solve_typed(const SolvePlan& p, cudaStream_t st) {
                        p.opts, &rg, &dyn, &ring);
     if (rc != LAP5CG_OK) return rc;
     const void* fn = reinterpret_cast<const void*>(&k_classic<T, V, true, EX>);
-    if constexpr (Lanes<V>::G > 1) {  // eight columns a lane exist with the ring only
+    if constexpr (RingOnly<T, V>::value) {
       if (!ring) return LAP5CG_ERR_UNSUPPORTED;
     } else if (!ring) {
       fn = reinterpret_cast<const void*>(&k_classic<T, V, false, EX>);
@@ -128,7 +136,7 @@ int solve_typed(const SolvePlan& p, cudaStream_t st) {
     rc = plan_units(fn, p.nx, p.ny, V, p.opts, dyn, &cfg, row_align);
     if (rc != LAP5CG_OK) return rc;
     if (ring && p.opts.ring_slots == 0 && cfg.seg_rows < kRingMinRows) {  // short units: register march
-      if constexpr (Lanes<V>::G > 1) {
+      if constexpr (RingOnly<T, V>::value) {
         return LAP5CG_ERR_UNSUPPORTED;  // the caller narrows the lane vector
       } else {
         ring = false;
@@ -152,8 +160,8 @@ int solve_typed(const SolvePlan& p, cudaStream_t st) {
     a.store_z = sz;
     void* args[] = {&a};
     return cooperative_launch(fn, cfg, args, st, rg);
-  } else if constexpr (Lanes<V>::G > 1) {
-    return LAP5CG_ERR_UNSUPPORTED;  // NewCG keeps six vectors live: one group per lane
+  } else if constexpr (RingOnly<T, V>::value) {
+    return LAP5CG_ERR_UNSUPPORTED;  // NewCG keeps six vectors live: narrow lane vectors only
   } else {
     RingGeom rg;
     size_t dyn = 0;

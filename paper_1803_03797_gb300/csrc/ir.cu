@@ -90,6 +90,7 @@ static int solve_ir_t(const SolvePlan& p, cudaStream_t st) {
 // binary32 solve; four with the register march.
 template <class TR>
 static int solve_ir_lanes(const SolvePlan& p, cudaStream_t st) {
+  if (p.opts.lane_vec == 2) return LAP5CG_ERR_UNSUPPORTED;
   const bool v8_ok = p.opts.ring_slots >= 0 && p.opts.store_z <= 0;
   if (p.opts.lane_vec == 8) return v8_ok ? solve_ir_t<TR, 8>(p, st) : LAP5CG_ERR_UNSUPPORTED;
   if (p.opts.lane_vec == 0 && v8_ok && p.nx >= 1024) {

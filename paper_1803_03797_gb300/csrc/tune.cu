@@ -139,6 +139,8 @@ extern "C" LAP5CG_API int lap5cg_tune(int nx, int ny, int ld, const void* b, voi
     params[np++] = {&lap5cg_opts::store_z, {0, 1}, 2};
   if (variant == LAP5CG_CLASSIC && precision != LAP5CG_PREC_F64)  // binary32 passes: lane vector width
     params[np++] = {&lap5cg_opts::lane_vec, {4, 8}, 2};
+  else if (variant == LAP5CG_CLASSIC)  // binary64 classic: two or four columns a lane
+    params[np++] = {&lap5cg_opts::lane_vec, {2, 4}, 2};
   return coordinate_descent(opts, params, np, run_single, &c, c.st, best_ms);
 }
 

@@ -247,6 +247,45 @@ def test_f32_lane_vec_8_converged_and_rejected_forms():
         _solve(b, tol=tol, maxit=10, precision="f32", nx=nx, opts=lap5cg.default_opts(lane_vec=6))
 
 
+@pytest.mark.parametrize("nx,ny", [(1, 9), (3, 40), (127, 33), (128, 30), (129, 41), (255, 64), (300, 77),
+                                   (513, 100)])
+@pytest.mark.parametrize("store_z", [0, 1])
+def test_f64_lane_vec_4_tracks_oracle_and_lane_vec_2(nx, ny, store_z):
+    # four binary64 columns a lane (32 bytes, ring kernel of classic CG):
+    # ragged strips of 128 columns, both z forms
+    b = gen.uniform_rhs(nx, ny, seed=3 * nx + ny, ld=gen.pitch(nx, 8, 32))
+    k = 25
+    xs = {}
+    for lv in (2, 4):
+        opts = lap5cg.default_opts(lane_vec=lv, ring_slots=4, store_z=store_z)
+        x, info = _solve(b, tol=0.0, maxit=k, variant="classic", nx=nx, opts=opts)
+        xs[lv] = x[:, :nx]
+        assert info[0]["iters"] <= k and info[0]["status"] in (lap5cg.OK, lap5cg.NOT_CONVERGED)
+    xo, io = oracle.cg_classic(b, tol=0.0, maxit=k, nx=nx)
+    assert _rel(xs[4], xo[:, :nx]) <= 1e-10
+    assert _rel(xs[4], xs[2]) <= 1e-10
+
+
+def test_f64_lane_vec_rejected_forms():
+    nx, ny = 200, 50
+    b4 = gen.uniform_rhs(nx, ny, seed=8, ld=gen.pitch(nx, 8, 32))
+    b2 = gen.uniform_rhs(nx, ny, seed=8, ld=202)  # a pitch of two (not four) columns
+    # (resident=-1: the streaming kernels; a grid this small would otherwise be
+    # solved in one cluster's shared memory, which has no lane-vector choice)
+    # the automatic choice falls back to two columns where four are not available
+    for b, opts in ((b2, {}), (b4, dict(ring_slots=-1)), (b4, dict(reproducible=1))):
+        x, info = _solve(b, tol=1e-10, maxit=2000, nx=nx, opts=lap5cg.default_opts(resident=-1, **opts))
+        assert info[0]["status"] == lap5cg.OK
+    for b, variant, opts in ((b2, "classic", dict(lane_vec=4)), (b4, "newcg", dict(lane_vec=4)),
+                             (b4, "classic", dict(lane_vec=4, ring_slots=-1)),
+                             (b4, "classic", dict(lane_vec=4, reproducible=1)), (b4, "classic", dict(lane_vec=8))):
+        with pytest.raises(RuntimeError):
+            _solve(b, tol=1e-10, maxit=10, variant=variant, nx=nx, opts=lap5cg.default_opts(resident=-1, **opts))
+    with pytest.raises(RuntimeError):  # binary32 passes have no two-column form
+        _solve(b4.astype(np.float32), tol=1e-5, maxit=10, precision="f32", nx=nx,
+               opts=lap5cg.default_opts(lane_vec=2, resident=-1))
+
+
 def test_f32_full_size_8192_fused_launch_tracks_oracle():
     # the 8192 x 8192 binary32 fused-iteration workload in its timed launch
     # configuration (automatic lane vector: 8), fixed iterations, against the

@@ -35,7 +35,8 @@ def _grid_view(raw, shape, dtype):
 
 CASES = [
     ("f64", "classic", {}), ("f64", "newcg", {}), ("f64", "classic", {"reproducible": 1}),
-    ("f64", "classic", {"resident": -1, "ring_slots": -1}), ("f32", "classic", {}), ("f32", "classic", {"lane_vec": 8, "ring_slots": 4}),
+    ("f64", "classic", {"resident": -1, "ring_slots": -1}), ("f64", "classic", {"lane_vec": 4, "ring_slots": 4}),
+    ("f32", "classic", {}), ("f32", "classic", {"lane_vec": 8, "ring_slots": 4}),
     ("ir_f32", "classic", {}), ("ir_bf16pr", "classic", {}), ("mg_f32", "classic", {}), ("mg_f64", "newcg", {}),
 ]
 SHAPES = [(100, 37, 101), (257, 130, 260), (1030, 70, 1032), (64, 64, 64), (1, 9, 4)]
