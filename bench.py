@@ -260,9 +260,13 @@ def time_to_solution(lap5cg, torch, dev, n, rhs, tol=1e-10):
         out[name] = {"ms": e0.elapsed_time(e1), "iters": rec["iters"], "outer_iters": rec["outer_iters"],
                      "status": rec["status"], "relres_true": rec["relres_true"]}
         del x
-    out["speedup_ir_f32_vs_f64_classic"] = out["f64_classic"]["ms"] / out["ir_f32"]["ms"]
-    out["speedup_ir_bf16pr_vs_f64_classic"] = out["f64_classic"]["ms"] / out["ir_bf16pr"]["ms"]
-    out["speedup_pcg_mg_f32_vs_f64_classic"] = out["f64_classic"]["ms"] / out["pcg_mg_f32"]["ms"]
+    def speedup(name):  # only between solves that both reached the tolerance
+        ok = out["f64_classic"]["status"] == 0 and out[name]["status"] == 0
+        return out["f64_classic"]["ms"] / out[name]["ms"] if ok else None
+
+    out["speedup_ir_f32_vs_f64_classic"] = speedup("ir_f32")
+    out["speedup_ir_bf16pr_vs_f64_classic"] = speedup("ir_bf16pr")
+    out["speedup_pcg_mg_f32_vs_f64_classic"] = speedup("pcg_mg_f32")
     return out
 
 

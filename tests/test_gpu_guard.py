@@ -109,3 +109,23 @@ def test_guard_bands_batched():
             assert torch.isnan(b[:, nx:]).all() and torch.isnan(x[:, nx:]).all()
             assert torch.isfinite(x[:, :nx]).all()
         assert all(r["status"] == lap5cg.OK for r in lap5cg.decode_info(info))
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32, torch.bfloat16])
+@pytest.mark.parametrize("nx,ny,ld", [(100, 37, 104), (257, 130, 260), (1030, 70, 1032), (63, 5, 63), (1, 9, 4)])
+def test_guard_bands_lap5_apply(dtype, nx, ny, ld):
+    es = torch.tensor([], dtype=dtype).element_size()
+    nb = ny * ld * es
+    xbuf, xraw = _guarded(nb)
+    ybuf, yraw = _guarded(nb)
+    x = xraw.view(dtype).view(ny, ld)
+    y = yraw.view(dtype).view(ny, ld)
+    x.copy_(torch.from_numpy(gen.uniform_rhs(nx, ny, seed=nx + ny, ld=ld)).to("cuda", dtype))
+    x[:, nx:] = float("nan")
+    y.fill_(7.0)
+    ref = lap5cg.lap5_apply(x[:, :nx].contiguous())
+    lap5cg.lap5_apply(x, nx=nx, out=y)
+    torch.cuda.synchronize()
+    assert _intact(xbuf, nb) and _intact(ybuf, nb), "guard band overwritten"
+    assert (y[:, nx:] == 7.0).all(), "padding columns of y were written"
+    assert torch.equal(y[:, :nx], ref), "padding values reached the result"
