@@ -320,6 +320,32 @@ def batched_workload(lap5cg, torch, dev, tune=True):
             "max_relres_true": max(r["relres_true"] for r in recs + recs_default), "tuned_opts": tuned}
 
 
+def autograd_workload(lap5cg, torch, dev, n=2048, k=16, tol=1e-10):
+    """The differentiable solve: n x n grid, k right-hand sides (U[-1,1), seeds
+    5000+s), x_target Gaussian (seeds 6000+s), loss = 0.5 ||x - x_target||^2;
+    forward = k solves to tol, backward = the k adjoint solves.  CUDA events
+    around forward and backward, per precision."""
+    b0 = np.stack([gen.uniform_rhs(n, n, seed=5000 + s) for s in range(k)])
+    xt = torch.from_numpy(np.stack([gen.gaussian_field(n, n, seed=6000 + s) for s in range(k)])).to(dev)
+    out = {"workload": "%dx%d grid, %d right-hand sides, loss 0.5||x - x_target||^2, tol %g" % (n, n, k, tol)}
+    for precision in ("f64", "ir_f32", "mg_f32"):
+        b = torch.from_numpy(b0).to(dev).requires_grad_(True)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record()
+        x, info = lap5cg.CGSolve.apply(b, tol, 10 ** 7, "classic", precision, None)
+        loss = 0.5 * ((x - xt) ** 2).sum()
+        ev[1].record()
+        loss.backward()
+        ev[2].record()
+        torch.cuda.synchronize(dev)
+        recs = lap5cg.decode_info(info)
+        out[precision] = {"forward_ms": ev[0].elapsed_time(ev[1]), "backward_ms": ev[1].elapsed_time(ev[2]),
+                          "forward_iters": int(sum(r["iters"] for r in recs)),
+                          "all_converged": all(r["status"] == 0 for r in recs)}
+        del b, x
+    return out
+
+
 def paper_size_workload(lap5cg, torch, dev, reps=20):
     """The paper's largest grid: 100 x 100 FP64, U[-1,1) (seed 1), x0 = 0, to 1e-8;
     latency-bound.  Through cg_solve ("cg_solve": the cluster-resident kernel,
@@ -435,6 +461,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the f32 roofline and time-to-solution runs")
     ap.add_argument("--tts", action="store_true", help="also time FP64 vs mixed precision to 1e-10 at 8192^2")
+    ap.add_argument("--autograd", action="store_true",
+                    help="also time the differentiable solve (2048^2, 16 right-hand sides, forward + adjoint)")
     # profiling-size overrides (the defaults are the benchmark workload)
     ap.add_argument("--n", type=int, default=NX, help="grid side (profiling only)")
     ap.add_argument("--iters", type=int, default=ITERS, help="iterations per solve (profiling only)")
@@ -627,6 +655,8 @@ def main():
         if args.tts:
             extras["time_to_1e-10_8192"] = time_to_solution(lap5cg, torch, dev, 8192,
                                                             gen.uniform_rhs(8192, 8192, seed=3))
+        if args.autograd:
+            extras["autograd_2048x16"] = autograd_workload(lap5cg, torch, dev)
 
     line = None
     if rank == 0:
