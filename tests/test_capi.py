@@ -94,6 +94,12 @@ def test_invalid_arguments_rejected_before_launch():
     o = lap5cg.default_opts(rr_period=5)
     assert L.cg_solve(8, 8, 8, vp(1 << 20), vp(2 << 20), 1e-8, 10, 0, 0, 1, ws, big, info, ctypes.byref(o),
                       None) == lap5cg.ERR_INVALID_ARG  # residual replacement is a NewCG option
+    # option values outside their documented ranges
+    for bad in (dict(lane_vec=3), dict(lane_vec=16), dict(lane_vec=-1), dict(reproducible=2), dict(reproducible=-1),
+                dict(mg_nu=-1), dict(mg_levels=-2), dict(ring_slots=99), dict(maxit_inner=-1)):
+        o = lap5cg.default_opts(**bad)
+        assert L.cg_solve(8, 8, 8, vp(1 << 20), vp(2 << 20), 1e-8, 10, 0, 0, 1, ws, big, info, ctypes.byref(o),
+                          None) == lap5cg.ERR_INVALID_ARG, bad
 
 
 def test_product_path_does_not_import_oracle():
