@@ -18,6 +18,7 @@ Functions and the passages they follow (arxiv 1803.03797):
                        residual replacement.
   cg_ir             -- FP64 iterative refinement around a binary32 (or bf16
                        p/r) inner Algorithm 1 with Dot2 inner dot products.
+  inner_cg_f32      -- that inner solve alone (for its own pins).
   dot2_f32          -- Dot2 (Ogita, Rump & Oishi 2005).
   mg_precond, cg_pcg -- preconditioned CG (Algorithm 1 with M) with a
                        geometric multigrid V-cycle as M^-1 (the cited
@@ -72,6 +73,8 @@ def lib():
         L.ora_cg_classic.argtypes = [i, i, i, vp, vp, d, i, ctypes.POINTER(_Trace), ctypes.POINTER(Info)]
         L.ora_cg_newcg.argtypes = [i, i, i, vp, vp, d, i, i, ctypes.POINTER(_Trace), ctypes.POINTER(Info)]
         L.ora_cg_ir.argtypes = [i, i, i, vp, vp, d, i, i, d, i, ctypes.POINTER(Info)]
+        L.ora_inner_cg_f32.argtypes = [i, i, i, vp, vp, d, i, i, vp, ctypes.POINTER(i)]
+        L.ora_inner_cg_f32.restype = i
         for name in ("ora_cg_classic", "ora_cg_newcg", "ora_cg_ir"):
             getattr(L, name).restype = i
         L.ora_repro_blocks.argtypes = [i, i, i, vp, vp, vp]
@@ -220,6 +223,24 @@ def cg_ir(b, x0=None, tol=1e-10, max_outer=60, inner="f32", tol_in=None, maxit_i
     info = Info()
     lib().ora_cg_ir(nx, ny, ld, _ptr(b), _ptr(x), tol, max_outer, storage, tol_in, maxit_in, ctypes.byref(info))
     return x, info.as_dict()
+
+
+def inner_cg_f32(rin, tol_in=1e-4, maxit_in=1000, storage="f32", nx=None):
+    """The refinement's inner solve alone: classic CG (Algorithm 1) on
+    A d = rin from d = 0 in binary32 arithmetic with Dot2 dot products; p and
+    r stored in binary32 ('f32') or bf16 ('bf16pr').  rin: binary32 (ny, ld).
+    Returns (d, r_final, iterations, breakdown)."""
+    ny, ld = rin.shape
+    nx = ld if nx is None else nx
+    rin = _grid(rin, np.float32, nx)
+    d = np.zeros_like(rin)
+    r = np.zeros_like(rin)
+    brk = ctypes.c_int(0)
+    k = lib().ora_inner_cg_f32(nx, ny, ld, _ptr(rin), _ptr(d), float(tol_in), int(maxit_in),
+                               {"f32": 1, "bf16pr": 2}[storage], _ptr(r), ctypes.byref(brk))
+    if k < 0:
+        raise ValueError("invalid arguments")
+    return d, r, k, bool(brk.value)
 
 
 def cg_solve(b, variant="classic", **kw):

@@ -459,6 +459,25 @@ static int inner_cg_f32(int nx, int ny, int ld, const float* rin, float* d, doub
   return k;
 }
 
+/* The inner solve alone, for the tests' pins: classic CG (Algorithm 1) on
+ * A d = rin from d = 0 with the inner storage above.  On return d holds the
+ * correction, r_out (may be NULL) the final stored inner residual, and
+ * *breakdown is 1 if (p, Ap) <= 0 or a dot was non-finite.  Returns the
+ * iterations done. */
+int ora_inner_cg_f32(int nx, int ny, int ld, const float* rin, float* d, double tol_in, int maxit_in,
+                     int inner_storage, float* r_out, int* breakdown) {
+  const size_t n = (size_t)ny * ld;
+  float *r = calloc(n, 4), *p = calloc(n, 4), *z = calloc(n, 4);
+  int brk = 0, k = -1;
+  if (r && p && z && (inner_storage == 1 || inner_storage == 2) && maxit_in >= 0) {
+    k = inner_cg_f32(nx, ny, ld, rin, d, tol_in, maxit_in, inner_storage == 2, r, p, z, &brk);
+    if (r_out) memcpy(r_out, r, n * sizeof(float));
+  }
+  free(r); free(p); free(z);
+  if (breakdown) *breakdown = brk;
+  return k;
+}
+
 int ora_cg_ir(int nx, int ny, int ld, const double* b, double* x, double tol, int max_outer,
               int inner_storage, double tol_in, int maxit_in, ora_info* info) {
   ora_info inf; memset(&inf, 0, sizeof inf);

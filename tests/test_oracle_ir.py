@@ -1,0 +1,171 @@
+"""Pins of the oracle's mixed-precision path: the inner binary32 / bf16-p,r
+classic CG on its own (oracle.inner_cg_f32) and the FP64 refinement loop
+around it (oracle.cg_ir).  The refinement is self-correcting, so "reaches
+1e-10" alone would not notice a wrong beta, a wrong sign or a missing bf16
+rounding; these pins do (tests/test_oracle_mutations.py plants each one).
+
+  * one-step termination on a sine mode (an eigenvector: Algorithm 1 ends
+    after one update with d = rin / lambda), binary32;
+  * m-step termination on m modes of distinct eigenvalues, binary32;
+  * at a fixed iteration count the binary32 iterate stays within a
+    rounding-level distance of the binary64 Algorithm 1 on the same data;
+  * bf16 p, r: bit-for-bit equality with an independent numpy restatement that
+    rounds p and r to bf16 (torch's round-to-nearest-even) after every update
+    and sums with its own Dot2 (TwoProduct from an exact binary64 product,
+    Knuth's TwoSum).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import lap5_inputs as gen
+import oracle
+
+U32 = 2.0 ** -24
+
+
+def _amplification(n, lams):
+    """max over the spectrum of |prod_t (1 - lambda / lambda_t)|: in exact
+    arithmetic Algorithm 1 on a combination of the modes lambda_t ends after
+    len(lams) updates with that polynomial applied to the residual, so a
+    rounding error of the input (~u32 per element) comes out scaled by at most
+    this factor."""
+    lo, hi = gen.mode_eigenvalue(n, n, 1, 1), gen.mode_eigenvalue(n, n, n, n)
+    grid = np.linspace(lo, hi, 20001)
+    poly = np.ones_like(grid)
+    for lam in lams:
+        poly *= 1.0 - grid / lam
+    return float(np.max(np.abs(poly)))
+
+
+@pytest.mark.parametrize("k,l", [(1, 1), (3, 5), (40, 2), (24, 30)])
+def test_inner_one_step_on_sine_mode(k, l):
+    n = 48
+    rin = gen.sine_mode(n, n, k, l).astype(np.float32)
+    lam = gen.mode_eigenvalue(n, n, k, l)
+    d, r, it, brk = oracle.inner_cg_f32(rin, tol_in=0.0, maxit_in=1, storage="f32")
+    assert not brk and it == 1
+    ref = rin.astype(np.float64) / lam
+    # alpha = (r, r) / (p, A p): the binary32 stencil rounds each of its four
+    # subtractions (|error| <= 3 u32 * 8 |p| a point), so (p, A p) = lambda ||p||^2
+    # carries a relative error of at most 24 u32 / lambda
+    assert np.max(np.abs(d - ref)) <= (16 + 24 / lam) * U32 * np.max(np.abs(ref))
+    assert np.linalg.norm(r) <= 4 * U32 * _amplification(n, [lam]) * np.linalg.norm(rin)
+    # bf16 p, r: one update moves along p = bf16(rin), within bf16 rounding of rin / lambda
+    d1, _, it1, _ = oracle.inner_cg_f32(rin, tol_in=0.0, maxit_in=1, storage="bf16pr")
+    assert it1 == 1
+    assert np.max(np.abs(d1 - ref)) <= 2.0 ** -8 * np.max(np.abs(ref))
+
+
+MODES = [(1, 1), (2, 3), (5, 2), (7, 7), (30, 11), (20, 37)]
+
+
+@pytest.mark.parametrize("first,m", [(0, 2), (0, 3), (0, 4), (4, 2)])
+def test_inner_m_modes_terminate_in_m_steps(first, m):
+    n = 40
+    ks = MODES[first:first + m]
+    lams = [gen.mode_eigenvalue(n, n, k, l) for k, l in ks]
+    assert len(set(round(x, 12) for x in lams)) == m
+    v = sum((0.5 ** t) * gen.sine_mode(n, n, k, l) for t, (k, l) in enumerate(ks))
+    rin = v.astype(np.float32)
+    d, r, it, brk = oracle.inner_cg_f32(rin, tol_in=0.0, maxit_in=m, storage="f32")
+    assert not brk and it == m
+    amp = _amplification(n, lams)
+    assert np.linalg.norm(r) <= 4 * U32 * amp * np.linalg.norm(rin)
+    _, r1, _, _ = oracle.inner_cg_f32(rin, tol_in=0.0, maxit_in=m - 1, storage="f32")
+    assert np.linalg.norm(r1) >= 1e-2 * np.linalg.norm(rin)  # not done one step early
+    # the solution of A d = rin is sum_t c_t v_t / lambda_t
+    ref = sum((0.5 ** t) * gen.sine_mode(n, n, k, l) / lam for t, ((k, l), lam) in enumerate(zip(ks, lams)))
+    assert np.linalg.norm(d - ref) <= 4 * U32 * amp / min(lams) * np.linalg.norm(rin) + 16 * U32 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("k", [5, 25])
+def test_inner_f32_tracks_fp64_algorithm1(k):
+    # binary32 rounding perturbs each step by ~u32; over k steps on a 64^2 grid
+    # (kappa ~ 1.7e3) the iterates stay within ~k * kappa * u32 ~ 3e-3 (a
+    # pessimistic bound; measured ~1e-6).  A wrong beta or sign is O(1).
+    n = 64
+    rin = gen.uniform_rhs(n, n, seed=71).astype(np.float32)
+    d, r, it, brk = oracle.inner_cg_f32(rin, tol_in=0.0, maxit_in=k, storage="f32")
+    assert it == k and not brk
+    x64, info = oracle.cg_classic(rin.astype(np.float64), tol=0.0, maxit=k)
+    assert info["iters"] == k
+    assert np.linalg.norm(d - x64) <= 1e-4 * np.linalg.norm(x64)
+    # the recursive residual tracks the true residual of d to rounding level
+    true_r = rin.astype(np.float64) - oracle.lap5_apply(d.astype(np.float64))
+    assert np.linalg.norm(r - true_r) <= 1e-5 * np.linalg.norm(rin)
+
+
+# ---------------------------------------------------------------------------
+# independent restatement of the bf16-p,r inner solve
+# ---------------------------------------------------------------------------
+def _bf16(v):
+    return torch.from_numpy(np.ascontiguousarray(v, dtype=np.float32)).to(torch.bfloat16).to(torch.float32).numpy()
+
+
+def _stencil32(x, nx, ny):
+    z = np.zeros((ny + 2, nx + 2), dtype=np.float32)
+    z[1:-1, 1:-1] = x[:, :nx]
+    c = z[1:-1, 1:-1]
+    acc = np.float32(4.0) * c
+    acc = acc - z[1:-1, :-2]
+    acc = acc - z[1:-1, 2:]
+    acc = acc - z[:-2, 1:-1]
+    acc = acc - z[2:, 1:-1]
+    y = np.zeros_like(x)
+    y[:, :nx] = acc
+    return y
+
+
+def _dot2(a, b, nx):
+    s = np.float32(0.0)
+    c = np.float32(0.0)
+    for ai, bi in zip(a[:, :nx].ravel().tolist(), b[:, :nx].ravel().tolist()):
+        ai, bi = np.float32(ai), np.float32(bi)
+        h = np.float32(ai * bi)
+        lo = np.float32(float(ai) * float(bi) - float(h))   # exact: the product error fits binary32
+        x = np.float32(s + h)
+        z = np.float32(x - s)
+        e = np.float32(np.float32(s - np.float32(x - z)) + np.float32(h - z))
+        s = x
+        c = np.float32(c + np.float32(e + lo))
+    return float(s) + float(c)
+
+
+def _restated_inner(rin, nx, maxit, bf):
+    ny = rin.shape[0]
+    st = _bf16 if bf else (lambda v: np.asarray(v, dtype=np.float32))
+    d = np.zeros_like(rin)
+    r = st(rin)
+    p = r.copy()
+    g = _dot2(r, r, nx)
+    k = 0
+    while k < maxit and g > 0.0:
+        z = _stencil32(p, nx, ny)
+        pz = _dot2(p, z, nx)
+        a = np.float32(g / pz)
+        d = (d + a * p).astype(np.float32)
+        r = st((r - a * z).astype(np.float32))
+        gn = _dot2(r, r, nx)
+        k += 1
+        bt = np.float32(gn / g)
+        g = gn
+        if g <= 0.0:
+            break
+        p = st((r + bt * p).astype(np.float32))
+    return d, r, k
+
+
+@pytest.mark.parametrize("storage", ["bf16pr", "f32"])
+def test_inner_matches_restatement_bit_for_bit(storage):
+    nx, ny, ld, k = 23, 17, 24, 30
+    rin = gen.uniform_rhs(nx, ny, seed=73, ld=ld).astype(np.float32)
+    d, r, it, brk = oracle.inner_cg_f32(rin, tol_in=0.0, maxit_in=k, storage=storage, nx=nx)
+    dr, rr, kr = _restated_inner(rin, nx, k, storage == "bf16pr")
+    assert it == kr == k and not brk
+    np.testing.assert_array_equal(d[:, :nx], dr[:, :nx])
+    np.testing.assert_array_equal(r[:, :nx], rr[:, :nx])
+    if storage == "bf16pr":  # the stored residual really is bf16
+        np.testing.assert_array_equal(r, _bf16(r))

@@ -32,6 +32,14 @@ MUTATIONS = {
                          "double denom = delta / gamma + beta / alpha;      /* de-garbled alpha update */"),
 }
 
+# mistakes in the mixed-precision path, caught by the pins of tests/test_oracle_ir.py
+IR_MUTATIONS = {
+    "inner_beta_inverted": ("float bt = (float)(gn / g);", "float bt = (float)(g / gn);"),
+    "inner_r_sign": ("r[t] = stor(r[t] - a * z[t], bf);", "r[t] = stor(r[t] + a * z[t], bf);"),
+    "inner_p_not_rounded_to_bf16": ("p[t] = stor(r[t] + bt * p[t], bf);", "p[t] = r[t] + bt * p[t];"),
+}
+MUTATIONS.update(IR_MUTATIONS)
+
 
 @pytest.fixture(scope="module")
 def mutant_dir(tmp_path_factory):
@@ -103,14 +111,31 @@ def _pins_pass():
     return True
 
 
+def _ir_pins_pass():
+    """The mixed-precision pins (tests/test_oracle_ir.py); True iff all hold."""
+    from tests import test_oracle_ir as t
+    checks = [lambda: t.test_inner_one_step_on_sine_mode(3, 5),
+              lambda: t.test_inner_m_modes_terminate_in_m_steps(0, 3),
+              lambda: t.test_inner_f32_tracks_fp64_algorithm1(25),
+              lambda: t.test_inner_matches_restatement_bit_for_bit("bf16pr"),
+              lambda: t.test_inner_matches_restatement_bit_for_bit("f32")]
+    for check in checks:
+        try:
+            check()
+        except (AssertionError, ValueError, FloatingPointError):
+            return False
+    return True
+
+
 def test_unmutated_oracle_passes_pins():
     assert _pins_pass()
+    assert _ir_pins_pass()
 
 
 @pytest.mark.parametrize("name", sorted(MUTATIONS))
 def test_planted_mistake_is_caught(name, mutant_dir):
     path = _load_mutant(name, mutant_dir)
     with _Swap(path):
-        caught = not _pins_pass()
+        caught = not (_ir_pins_pass() if name in IR_MUTATIONS else _pins_pass())
     assert caught, "pins did not catch the planted mistake " + name
 
