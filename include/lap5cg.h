@@ -19,8 +19,13 @@
  * not stored.
  *
  * Ownership: the caller owns every buffer (inputs, outputs, workspace, info).
- * The library allocates no device memory on any entry point below and keeps no
- * mutable global state apart from a per-device cache of device properties.
+ * No entry point below allocates device memory at call time, and the library
+ * keeps no mutable global state apart from a per-device cache of device
+ * properties.  One exception to "the caller owns every buffer":
+ * cg_solve_classic_f64_noalloc uses a fixed 8.25 MiB __device__ array of the
+ * library as scratch; the CUDA runtime commits it on a device when it loads
+ * the library's module there (with lazy module loading, at the first call
+ * into the library on that device, not at dlopen).
  *
  * Ordering: every call is asynchronous on the given CUDA stream (a
  * cudaStream_t passed as void*; NULL = the legacy default stream).  The return
@@ -266,14 +271,29 @@ LAP5CG_API int lap5cg_tune_batched(int count, const int* nx, const int* ny, cons
                                    size_t ws_bytes, lap5cg_info* info, lap5cg_opts* opts, double* best_ms,
                                    void* stream);
 
+/*
+ * Measurement helper (no paper counterpart): the binary64 instruction rates of
+ * the current GPU, in lane operations per second -- fused multiply-adds
+ * (*fma_per_s) and additions (*add_per_s) -- from a throughput kernel with
+ * eight independent dependency chains a thread on every SM, timed with CUDA
+ * events on `stream` (best of three launches of about 40 ms each).  The
+ * binary64 solves are bound by this pipe rather than by memory bandwidth.
+ * Synchronises the stream; allocates no device memory.
+ * Returns LAP5CG_OK, LAP5CG_ERR_INVALID_ARG (NULL outputs) or LAP5CG_ERR_CUDA.
+ */
+LAP5CG_API int lap5cg_fp64_rate(double* fma_per_s, double* add_per_s, void* stream);
+
 /* Largest ny*ld that cg_solve_classic_f64_noalloc accepts. */
 #define LAP5CG_NOALLOC_MAX_POINTS 262144
 
 /*
- * The binary64 classic CG solve (as cg_solve with variant CLASSIC, precision
- * F64, nrhs 1, default options) for callers that cannot allocate device
- * memory: its scratch space is a fixed array inside this library, so no
- * workspace argument is needed.  The paper has no counterpart; this entry
+ * The binary64 classic CG solve (Algorithm 1, the arithmetic of cg_solve with
+ * variant CLASSIC, precision F64, nrhs 1, default options, always on the
+ * streaming kernels: grids that cg_solve would solve in one cluster's shared
+ * memory take the streaming path here, so iteration counts and low-order bits
+ * may differ from cg_solve on such grids) for callers that cannot allocate
+ * device memory: its scratch space is a fixed array inside this library, so
+ * no workspace argument is needed.  The paper has no counterpart; this entry
  * point exists for the library's users.
  *
  * Who needs it: applications that fix their device-memory budget at start-up
@@ -288,9 +308,13 @@ LAP5CG_API int lap5cg_tune_batched(int count, const int* nx, const int* ny, cons
  *     aligned (LAP5CG_ERR_INVALID_ARG otherwise): there is no staging space.
  *   - The scratch array (8.25 MiB) is a static __device__ object: every GPU
  *     that loads this library holds it until the process exits.
- *   - The first call on a device, with that device current, looks up the
- *     array's device address (cudaGetSymbolAddress) and caches it; make that
- *     first call before any stream capture.
+ *   - Every call looks up the array's device address on the current device
+ *     (cudaGetSymbolAddress; nothing is cached, so the address stays right
+ *     after a device reset reloads the module).  The first call on a device
+ *     may load the module and commit the array: make one warm-up call per
+ *     device at start-up, before any stream capture, so that a fixed memory
+ *     budget sees the array from the start.
+ *   - The device is the current one: b, x and info must live on it.
  *   - All calls share the one array and the solver re-initialises what must
  *     start at zero, but calls that overlap on the GPU (different streams, or
  *     different host threads, on the same device) race on it: serialise them.

@@ -87,6 +87,8 @@ def lib():
         L.cg_solve_classic_f64_noalloc.argtypes = [i, i, i, vp, vp, d, i, vp, vp]
         L.cg_solve_classic_f64_noalloc.restype = i
         DP = ctypes.POINTER(ctypes.c_double)
+        L.lap5cg_fp64_rate.argtypes = [DP, DP, vp]
+        L.lap5cg_fp64_rate.restype = i
         L.lap5cg_tune.argtypes = [i, i, i, vp, vp, i, i, i, vp, sz, vp, ctypes.POINTER(Opts), DP, vp]
         L.lap5cg_tune.restype = i
         L.lap5cg_tune_batched.argtypes = [i, IP, IP, IP, VPP, VPP, i, i, i, vp, sz, vp, ctypes.POINTER(Opts), DP, vp]
@@ -97,7 +99,7 @@ def lib():
 
 EXPORTED = ("lap5cg_opts_default", "lap5cg_status_string", "lap5_apply", "cg_workspace_size", "cg_solve",
             "cg_batched_workspace_size", "cg_solve_batched", "cg_solve_classic_f64_noalloc", "lap5cg_tune",
-            "lap5cg_tune_batched")
+            "lap5cg_tune_batched", "lap5cg_fp64_rate")
 NOALLOC_MAX_POINTS = 262144
 
 
@@ -121,9 +123,9 @@ def default_opts(**kw) -> Opts:
     return o
 
 
-def _stream(stream):
+def _stream(stream, device=None):
     if stream is None:
-        stream = torch.cuda.current_stream()
+        stream = torch.cuda.current_stream(device)
     return ctypes.c_void_p(stream.cuda_stream)
 
 
@@ -132,6 +134,23 @@ def _check_grid(t, name):
         raise ValueError("%s must be a CUDA tensor" % name)
     if not t.is_contiguous():
         raise ValueError("%s must be contiguous" % name)
+
+
+def _check_like(t, ref, name, ref_name="b"):
+    """t must be a contiguous CUDA tensor with ref's shape, dtype and device:
+    the library reads and writes it with ref's layout."""
+    _check_grid(t, name)
+    if t.shape != ref.shape or t.dtype != ref.dtype or t.device != ref.device:
+        raise ValueError("%s must match %s: shape %s, dtype %s, device %s (got %s, %s, %s)"
+                         % (name, ref_name, tuple(ref.shape), ref.dtype, ref.device, tuple(t.shape), t.dtype,
+                            t.device))
+
+
+def _check_info(info, count, device):
+    """info must be a contiguous uint8 CUDA tensor of at least count records on device."""
+    _check_grid(info, "info")
+    if info.dtype != torch.uint8 or info.numel() < count * INFO_BYTES or info.device != device:
+        raise ValueError("info must be a uint8 tensor of at least %d bytes on %s" % (count * INFO_BYTES, device))
 
 
 _DT = {torch.float64: DT_F64, torch.float32: DT_F32, torch.bfloat16: DT_BF16}
@@ -144,9 +163,12 @@ def lap5_apply(x: torch.Tensor, nx: int = None, out: torch.Tensor = None, stream
         raise ValueError("x must be a 2D float64/float32/bfloat16 tensor")
     ny, ld = x.shape
     nx = ld if nx is None else int(nx)
+    if out is not None:
+        _check_like(out, x, "out", "x")
     y = torch.zeros_like(x) if out is None else out
-    rc = lib().lap5_apply(nx, ny, ld, _DT[x.dtype], ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
-                          _stream(stream))
+    with torch.cuda.device(x.device):
+        rc = lib().lap5_apply(nx, ny, ld, _DT[x.dtype], ctypes.c_void_p(x.data_ptr()),
+                              ctypes.c_void_p(y.data_ptr()), _stream(stream, x.device))
     if rc != OK:
         raise Lap5cgError(rc, "lap5_apply")
     return y
@@ -186,7 +208,10 @@ def cg_solve(b: torch.Tensor, x0: torch.Tensor = None, tol: float = 1e-10, maxit
         raise ValueError("b must be (ny, ld) or (nrhs, ny, ld)")
     nx = ld if nx is None else int(nx)
     v, p = _VARIANTS[variant], _PRECISIONS[precision]
+    if x0 is not None:
+        _check_like(x0, b, "x0")
     if out is not None:
+        _check_like(out, b, "out")
         x = out
         if x0 is not None and x0.data_ptr() != x.data_ptr():
             x.copy_(x0)
@@ -194,18 +219,23 @@ def cg_solve(b: torch.Tensor, x0: torch.Tensor = None, tol: float = 1e-10, maxit
             x.zero_()
     else:
         x = torch.zeros_like(b) if x0 is None else x0.clone()
-    _check_grid(x, "x")
     need = workspace_size(nx, ny, ld, v, p, nrhs)
     if need == 0:
         raise Lap5cgError(ERR_UNSUPPORTED, "cg_workspace_size")
-    if workspace is None or workspace.numel() < need:
+    if workspace is not None:
+        _check_grid(workspace, "workspace")
+        if workspace.device != b.device:
+            raise ValueError("workspace must be on %s" % b.device)
+    if workspace is None or workspace.numel() * workspace.element_size() < need:
         workspace = torch.empty(need, dtype=torch.uint8, device=b.device)
     if info is None:
         info = torch.empty(nrhs * INFO_BYTES, dtype=torch.uint8, device=b.device)
-    rc = lib().cg_solve(nx, ny, ld, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()), float(tol),
-                        int(maxit), v, p, nrhs, ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
-                        ctypes.c_void_p(info.data_ptr()), ctypes.byref(opts) if opts is not None else None,
-                        _stream(stream))
+    _check_info(info, nrhs, b.device)
+    with torch.cuda.device(b.device):
+        rc = lib().cg_solve(nx, ny, ld, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()), float(tol),
+                            int(maxit), v, p, nrhs, ctypes.c_void_p(workspace.data_ptr()),
+                            workspace.numel() * workspace.element_size(), ctypes.c_void_p(info.data_ptr()),
+                            ctypes.byref(opts) if opts is not None else None, _stream(stream, b.device))
     if rc != OK:
         raise Lap5cgError(rc, "cg_solve")
     if check:
@@ -229,28 +259,41 @@ def cg_solve_batched(bs, xs=None, tol=1e-10, maxit=100000, variant="classic", pr
     n = len(bs)
     if n < 1:
         raise ValueError("empty batch")
+    dev = bs[0].device
     for t in bs:
         _check_grid(t, "b")
+        if t.dim() != 2 or t.device != dev:
+            raise ValueError("every b must be a 2D tensor on %s" % dev)
     nxs = [t.shape[1] for t in bs] if nx_list is None else list(nx_list)
     nys = [t.shape[0] for t in bs]
     lds = [t.shape[1] for t in bs]
     if xs is None:
         xs = [torch.zeros_like(t) for t in bs]
+    if len(xs) != n:
+        raise ValueError("xs must have one tensor per b")
+    for t, bt in zip(xs, bs):
+        _check_like(t, bt, "x")
     v, p = _VARIANTS[variant], _PRECISIONS[precision]
     need = batched_workspace_size(nxs, nys, lds, v, p)
     if need == 0:
         raise Lap5cgError(ERR_UNSUPPORTED, "cg_batched_workspace_size")
-    if workspace is None or workspace.numel() < need:
-        workspace = torch.empty(need, dtype=torch.uint8, device=bs[0].device)
+    if workspace is not None:
+        _check_grid(workspace, "workspace")
+        if workspace.device != dev:
+            raise ValueError("workspace must be on %s" % dev)
+    if workspace is None or workspace.numel() * workspace.element_size() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=dev)
     if info is None:
-        info = torch.empty(n * INFO_BYTES, dtype=torch.uint8, device=bs[0].device)
+        info = torch.empty(n * INFO_BYTES, dtype=torch.uint8, device=dev)
+    _check_info(info, n, dev)
     arr = ctypes.c_int * n
     ptrs = ctypes.c_void_p * n
-    rc = lib().cg_solve_batched(n, arr(*nxs), arr(*nys), arr(*lds), ptrs(*[t.data_ptr() for t in bs]),
-                                ptrs(*[t.data_ptr() for t in xs]), float(tol), int(maxit), v, p,
-                                ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
-                                ctypes.c_void_p(info.data_ptr()), ctypes.byref(opts) if opts is not None else None,
-                                _stream(stream))
+    with torch.cuda.device(dev):
+        rc = lib().cg_solve_batched(n, arr(*nxs), arr(*nys), arr(*lds), ptrs(*[t.data_ptr() for t in bs]),
+                                    ptrs(*[t.data_ptr() for t in xs]), float(tol), int(maxit), v, p,
+                                    ctypes.c_void_p(workspace.data_ptr()), workspace.numel() * workspace.element_size(),
+                                    ctypes.c_void_p(info.data_ptr()),
+                                    ctypes.byref(opts) if opts is not None else None, _stream(stream, dev))
     if rc != OK:
         raise Lap5cgError(rc, "cg_solve_batched")
     return xs, info
@@ -266,18 +309,38 @@ def cg_solve_classic_f64_noalloc(b: torch.Tensor, x0: torch.Tensor = None, tol: 
         raise ValueError("b must be a 2D float64 CUDA tensor")
     ny, ld = b.shape
     nx = ld if nx is None else int(nx)
+    if x0 is not None:
+        _check_like(x0, b, "x0")
+    if out is not None:
+        _check_like(out, b, "out")
     x = out if out is not None else torch.zeros_like(b)
     if x0 is not None:
-        x.copy_(x0)
+        if x0.data_ptr() != x.data_ptr():
+            x.copy_(x0)
     elif out is not None:
         x.zero_()
     if info is None:
         info = torch.empty(INFO_BYTES, dtype=torch.uint8, device=b.device)
-    rc = lib().cg_solve_classic_f64_noalloc(nx, ny, ld, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()),
-                                            float(tol), int(maxit), ctypes.c_void_p(info.data_ptr()), _stream(stream))
+    _check_info(info, 1, b.device)
+    with torch.cuda.device(b.device):  # the library's scratch array is looked up on the current device
+        rc = lib().cg_solve_classic_f64_noalloc(nx, ny, ld, ctypes.c_void_p(b.data_ptr()),
+                                                ctypes.c_void_p(x.data_ptr()), float(tol), int(maxit),
+                                                ctypes.c_void_p(info.data_ptr()), _stream(stream, b.device))
     if rc != OK:
         raise Lap5cgError(rc, "cg_solve_classic_f64_noalloc")
     return x, info
+
+
+def fp64_rate(device=None):
+    """Measured binary64 lane-operation rates of the GPU: {"fma_per_s", "add_per_s"}
+    (a throughput kernel timed on the device; synchronises)."""
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    f, a = ctypes.c_double(), ctypes.c_double()
+    with torch.cuda.device(dev):
+        rc = lib().lap5cg_fp64_rate(ctypes.byref(f), ctypes.byref(a), _stream(None, dev))
+    if rc != OK:
+        raise Lap5cgError(rc, "lap5cg_fp64_rate")
+    return {"fma_per_s": f.value, "add_per_s": a.value}
 
 
 # ---------------------------------------------------------------------------
@@ -343,9 +406,11 @@ def autotune(b: torch.Tensor, variant="classic", precision="f64", iters=100, nx=
     info = torch.empty(INFO_BYTES, dtype=torch.uint8, device=b.device)
     o = start if start is not None else default_opts()
     ms = ctypes.c_double()
-    rc = lib().lap5cg_tune(nx, ny, ld, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()), v, p,
-                           int(iters), ctypes.c_void_p(ws.data_ptr()), ws.numel(), ctypes.c_void_p(info.data_ptr()),
-                           ctypes.byref(o), ctypes.byref(ms), _stream(stream))
+    with torch.cuda.device(b.device):
+        rc = lib().lap5cg_tune(nx, ny, ld, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()), v, p,
+                               int(iters), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                               ctypes.c_void_p(info.data_ptr()), ctypes.byref(o), ctypes.byref(ms),
+                               _stream(stream, b.device))
     if rc != OK:
         raise Lap5cgError(rc, "lap5cg_tune")
     if cache:
@@ -368,10 +433,11 @@ def autotune_batched(bs, variant="classic", precision="ir_f32", iters=100, nx_li
     ms = ctypes.c_double()
     arr = ctypes.c_int * n
     ptrs = ctypes.c_void_p * n
-    rc = lib().lap5cg_tune_batched(n, arr(*nxs), arr(*nys), arr(*lds), ptrs(*[t.data_ptr() for t in bs]),
-                                   ptrs(*[t.data_ptr() for t in xs]), v, p, int(iters),
-                                   ctypes.c_void_p(ws.data_ptr()), ws.numel(), ctypes.c_void_p(info.data_ptr()),
-                                   ctypes.byref(o), ctypes.byref(ms), _stream(stream))
+    with torch.cuda.device(bs[0].device):
+        rc = lib().lap5cg_tune_batched(n, arr(*nxs), arr(*nys), arr(*lds), ptrs(*[t.data_ptr() for t in bs]),
+                                       ptrs(*[t.data_ptr() for t in xs]), v, p, int(iters),
+                                       ctypes.c_void_p(ws.data_ptr()), ws.numel(), ctypes.c_void_p(info.data_ptr()),
+                                       ctypes.byref(o), ctypes.byref(ms), _stream(stream, bs[0].device))
     if rc != OK:
         raise Lap5cgError(rc, "lap5cg_tune_batched")
     if cache:

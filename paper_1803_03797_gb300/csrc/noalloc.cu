@@ -5,10 +5,11 @@
 // The array (control block + r, p, p', z) is a static __device__ object, so
 // every GPU that loads this library holds it until the process exits.  Host
 // code cannot use the symbol g_noalloc_scratch as a device address (on the
-// host it names a stand-in object); the real address is looked up once per
-// device with cudaGetSymbolAddress while that device is current.
-#include <mutex>
-
+// host it names a stand-in object); the real address is looked up with
+// cudaGetSymbolAddress, with the caller's device current, on every call.  The
+// lookup allocates nothing and costs far less than the launch; not caching it
+// keeps the address right after a device reset, which reloads the module and
+// may move the array.
 #include "launch.h"
 
 namespace lap5 {
@@ -18,20 +19,11 @@ constexpr size_t kNoallocBytes = kCtlBytes + 4 * kNoallocMaxPoints * sizeof(doub
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 
-// Device address of g_noalloc_scratch on the current device (looked up on the
-// first call per device, then cached).
+// Device address of g_noalloc_scratch on the current device.
 static int noalloc_scratch(unsigned char** out) {
-  static std::mutex mu;
-  static unsigned char* addr[128] = {nullptr};
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return LAP5CG_ERR_CUDA;
-  std::lock_guard<std::mutex> lock(mu);
-  if (!addr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return LAP5CG_ERR_CUDA;
-    addr[dev] = static_cast<unsigned char*>(p);
-  }
-  *out = addr[dev];
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return LAP5CG_ERR_CUDA;
+  *out = static_cast<unsigned char*>(p);
   return LAP5CG_OK;
 }
 
