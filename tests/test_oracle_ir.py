@@ -169,3 +169,65 @@ def test_inner_matches_restatement_bit_for_bit(storage):
     np.testing.assert_array_equal(r[:, :nx], rr[:, :nx])
     if storage == "bf16pr":  # the stored residual really is bf16
         np.testing.assert_array_equal(r, _bf16(r))
+
+
+# ---------------------------------------------------------------------------
+# the refinement loop, composed from pinned parts
+# ---------------------------------------------------------------------------
+def _composed_ir(b, nx, max_outer, storage, tol_in, maxit_in):
+    """FP64 iterative refinement written out from its definition: r = b - A x
+    and (r, r) in binary64 (oracle stencil and index-order dot, both pinned
+    elsewhere), r rounded to binary32, the inner solve (pinned above), x += d
+    in binary64; a step whose residual is not below the previous one is undone
+    and ends the solve (the stagnation guard)."""
+    x = np.zeros_like(b)
+    d, rr_prev, total, outer, reverted = None, None, 0, 0, False
+    while True:
+        r = b - oracle.lap5_apply(x, nx=nx)
+        rr = oracle.dot(r, r, nx=nx)
+        if outer > 0 and not rr < rr_prev:
+            x = x - d.astype(np.float64)
+            reverted = True
+            break
+        rr_prev = rr
+        if outer >= max_outer:
+            break
+        d, _, k, brk = oracle.inner_cg_f32(r.astype(np.float32), tol_in=tol_in, maxit_in=maxit_in,
+                                           storage=storage, nx=nx)
+        assert not brk
+        total += k
+        x = x + d.astype(np.float64)
+        outer += 1
+    return x, total, outer, reverted
+
+
+@pytest.mark.parametrize("n,storage,tol_in,maxit_in,max_outer,guard", [
+    (40, "f32", 1e-4, 500, 3, False),
+    (40, "bf16pr", 1e-2, 500, 3, False),
+    (64, "bf16pr", 1e-2, 20, 6, False),
+    (64, "bf16pr", 1e-2, 5, 12, True),    # the guard undoes step 4
+    (96, "bf16pr", 0.5, 10, 12, True),
+])
+def test_refinement_equals_its_composition(n, storage, tol_in, maxit_in, max_outer, guard):
+    b = gen.uniform_rhs(n, n, seed=81)
+    x, info = oracle.cg_ir(b, tol=0.0, max_outer=max_outer, inner=storage, tol_in=tol_in, maxit_in=maxit_in)
+    xc, total, outer, reverted = _composed_ir(b, n, max_outer, storage, tol_in, maxit_in)
+    assert reverted == guard
+    assert info["outer_iters"] == outer and info["iters"] == total
+    assert info["status"] == oracle.NOT_CONVERGED
+    np.testing.assert_array_equal(x[:, :n], xc[:, :n])
+    # the solve returns the better iterate: its residual is the smallest seen
+    if guard:
+        assert info["relres_true"] <= info["relres_recursive"] * (1 + 1e-12)
+
+
+def test_refinement_contracts_by_the_inner_tolerance():
+    # each binary32 refinement step solves A d = r to tol_in (recursive), so
+    # the FP64 residual shrinks by about tol_in per step, down to ~1e-10
+    n = 64
+    b = gen.uniform_rhs(n, n, seed=83)
+    res = []
+    for k in range(1, 4):
+        x, info = oracle.cg_ir(b, tol=0.0, max_outer=k, inner="f32", tol_in=1e-4, maxit_in=2000)
+        res.append(info["relres_true"])
+    assert res[0] <= 2e-4 and res[1] <= 2e-4 * res[0] * 10 and res[2] <= 1e-10

@@ -37,6 +37,9 @@ IR_MUTATIONS = {
     "inner_beta_inverted": ("float bt = (float)(gn / g);", "float bt = (float)(g / gn);"),
     "inner_r_sign": ("r[t] = stor(r[t] - a * z[t], bf);", "r[t] = stor(r[t] + a * z[t], bf);"),
     "inner_p_not_rounded_to_bf16": ("p[t] = stor(r[t] + bt * p[t], bf);", "p[t] = r[t] + bt * p[t];"),
+    "ir_update_sign": ("x[(size_t)j * ld + i] = x[(size_t)j * ld + i] + (double)d[(size_t)j * ld + i];",
+                       "x[(size_t)j * ld + i] = x[(size_t)j * ld + i] - (double)d[(size_t)j * ld + i];"),
+    "ir_guard_dropped": ("if (outer > 0 && !(rr < rr_prev)) {", "if (0) {"),
 }
 MUTATIONS.update(IR_MUTATIONS)
 
@@ -118,7 +121,9 @@ def _ir_pins_pass():
               lambda: t.test_inner_m_modes_terminate_in_m_steps(0, 3),
               lambda: t.test_inner_f32_tracks_fp64_algorithm1(25),
               lambda: t.test_inner_matches_restatement_bit_for_bit("bf16pr"),
-              lambda: t.test_inner_matches_restatement_bit_for_bit("f32")]
+              lambda: t.test_inner_matches_restatement_bit_for_bit("f32"),
+              lambda: t.test_refinement_equals_its_composition(40, "f32", 1e-4, 500, 3, False),
+              lambda: t.test_refinement_equals_its_composition(64, "bf16pr", 1e-2, 5, 12, True)]
     for check in checks:
         try:
             check()
