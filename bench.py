@@ -47,6 +47,18 @@ COST = {
     "newcg": {"bytes": 96, "fp64_ops": 12, "kernel": "k_newcg<double,2>"},
 }
 FP64_PEAK_TFLOPS = 1.25  # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (nominal GB300 FP64)
+FP64_PEAK = {"tflops": FP64_PEAK_TFLOPS, "kind": "nominal"}  # replaced by the measured rate at start-up
+
+
+def measure_fp64_peak(lap5cg, dev):
+    """The FP64 roofline denominator measured in this run: the library's FMA
+    throughput kernel (lap5cg_fp64_rate), FMA = 2 flop."""
+    try:
+        r = lap5cg.fp64_rate(dev)
+    except Exception as e:
+        return {"tflops": FP64_PEAK_TFLOPS, "kind": "nominal (measurement failed: %s)" % str(e)[:100]}
+    return {"tflops": 2 * r["fma_per_s"] / 1e12, "kind": "measured", "add_tflops": 2 * r["add_per_s"] / 1e12,
+            "nominal_tflops": FP64_PEAK_TFLOPS}
 
 
 def captured_traffic(kernel):
@@ -149,19 +161,44 @@ def dist_env():
     return ws, rank, local
 
 
-def cpu_baseline(sample_iters=4):
-    """The oracle (single-threaded C, as it stands) on a bounded sample of the
-    step: both variants for sample_iters iterations on the full 4096^2 grid."""
-    import oracle
-    b = gen.manufactured_rhs(NX, NY, seed=SEED)
+def host_cores():
+    """Cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def _oracle_sample(oracle, b, sample_iters):
     t0 = time.perf_counter()
     for v in VARIANTS:
         oracle.cg_solve(b, variant=v, tol=0.0, maxit=sample_iters)
-    dt = time.perf_counter() - t0
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(sample_iters=4):
+    """The oracle (plain C, as it stands) on a bounded sample of the step: both
+    variants for sample_iters iterations on the full grid, in its two timing
+    modes -- the sequential parity build (one core) and the OpenMP build (its
+    row loops and per-thread partial dot products on every core this process
+    may use).  value / cores are the OpenMP mode's when that build is
+    available, else the sequential one's."""
+    import oracle
+    b = gen.manufactured_rhs(NX, NY, seed=SEED)
     units = len(VARIANTS) * NX * NY * sample_iters
-    return {"value": units / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "4096x4096 FP64, classic + NewCG, %d iterations each (incl. setup and final true-residual "
-                      "pass), single-threaded C oracle" % sample_iters, "seconds": dt}
+    dt1 = _oracle_sample(oracle, b, sample_iters)
+    out = {"value": units / dt1, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": "%dx%d FP64, classic + NewCG, %d iterations each (incl. setup and final true-residual pass)"
+                     % (NX, NY, sample_iters), "seconds": dt1, "value_single_thread": units / dt1,
+           "cores_available": host_cores()}
+    try:
+        with oracle.timing_build() as tb:
+            _oracle_sample(oracle, b, 1)  # thread pool start-up outside the timing
+            dtn = _oracle_sample(oracle, b, sample_iters)
+        out.update({"value": units / dtn, "cores": tb.threads, "seconds": dtn, "mode": "openmp"})
+    except Exception as e:  # no OpenMP toolchain: the sequential figure stands
+        out["mode"] = "single-thread (OpenMP build unavailable: %s)" % str(e).splitlines()[0][:120]
+    return out
 
 
 def fused_f32_roofline(lap5cg, torch, dev, hbm_peak, n=8192, iters=200, reps=3):
@@ -229,8 +266,8 @@ def stencil_roofline(lap5cg, torch, dev, hbm_peak, n=8192, reps=11):
                                             "bytes_per_pt": 2 * x.element_size()}}
         if name == "f64":
             tfl = 2 * 4 * n * n / t / 1e12
-            out[name]["fp64"] = {"achieved": tfl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                                 "frac": tfl / FP64_PEAK_TFLOPS, "ops_per_pt": 4}
+            out[name]["fp64"] = {"achieved": tfl, "peak": FP64_PEAK["tflops"], "unit": "TFLOP/s",
+                                 "frac": tfl / FP64_PEAK["tflops"], "peak_kind": FP64_PEAK["kind"], "ops_per_pt": 4}
         del x, y
     out["workload"] = "%dx%d grid, U[-1,1) (seed 5), one lap5_apply per storage type" % (n, n)
     return out
@@ -413,6 +450,38 @@ def reproducible_workload(lap5cg, torch, dev, b, iters=500, reps=2):
     return out
 
 
+def targets_summary(extras, roofline):
+    """The benchmark spec's figures as flat scalars (None where not measured)."""
+    def get(*path):
+        d = extras
+        for k in path:
+            if not isinstance(d, dict) or k not in d:
+                return None
+            d = d[k]
+        return d
+
+    t = {"fp64_fma_peak_tflops": FP64_PEAK["tflops"], "fp64_peak_kind": FP64_PEAK["kind"],
+         "dominant_kernel_fp64_frac": roofline["frac"], "dominant_kernel_hbm_frac": roofline["hbm_frac"],
+         "fused_f32_8192_hbm_frac": get("fused_f32_8192", "hbm", "frac"),
+         "lap5_apply_8192_f32_hbm_frac": get("lap5_apply_8192", "f32", "hbm", "frac"),
+         "lap5_apply_8192_bf16_hbm_frac": get("lap5_apply_8192", "bf16", "hbm", "frac")}
+    for n in (4096, 8192):
+        key = "time_to_1e-10_%d" % n
+        if key not in extras:
+            continue
+        for name in ("f64_classic", "ir_f32", "ir_bf16pr", "pcg_mg_f32"):
+            t["tts%d_%s_ms" % (n, name)] = get(key, name, "ms")
+            t["tts%d_%s_status" % (n, name)] = get(key, name, "status")
+        t["tts%d_speedup_ir_f32_vs_f64" % n] = get(key, "speedup_ir_f32_vs_f64_classic")
+        t["tts%d_speedup_ir_bf16pr_vs_f64" % n] = get(key, "speedup_ir_bf16pr_vs_f64_classic")
+    p = extras.get("paper_100x100_to_1e-8")
+    if p:
+        t["paper100_us_per_iter_classic"] = p["classic_cg_solve"]["us_per_iter"]
+        t["paper100_us_per_iter_newcg"] = p["newcg_cg_solve"]["us_per_iter"]
+    t["batched_256_ms"] = get("batched_256_ir_f32", "ms")
+    return t
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -420,6 +489,15 @@ def run_reference(args):
     b = gen.manufactured_rhs(NX, NY, seed=SEED)
     import oracle
     sample_iters = 3
+    cores, mode = 1, "single-thread"
+    tb = None
+    try:  # the oracle's OpenMP timing build on every core this process may use
+        tb = oracle.timing_build()
+        tb.__enter__()
+        cores, mode = tb.threads, "openmp"
+    except Exception as e:
+        tb = None
+        mode = "single-thread (OpenMP build unavailable: %s)" % str(e).splitlines()[0][:120]
 
     def step():
         for v in VARIANTS:
@@ -431,6 +509,8 @@ def run_reference(args):
     for _ in range(args.steps):
         step()
     dt = time.perf_counter() - t0
+    if tb is not None:
+        tb.__exit__(None, None, None)
     units = args.steps * len(VARIANTS) * NX * NY * sample_iters
     value = units / dt
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
@@ -439,7 +519,8 @@ def run_reference(args):
             "data": "synthetic",
             "config": {"workload": WORKLOAD + " (reference arm: the CPU oracle, %d iterations per variant per step)"
                                    % sample_iters, "nx": NX, "ny": NY},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "mode": mode,
+                             "cores_available": host_cores(),
                              "sample": "%d iterations per variant per step on the full grid" % sample_iters},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -555,6 +636,8 @@ def main():
         rec = lap5cg.decode_info(info[v])[0]
         if rec["iters"] != ITERS or rec["status"] not in (lap5cg.OK, lap5cg.NOT_CONVERGED):
             raise RuntimeError("warm-up solve failed: %s %r" % (v, rec))
+    # the FP64 roofline denominator, measured right after the warm-up (clocks up)
+    FP64_PEAK.update(measure_fp64_peak(lap5cg, dev))
 
     ev = {v: [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(args.steps)] for v in VARIANTS}
@@ -583,17 +666,23 @@ def main():
         pts_it = NX * NY * ITERS
         gbs = COST[v]["bytes"] * pts_it / (ms * 1e-3) / 1e9
         tfl = 2 * COST[v]["fp64_ops"] * pts_it / (ms * 1e-3) / 1e12
+        fp64_peak = FP64_PEAK["tflops"]
         per_kernel[v] = {"kernel": COST[v]["kernel"], "ms_per_launch": ms, "pts_iters_per_s": pts_it / (ms * 1e-3),
                          "hbm": {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
                                  "bytes_per_pt_iter": COST[v]["bytes"]},
-                         "fp64": {"achieved": tfl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                                  "frac": tfl / FP64_PEAK_TFLOPS, "ops_per_pt_iter": COST[v]["fp64_ops"]}}
+                         "fp64": {"achieved": tfl, "peak": fp64_peak, "unit": "TFLOP/s",
+                                  "frac": tfl / fp64_peak, "frac_of_nominal": tfl / FP64_PEAK_TFLOPS,
+                                  "ops_per_pt_iter": COST[v]["fp64_ops"]}}
     dom = max(VARIANTS, key=lambda v: per_kernel[v]["ms_per_launch"])
     pk = per_kernel[dom]
     traffic = captured_traffic(COST[dom]["kernel"]) if (NX, ITERS) == (4096, 500) else None
-    roofline = {"bound": "alu", "achieved": pk["fp64"]["achieved"], "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+    roofline = {"bound": "alu", "achieved": pk["fp64"]["achieved"], "peak": FP64_PEAK["tflops"], "unit": "TFLOP/s",
                 "frac": pk["fp64"]["frac"], "traffic": traffic, "kernel": pk["kernel"],
-                "peak_kind": "nominal FP64 pipe (FMA = 2 flop; every FP64 instruction counted as one FMA)",
+                "peak_kind": FP64_PEAK["kind"] + " FP64 FMA rate (lap5cg_fp64_rate throughput kernel in this run; "
+                             "FMA = 2 flop; every FP64 instruction of the solver counted as one FMA)",
+                "peak_nominal": FP64_PEAK_TFLOPS, "frac_of_nominal": pk["fp64"]["frac_of_nominal"],
+                "peak_fp64_add_tflops": FP64_PEAK.get("add_tflops"),
+                "hbm_achieved": pk["hbm"]["achieved"], "hbm_peak": hbm_peak, "hbm_frac": pk["hbm"]["frac"],
                 "hbm_view": pk["hbm"], "hbm_peak_kind": peak_kind}
 
     e2e = None
@@ -678,6 +767,7 @@ def main():
                                  "working set ~1 GB"},
                 "roofline": roofline, "per_kernel": per_kernel, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clk, "gpu_launches": len(VARIANTS) * args.steps, "extras": extras}
+        line["targets"] = targets_summary(extras, roofline)  # last: compact figures, kept in short tails
         print(json.dumps(line))
     if ws > 1:
         torch.distributed.barrier()

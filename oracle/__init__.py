@@ -60,43 +60,73 @@ class _Trace(ctypes.Structure):
 def lib():
     global _lib
     if _lib is None:
-        path = _build.build()
-        L = ctypes.CDLL(path)
-        i, d, vp = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
-        for name in ("ora_lap5_apply_f64", "ora_lap5_apply_f32", "ora_lap5_apply_bf16"):
-            getattr(L, name).argtypes = [i, i, i, vp, vp]
-            getattr(L, name).restype = None
-        L.ora_dot_f64.argtypes = [i, i, i, vp, vp]
-        L.ora_dot_f64.restype = d
-        L.ora_dot2_f32.argtypes = [i, i, i, vp, vp, ctypes.POINTER(d), ctypes.POINTER(d)]
-        L.ora_dot2_f32.restype = None
-        L.ora_cg_classic.argtypes = [i, i, i, vp, vp, d, i, ctypes.POINTER(_Trace), ctypes.POINTER(Info)]
-        L.ora_cg_newcg.argtypes = [i, i, i, vp, vp, d, i, i, ctypes.POINTER(_Trace), ctypes.POINTER(Info)]
-        L.ora_cg_ir.argtypes = [i, i, i, vp, vp, d, i, i, d, i, ctypes.POINTER(Info)]
-        L.ora_inner_cg_f32.argtypes = [i, i, i, vp, vp, d, i, i, vp, ctypes.POINTER(i)]
-        L.ora_inner_cg_f32.restype = i
-        for name in ("ora_cg_classic", "ora_cg_newcg", "ora_cg_ir"):
-            getattr(L, name).restype = i
-        L.ora_repro_blocks.argtypes = [i, i, i, vp, vp, vp]
-        L.ora_repro_blocks.restype = None
-        L.ora_fma_axpy.argtypes = [i, i, i, vp, d, vp]
-        L.ora_fma_axpy.restype = None
-        L.ora_fma_xpby.argtypes = [i, i, i, vp, d, vp]
-        L.ora_fma_xpby.restype = None
-        L.ora_mg_restrict.argtypes = [i, i, vp, vp]
-        L.ora_mg_restrict.restype = None
-        L.ora_mg_prolong_add.argtypes = [i, i, vp, vp]
-        L.ora_mg_prolong_add.restype = None
-        L.ora_mg_precond.argtypes = [i, i, i, vp, vp, i, i, i]
-        L.ora_mg_precond.restype = i
-        L.ora_cg_pcg.argtypes = [i, i, i, vp, vp, d, i, i, i, i, vp, ctypes.POINTER(Info)]
-        L.ora_cg_pcg.restype = i
-        L.ora_cg_ppcg.argtypes = [i, i, i, vp, vp, d, i, i, i, i, ctypes.POINTER(Info)]
-        L.ora_cg_ppcg.restype = i
-        L.ora_f32_to_bf16.argtypes = [ctypes.c_float]
-        L.ora_f32_to_bf16.restype = ctypes.c_uint16
-        _lib = L
+        _lib = _load(_build.build())
     return _lib
+
+
+_lib_omp = None
+
+
+class timing_build:
+    """Context manager: inside it, every oracle function runs the OpenMP timing
+    build of lap5_oracle.c (its binary64 row loops on all threads, dot products
+    as per-thread partial sums added in thread order).  For the benchmark's
+    CPU-baseline timing only; parity always uses the sequential build.
+    ``threads`` is the number of threads that build uses."""
+
+    def __enter__(self):
+        global _lib, _lib_omp
+        if _lib_omp is None:
+            _lib_omp = _load(_build.build(openmp=True))
+        self.saved = _lib
+        _lib = _lib_omp
+        self.threads = int(_lib_omp.ora_threads())
+        return self
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self.saved
+        return False
+
+
+def _load(path):
+    L = ctypes.CDLL(path)
+    i, d, vp = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+    for name in ("ora_lap5_apply_f64", "ora_lap5_apply_f32", "ora_lap5_apply_bf16"):
+        getattr(L, name).argtypes = [i, i, i, vp, vp]
+        getattr(L, name).restype = None
+    L.ora_dot_f64.argtypes = [i, i, i, vp, vp]
+    L.ora_dot_f64.restype = d
+    L.ora_dot2_f32.argtypes = [i, i, i, vp, vp, ctypes.POINTER(d), ctypes.POINTER(d)]
+    L.ora_dot2_f32.restype = None
+    L.ora_cg_classic.argtypes = [i, i, i, vp, vp, d, i, ctypes.POINTER(_Trace), ctypes.POINTER(Info)]
+    L.ora_cg_newcg.argtypes = [i, i, i, vp, vp, d, i, i, ctypes.POINTER(_Trace), ctypes.POINTER(Info)]
+    L.ora_cg_ir.argtypes = [i, i, i, vp, vp, d, i, i, d, i, ctypes.POINTER(Info)]
+    L.ora_inner_cg_f32.argtypes = [i, i, i, vp, vp, d, i, i, vp, ctypes.POINTER(i)]
+    L.ora_inner_cg_f32.restype = i
+    for name in ("ora_cg_classic", "ora_cg_newcg", "ora_cg_ir"):
+        getattr(L, name).restype = i
+    L.ora_repro_blocks.argtypes = [i, i, i, vp, vp, vp]
+    L.ora_repro_blocks.restype = None
+    L.ora_fma_axpy.argtypes = [i, i, i, vp, d, vp]
+    L.ora_fma_axpy.restype = None
+    L.ora_fma_xpby.argtypes = [i, i, i, vp, d, vp]
+    L.ora_fma_xpby.restype = None
+    L.ora_mg_restrict.argtypes = [i, i, vp, vp]
+    L.ora_mg_restrict.restype = None
+    L.ora_mg_prolong_add.argtypes = [i, i, vp, vp]
+    L.ora_mg_prolong_add.restype = None
+    L.ora_mg_precond.argtypes = [i, i, i, vp, vp, i, i, i]
+    L.ora_mg_precond.restype = i
+    L.ora_cg_pcg.argtypes = [i, i, i, vp, vp, d, i, i, i, i, vp, ctypes.POINTER(Info)]
+    L.ora_cg_pcg.restype = i
+    L.ora_cg_ppcg.argtypes = [i, i, i, vp, vp, d, i, i, i, i, ctypes.POINTER(Info)]
+    L.ora_cg_ppcg.restype = i
+    L.ora_f32_to_bf16.argtypes = [ctypes.c_float]
+    L.ora_f32_to_bf16.restype = ctypes.c_uint16
+    L.ora_threads.argtypes = []
+    L.ora_threads.restype = i
+    return L
 
 
 def _grid(a, dtype, nx):

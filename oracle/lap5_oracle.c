@@ -36,6 +36,18 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* Timing build (oracle/build.py, -fopenmp -DORA_OMP): the row loops of the
+ * binary64 stencil and vector helpers run on all threads, and ora_dot_f64 sums
+ * per-thread partials of contiguous row blocks in thread order.  Only the
+ * benchmark's CPU-baseline timing loads that build; the parity build (no
+ * ORA_OMP) is the plain sequential code below, and ORA_ROWS is empty there. */
+#ifdef ORA_OMP
+#include <omp.h>
+#define ORA_ROWS _Pragma("omp parallel for schedule(static)")
+#else
+#define ORA_ROWS
+#endif
+
 enum { ORA_OK = 0, ORA_NOT_CONVERGED = 1, ORA_ERR_INVALID_ARG = -1,
        ORA_ERR_BREAKDOWN = -3, ORA_ERR_NONFINITE = -5 };
 
@@ -72,6 +84,7 @@ static double at64(const double* x, int nx, int ny, int ld, int i, int j) {
 }
 
 void ora_lap5_apply_f64(int nx, int ny, int ld, const double* x, double* y) {
+  ORA_ROWS
   for (int j = 0; j < ny; ++j)
     for (int i = 0; i < nx; ++i) {
       double acc = 4.0 * at64(x, nx, ny, ld, i, j);
@@ -140,34 +153,66 @@ void ora_lap5_apply_bf16(int nx, int ny, int ld, const uint16_t* x, uint16_t* y)
 
 /* (a, b) summed in index order (row by row, i fastest), binary64. */
 double ora_dot_f64(int nx, int ny, int ld, const double* a, const double* b) {
+#ifdef ORA_OMP
+  double part[256];
+  int used = 1;
+#pragma omp parallel num_threads(omp_get_max_threads() < 256 ? omp_get_max_threads() : 256)
+  {
+    const int t = omp_get_thread_num(), T = omp_get_num_threads();
+    const int j0 = (int)((long long)ny * t / T), j1 = (int)((long long)ny * (t + 1) / T);
+    double s = 0.0;
+    for (int j = j0; j < j1; ++j)
+      for (int i = 0; i < nx; ++i) s += a[(size_t)j * ld + i] * b[(size_t)j * ld + i];
+    part[t] = s;
+    if (t == 0) used = T;
+  }
+  double s = 0.0;
+  for (int t = 0; t < used; ++t) s += part[t];
+  return s;
+#else
   double s = 0.0;
   for (int j = 0; j < ny; ++j)
     for (int i = 0; i < nx; ++i) s += a[(size_t)j * ld + i] * b[(size_t)j * ld + i];
   return s;
+#endif
+}
+
+/* threads of the timing build (1 in the parity build) */
+int ora_threads(void) {
+#ifdef ORA_OMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
 }
 
 static void axpy64(int nx, int ny, int ld, double* y, double a, const double* x) {
+  ORA_ROWS
   for (int j = 0; j < ny; ++j)
     for (int i = 0; i < nx; ++i) y[(size_t)j * ld + i] = y[(size_t)j * ld + i] + a * x[(size_t)j * ld + i];
 }
 
 /* y = x + beta * y */
 static void xpby64(int nx, int ny, int ld, const double* x, double beta, double* y) {
+  ORA_ROWS
   for (int j = 0; j < ny; ++j)
     for (int i = 0; i < nx; ++i) y[(size_t)j * ld + i] = x[(size_t)j * ld + i] + beta * y[(size_t)j * ld + i];
 }
 
 static void copy64(int nx, int ny, int ld, double* y, const double* x) {
+  ORA_ROWS
   for (int j = 0; j < ny; ++j) memcpy(y + (size_t)j * ld, x + (size_t)j * ld, sizeof(double) * (size_t)nx);
 }
 
 static void zero64(int nx, int ny, int ld, double* y) {
+  ORA_ROWS
   for (int j = 0; j < ny; ++j) memset(y + (size_t)j * ld, 0, sizeof(double) * (size_t)nx);
 }
 
 /* r = b - A x */
 static void residual64(int nx, int ny, int ld, const double* b, const double* x, double* r) {
   ora_lap5_apply_f64(nx, ny, ld, x, r);
+  ORA_ROWS
   for (int j = 0; j < ny; ++j)
     for (int i = 0; i < nx; ++i) r[(size_t)j * ld + i] = b[(size_t)j * ld + i] - r[(size_t)j * ld + i];
 }

@@ -24,3 +24,18 @@ def unflat(v: np.ndarray, nx: int, ny: int, ld: int = None) -> np.ndarray:
     out = np.zeros((ny, ld), dtype=v.dtype)
     out[:, :nx] = v.reshape(ny, nx)
     return out
+
+
+def rel_err(a: np.ndarray, b: np.ndarray) -> float:
+    """Relative difference of a from b, the larger of the norm-wise
+    ||a - b||_2 / ||b||_2 and the element-wise max|a - b| / max|b|: a defect in
+    a few points (a halo, a strip edge) that a norm would average away still
+    shows in the second."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    d = a - b
+    nb = np.linalg.norm(b)
+    mb = np.max(np.abs(b)) if b.size else 0.0
+    norm = np.linalg.norm(d) / (nb if nb > 0 else 1.0)
+    elem = (np.max(np.abs(d)) if d.size else 0.0) / (mb if mb > 0 else 1.0)
+    return float(max(norm, elem))

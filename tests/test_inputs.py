@@ -75,3 +75,15 @@ def test_pitch():
         for es, al in ((8, 16), (4, 16), (8, 32), (2, 16)):
             ld = gen.pitch(nx, es, al)
             assert ld >= nx and (ld * es) % al == 0 and ld - nx < al // es
+
+
+def test_rel_err_sees_a_single_wrong_point():
+    # the GPU parity tests compare with the larger of the norm-wise and the
+    # element-wise relative difference
+    from tests.helpers import rel_err
+    b = np.ones(4096 * 4096 // 64)
+    a = b.copy()
+    a[123] += 1e-7
+    assert np.linalg.norm(a - b) / np.linalg.norm(b) < 2e-10  # a norm averages it away
+    assert rel_err(a, b) >= 1e-7
+    assert rel_err(b, b) == 0.0 and rel_err(np.zeros(3), np.zeros(3)) == 0.0
