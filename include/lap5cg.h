@@ -275,8 +275,9 @@ LAP5CG_API int lap5cg_tune_batched(int count, const int* nx, const int* ny, cons
  * Measurement helper (no paper counterpart): the binary64 instruction rates of
  * the current GPU, in lane operations per second -- fused multiply-adds
  * (*fma_per_s) and additions (*add_per_s) -- from a throughput kernel with
- * eight independent dependency chains a thread on every SM, timed with CUDA
- * events on `stream` (best of three launches of about 40 ms each).  The
+ * eight independent dependency chains a thread and 64 warps on every SM,
+ * timed with CUDA events on `stream` (best of five launches of about 40 ms
+ * each; the GPU's clocks should be up, e.g. after other work).  The
  * binary64 solves are bound by this pipe rather than by memory bandwidth.
  * Synchronises the stream; allocates no device memory.
  * Returns LAP5CG_OK, LAP5CG_ERR_INVALID_ARG (NULL outputs) or LAP5CG_ERR_CUDA.
