@@ -461,6 +461,12 @@ void ora_dot2_f32(int nx, int ny, int ld, const float* a, const float* b, double
 /* binary32 d and z.  Inner arithmetic is binary32; inner dots are Dot2;  */
 /* inner scalars (alpha, beta) are formed in binary64 and rounded to      */
 /* binary32 for the vector updates.  Inner variant: classic CG (Alg. 1).  */
+/* With bf16 p, r the inner beta takes the Polak-Ribiere form             */
+/* (r_new, r_new - r_old) / (r_old, r_old): equal to Algorithm 1's        */
+/* (r_new, r_new) / (r_old, r_old) in exact arithmetic, where consecutive */
+/* residuals are orthogonal, but it discounts the part of r_new that the  */
+/* bf16 rounding left along r_old (without it the stored residual stalls  */
+/* near 3e-2 of its start at 4096^2 and then grows).                      */
 /* ------------------------------------------------------------------ */
 static float stor(float v, int bf) { return bf ? bf16_to_f32(f32_to_bf16(v)) : v; }
 
@@ -470,7 +476,7 @@ static double dot2_pair(int nx, int ny, int ld, const float* a, const float* b) 
 
 /* Inner classic CG on A d = rin from d = 0; returns iterations used. */
 static int inner_cg_f32(int nx, int ny, int ld, const float* rin, float* d, double tol_in, int maxit_in,
-                        int bf, float* r, float* p, float* z, int* brk) {
+                        int bf, float* r, float* p, float* z, float* rp, int* brk) {
   size_t n = (size_t)ny * ld;
   memset(d, 0, n * sizeof(float));
   for (size_t t = 0; t < n; ++t) { r[t] = stor(rin[t], bf); p[t] = r[t]; }
@@ -483,6 +489,7 @@ static int inner_cg_f32(int nx, int ny, int ld, const float* rin, float* d, doub
     double pz = dot2_pair(nx, ny, ld, p, z);
     if (!(pz > 0.0) || !isfinite(pz)) { *brk = 1; break; }
     float a = (float)(g / pz);
+    if (bf) memcpy(rp, r, n * sizeof(float));        /* r_old, for the Polak-Ribiere beta */
     for (int j = 0; j < ny; ++j)
       for (int i = 0; i < nx; ++i) {
         size_t t = (size_t)j * ld + i;
@@ -492,7 +499,8 @@ static int inner_cg_f32(int nx, int ny, int ld, const float* rin, float* d, doub
     double gn = dot2_pair(nx, ny, ld, r, r);
     ++k;
     if (!isfinite(gn)) { *brk = 1; break; }
-    float bt = (float)(gn / g);
+    double num = bf ? gn - dot2_pair(nx, ny, ld, r, rp) : gn;
+    float bt = (float)(num / g);
     g = gn;
     if (g <= thr) break;
     for (int j = 0; j < ny; ++j)
@@ -512,13 +520,13 @@ static int inner_cg_f32(int nx, int ny, int ld, const float* rin, float* d, doub
 int ora_inner_cg_f32(int nx, int ny, int ld, const float* rin, float* d, double tol_in, int maxit_in,
                      int inner_storage, float* r_out, int* breakdown) {
   const size_t n = (size_t)ny * ld;
-  float *r = calloc(n, 4), *p = calloc(n, 4), *z = calloc(n, 4);
+  float *r = calloc(n, 4), *p = calloc(n, 4), *z = calloc(n, 4), *rp = calloc(n, 4);
   int brk = 0, k = -1;
-  if (r && p && z && (inner_storage == 1 || inner_storage == 2) && maxit_in >= 0) {
-    k = inner_cg_f32(nx, ny, ld, rin, d, tol_in, maxit_in, inner_storage == 2, r, p, z, &brk);
+  if (r && p && z && rp && (inner_storage == 1 || inner_storage == 2) && maxit_in >= 0) {
+    k = inner_cg_f32(nx, ny, ld, rin, d, tol_in, maxit_in, inner_storage == 2, r, p, z, rp, &brk);
     if (r_out) memcpy(r_out, r, n * sizeof(float));
   }
-  free(r); free(p); free(z);
+  free(r); free(p); free(z); free(rp);
   if (breakdown) *breakdown = brk;
   return k;
 }
@@ -536,8 +544,9 @@ int ora_cg_ir(int nx, int ny, int ld, const double* b, double* x, double tol, in
   const double thr = tol > 0.0 ? tol * tol * bb : 0.0;
   const int bf = inner_storage == 2;
   double* r = calloc(n, 8);
-  float *rin = calloc(n, 4), *d = calloc(n, 4), *ri = calloc(n, 4), *pi = calloc(n, 4), *zi = calloc(n, 4);
-  if (!r || !rin || !d || !ri || !pi || !zi) { free(r); free(rin); free(d); free(ri); free(pi); free(zi); inf.status = ORA_ERR_INVALID_ARG; if (info) *info = inf; return inf.status; }
+  float *rin = calloc(n, 4), *d = calloc(n, 4), *ri = calloc(n, 4), *pi = calloc(n, 4), *zi = calloc(n, 4),
+        *rp = calloc(n, 4);
+  if (!r || !rin || !d || !ri || !pi || !zi || !rp) { free(r); free(rin); free(d); free(ri); free(pi); free(zi); free(rp); inf.status = ORA_ERR_INVALID_ARG; if (info) *info = inf; return inf.status; }
   int status = ORA_NOT_CONVERGED, outer = 0, total_inner = 0;
   double rr = 0.0, rr_prev = 0.0;
   for (;;) {
@@ -559,7 +568,7 @@ int ora_cg_ir(int nx, int ny, int ld, const double* b, double* x, double tol, in
     if (outer >= max_outer) break;
     for (size_t t = 0; t < n; ++t) rin[t] = (float)r[t]; /* round to nearest */
     int brk = 0;
-    total_inner += inner_cg_f32(nx, ny, ld, rin, d, tol_in, maxit_in, bf, ri, pi, zi, &brk);
+    total_inner += inner_cg_f32(nx, ny, ld, rin, d, tol_in, maxit_in, bf, ri, pi, zi, rp, &brk);
     if (brk) { status = ORA_ERR_BREAKDOWN; break; }
     for (int j = 0; j < ny; ++j)                        /* FP64 update */
       for (int i = 0; i < nx; ++i) x[(size_t)j * ld + i] = x[(size_t)j * ld + i] + (double)d[(size_t)j * ld + i];
@@ -568,7 +577,7 @@ int ora_cg_ir(int nx, int ny, int ld, const double* b, double* x, double tol, in
   inf.status = status; inf.iters = total_inner; inf.outer_iters = outer;
   inf.relres_recursive = sqrt(rr / bb);
   inf.relres_true = true_relres(nx, ny, ld, b, x, bb);
-  free(r); free(rin); free(d); free(ri); free(pi); free(zi);
+  free(r); free(rin); free(d); free(ri); free(pi); free(zi); free(rp);
   if (info) *info = inf;
   return status;
 }

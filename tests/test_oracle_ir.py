@@ -10,9 +10,10 @@ rounding; these pins do (tests/test_oracle_mutations.py plants each one).
   * at a fixed iteration count the binary32 iterate stays within a
     rounding-level distance of the binary64 Algorithm 1 on the same data;
   * bf16 p, r: bit-for-bit equality with an independent numpy restatement that
-    rounds p and r to bf16 (torch's round-to-nearest-even) after every update
-    and sums with its own Dot2 (TwoProduct from an exact binary64 product,
-    Knuth's TwoSum).
+    rounds p and r to bf16 (torch's round-to-nearest-even) after every update,
+    takes the Polak-Ribiere beta (r_new, r_new - r_old) / (r_old, r_old) and
+    sums with its own Dot2 (TwoProduct from an exact binary64 product, Knuth's
+    TwoSum).
 """
 import math
 
@@ -147,10 +148,13 @@ def _restated_inner(rin, nx, maxit, bf):
         pz = _dot2(p, z, nx)
         a = np.float32(g / pz)
         d = (d + a * p).astype(np.float32)
+        r_old = r
         r = st((r - a * z).astype(np.float32))
         gn = _dot2(r, r, nx)
         k += 1
-        bt = np.float32(gn / g)
+        # bf16 p, r: Polak-Ribiere beta (r_new, r_new - r_old) / (r_old, r_old)
+        num = gn - _dot2(r, r_old, nx) if bf else gn
+        bt = np.float32(num / g)
         g = gn
         if g <= 0.0:
             break

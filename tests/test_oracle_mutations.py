@@ -34,7 +34,9 @@ MUTATIONS = {
 
 # mistakes in the mixed-precision path, caught by the pins of tests/test_oracle_ir.py
 IR_MUTATIONS = {
-    "inner_beta_inverted": ("float bt = (float)(gn / g);", "float bt = (float)(g / gn);"),
+    "inner_beta_inverted": ("float bt = (float)(num / g);", "float bt = (float)(g / num);"),
+    "inner_pr_beta_sign": ("double num = bf ? gn - dot2_pair(nx, ny, ld, r, rp) : gn;",
+                           "double num = bf ? gn + dot2_pair(nx, ny, ld, r, rp) : gn;"),
     "inner_r_sign": ("r[t] = stor(r[t] - a * z[t], bf);", "r[t] = stor(r[t] + a * z[t], bf);"),
     "inner_p_not_rounded_to_bf16": ("p[t] = stor(r[t] + bt * p[t], bf);", "p[t] = r[t] + bt * p[t];"),
     "ir_update_sign": ("x[(size_t)j * ld + i] = x[(size_t)j * ld + i] + (double)d[(size_t)j * ld + i];",
