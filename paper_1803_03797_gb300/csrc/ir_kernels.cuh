@@ -43,6 +43,10 @@ __device__ void ir_solve(const IrArgs<TR>& a, Team& tm, double* red, unsigned ch
   WarpRing ring;
   ring_setup(ring, c, dsm);
   constexpr int ES = (int)sizeof(TR);
+  // bf16 p, r: Polak-Ribiere beta (r_new, r_new - r_old) / (r_old, r_old), equal
+  // to Algorithm 1's beta in exact arithmetic; it discounts the part of r_new
+  // that the bf16 rounding left along r_old (the same rule as the oracle's)
+  constexpr bool kPR = (ES == 2);
   // A p stored (zs) only with four columns a lane: the stored form's register
   // march would not fit the register budget with eight
   const int zs = Lanes<V>::G > 1 ? 0 : a.store_z;
@@ -248,7 +252,7 @@ __device__ void ir_solve(const IrArgs<TR>& a, Team& tm, double* red, unsigned ch
         if (!(pz > 0.0) || !isfinite(pz)) { status = LAP5CG_ERR_BREAKDOWN; goto done; }
         {  // phase R
           const float am = (float)(gamma / pz);
-          Acc acc;
+          Acc acc, aro;  // (r, r) and, for bf16 storage, (r_new, r_old)
           if (R && !zs) {
             const RingVec vv[3] = {
                 {reinterpret_cast<const unsigned char*>(pnew.ptr), pnew.ld, ES, RV_HALO | RV_ALWAYS},
@@ -269,16 +273,18 @@ __device__ void ir_solve(const IrArgs<TR>& a, Team& tm, double* red, unsigned ch
               };
               auto finish = [&](int j, const unsigned char* sl, const FRow<V, float>& S, const FRow<V, float>& C,
                                 const FRow<V, float>& N) {
-                float ap[V], dv[V], rv[V];
+                float ap[V], dv[V], rv[V], ro[V];
                 stencil_row<V>(S, C, N, wk.lane, ap);
                 ring_lane<V, TR>(sl, off[2], false, wk.lane, xl, c.nx, rv);
                 if (!first) ring_lane<V, float>(sl, off[1], false, wk.lane, xl, c.nx, dv);
 #pragma unroll
                 for (int q = 0; q < V; ++q) {
+                  ro[q] = rv[q];
                   dv[q] = first ? __fmul_rn(am, C.f[q]) : fmx(am, C.f[q], dv[q]);
                   rv[q] = quantize<TR>(fmx(-am, ap[q], rv[q]));
                 }
                 acc_dot<V>(acc, j, rv, rv, nval);
+                if constexpr (kPR) acc_dot<V>(aro, j, rv, ro, nval);
                 store_row<V>(a.d, j, xl, c.nx, dv);
                 store_row<V>(a.r, j, xl, c.nx, rv);
               };
@@ -306,6 +312,7 @@ __device__ void ir_solve(const IrArgs<TR>& a, Team& tm, double* red, unsigned ch
                   rv[q] = quantize<TR>(fmx(-am, dd.z[q], dd.r[q]));
                 }
                 acc_dot<V>(acc, j, rv, rv, nval);
+                if constexpr (kPR) acc_dot<V>(aro, j, rv, dd.r, nval);
                 store_row<V>(a.d, j, xl, c.nx, dv);
                 store_row<V>(a.r, j, xl, c.nx, rv);
               };
@@ -327,6 +334,7 @@ __device__ void ir_solve(const IrArgs<TR>& a, Team& tm, double* red, unsigned ch
                   rv[q] = quantize<TR>(fmx(-am, ap[q], dd.r[q]));
                 }
                 acc_dot<V>(acc, j, rv, rv, nval);
+                if constexpr (kPR) acc_dot<V>(aro, j, rv, dd.r, nval);
                 store_row<V>(a.d, j, xl, c.nx, dv);
                 store_row<V>(a.r, j, xl, c.nx, rv);
               };
@@ -334,13 +342,16 @@ __device__ void ir_solve(const IrArgs<TR>& a, Team& tm, double* red, unsigned ch
             }
           }
           ++wk.pc;
-          double v[1] = {acc.value()}, o[1];
-          if (!tm.template reduce<1>(v, o, red)) { aborted = true; goto done; }
+          constexpr int NR = kPR ? 2 : 1;
+          double v[NR], o[NR];
+          v[0] = acc.value();
+          if constexpr (kPR) v[NR - 1] = aro.value();
+          if (!tm.template reduce<NR>(v, o, red)) { aborted = true; goto done; }
           const double gnew = o[0];
           ++k;
           ++total;
           if (!isfinite(gnew)) { status = LAP5CG_ERR_BREAKDOWN; goto done; }
-          beta = gnew / gamma;
+          beta = (kPR ? gnew - o[NR - 1] : gnew) / gamma;
           gamma = gnew;
           cur ^= 1;
         }

@@ -46,9 +46,20 @@ __device__ __forceinline__ void small_rows(int ny, int C, int c, int& r0, int& n
 // Cluster reduction of NV values (per-thread contributions): warp shuffle
 // tree, CTA partial, then every CTA reads all CTA partials through distributed
 // shared memory in rank order.  Parity-double-buffered slots.
-template <int NV>
+// No scalar follow-up (see the overload below).
+struct NoPost {
+  __device__ void operator()(const double*, double*) const {}
+};
+
+// Cluster reduction of NV values, then post(sums, extra) on one thread (warp
+// 0, lane 0) with its NE results broadcast to the CTA with the sums: the
+// scalar arithmetic of the iteration (divisions) runs once a CTA instead of
+// once a thread -- on this GPU's FP64 pipe a division in every thread of a
+// CTA costs microseconds.
+template <int NV, int NE = 0, class Post = NoPost>
 __device__ __forceinline__ void small_reduce(const double (&v)[NV], double (&out)[NV], double* red,
-                                             unsigned& epoch) {
+                                             unsigned& epoch, Post post = Post(), double* extra = nullptr) {
+  static_assert(NV + NE <= kMaxVals, "reduction slots");
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   auto cl = cgx::this_cluster();
   double* slot = red + 33 * kMaxVals + (int)(epoch & 1u) * kMaxVals;
@@ -79,12 +90,78 @@ __device__ __forceinline__ void small_reduce(const double (&v)[NV], double (&out
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
       if (lane == 0) red[32 * kMaxVals + k] = s;
     }
+    if constexpr (NE > 0)
+      if (lane == 0) post(red + 32 * kMaxVals, red + 32 * kMaxVals + NV);
   }
   __syncthreads();
 #pragma unroll
   for (int k = 0; k < NV; ++k) out[k] = red[32 * kMaxVals + k];
+  if constexpr (NE > 0)
+#pragma unroll
+    for (int k = 0; k < NE; ++k) extra[k] = red[32 * kMaxVals + NV + k];
   __syncthreads();
   ++epoch;
+}
+
+// The cluster barrier split in two (PTX barrier.cluster): arrive with release
+// semantics (this thread's earlier shared / distributed-shared writes become
+// visible to every thread that has waited), wait with acquire semantics.
+// Work placed between the two overlaps the barrier's latency.
+// Every thread of the cluster calls both, once per phase; the .aligned forms
+// need the warp converged, hence the __syncwarp.
+__device__ __forceinline__ void cluster_arrive_release() {
+  __syncwarp();
+  asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait_acquire() {
+  __syncwarp();
+  asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+
+// Pipelined NewCG exchange area of a CTA (after the vectors in dynamic shared
+// memory): the w halo rows and the CTA partials of (gamma, delta), both
+// double-buffered by iteration parity.  Neighbours write the halo rows and
+// every CTA writes its partials into every CTA's slots, so that after the
+// barrier each CTA reads them from its own shared memory.
+template <class T>
+struct SmallXchg {
+  T* halo;        // [2 parities][2: above, below][ldp]
+  double* slots;  // [2 parities][kMaxCtas16][2]
+  int ldp;
+  __device__ __forceinline__ T* row(int par, int below) const { return halo + (size_t)(2 * par + below) * ldp; }
+  __device__ __forceinline__ double* slot(int par, int rank) const { return slots + (size_t)(par * 16 + rank) * 2; }
+};
+
+// CTA sum of two per-thread values (warp shuffle tree, then warp 0 over the
+// warps), stored into slot(par, my rank) of every CTA of the cluster.
+__device__ __forceinline__ void small_publish2(double v0, double v1, const SmallXchg<double>& xs_d, int par,
+                                               int rank, int C, double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v0 += __shfl_xor_sync(0xffffffffu, v0, o);
+    v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+  }
+  if (lane == 0) {
+    red[warp * kMaxVals + 0] = v0;
+    red[warp * kMaxVals + 1] = v1;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    double s0 = lane < nwarps ? red[lane * kMaxVals + 0] : 0.0;
+    double s1 = lane < nwarps ? red[lane * kMaxVals + 1] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    }
+    if (lane < C) {
+      auto cl = cgx::this_cluster();
+      double* dst = cl.map_shared_rank(xs_d.slot(par, rank), (unsigned)lane);
+      dst[0] = s0;
+      dst[1] = s1;
+    }
+  }
 }
 
 template <class T>
@@ -132,13 +209,19 @@ __device__ __forceinline__ void small_push(const SmallView<T>& sv, int g, int nr
 }
 
 // vector slots in shared memory
-enum { SV_B = 0, SV_X, SV_R, SV_P, SV_Z, SV_W, SV_Q, SV_COUNT_CLASSIC = 5, SV_COUNT_NEWCG = 7 };
+enum { SV_B = 0, SV_X, SV_R, SV_P, SV_Z, SV_W, SV_Q, SV_N, SV_COUNT_CLASSIC = 5, SV_COUNT_NEWCG = 8 };
+
+// Bytes of the NewCG exchange area (w halo rows and partial slots).
+__host__ __device__ inline size_t small_xchg_bytes(int ldp, size_t es) {
+  return align_up((size_t)4 * ldp * es, 16) + (size_t)2 * 16 * 2 * sizeof(double);
+}
 
 template <class T>
-__global__ void __launch_bounds__(512) k_small(const SmallArgs<T> a) {
+__global__ void __launch_bounds__(512, 1) k_small(const SmallArgs<T> a) {
   using M = typename Math<T>::type;
   using Acc = typename AccOf<M>::type;
   __shared__ double red[kRedDoubles];
+  __shared__ double scal[5];  // NewCG: gamma, delta, alpha, beta, continue / stop / status
   extern __shared__ __align__(16) unsigned char dsm[];
   auto cl = cgx::this_cluster();
   const int rank = (int)cl.block_rank(), C = (int)cl.num_blocks();
@@ -154,6 +237,20 @@ __global__ void __launch_bounds__(512) k_small(const SmallArgs<T> a) {
   // zero everything (halo rows at the grid edge stay zero), load b and x0
   for (int v = 0; v < nvec; ++v)
     for (int e = tid; e < sv.rows * sv.ldp; e += nt) sv.vec(v)[e] = from_math<T, M>(M(0));
+  SmallXchg<T> xh;
+  SmallXchg<double> xd;
+  {
+    unsigned char* xbase = dsm + (size_t)nvec * sv.rows * sv.ldp * sizeof(T);
+    xh.halo = reinterpret_cast<T*>(xbase);
+    xh.ldp = sv.ldp;
+    xd.slots = reinterpret_cast<double*>(xbase + align_up((size_t)4 * sv.ldp * sizeof(T), 16));
+    xd.ldp = sv.ldp;
+    xh.slots = xd.slots;
+    if (a.variant == LAP5CG_NEWCG) {
+      for (int e = tid; e < 4 * sv.ldp; e += nt) xh.halo[e] = from_math<T, M>(M(0));
+      for (int e = tid; e < 2 * 16 * 2; e += nt) xd.slots[e] = 0.0;
+    }
+  }
   __syncthreads();
   for (int e = tid; e < npts; e += nt) {
     const int i = e / nx, k = e - i * nx;
@@ -202,7 +299,7 @@ __global__ void __launch_bounds__(512) k_small(const SmallArgs<T> a) {
       if (a.history && rank == 0 && tid == 0) a.history[0] = sqrt(gamma / bb);
       if (!isfinite(gamma)) { status = LAP5CG_ERR_NONFINITE; goto truecheck; }
       if (gamma <= thr) { status = LAP5CG_OK; goto truecheck; }
-      double beta = 0.0;
+      double beta = 0.0, alpha_bc = 0.0, beta_bc = 0.0;
       while (iters < a.maxit) {
         const M bm = (M)beta;
         for (int e = tid; e < npts; e += nt) {  // p = r + beta p
@@ -222,12 +319,14 @@ __global__ void __launch_bounds__(512) k_small(const SmallArgs<T> a) {
             sv.at(SV_Z, i, k) = from_math<T, M>(zv);
             acc.add(to_math<M, T>(sv.at(SV_P, i, k)), zv);
           }
-          double v[1] = {acc.value()}, o[1];
-          small_reduce<1>(v, o, red, epoch);
+          double v[1] = {acc.value()}, o[1], e[1];
+          const double gm = gamma;
+          small_reduce<1, 1>(v, o, red, epoch, [gm](const double* sum, double* ex) { ex[0] = gm / sum[0]; }, e);
           pz = o[0];
+          alpha_bc = e[0];
         }
         if (!(pz > 0.0) || !isfinite(pz)) { status = LAP5CG_ERR_BREAKDOWN; goto truecheck; }
-        const double alpha = gamma / pz;
+        const double alpha = alpha_bc;
         const M am = (M)alpha;
         double gnew;
         {
@@ -239,20 +338,30 @@ __global__ void __launch_bounds__(512) k_small(const SmallArgs<T> a) {
             sv.at(SV_R, i, k) = from_math<T, M>(rv);
             acc.add(rv, rv);
           }
-          double v[1] = {acc.value()}, o[1];
-          small_reduce<1>(v, o, red, epoch);
+          double v[1] = {acc.value()}, o[1], e[1];
+          const double gm = gamma;
+          small_reduce<1, 1>(v, o, red, epoch, [gm](const double* sum, double* ex) { ex[0] = sum[0] / gm; }, e);
           gnew = o[0];
+          beta_bc = e[0];
         }
         ++iters;
         if (a.history && rank == 0 && tid == 0) a.history[iters] = sqrt(gnew / bb);
         if (!isfinite(gnew)) { status = LAP5CG_ERR_NONFINITE; gamma = gnew; goto truecheck; }
-        beta = gnew / gamma;
+        beta = beta_bc;
         gamma = gnew;
         if (gnew <= thr) { status = LAP5CG_OK; goto truecheck; }
       }
     } else {
       // ------------------------------ Algorithm 2 ------------------------------
-      {  // w = A r, gamma = (r, r), delta = (w, r)
+      // One cluster barrier per iteration, split into arrive and wait: a CTA
+      // publishes its (gamma, delta) partials and its new w boundary rows,
+      // arrives, computes n = A w on the rows that need no neighbour row, and
+      // only then waits -- the reduction overlaps the stencil (Sec. II, Fig.
+      // NewCG).  The remaining rows of n, the scalars and the six pointwise
+      // updates follow the wait.  Halo rows and partial slots alternate
+      // between two buffers by iteration parity, so a CTA that runs ahead
+      // never overwrites what a neighbour has yet to read.
+      {  // w = A r, gamma = (r, r), delta = (w, r); publish for the first wait
         __syncthreads();
         small_push<T>(sv, SV_R, nr, nx, rank, C, ny);
         cl.sync();
@@ -265,73 +374,129 @@ __global__ void __launch_bounds__(512) k_small(const SmallArgs<T> a) {
           ag.add(rv, rv);
           ad.add(wv, rv);
         }
-        double v[2] = {ag.value(), ad.value()}, o[2];
-        small_reduce<2>(v, o, red, epoch);
-        gamma = o[0];
-        delta = o[1];
+        small_publish2(ag.value(), ad.value(), xd, 0, rank, C, red);  // its __syncthreads orders the w writes
+        if (rank > 0)
+          for (int k = tid; k < nx; k += nt) cl.map_shared_rank(xh.row(0, 1), (unsigned)(rank - 1))[k] = sv.at(SV_W, 0, k);
+        if (rank + 1 < C)
+          for (int k = tid; k < nx; k += nt) cl.map_shared_rank(xh.row(0, 0), (unsigned)(rank + 1))[k] = sv.at(SV_W, nr - 1, k);
+        cluster_arrive_release();
       }
-      if (a.history && rank == 0 && tid == 0) a.history[0] = sqrt(gamma / bb);
-      if (!isfinite(gamma)) { status = LAP5CG_ERR_NONFINITE; goto truecheck; }
-      if (gamma <= thr) { status = LAP5CG_OK; goto truecheck; }
-      if (a.maxit <= 0) goto truecheck;
-      if (!(delta > 0.0) || !isfinite(delta)) { status = LAP5CG_ERR_BREAKDOWN; goto truecheck; }
-      double alpha = gamma / delta, beta = 0.0;
+      double alpha = 0.0, gold = 0.0;
+      int par = 0;
       for (;;) {
         const bool first = (iters == 0);
-        const M am = (M)alpha, bm = (M)beta;
-        __syncthreads();
-        small_push<T>(sv, SV_W, nr, nx, rank, C, ny);
-        cl.sync();
-        // stage 1: n = A w (reads w on the own rows and halos) and the
-        // pointwise z, q, p recurrences
-        for (int e = tid; e < npts; e += nt) {
-          const int i = e / nx, k = e - i * nx;
-          const M nv = small_stencil<T, M>(sv, SV_W, i, k, nx);
-          const M wv = to_math<M, T>(sv.at(SV_W, i, k));
-          const M rv = to_math<M, T>(sv.at(SV_R, i, k));
-          M zv, qv, pv;
-          if (first) {
-            zv = nv;
-            qv = wv;
-            pv = rv;
-          } else {
-            zv = fmx(bm, to_math<M, T>(sv.at(SV_Z, i, k)), nv);
-            qv = fmx(bm, to_math<M, T>(sv.at(SV_Q, i, k)), wv);
-            pv = fmx(bm, to_math<M, T>(sv.at(SV_P, i, k)), rv);
-          }
-          sv.at(SV_Z, i, k) = from_math<T, M>(zv);
-          sv.at(SV_Q, i, k) = from_math<T, M>(qv);
-          sv.at(SV_P, i, k) = from_math<T, M>(pv);
+        // n = A w on the rows whose neighbours are this CTA's own (overlaps the barrier)
+        const int ni = nr > 2 ? (nr - 2) * nx : 0;
+        for (int e = tid; e < ni; e += nt) {
+          const int i = 1 + e / nx, k = e - (i - 1) * nx;
+          sv.at(SV_N, i, k) = from_math<T, M>(small_stencil<T, M>(sv, SV_W, i, k, nx));
         }
-        __syncthreads();  // every stencil read of w is done before w changes
+        cluster_wait_acquire();
+        if (tid < 32) {  // one warp forms the scalars while the others start the boundary rows
+          const int lane = tid;
+          double g = lane < C ? xd.slot(par, lane)[0] : 0.0;
+          double d = lane < C ? xd.slot(par, lane)[1] : 0.0;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {  // the same tree in every CTA: identical scalars
+            g += __shfl_xor_sync(0xffffffffu, g, o);
+            d += __shfl_xor_sync(0xffffffffu, d, o);
+          }
+          if (lane == 0) {
+            double st = 0.0, al = alpha, be = 0.0;  // st: 0 go on, 1 stop, or a (negative) status
+            if (!isfinite(g)) {
+              st = LAP5CG_ERR_NONFINITE;
+            } else if (g <= thr) {
+              st = 1.0;
+            } else if (iters >= a.maxit) {
+              st = 2.0;
+            } else if (first) {
+              if (!(d > 0.0) || !isfinite(d)) st = LAP5CG_ERR_BREAKDOWN;
+              else al = g / d;
+            } else {
+              be = g / gold;
+              const double denom = d / g - be / alpha;
+              if (!(denom > 0.0) || !isfinite(denom)) st = LAP5CG_ERR_BREAKDOWN;
+              else al = 1.0 / denom;
+            }
+            scal[0] = g;
+            scal[1] = d;
+            scal[2] = al;
+            scal[3] = be;
+            scal[4] = st;
+            if (a.history && rank == 0) a.history[iters] = sqrt(g / bb);
+          }
+        }
+        // n on the first and last own rows: their outer neighbours are the halo rows of this parity
+        {
+          const int nb = nr > 1 ? 2 * nx : nx;
+          for (int e = tid; e < nb; e += nt) {
+            const int i = (e < nx) ? 0 : nr - 1, k = e < nx ? e : e - nx;
+            const M c = to_math<M, T>(sv.at(SV_W, i, k));
+            const M w = k > 0 ? to_math<M, T>(sv.at(SV_W, i, k - 1)) : M(0);
+            const M ee = k + 1 < nx ? to_math<M, T>(sv.at(SV_W, i, k + 1)) : M(0);
+            const M so = to_math<M, T>(i == 0 ? xh.row(par, 0)[k] : sv.at(SV_W, i - 1, k));
+            const M no = to_math<M, T>(i == nr - 1 ? xh.row(par, 1)[k] : sv.at(SV_W, i + 1, k));
+            M acc = M(4) * c;
+            acc -= w;
+            acc -= ee;
+            acc -= so;
+            acc -= no;
+            sv.at(SV_N, i, k) = from_math<T, M>(acc);
+          }
+        }
+        __syncthreads();  // n and the scalars complete, every read of w done before w changes
+        gamma = scal[0];
+        delta = scal[1];
+        const double beta = scal[3];
+        {
+          const double st = scal[4];
+          if (st != 0.0) {
+            if (st == 1.0) status = LAP5CG_OK;
+            else if (st < 0.0) status = (int)st;
+            goto truecheck;
+          }
+        }
+        alpha = scal[2];
+        const M am = (M)alpha, bm = (M)beta;
         Acc ag, ad;
         for (int e = tid; e < npts; e += nt) {
           const int i = e / nx, k = e - i * nx;
-          const M pv = to_math<M, T>(sv.at(SV_P, i, k));
-          const M qv = to_math<M, T>(sv.at(SV_Q, i, k));
-          const M zv = to_math<M, T>(sv.at(SV_Z, i, k));
-          sv.at(SV_X, i, k) = from_math<T, M>(fmx(am, pv, to_math<M, T>(sv.at(SV_X, i, k))));
-          const M rv = fmx(-am, qv, to_math<M, T>(sv.at(SV_R, i, k)));
-          const M wv = fmx(-am, zv, to_math<M, T>(sv.at(SV_W, i, k)));
+          const M nv = to_math<M, T>(sv.at(SV_N, i, k));
+          const M wv0 = to_math<M, T>(sv.at(SV_W, i, k));
+          const M rv0 = to_math<M, T>(sv.at(SV_R, i, k));
+          M zv, qv, pv;
+          if (first) {
+            zv = nv;
+            qv = wv0;
+            pv = rv0;
+          } else {
+            zv = fmx(bm, to_math<M, T>(sv.at(SV_Z, i, k)), nv);
+            qv = fmx(bm, to_math<M, T>(sv.at(SV_Q, i, k)), wv0);
+            pv = fmx(bm, to_math<M, T>(sv.at(SV_P, i, k)), rv0);
+          }
+          // stored then re-read (rounded to T), as the streaming kernels use them
+          const M zs = to_math<M, T>(from_math<T, M>(zv)), qs = to_math<M, T>(from_math<T, M>(qv));
+          const M ps = to_math<M, T>(from_math<T, M>(pv));
+          sv.at(SV_Z, i, k) = from_math<T, M>(zv);
+          sv.at(SV_Q, i, k) = from_math<T, M>(qv);
+          sv.at(SV_P, i, k) = from_math<T, M>(pv);
+          sv.at(SV_X, i, k) = from_math<T, M>(fmx(am, ps, to_math<M, T>(sv.at(SV_X, i, k))));
+          const M rv = fmx(-am, qs, rv0);
+          const M wv = fmx(-am, zs, wv0);
           sv.at(SV_R, i, k) = from_math<T, M>(rv);
           sv.at(SV_W, i, k) = from_math<T, M>(wv);
           ag.add(rv, rv);
           ad.add(wv, rv);
         }
-        double v[2] = {ag.value(), ad.value()}, o[2];
-        small_reduce<2>(v, o, red, epoch);
         ++iters;
-        if (a.history && rank == 0 && tid == 0) a.history[iters] = sqrt(o[0] / bb);
-        const double gold = gamma;
-        gamma = o[0];
-        delta = o[1];
-        if (!isfinite(gamma)) { status = LAP5CG_ERR_NONFINITE; goto truecheck; }
-        if (gamma <= thr) { status = LAP5CG_OK; goto truecheck; }
-        if (iters >= a.maxit) break;
-        beta = gamma / gold;
-        const double denom = delta / gamma - beta / alpha;
-        if (!(denom > 0.0) || !isfinite(denom)) { status = LAP5CG_ERR_BREAKDOWN; goto truecheck; }
-        alpha = 1.0 / denom;
+        gold = gamma;
+        par ^= 1;
+        small_publish2(ag.value(), ad.value(), xd, par, rank, C, red);  // its __syncthreads orders the w writes
+        if (rank > 0)
+          for (int k = tid; k < nx; k += nt) cl.map_shared_rank(xh.row(par, 1), (unsigned)(rank - 1))[k] = sv.at(SV_W, 0, k);
+        if (rank + 1 < C)
+          for (int k = tid; k < nx; k += nt) cl.map_shared_rank(xh.row(par, 0), (unsigned)(rank + 1))[k] = sv.at(SV_W, nr - 1, k);
+        cluster_arrive_release();
       }
     }
   }
@@ -378,7 +543,8 @@ static size_t small_smem(int nx, int ny, int variant, int C, int* R_out, int* ld
   const int nvec = variant == LAP5CG_NEWCG ? SV_COUNT_NEWCG : SV_COUNT_CLASSIC;
   *R_out = R;
   *ldp_out = ldp;
-  return (size_t)nvec * (R + 2) * ldp * sizeof(T);
+  const size_t vec_bytes = (size_t)nvec * (R + 2) * ldp * sizeof(T);
+  return variant == LAP5CG_NEWCG ? vec_bytes + small_xchg_bytes(ldp, sizeof(T)) : vec_bytes;
 }
 
 template <class T>

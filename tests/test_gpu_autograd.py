@@ -85,14 +85,28 @@ def test_gradient_workload_2048x16(precision):
     assert all(r["status"] == lap5cg.OK for r in recs), recs
     g = b.grad.detach().cpu().numpy()
     rhs = x.detach().cpu().numpy() - xt0
-    # the adjoint equation A g = x - x_target, residual by the oracle's stencil.
-    # Binary64 CG stops on its recursive residual; for this noise-like
-    # right-hand side its true residual levels off near 1e-9 (attainable
-    # accuracy); the refinement path stops on the FP64 true residual itself.
-    for s in (0, k // 2, k - 1):
+    # The adjoint equation A g = x - x_target for every right-hand side,
+    # residual by the oracle's stencil.  Binary64 CG stops on its recursive
+    # residual (1e-10); the adjoint right-hand side x - x_target is dominated
+    # by the Gaussian x_target, and for it the true residual of binary64 CG
+    # levels off above the recursive one (CG's attainable accuracy: rounding
+    # in the x and r recurrences, here ~1e-9 at kappa = 1.7e6); the
+    # refinement and multigrid paths stop on the FP64 true residual itself.
+    rels = []
+    for s in range(k):
         res = rhs[s] - oracle.lap5_apply(g[s])
-        rel = np.linalg.norm(res) / np.linalg.norm(rhs[s])
-        assert rel <= {"f64": 5e-9, "ir_f32": 1.5e-10, "mg_f32": 2e-10}[precision], (s, rel)
+        rels.append(np.linalg.norm(res) / np.linalg.norm(rhs[s]))
+    print("\n[adjoint true residual] %s: max %.3g, median %.3g" % (precision, max(rels), float(np.median(rels))))
+    assert max(rels) <= {"f64": 5e-9, "ir_f32": 1.5e-10, "mg_f32": 2e-10}[precision], rels
+    # one gradient element-wise against the oracle's solve of the same adjoint
+    # equation (multigrid PCG to a true residual ~5e-13): |g - g*| <= ||A g - rhs||_2 / lambda_min
+    gr, ir = oracle.cg_pcg(rhs[0], tol=1e-13, maxit=200)
+    assert ir["status"] == oracle.OK
+    lam_min = gen.mode_eigenvalue(n, n, 1, 1)
+    bound = (rels[0] + ir["relres_true"]) * np.linalg.norm(rhs[0]) / lam_min
+    assert np.max(np.abs(g[0] - gr)) <= bound
+    print("[gradient vs oracle] %s: max|g - g*|/max|g*| %.3g (bound %.3g)"
+          % (precision, np.max(np.abs(g[0] - gr)) / np.max(np.abs(gr)), bound / np.max(np.abs(gr))))
 
 
 def test_f32_gradient_small():

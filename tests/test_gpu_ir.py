@@ -11,6 +11,7 @@ import torch
 import lap5_inputs as gen
 import oracle
 import paper_1803_03797_gb300 as lap5cg
+from tests.helpers import rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -22,7 +23,7 @@ def _dev(a):
 
 
 def _rel(a, b):
-    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+    return rel_err(a, b)  # norm-wise and element-wise
 
 
 @pytest.mark.parametrize("precision", ["ir_f32", "ir_bf16pr"])
@@ -125,3 +126,29 @@ def test_ir_8192_full_size_reaches_1e10():
     x_np = x.cpu().numpy()
     res = b_np - oracle.lap5_apply(x_np)
     assert np.linalg.norm(res) <= 1.05e-10 * np.linalg.norm(b_np)
+
+
+@pytest.mark.parametrize("precision", ["ir_f32", "ir_bf16pr"])
+@pytest.mark.parametrize("n", [1024, 2048])
+def test_ir_config_size_against_oracle_reference(precision, n):
+    # the manufactured right-hand side at kappa = 4.3e5 / 1.7e6: the FP64 true
+    # residual reaches 1e-10 and the solution is element-wise within the bound
+    # ||x - x*||_inf <= ||b - A x||_2 / lambda_min of the oracle's multigrid
+    # PCG solution x* (true residual ~5e-13)
+    tol = 1e-10
+    b = gen.manufactured_rhs(n, n, seed=2)
+    xr, ir = oracle.cg_pcg(b, tol=1e-13, maxit=200)
+    assert ir["status"] == oracle.OK
+    x, info = lap5cg.cg_solve(_dev(b), tol=tol, maxit=10 ** 7, precision=precision)
+    rec = lap5cg.decode_info(info)[0]
+    assert rec["status"] == lap5cg.OK, rec
+    assert rec["relres_true"] <= tol
+    x = x.cpu().numpy()
+    lam_min = gen.mode_eigenvalue(n, n, 1, 1)
+    bound = (rec["relres_true"] + ir["relres_true"]) * np.linalg.norm(b) / lam_min
+    assert np.linalg.norm(x - xr) <= bound
+    assert np.max(np.abs(x - xr)) <= bound
+    print("\n[error vs oracle] %s %d^2: %d refinements, %d inner iterations, relres_true %.3g, "
+          "max|x - x*|/max|x*| %.3g (bound %.3g)" % (precision, n, rec["outer_iters"], rec["iters"],
+                                                     rec["relres_true"], np.max(np.abs(x - xr)) / np.max(np.abs(xr)),
+                                                     bound / np.max(np.abs(xr))))

@@ -44,10 +44,13 @@ def test_f32_bit_exact(nx, ny, pitch):
     np.testing.assert_array_equal(y[:, :nx], ref[:, :nx])
 
 
-@pytest.mark.parametrize("nx,ny", [(1, 1), (3, 5), (64, 64), (129, 70), (300, 257)])
-@pytest.mark.parametrize("pitch", ["tight", "aligned"])
+@pytest.mark.parametrize("nx,ny", [(1, 1), (3, 5), (64, 64), (129, 70), (300, 257), (513, 19), (1000, 37),
+                                   (2049, 17)])
+@pytest.mark.parametrize("pitch", ["tight", "aligned", "quad"])
 def test_bf16_bit_exact(nx, ny, pitch):
-    ld = nx if pitch == "tight" else gen.pitch(nx, 2)
+    # aligned: ld a multiple of 8 (sixteen columns a lane, two 16-byte groups);
+    # quad: ld = 4 mod 8 (four columns a lane); tight: scalar accesses
+    ld = {"tight": nx, "aligned": gen.pitch(nx, 2), "quad": gen.pitch(nx, 2) + 4}[pitch]
     xf = gen.uniform_rhs(nx, ny, seed=nx + ny, ld=ld, dtype=np.float32)
     xb = oracle.f32_to_bf16_bits(xf)
     xt = torch.from_numpy(xb.view(np.int16)).to("cuda").view(torch.bfloat16)
@@ -74,7 +77,7 @@ def test_full_size_f64(n):
 
 @pytest.mark.parametrize("dtype", ["f32", "bf16"])
 def test_full_size_8192_narrow_types(dtype):
-    # binary32 runs eight columns a lane (two 16-byte groups), bf16 four
+    # binary32 runs eight columns a lane (two 16-byte groups), bf16 sixteen
     n = 8192
     xf = gen.uniform_rhs(n, n, seed=4, dtype=np.float32)
     if dtype == "f32":

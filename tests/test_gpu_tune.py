@@ -7,12 +7,13 @@ import torch
 import lap5_inputs as gen
 import oracle
 import paper_1803_03797_gb300 as lap5cg
+from tests.helpers import rel_err
 
 pytestmark = pytest.mark.gpu
 
 
 def _rel(a, b):
-    return np.linalg.norm(a - b) / np.linalg.norm(b)
+    return rel_err(a, b)  # norm-wise and element-wise
 
 
 @pytest.mark.parametrize("variant,precision", [("classic", "f64"), ("newcg", "f64"), ("classic", "f32"),
