@@ -19,7 +19,8 @@ __global__ void __launch_bounds__(kProbeThreads) k_fp64_rate(int iters, double s
   double a[kProbeChains];
 #pragma unroll
   for (int k = 0; k < kProbeChains; ++k) a[k] = seed + (double)k + 1e-9 * threadIdx.x;
-  const double m = 1.0 - 1e-12, c = 1e-13;
+  // multiplier and addend in registers (per-thread values), not constant operands
+  const double m = 1.0 - 1e-12 * (double)(1 + (threadIdx.x & 1)), c = 1e-13 * (double)(1 + (threadIdx.x & 2));
 #pragma unroll 4
   for (int i = 0; i < iters; ++i) {
 #pragma unroll
