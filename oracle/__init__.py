@@ -15,7 +15,8 @@ Functions and the passages they follow (arxiv 1803.03797):
   cg_classic        -- Algorithm 1 (stdCG), x0 allowed.
   cg_newcg          -- Algorithm 2 (NewCG), de-garbled after the cited
                        Ghysels-Vanroose pipelined CG with M = I; optional
-                       residual replacement.
+                       residual replacement; optional alpha from dot
+                       products of the current vectors (stable=True).
   cg_ir             -- FP64 iterative refinement around a binary32 (or bf16
                        p/r) inner Algorithm 1 with Dot2 inner dot products.
   inner_cg_f32      -- that inner solve alone (for its own pins).
@@ -101,6 +102,8 @@ def _load(path):
     L.ora_dot2_f32.restype = None
     L.ora_cg_classic.argtypes = [i, i, i, vp, vp, d, i, ctypes.POINTER(_Trace), ctypes.POINTER(Info)]
     L.ora_cg_newcg.argtypes = [i, i, i, vp, vp, d, i, i, ctypes.POINTER(_Trace), ctypes.POINTER(Info)]
+    L.ora_cg_newcg_stable.argtypes = [i, i, i, vp, vp, d, i, i, ctypes.POINTER(_Trace), ctypes.POINTER(Info)]
+    L.ora_cg_newcg_stable.restype = i
     L.ora_cg_ir.argtypes = [i, i, i, vp, vp, d, i, i, d, i, ctypes.POINTER(Info)]
     L.ora_inner_cg_f32.argtypes = [i, i, i, vp, vp, d, i, i, vp, ctypes.POINTER(i)]
     L.ora_inner_cg_f32.restype = i
@@ -226,15 +229,18 @@ def cg_classic(b, x0=None, tol=1e-10, maxit=1000, nx=None, trace=None):
     return x, info.as_dict()
 
 
-def cg_newcg(b, x0=None, tol=1e-10, maxit=1000, nx=None, rr_period=0, trace=None):
-    """Algorithm 2 (de-garbled).  Returns (x, info dict)."""
+def cg_newcg(b, x0=None, tol=1e-10, maxit=1000, nx=None, rr_period=0, trace=None, stable=False):
+    """Algorithm 2 (de-garbled).  stable=True forms alpha from (p, A p)
+    expanded into dot products of the current vectors instead of the scalar
+    recurrence.  Returns (x, info dict)."""
     ny, ld = b.shape
     nx = ld if nx is None else nx
     b = _grid(b, np.float64, nx)
     x = np.zeros_like(b) if x0 is None else _grid(x0, np.float64, nx).copy()
     info = Info()
-    lib().ora_cg_newcg(nx, ny, ld, _ptr(b), _ptr(x), tol, maxit, rr_period,
-                       ctypes.byref(trace._c) if trace is not None else None, ctypes.byref(info))
+    fn = lib().ora_cg_newcg_stable if stable else lib().ora_cg_newcg
+    fn(nx, ny, ld, _ptr(b), _ptr(x), tol, maxit, rr_period,
+       ctypes.byref(trace._c) if trace is not None else None, ctypes.byref(info))
     return x, info.as_dict()
 
 

@@ -296,8 +296,32 @@ int ora_cg_classic(int nx, int ny, int ld, const double* b, double* x, double to
 /* rr_period > 0 enables residual replacement every rr_period updates:   */
 /* r = b - A x, w = A r, q = A p, z = A q are recomputed from x and p.   */
 /* ------------------------------------------------------------------ */
+/* stable = 1 forms alpha from (p, A p) of the new direction p = r + beta p_old
+ * expanded into dot products of the current vectors,
+ *   (p, A p) = delta + 2 beta (r, q_old) + beta^2 (p_old, q_old),
+ * instead of the scalar recurrence alpha = 1/(delta/gamma - beta/alpha_old).
+ * The two are equal in exact arithmetic ((r, q_old) = -gamma/alpha_old and
+ * (p_old, q_old) = gamma_old/alpha_old there); the recurrence assumes that
+ * consecutive residuals are orthogonal, which rounding undoes once the
+ * residual nears its attainable accuracy -- alpha then drifts by percents and
+ * the iteration breaks down.  The extra dots need no extra synchronisation
+ * (the predict-and-recompute idea of Chen & Carson, SIAM J. Sci. Comput. 2020:
+ * form the needed inner products from the vectors at hand). */
+static int cg_newcg_impl(int nx, int ny, int ld, const double* b, double* x, double tol, int maxit,
+                         int rr_period, int stable, ora_trace* tr, ora_info* info);
+
 int ora_cg_newcg(int nx, int ny, int ld, const double* b, double* x, double tol, int maxit,
                  int rr_period, ora_trace* tr, ora_info* info) {
+  return cg_newcg_impl(nx, ny, ld, b, x, tol, maxit, rr_period, 0, tr, info);
+}
+
+int ora_cg_newcg_stable(int nx, int ny, int ld, const double* b, double* x, double tol, int maxit,
+                        int rr_period, ora_trace* tr, ora_info* info) {
+  return cg_newcg_impl(nx, ny, ld, b, x, tol, maxit, rr_period, 1, tr, info);
+}
+
+static int cg_newcg_impl(int nx, int ny, int ld, const double* b, double* x, double tol, int maxit,
+                         int rr_period, int stable, ora_trace* tr, ora_info* info) {
   ora_info inf; memset(&inf, 0, sizeof inf);
   if (!arg_ok(nx, ny, ld, maxit) || !b || !x || rr_period < 0) { inf.status = ORA_ERR_INVALID_ARG; if (info) *info = inf; return inf.status; }
   const size_t n = (size_t)ny * ld;
@@ -353,9 +377,17 @@ int ora_cg_newcg(int nx, int ny, int ld, const double* b, double* x, double tol,
     double delta = ora_dot_f64(nx, ny, ld, w, r);     /* delta = (w, r) */
     ora_lap5_apply_f64(nx, ny, ld, w, nv);            /* n = A w */
     double beta = gamma / gamma_old;                  /* beta = gamma / gamma_old */
-    double denom = delta / gamma - beta / alpha;      /* de-garbled alpha update */
-    if (!(denom > 0.0) || !isfinite(denom)) { status = ORA_ERR_BREAKDOWN; break; }
-    alpha = 1.0 / denom;
+    if (stable) {                                     /* (p, A p) from the current vectors */
+      double eps = ora_dot_f64(nx, ny, ld, r, q);     /* (r, q_old) */
+      double mu = ora_dot_f64(nx, ny, ld, p, q);      /* (p_old, q_old) */
+      double pap = (delta + (2.0 * beta) * eps) + (beta * beta) * mu;
+      if (!(pap > 0.0) || !isfinite(pap)) { status = ORA_ERR_BREAKDOWN; break; }
+      alpha = gamma / pap;
+    } else {
+      double denom = delta / gamma - beta / alpha;    /* de-garbled alpha update */
+      if (!(denom > 0.0) || !isfinite(denom)) { status = ORA_ERR_BREAKDOWN; break; }
+      alpha = 1.0 / denom;
+    }
     xpby64(nx, ny, ld, nv, beta, z);                  /* z = n + beta z */
     xpby64(nx, ny, ld, w, beta, q);                   /* q = w + beta q */
     xpby64(nx, ny, ld, r, beta, p);                   /* p = r + beta p */

@@ -179,6 +179,51 @@ def test_newcg_iterates_equal_classic(n, kmax):
     np.testing.assert_allclose(tn.beta[1:kmax], tc.beta[1:kmax], rtol=1e-8)
 
 
+@pytest.mark.parametrize("n,kmax", [(32, 30), (100, 30)])
+def test_newcg_stable_iterates_equal_classic(n, kmax):
+    # alpha from (p, A p) = delta + 2 beta (r, q_old) + beta^2 (p_old, q_old):
+    # equal to Algorithm 2's (and Algorithm 1's) alpha in exact arithmetic
+    b = gen.uniform_rhs(n, n, seed=n + 7)
+    tc = oracle.Trace(n, n, kmax + 1, kmax)
+    ts = oracle.Trace(n, n, kmax + 1, kmax, newcg=True)
+    oracle.cg_classic(b, tol=0.0, maxit=kmax, trace=tc)
+    oracle.cg_newcg(b, tol=0.0, maxit=kmax, trace=ts, stable=True)
+    for k in range(1, kmax + 1):
+        rel = np.linalg.norm(tc.x[k] - ts.x[k]) / np.linalg.norm(tc.x[k])
+        assert rel <= 1e-10, (k, rel)
+    np.testing.assert_allclose(ts.alpha[:kmax], tc.alpha[:kmax], rtol=1e-9)
+    np.testing.assert_allclose(ts.beta[1:kmax], tc.beta[1:kmax], rtol=1e-8)
+
+
+@pytest.mark.parametrize("nx,ny", [(1, 1), (3, 5), (16, 16), (9, 14)])
+def test_newcg_stable_dense_cholesky(nx, ny):
+    A = kron_laplacian(nx, ny).toarray()
+    b = gen.uniform_rhs(nx, ny, seed=nx * 5 + ny)
+    x_ref = sla.cho_solve(sla.cho_factor(A), flat(b, nx))
+    x, info = oracle.cg_newcg(b, tol=1e-13, maxit=2000, stable=True)
+    assert info["status"] == oracle.OK
+    assert np.linalg.norm(flat(x, nx) - x_ref) <= 1e-11 * np.linalg.norm(x_ref) * gen.condition_number(nx, ny)
+
+
+def test_newcg_stable_survives_the_attainable_accuracy_floor():
+    # Near its attainable accuracy Algorithm 2's scalar recurrence for alpha
+    # drifts (consecutive residuals are no longer orthogonal) and the
+    # iteration breaks down; alpha from the current vectors keeps going down to
+    # classic CG's true-residual floor.
+    n = 128
+    b = gen.manufactured_rhs(n, n, seed=2)
+    _, ia = oracle.cg_newcg(b, tol=1e-15, maxit=2000, rr_period=100)
+    assert ia["status"] == oracle.ERR_BREAKDOWN
+    xs, i_s = oracle.cg_newcg(b, tol=1e-15, maxit=2000, rr_period=100, stable=True)
+    _, ic = oracle.cg_classic(b, tol=1e-15, maxit=2000)
+    assert i_s["status"] == oracle.NOT_CONVERGED and i_s["iters"] == 2000
+    assert i_s["relres_true"] <= 3 * ic["relres_true"] and i_s["relres_true"] <= 1e-11
+    # and to a tolerance that Algorithm 2 also meets, the two agree
+    x2, i2 = oracle.cg_newcg(b, tol=1e-10, maxit=2000, rr_period=100)
+    x3, i3 = oracle.cg_newcg(b, tol=1e-10, maxit=2000, rr_period=100, stable=True)
+    assert i2["status"] == i3["status"] == oracle.OK and abs(i2["iters"] - i3["iters"]) <= 2
+
+
 def test_newcg_auxiliary_identities():
     nx, ny = 40, 24
     A = kron_laplacian(nx, ny)

@@ -28,8 +28,12 @@ MUTATIONS = {
                        "axpy64(nx, ny, ld, w, -alpha, q);                 /* w = w - alpha z */"),
     "newcg_z_drops_beta": ("xpby64(nx, ny, ld, nv, beta, z);                  /* z = n + beta z */",
                            "xpby64(nx, ny, ld, nv, 0.0, z);                  /* z = n + beta z */"),
-    "newcg_alpha_sign": ("double denom = delta / gamma - beta / alpha;      /* de-garbled alpha update */",
-                         "double denom = delta / gamma + beta / alpha;      /* de-garbled alpha update */"),
+    "newcg_alpha_sign": ("double denom = delta / gamma - beta / alpha;    /* de-garbled alpha update */",
+                         "double denom = delta / gamma + beta / alpha;    /* de-garbled alpha update */"),
+    "newcg_stable_cross_term_sign": ("double pap = (delta + (2.0 * beta) * eps) + (beta * beta) * mu;",
+                                     "double pap = (delta - (2.0 * beta) * eps) + (beta * beta) * mu;"),
+    "newcg_stable_mu_dropped": ("double pap = (delta + (2.0 * beta) * eps) + (beta * beta) * mu;",
+                                "double pap = (delta + (2.0 * beta) * eps);"),
 }
 
 # mistakes in the mixed-precision path, caught by the pins of tests/test_oracle_ir.py
@@ -99,6 +103,10 @@ def _pins_pass():
             return False
         if np.linalg.norm(flat(x, nx) - x_ref) > 1e-9 * np.linalg.norm(x_ref):
             return False
+    for stable in (False, True):  # NewCG with its own and with the stabilised alpha
+        x, info = oracle.cg_newcg(b, tol=1e-12, maxit=400, stable=stable)
+        if info["status"] != oracle.OK or np.linalg.norm(flat(x, nx) - x_ref) > 1e-9 * np.linalg.norm(x_ref):
+            return False
     n, K = 24, 12
     bb = gen.uniform_rhs(n, n, seed=5)
     tc = oracle.Trace(n, n, K + 1, K)
@@ -106,6 +114,10 @@ def _pins_pass():
     oracle.cg_classic(bb, tol=0.0, maxit=K, trace=tc)
     oracle.cg_newcg(bb, tol=0.0, maxit=K, trace=tn)
     if not np.all(np.isfinite(tn.x[K])) or np.linalg.norm(tc.x[K] - tn.x[K]) > 1e-10 * np.linalg.norm(tc.x[K]):
+        return False
+    ts = oracle.Trace(n, n, K + 1, K, newcg=True)
+    oracle.cg_newcg(bb, tol=0.0, maxit=K, trace=ts, stable=True)
+    if not np.all(np.isfinite(ts.x[K])) or np.linalg.norm(tc.x[K] - ts.x[K]) > 1e-10 * np.linalg.norm(tc.x[K]):
         return False
     A2 = kron_laplacian(n, n)
     for k in range(K):
