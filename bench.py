@@ -281,11 +281,14 @@ def time_to_solution(lap5cg, torch, dev, n, rhs, tol=1e-10):
     out = {}
     # NewCG to 1e-10 at these condition numbers needs residual replacement
     # (without it Algorithm 2 breaks down in binary64, on the oracle as well)
-    for name, variant, prec, rr in (("f64_classic", "classic", "f64", 0), ("f64_newcg_rr100", "newcg", "f64", 100),
-                                    ("ir_f32", "classic", "ir_f32", 0), ("ir_bf16pr", "classic", "ir_bf16pr", 0),
-                                    ("pcg_mg_f32", "classic", "mg_f32", 0), ("pcg_mg_f64", "classic", "mg_f64", 0),
-                                    ("pipelined_pcg_mg_f64", "newcg", "mg_f64", 0)):
-        opts = lap5cg.default_opts(rr_period=rr)
+    # (the stabilised NewCG forms alpha from dot products of the current vectors)
+    for name, variant, prec, rr, stab in (("f64_classic", "classic", "f64", 0, 0),
+                                          ("f64_newcg_rr100", "newcg", "f64", 100, 0),
+                                          ("f64_newcg_stable_rr100", "newcg", "f64", 100, 1),
+                                          ("ir_f32", "classic", "ir_f32", 0, 0), ("ir_bf16pr", "classic", "ir_bf16pr", 0, 0),
+                                          ("pcg_mg_f32", "classic", "mg_f32", 0, 0), ("pcg_mg_f64", "classic", "mg_f64", 0, 0),
+                                          ("pipelined_pcg_mg_f64", "newcg", "mg_f64", 0, 0)):
+        opts = lap5cg.default_opts(rr_period=rr, stabilized=stab)
         lap5cg.cg_solve(b, tol=tol, maxit=10 ** 6, variant=variant, precision=prec, opts=opts)  # warm-up
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -469,7 +472,7 @@ def targets_summary(extras, roofline):
         key = "time_to_1e-10_%d" % n
         if key not in extras:
             continue
-        for name in ("f64_classic", "ir_f32", "ir_bf16pr", "pcg_mg_f32"):
+        for name in ("f64_classic", "f64_newcg_rr100", "f64_newcg_stable_rr100", "ir_f32", "ir_bf16pr", "pcg_mg_f32"):
             t["tts%d_%s_ms" % (n, name)] = get(key, name, "ms")
             t["tts%d_%s_status" % (n, name)] = get(key, name, "status")
         t["tts%d_speedup_ir_f32_vs_f64" % n] = get(key, "speedup_ir_f32_vs_f64_classic")

@@ -118,7 +118,8 @@ typedef struct {
                                multigrid solves: 16) */
   int32_t min_rows;         /* minimum rows per warp unit; 0 = default (2) */
   int32_t true_residual;    /* 1 (default) recompute ||b - A x|| at exit, 0 skip */
-  int32_t maxit_inner;      /* IR: inner iteration cap per refinement step; 0 = default */
+  int32_t maxit_inner;      /* IR: inner iteration cap per refinement step; 0 = default
+                               (IR_F32: 4 (nx + ny) + 50; IR_BF16PR: nx + ny + 50) */
   int32_t max_outer;        /* IR: refinement step cap; 0 = default (60) */
   double tol_inner;         /* IR: inner relative tolerance; <= 0 = default (1e-4 F32, 1e-2 BF16) */
   double timeout_s;         /* device barrier time limit in seconds; <= 0 = default (2 s) */
@@ -165,6 +166,17 @@ typedef struct {
                                sides allow */
   int32_t mg_coarse_sweeps; /* MG_F32 / MG_F64: damped Jacobi sweeps on the coarsest grid;
                                0 = default (8) */
+  int32_t stabilized;       /* cg_solve, NEWCG, F64 / F32: 1 = alpha = gamma / (p, A p) with
+                               (p, A p) = delta + 2 beta (r, q_old) + beta^2 (p_old, q_old) formed
+                               from dot products of the current vectors, reduced together with
+                               gamma and delta (still one reduction per iteration), instead of
+                               Algorithm 2's recurrence alpha = 1/(delta/gamma - beta/alpha_old).
+                               Equal in exact arithmetic; the recurrence assumes orthogonal
+                               consecutive residuals and breaks down near the attainable accuracy
+                               (e.g. above 1e-10 at 8192 x 8192).  Two more multiply-adds a point.
+                               0 = Algorithm 2 (default).  CLASSIC: LAP5CG_ERR_INVALID_ARG; other
+                               precisions, reproducible mode and batched solves:
+                               LAP5CG_ERR_UNSUPPORTED.  Solves always take the streaming kernels. */
 } lap5cg_opts;
 
 /* Fill *o with the defaults above. */

@@ -52,7 +52,7 @@ class Opts(ctypes.Structure):
                 ("history", ctypes.c_void_p), ("team_ctas", ctypes.c_int32), ("ring_slots", ctypes.c_int32),
                 ("resident", ctypes.c_int32), ("lane_vec", ctypes.c_int32),
                 ("reproducible", ctypes.c_int32), ("mg_nu", ctypes.c_int32), ("mg_levels", ctypes.c_int32),
-                ("mg_coarse_sweeps", ctypes.c_int32)]
+                ("mg_coarse_sweeps", ctypes.c_int32), ("stabilized", ctypes.c_int32)]
 
 
 _lib = None

@@ -161,6 +161,7 @@ void lap5cg_opts_default(lap5cg_opts* o) {
   o->mg_nu = 0;
   o->mg_levels = 0;
   o->mg_coarse_sweeps = 0;
+  o->stabilized = 0;
 }
 
 const char* lap5cg_status_string(int status) {
@@ -216,6 +217,9 @@ int cg_solve(int nx, int ny, int ld, const void* b, void* x, double tol, int max
   if (o.reproducible && precision != LAP5CG_PREC_F64) return LAP5CG_ERR_UNSUPPORTED;
   if (o.reproducible && (long long)nx * (long long)ny >= (1ll << 36)) return LAP5CG_ERR_UNSUPPORTED;  // limb range
   if (o.rr_period > 0 && variant != LAP5CG_NEWCG) return LAP5CG_ERR_INVALID_ARG;
+  if (o.stabilized < 0 || o.stabilized > 1 || (o.stabilized && variant != LAP5CG_NEWCG)) return LAP5CG_ERR_INVALID_ARG;
+  if (o.stabilized && (o.reproducible || (precision != LAP5CG_PREC_F64 && precision != LAP5CG_PREC_F32)))
+    return LAP5CG_ERR_UNSUPPORTED;
   const size_t need = cg_workspace_size(nx, ny, ld, variant, precision, nrhs);
   if (need == 0) return LAP5CG_ERR_UNSUPPORTED;
   if (!workspace || !aligned(workspace, kAlign) || ws_bytes < need) return LAP5CG_ERR_WORKSPACE;
@@ -310,6 +314,7 @@ int cg_solve_batched(int count, const int* nx, const int* ny, const int* ld, con
     return LAP5CG_ERR_INVALID_ARG;
   if (o.rr_period > 0 && variant != LAP5CG_NEWCG) return LAP5CG_ERR_INVALID_ARG;
   if (o.reproducible) return LAP5CG_ERR_UNSUPPORTED;  // exact dot products: single solves only
+  if (o.stabilized) return LAP5CG_ERR_UNSUPPORTED;    // single solves only
   return solve_batched(count, nx, ny, ld, b, x, tol, maxit, variant, precision, workspace, ws_bytes, info, o,
                        static_cast<cudaStream_t>(stream));
 }

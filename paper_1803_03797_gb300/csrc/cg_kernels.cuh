@@ -493,6 +493,12 @@ done:
 // w is double-buffered because its halo is read while it is rewritten.
 // Residual replacement (rr_period > 0) recomputes r = b - A x, w = A r,
 // q = A p, z = A q from x and p every rr_period updates.
+// ST (the stabilised form): the same pass also accumulates (r_new, q) and
+// (p, q) of the p, q it used, and alpha is gamma / (p, A p) with (p, A p) = delta +
+// 2 beta (r, q_old) + beta^2 (p_old, q_old) -- equal to Algorithm 2's
+// 1/(delta/gamma - beta/alpha_old) in exact arithmetic, without its
+// assumption that consecutive residuals are orthogonal (which fails near the
+// attainable accuracy).  Still one reduction (of four values) per iteration.
 // ---------------------------------------------------------------------------
 template <class T>
 struct NewcgArgs {
@@ -501,6 +507,31 @@ struct NewcgArgs {
   Grid<T> x, r, w0, w1, z, q, p;
   int rr_period;
 };
+
+// q = A p with (r, q) and (p, q) (residual replacement of the stabilised form).
+template <int V, class T, class Acc>
+__device__ __forceinline__ void pass_q_from_p(const SolveCommon& c, Walker& wk, const Grid<T>& p, const Grid<T>& q,
+                                              const Grid<T>& r, Acc& ae, Acc& amu) {
+  using M = typename Math<T>::type;
+  struct D { M r[V]; };
+  for (int u = wk.gw; u < c.un.nunits; u += wk.nw) {
+    int s, y0, y1;
+    unit_bounds(c.un, u, c.ny, s, y0, y1);
+    const int xs = s * 32 * V, xl = Lanes<V>::first(xs, wk.lane);
+    const int nval = c.nx - xl;
+    auto field = [&](int j, FRow<V, M>& f) { field_plain<V>(p, c.nx, c.ny, j, xl, xs, wk.lane, f); };
+    auto load = [&](int j, D& d) { load_row<V>(r, j, xl, c.nx, d.r); };
+    auto finish = [&](int j, const D& d, const FRow<V, M>& S, const FRow<V, M>& C, const FRow<V, M>& N) {
+      M qv[V];
+      stencil_row<V>(S, C, N, wk.lane, qv);
+      store_row<V>(q, j, xl, c.nx, qv);
+      acc_dot<V>(ae, j, d.r, qv, nval);
+      acc_dot<V>(amu, j, C.f, qv, nval);
+    };
+    march<V, M, D>(y0, y1, wk.rev(), field, load, finish);
+  }
+  ++wk.pc;
+}
 
 // y = A g for a stored g (whole grid), with optional (y, other) / (g, g) sums.
 template <int V, class T>
@@ -548,8 +579,9 @@ __device__ __forceinline__ void pass_w_from_r(const SolveCommon& c, Walker& wk, 
   ++wk.pc;
 }
 
-template <class T, int V, bool R, bool EX = false, class Team>
+template <class T, int V, bool R, bool EX = false, bool ST = false, class Team>
 __device__ void newcg_solve(const NewcgArgs<T>& a, Team& tm, double* red, unsigned char* dsm) {
+  static_assert(!(EX && ST), "the stabilised alpha takes plain dot products");
   using M = typename Math<T>::type;
   // EX: reproducible (exact) dot products
   using Acc = typename std::conditional<EX, AccExact, typename AccOf<M>::type>::type;
@@ -561,6 +593,7 @@ __device__ void newcg_solve(const NewcgArgs<T>& a, Team& tm, double* red, unsign
 
   int status = LAP5CG_NOT_CONVERGED, iters = 0;
   double bb = 0.0, gamma = 0.0, delta = 0.0, alpha = 0.0, beta = 0.0, relres_true = nan("");
+  double eps = 0.0, mu = 0.0;  // stabilised form: (r, q_old), (p_old, q_old)
   bool aborted = false;
   int cur = 0;  // current w lives in w[cur]
 
@@ -601,6 +634,7 @@ __device__ void newcg_solve(const NewcgArgs<T>& a, Team& tm, double* red, unsign
       const Grid<T> wn = cur ? a.w0 : a.w1;
       const M am = (M)alpha, bm = (M)beta;
       Acc ag = make_acc<Acc>(tm, 0, c.ny, wk.rev()), ad = make_acc<Acc>(tm, 1, c.ny, wk.rev());
+      Acc ae{}, amu{};  // (r_new, q), (p, q): the stabilised form only
       struct D { M z[V], q[V], p[V], x[V], r[V]; };
       if constexpr (R) {
         ring.fence_global_to_async();
@@ -654,6 +688,10 @@ __device__ void newcg_solve(const NewcgArgs<T>& a, Team& tm, double* red, unsign
             }
             acc_dot<V>(ag, j, rv, rv, nval);
             acc_dot<V>(ad, j, wv, rv, nval);
+            if constexpr (ST) {
+              acc_dot<V>(ae, j, rv, qv, nval);
+              acc_dot<V>(amu, j, pv, qv, nval);
+            }
             store_row<V>(a.z, j, xl, c.nx, zv);
             store_row<V>(a.q, j, xl, c.nx, qv);
             store_row<V>(a.p, j, xl, c.nx, pv);
@@ -699,6 +737,10 @@ __device__ void newcg_solve(const NewcgArgs<T>& a, Team& tm, double* red, unsign
           }
           acc_dot<V>(ag, j, rv, rv, nval);
           acc_dot<V>(ad, j, wv, rv, nval);
+          if constexpr (ST) {
+            acc_dot<V>(ae, j, rv, qv, nval);
+            acc_dot<V>(amu, j, pv, qv, nval);
+          }
           store_row<V>(a.z, j, xl, c.nx, zv);
           store_row<V>(a.q, j, xl, c.nx, qv);
           store_row<V>(a.p, j, xl, c.nx, pv);
@@ -722,18 +764,38 @@ __device__ void newcg_solve(const NewcgArgs<T>& a, Team& tm, double* red, unsign
         const Grid<T> wr = cur ? a.w1 : a.w0;
         Acc ag2 = make_acc<Acc>(tm, 0, c.ny, wk.rev()), ad2 = make_acc<Acc>(tm, 1, c.ny, wk.rev());
         pass_w_from_r<V>(c, wk, a.r, wr, ag2, ad2);
-        pass_apply<V>(c, wk, a.p, a.q);
-        double o[2];
-        if (!acc_reduce<2>(tm, {&ag2, &ad2}, o, red)) { aborted = true; goto done; }
+        if constexpr (ST) {  // q = A p with (r, q), (p, q) of the replaced vectors
+          Acc ae2{}, amu2{};
+          pass_q_from_p<V>(c, wk, a.p, a.q, a.r, ae2, amu2);
+          double o[4];
+          if (!acc_reduce<4>(tm, {&ag2, &ad2, &ae2, &amu2}, o, red)) { aborted = true; goto done; }
+          gnew = o[0];
+          dnew = o[1];
+          eps = o[2];
+          mu = o[3];
+        } else {
+          pass_apply<V>(c, wk, a.p, a.q);
+          double o[2];
+          if (!acc_reduce<2>(tm, {&ag2, &ad2}, o, red)) { aborted = true; goto done; }
+          gnew = o[0];
+          dnew = o[1];
+        }
         pass_apply<V>(c, wk, a.q, a.z);
         if (!tm.sync(red)) { aborted = true; goto done; }
-        gnew = o[0];
-        dnew = o[1];
       } else {
-        double o[2];
-        if (!acc_reduce<2>(tm, {&ag, &ad}, o, red)) { aborted = true; goto done; }
-        gnew = o[0];
-        dnew = o[1];
+        if constexpr (ST) {
+          double o[4];
+          if (!acc_reduce<4>(tm, {&ag, &ad, &ae, &amu}, o, red)) { aborted = true; goto done; }
+          gnew = o[0];
+          dnew = o[1];
+          eps = o[2];
+          mu = o[3];
+        } else {
+          double o[2];
+          if (!acc_reduce<2>(tm, {&ag, &ad}, o, red)) { aborted = true; goto done; }
+          gnew = o[0];
+          dnew = o[1];
+        }
       }
       if (c.history && tm.rank() == 0 && threadIdx.x == 0) c.history[iters] = sqrt(gnew / bb);
       const double gold = gamma;
@@ -743,9 +805,16 @@ __device__ void newcg_solve(const NewcgArgs<T>& a, Team& tm, double* red, unsign
       if (gamma <= thr) { status = LAP5CG_OK; goto truecheck; }
       if (iters >= c.maxit) break;
       beta = gamma / gold;
-      const double denom = delta / gamma - beta / alpha;  // de-garbled alpha update
-      if (!(denom > 0.0) || !isfinite(denom)) { status = LAP5CG_ERR_BREAKDOWN; goto truecheck; }
-      alpha = 1.0 / denom;
+      if constexpr (ST) {  // (p, A p) of p = r + beta p_old from the current vectors, in a fixed order
+        const double pap = __dadd_rn(__dadd_rn(delta, __dmul_rn(__dmul_rn(2.0, beta), eps)),
+                                     __dmul_rn(__dmul_rn(beta, beta), mu));
+        if (!(pap > 0.0) || !isfinite(pap)) { status = LAP5CG_ERR_BREAKDOWN; goto truecheck; }
+        alpha = gamma / pap;
+      } else {
+        const double denom = delta / gamma - beta / alpha;  // de-garbled alpha update
+        if (!(denom > 0.0) || !isfinite(denom)) { status = LAP5CG_ERR_BREAKDOWN; goto truecheck; }
+        alpha = 1.0 / denom;
+      }
     }
   }
 truecheck:

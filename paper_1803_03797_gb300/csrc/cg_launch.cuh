@@ -35,13 +35,14 @@ __global__ void __launch_bounds__(512) k_classic(const ClassicArgs<T> a) {
   classic_solve<T, V, R, EX>(a, tm, red, dsm);
 }
 
-template <class T, int V, bool R, bool EX = false>
+// ST: the stabilised alpha (plain dot products only)
+template <class T, int V, bool R, bool EX = false, bool ST = false>
 __global__ void __launch_bounds__(512) k_newcg(const NewcgArgs<T> a) {
   __shared__ double red[kRedDoubles];
   extern __shared__ __align__(128) unsigned char dsm[];
   GridTeam tm{a.c.ctl, a.c.timeout_ns, 0ull};
   ExactSmem<EX>().attach(tm);
-  newcg_solve<T, V, R, EX>(a, tm, red, dsm);
+  newcg_solve<T, V, R, EX, ST>(a, tm, red, dsm);
 }
 
 // Ring geometry for a kernel pair: tries the ring kernel first; falls back to
@@ -166,18 +167,22 @@ int solve_typed(const SolvePlan& p, cudaStream_t st) {
     RingGeom rg;
     size_t dyn = 0;
     bool ring = false;
-    int rc = pick_ring(reinterpret_cast<const void*>(&k_newcg<T, V, true, EX>), ring_slot_newcg(V, (int)sizeof(T)),
-                       p.opts, &rg, &dyn, &ring);
+    // the stabilised form (host-checked: never with exact dot products)
+    const bool stab = p.opts.stabilized != 0 && !EX;
+    const void* fn_ring = stab ? reinterpret_cast<const void*>(&k_newcg<T, V, true, EX, !EX>)
+                               : reinterpret_cast<const void*>(&k_newcg<T, V, true, EX>);
+    const void* fn_march = stab ? reinterpret_cast<const void*>(&k_newcg<T, V, false, EX, !EX>)
+                                : reinterpret_cast<const void*>(&k_newcg<T, V, false, EX>);
+    int rc = pick_ring(fn_ring, ring_slot_newcg(V, (int)sizeof(T)), p.opts, &rg, &dyn, &ring);
     if (rc != LAP5CG_OK) return rc;
-    const void* fn = ring ? reinterpret_cast<const void*>(&k_newcg<T, V, true, EX>)
-                          : reinterpret_cast<const void*>(&k_newcg<T, V, false, EX>);
+    const void* fn = ring ? fn_ring : fn_march;
     rc = plan_units(fn, p.nx, p.ny, V, p.opts, dyn, &cfg, row_align);
     if (rc != LAP5CG_OK) return rc;
     if (ring && p.opts.ring_slots == 0 && cfg.seg_rows < kRingMinRows) {  // short units: register march
       ring = false;
       rg.S = 0;
       dyn = 0;
-      fn = reinterpret_cast<const void*>(&k_newcg<T, V, false, EX>);
+      fn = fn_march;
       rc = plan_units(fn, p.nx, p.ny, V, p.opts, dyn, &cfg, row_align);
       if (rc != LAP5CG_OK) return rc;
     }

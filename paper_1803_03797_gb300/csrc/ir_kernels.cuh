@@ -45,7 +45,7 @@ __device__ void ir_solve(const IrArgs<TR>& a, Team& tm, double* red, unsigned ch
   constexpr int ES = (int)sizeof(TR);
   // bf16 p, r: Polak-Ribiere beta (r_new, r_new - r_old) / (r_old, r_old), equal
   // to Algorithm 1's beta in exact arithmetic; it discounts the part of r_new
-  // that the bf16 rounding left along r_old (the same rule as the oracle's)
+  // that the bf16 rounding left along r_old
   constexpr bool kPR = (ES == 2);
   // A p stored (zs) only with four columns a lane: the stored form's register
   // march would not fit the register budget with eight

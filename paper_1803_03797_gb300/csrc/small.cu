@@ -551,7 +551,9 @@ template <class T>
 static int try_small_t(const SolvePlan& p, cudaStream_t st, bool* used) {
   *used = false;
   // an explicit march choice or residual replacement asks for the streaming kernels
-  if (p.opts.resident < 0 || p.opts.ring_slots != 0 || p.opts.rr_period > 0 || p.opts.reproducible) return LAP5CG_OK;
+  if (p.opts.resident < 0 || p.opts.ring_slots != 0 || p.opts.rr_period > 0 || p.opts.reproducible ||
+      p.opts.stabilized)
+    return LAP5CG_OK;
   DevProps dp;
   int rc = dev_props(&dp);
   if (rc != LAP5CG_OK) return rc;

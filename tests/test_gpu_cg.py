@@ -352,9 +352,10 @@ def _reference_4096():
 
 
 @pytest.mark.parametrize("name,variant,precision,rr", [
-    ("f64_classic", "classic", "f64", 0), ("f64_newcg_rr100", "newcg", "f64", 100), ("ir_f32", "classic", "ir_f32", 0),
-    ("pcg_mg_f32", "classic", "mg_f32", 0), ("pcg_mg_f64", "classic", "mg_f64", 0),
-    ("pipelined_pcg_mg_f64", "newcg", "mg_f64", 0)])
+    ("f64_classic", "classic", "f64", 0), ("f64_newcg_rr100", "newcg", "f64", 100),
+    ("f64_newcg_stable_rr100", "newcg", "f64", -100), ("ir_f32", "classic", "ir_f32", 0),
+    ("ir_bf16pr", "classic", "ir_bf16pr", 0), ("pcg_mg_f32", "classic", "mg_f32", 0),
+    ("pcg_mg_f64", "classic", "mg_f64", 0), ("pipelined_pcg_mg_f64", "newcg", "mg_f64", 0)])
 def test_full_size_4096_converged_error_vs_oracle(name, variant, precision, rr):
     # Every solver of the time-to-1e-10 comparison at the benchmark size
     # (kappa = 6.8e6), element-wise against an oracle solution 200x tighter.
@@ -362,8 +363,8 @@ def test_full_size_4096_converged_error_vs_oracle(name, variant, precision, rr):
     # the true residual the solve reports (plus the reference's own).
     b, xr, ir = _reference_4096()
     n, tol = 4096, 1e-10
-    x, info = _solve(b, tol=tol, maxit=10 ** 6, variant=variant, precision=precision,
-                     opts=lap5cg.default_opts(rr_period=rr))
+    x, info = _solve(b, tol=tol, maxit=10 ** 7, variant=variant, precision=precision,
+                     opts=lap5cg.default_opts(rr_period=abs(rr), stabilized=int(rr < 0)))
     rec = info[0]
     assert rec["status"] == lap5cg.OK, rec
     assert rec["relres_true"] <= 1.5 * tol, rec
@@ -431,3 +432,66 @@ def test_extreme_aspect_ratios(variant, nx, ny):
     xo, io = oracle.cg_solve(b, variant=variant, tol=0.0, maxit=20, nx=nx)
     assert info[0]["iters"] == io["iters"]
     assert _rel(x[:, :nx], xo[:, :nx]) <= 1e-10
+
+
+# ---------------------------------------------------------------------------
+# NewCG with the stabilised alpha (alpha = gamma / (p, A p), (p, A p) from dot
+# products of the current vectors) against the oracle's stabilised NewCG
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+@pytest.mark.parametrize("nx,ny,k", [(100, 100, 40), (257, 130, 25), (65, 64, 30), (3, 5, 4)])
+def test_newcg_stable_trajectory(precision, nx, ny, k):
+    dt = np.float64 if precision == "f64" else np.float32
+    b = gen.uniform_rhs(nx, ny, seed=k + 3 * nx, ld=gen.pitch(nx, 8)).astype(dt)
+    x, info = _solve(b, tol=0.0, maxit=k, variant="newcg", precision=precision, nx=nx,
+                     opts=lap5cg.default_opts(stabilized=1))
+    xo, io = oracle.cg_newcg(b.astype(np.float64), tol=0.0, maxit=k, nx=nx, stable=True)
+    assert info[0]["iters"] == min(k, io["iters"])
+    bound = 1e-10 if precision == "f64" else 1e-3  # binary32: rounding drift of the pipelined recurrences
+    assert _rel(x[:, :nx].astype(np.float64), xo[:, :nx]) <= bound
+
+
+@pytest.mark.parametrize("rr", [0, 25])
+@pytest.mark.parametrize("nx,ny", [(100, 100), (255, 257), (33, 70)])
+def test_newcg_stable_converged(nx, ny, rr):
+    b = gen.uniform_rhs(nx, ny, seed=nx + 11 * ny, ld=gen.pitch(nx, 8))
+    tol = 1e-10
+    x, info = _solve(b, tol=tol, maxit=20000, variant="newcg", nx=nx,
+                     opts=lap5cg.default_opts(stabilized=1, rr_period=rr))
+    xo, io = oracle.cg_newcg(b, tol=tol, maxit=20000, nx=nx, rr_period=rr, stable=True)
+    rec = info[0]
+    assert rec["status"] == lap5cg.OK and io["status"] == oracle.OK, (rec, io)
+    assert abs(rec["iters"] - io["iters"]) <= 2
+    kappa = gen.condition_number(nx, ny)
+    assert _rel(x[:, :nx], xo[:, :nx]) <= kappa * max(tol, io["relres_true"])
+    assert rec["relres_true"] <= 3 * max(io["relres_true"], tol)
+
+
+def test_newcg_stable_survives_where_algorithm2_breaks_down():
+    # 128^2 to 1e-15 with replacement every 100: Algorithm 2's recurrence for
+    # alpha breaks down near the attainable accuracy, the stabilised form does
+    # not (the oracle shows the same, tests/test_oracle_cg.py)
+    n = 128
+    b = gen.manufactured_rhs(n, n, seed=2)
+    _, info = _solve(b, tol=1e-15, maxit=2000, variant="newcg", opts=lap5cg.default_opts(rr_period=100, resident=-1))
+    assert info[0]["status"] == lap5cg.ERR_BREAKDOWN
+    x, info = _solve(b, tol=1e-15, maxit=2000, variant="newcg",
+                     opts=lap5cg.default_opts(rr_period=100, stabilized=1))
+    assert info[0]["status"] == lap5cg.NOT_CONVERGED and info[0]["iters"] == 2000
+    assert info[0]["relres_true"] <= 1e-11
+
+
+def test_newcg_stable_rejected_forms():
+    b = gen.uniform_rhs(64, 64, seed=5)
+    with pytest.raises(lap5cg.Lap5cgError) as e:
+        _solve(b, tol=1e-10, maxit=10, variant="classic", opts=lap5cg.default_opts(stabilized=1))
+    assert e.value.code == lap5cg.ERR_INVALID_ARG
+    for kw in (dict(precision="ir_f32"), dict(precision="mg_f64"), dict(opts_extra=dict(reproducible=1))):
+        extra = kw.pop("opts_extra", {})
+        with pytest.raises(lap5cg.Lap5cgError) as e:
+            _solve(b, tol=1e-10, maxit=10, variant="newcg", opts=lap5cg.default_opts(stabilized=1, **extra), **kw)
+        assert e.value.code == lap5cg.ERR_UNSUPPORTED
+    with pytest.raises(lap5cg.Lap5cgError) as e:
+        lap5cg.cg_solve_batched([_dev(b)], tol=1e-10, variant="newcg", precision="f64",
+                                opts=lap5cg.default_opts(stabilized=1))
+    assert e.value.code == lap5cg.ERR_UNSUPPORTED
