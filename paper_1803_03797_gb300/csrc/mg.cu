@@ -63,54 +63,14 @@ __device__ __forceinline__ double mg_fma(double a, double b, double c) { return 
 
 // Damped Jacobi sweep (JAC) out = in + c (b - A in), or residual out = b - A in;
 // with DOT also accumulates (r, out) against the binary64 grid r (level 0).
-// Levels whose warp units are at least kRingMinRows tall stream `in` (with
-// its halo chunks) and b through the warp's shared-memory ring of bulk
-// asynchronous copies, as the CG passes do; the others march rows through
-// registers.
 template <class TM, bool JAC, bool DOT>
 __device__ void mg_stencil_pass(const Sched& s, const MgLevel<TM>& L, const TM* in, TM* out,
-                                const Grid<const double>& r, Acc64& acc, WarpRing* ring) {
+                                const Grid<const double>& r, Acc64& acc) {
   constexpr int V = MgVec<TM>::V;
   const Units un = make_units(L.nx, L.ny, V, s.nw, 2);
   const Grid<const TM> gi{in, L.ld}, gb{L.b, L.ld};
   const Grid<TM> go{out, L.ld};
   const TM c = (TM)kMgC;
-  if (ring && ring->S > 0 && un.seg_rows >= kRingMinRows) {
-    const RingVec vv[2] = {{reinterpret_cast<const unsigned char*>(in), L.ld, (int)sizeof(TM), RV_HALO | RV_ALWAYS},
-                           {reinterpret_cast<const unsigned char*>(L.b), L.ld, (int)sizeof(TM), 0}};
-    int off[2];
-    ring_layout<V>(vv, off);
-    ring->fence_global_to_async();
-    for (int u = s.w; u < un.nunits; u += s.nw) {
-      int st, y0, y1;
-      unit_bounds(un, u, L.ny, st, y0, y1);
-      const int xs = st * 32 * V, xl = Lanes<V>::first(xs, s.lane);
-      const int nval = L.nx - xl;
-      auto field = [&](int, const unsigned char* sl, FRow<V, TM>& f) {
-        ring_lane<V, TM>(sl, off[0], true, s.lane, xl, L.nx, f.f);
-        f.hl = ring_halo<V, TM, TM>(sl, off[0], s.lane, xs, L.nx);
-        f.hr = f.hl;
-      };
-      auto finish = [&](int j, const unsigned char* sl, const FRow<V, TM>& S, const FRow<V, TM>& C,
-                        const FRow<V, TM>& N) {
-        TM ax[V], o[V], bv[V];
-        stencil_row<V>(S, C, N, s.lane, ax);
-        ring_lane<V, TM>(sl, off[1], false, s.lane, xl, L.nx, bv);
-#pragma unroll
-        for (int k = 0; k < V; ++k) o[k] = JAC ? mg_fma(c, bv[k] - ax[k], C.f[k]) : bv[k] - ax[k];
-        store_row<V>(go, j, xl, L.nx, o);
-        if constexpr (DOT) {
-          double rv[V], zv[V];
-          load_row<V>(r, j, xl, L.nx, rv);
-#pragma unroll
-          for (int k = 0; k < V; ++k) zv[k] = (double)o[k];
-          acc_dot<V>(acc, j, rv, zv, nval);
-        }
-      };
-      march_ring<V, TM>(*ring, L.ny, xs, y0, y1, s.rev, vv, off, field, finish);
-    }
-    return;
-  }
   struct D { TM b[V]; };
   for (int u = s.w; u < un.nunits; u += s.nw) {
     int st, y0, y1;
@@ -277,7 +237,6 @@ struct Vcycle {
   Sched grid, cta;
   Grid<const double> r;        // for the fused (r, z) of level 0's last sweep
   Acc64* dot;
-  WarpRing* ring;              // this warp's row ring (S = 0: register march only)
   int cur[kMgMaxLevels];  // 0: the level's iterate is in u, 1: in v
   bool exec;              // this CTA runs the passes it meets (small levels: CTA 0 only)
   bool dot_done;          // (r, z) was accumulated (and the last barrier left to the caller)
@@ -311,13 +270,13 @@ struct Vcycle {
     const Sched s = sched(l);
     Acc64 dummy;
     if (l == 0 && last && dot) {
-      mg_stencil_pass<TM, true, true>(s, lv[l], it(l), other(l), r, *dot, ring);
+      mg_stencil_pass<TM, true, true>(s, lv[l], it(l), other(l), r, *dot);
       dot_done = true;
       cur[l] ^= 1;
       if (small(l)) __syncthreads();
       return true;
     }
-    mg_stencil_pass<TM, true, false>(s, lv[l], it(l), other(l), r, dummy, ring);
+    mg_stencil_pass<TM, true, false>(s, lv[l], it(l), other(l), r, dummy);
     cur[l] ^= 1;
     return sync(l);
   }
@@ -331,7 +290,7 @@ struct Vcycle {
     if (!sweeps(l, nu, false)) return false;
     if (exec) {
       Acc64 dummy;
-      mg_stencil_pass<TM, false, false>(sched(l), lv[l], it(l), other(l), r, dummy, ring);
+      mg_stencil_pass<TM, false, false>(sched(l), lv[l], it(l), other(l), r, dummy);
       if (!sync(l)) return false;
       mg_restrict(sched(l), lv[l], other(l), lv[l + 1]);
       if (!sync(l)) return false;
@@ -378,8 +337,7 @@ struct Vcycle {
 };
 
 template <class TM>
-__device__ __forceinline__ void pcg_solve(const PcgArgs<TM>& a, const MgLevel<TM>* lv, GridTeam& tm, double* red,
-                                          unsigned char* dsm) {
+__device__ __forceinline__ void pcg_solve(const PcgArgs<TM>& a, const MgLevel<TM>* lv, GridTeam& tm, double* red) {
   constexpr int V = 2;  // binary64 passes: two columns a lane
   const SolveCommon& c = a.c;
   const int lane = threadIdx.x & 31;
@@ -393,10 +351,8 @@ __device__ __forceinline__ void pcg_solve(const PcgArgs<TM>& a, const MgLevel<TM
   double bb = 0.0, rr = 0.0, gamma = 0.0, relres_true = nan("");
   bool aborted = false;
   Acc64 arz;
-  WarpRing ring;
-  ring_setup(ring, c, dsm);
   Vcycle<TM> vc{a.nlev, a.lsmall, a.nu, a.nu_c, lv, tm, red, grid, cta,
-                Grid<const double>{a.r.ptr, a.r.ld}, &arz, &ring, {}, true, false, 0u};
+                Grid<const double>{a.r.ptr, a.r.ld}, &arz, {}, true, false, 0u};
   Walker wk;
   wk.init(tm.rank(), tm.size());
   int cur = 0;  // p lives in p[cur]
@@ -586,7 +542,6 @@ truecheck:
     relres_true = sqrt(o[0] / bb);
   }
 done:
-  if (ring.S > 0) ring.teardown();
   write_info(c, tm.rank(), status, aborted, iters, 0, rr, bb, relres_true);
 }
 
@@ -599,8 +554,7 @@ done:
 // and level 0's right-hand side (w) and first sweep for the next V-cycle --
 // written into the buffer the pass does not read.
 template <class TM>
-__device__ __forceinline__ void ppcg_solve(const PcgArgs<TM>& a, const MgLevel<TM>* lv, GridTeam& tm, double* red,
-                                           unsigned char* dsm) {
+__device__ __forceinline__ void ppcg_solve(const PcgArgs<TM>& a, const MgLevel<TM>* lv, GridTeam& tm, double* red) {
   constexpr int V = 2;
   const SolveCommon& c = a.c;
   const int lane = threadIdx.x & 31;
@@ -613,10 +567,8 @@ __device__ __forceinline__ void ppcg_solve(const PcgArgs<TM>& a, const MgLevel<T
   int status = LAP5CG_NOT_CONVERGED, iters = 0;
   double bb = 0.0, rr = 0.0, gamma = 0.0, delta = 0.0, alpha = 0.0, relres_true = nan("");
   bool aborted = false;
-  WarpRing ring;
-  ring_setup(ring, c, dsm);
   Vcycle<TM> vc{a.nlev, a.lsmall, a.nu, a.nu_c, lv, tm, red, grid, cta,
-                Grid<const double>{a.r.ptr, a.r.ld}, nullptr, &ring, {}, true, false, 0u};
+                Grid<const double>{a.r.ptr, a.r.ld}, nullptr, {}, true, false, 0u};
   Walker wk;
   wk.init(tm.rank(), tm.size());
   const Grid<double> pp = a.p0;
@@ -820,7 +772,6 @@ truecheck:
     relres_true = sqrt(o[0] / bb);
   }
 done:
-  if (ring.S > 0) ring.teardown();
   write_info(c, tm.rank(), status, aborted, iters, 0, rr, bb, relres_true);
 }
 
@@ -828,22 +779,20 @@ template <class TM>
 __global__ void __launch_bounds__(512) k_pcg(const PcgArgs<TM> a) {
   __shared__ double red[kRedDoubles];
   __shared__ MgLevel<TM> lv[kMgMaxLevels];
-  extern __shared__ __align__(128) unsigned char dsm[];
   if (threadIdx.x < kMgMaxLevels) lv[threadIdx.x] = a.lv[threadIdx.x];
   __syncthreads();
   GridTeam tm{a.c.ctl, a.c.timeout_ns, 0ull};
-  pcg_solve<TM>(a, lv, tm, red, dsm);
+  pcg_solve<TM>(a, lv, tm, red);
 }
 
 template <class TM>
 __global__ void __launch_bounds__(512) k_ppcg(const PcgArgs<TM> a) {
   __shared__ double red[kRedDoubles];
   __shared__ MgLevel<TM> lv[kMgMaxLevels];
-  extern __shared__ __align__(128) unsigned char dsm[];
   if (threadIdx.x < kMgMaxLevels) lv[threadIdx.x] = a.lv[threadIdx.x];
   __syncthreads();
   GridTeam tm{a.c.ctl, a.c.timeout_ns, 0ull};
-  ppcg_solve<TM>(a, lv, tm, red, dsm);
+  ppcg_solve<TM>(a, lv, tm, red);
 }
 
 // Level geometry: sides shrink to (n-1)/2 until one would be 0 (or max levels).
@@ -909,14 +858,9 @@ static int solve_mg_t(const SolvePlan& p, cudaStream_t st) {
                                              : reinterpret_cast<const void*>(&k_pcg<TM>);
   lap5cg_opts o = p.opts;
   if (o.warps_per_cta <= 0) o.warps_per_cta = 16;  // a wide CTA 0 for the small levels
-  // the level passes' row ring: the stencil operand with its halo chunks and b, one 16-byte vector a lane
+  int rc = plan_units(fn, p.nx, p.ny, 2, o, 0, &cfg);
+  if (rc != LAP5CG_OK) return rc;
   RingGeom rg{0, 0, 0};
-  size_t dyn = 0;
-  const int slot = ring_seg_bytes(MgVec<TM>::V, (int)sizeof(TM), true) + ring_seg_bytes(MgVec<TM>::V, (int)sizeof(TM), false);
-  int rc = choose_ring(fn, slot, o, warps_of(o), &rg, &dyn, true);
-  if (rc != LAP5CG_OK) return rc;
-  rc = plan_units(fn, p.nx, p.ny, 2, o, dyn, &cfg);
-  if (rc != LAP5CG_OK) return rc;
   a.c = make_common(p, cfg, rg);
   a.b = Grid<const double>{static_cast<const double*>(p.b), p.ld};
   a.x = Grid<double>{static_cast<double*>(p.x), p.ld};
