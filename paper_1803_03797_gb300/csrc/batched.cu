@@ -273,6 +273,14 @@ int solve_batched(int count, const int* nx, const int* ny, const int* ld, const 
     if (b0 < x0 + bytes && x0 < b0 + bytes) return LAP5CG_ERR_INVALID_ARG;
     order[k] = k;
   }
+  // instances that fit in one cluster's shared memory (F64 / F32): the
+  // cluster-resident kernel, one cluster an instance, launched first
+  std::vector<char> taken;
+  int rc = small_batched(count, nx, ny, ld, b, x, tol, maxit, variant, precision, info, o, st, taken);
+  if (rc != LAP5CG_OK) return rc;
+  order.erase(std::remove_if(order.begin(), order.end(), [&](int k) { return taken[k] != 0; }), order.end());
+  const int nbig = (int)order.size();
+  if (nbig == 0) return LAP5CG_OK;
   // largest estimated work first (LPT)
   std::stable_sort(order.begin(), order.end(), [&](int i, int j) {
     const double wi = (double)nx[i] * ny[i] * (nx[i] + ny[i]), wj = (double)nx[j] * ny[j] * (nx[j] + ny[j]);
@@ -284,7 +292,8 @@ int solve_batched(int count, const int* nx, const int* ny, const int* ld, const 
   int* errs = reinterpret_cast<int*>(ws + kAlign + align_up((size_t)count * sizeof(BatchEntry), kAlign));
   const size_t inst0 = kAlign + table_bytes(count);
   size_t off = inst0;
-  for (int k = 0; k < count; ++k) {
+  tab.resize(nbig);
+  for (int k = 0; k < nbig; ++k) {
     const int i = order[k];
     tab[k].b = b[i];
     tab[k].x = x[i];
@@ -295,23 +304,23 @@ int solve_batched(int count, const int* nx, const int* ny, const int* ld, const 
     tab[k].idx = i;
     off += instance_bytes(kind, nx[i], ny[i], ld[i]);
   }
-  for (int first = 0; first < count; first += kFillChunk) {
+  for (int first = 0; first < nbig; first += kFillChunk) {
     FillArgs fa;
     fa.dst = dtab;
     fa.first = first;
-    fa.n = std::min(kFillChunk, count - first);
+    fa.n = std::min(kFillChunk, nbig - first);
     for (int k = 0; k < fa.n; ++k) fa.e[k] = tab[first + k];
     k_fill_table<<<1, kFillChunk, 0, st>>>(fa);
     if (cudaGetLastError() != cudaSuccess) return LAP5CG_ERR_CUDA;
   }
   if (cudaMemsetAsync(bctl, 0, sizeof(BatchCtl), st) != cudaSuccess) return LAP5CG_ERR_CUDA;
-  if (cudaMemsetAsync(errs, 0, (size_t)count * sizeof(int), st) != cudaSuccess) return LAP5CG_ERR_CUDA;
+  if (cudaMemsetAsync(errs, 0, (size_t)count * sizeof(int), st) != cudaSuccess) return LAP5CG_ERR_CUDA;  // caller order
 
   int wpc = o.warps_per_cta > 0 ? o.warps_per_cta : 8;  // batched teams measured best with 8
   if (wpc > 16) wpc = 16;
   BatchArgs a;
   a.errs = errs;
-  a.count = count;
+  a.count = nbig;
   a.tab = dtab;
   a.bctl = bctl;
   a.ws = ws;
@@ -330,7 +339,7 @@ int solve_batched(int count, const int* nx, const int* ny, const int* ld, const 
   if (team != 1 && team != 2 && team != 4 && team != 8 && team != 16) return LAP5CG_ERR_INVALID_ARG;
   size_t dyn = 0;
   const bool auto_on = true;  // as for single solves
-  int rc = choose_ring(kernel_of(kind, true), ring_slot_kind(kind), o, wpc, &a.rg, &dyn, auto_on);
+  rc = choose_ring(kernel_of(kind, true), ring_slot_kind(kind), o, wpc, &a.rg, &dyn, auto_on);
   if (rc != LAP5CG_OK) return rc;
   if (a.rg.S > 0 && dyn < (size_t)wpc * (size_t)a.rg.warp_bytes) return LAP5CG_ERR_INVALID_ARG;
   const void* fn = kernel_of(kind, a.rg.S > 0);
@@ -353,7 +362,7 @@ int solve_batched(int count, const int* nx, const int* ny, const int* ld, const 
     return LAP5CG_ERR_UNSUPPORTED;
   int nclusters = o.ctas > 0 ? std::max(1, o.ctas / team) : maxclusters;
   if (nclusters > maxclusters) nclusters = maxclusters;
-  if (nclusters > count) nclusters = count;
+  if (nclusters > nbig) nclusters = nbig;
   lc.gridDim = dim3(nclusters * team);
   void* args[] = {&a};
   return cudaLaunchKernelExC(&lc, fn, args) == cudaSuccess ? LAP5CG_OK : LAP5CG_ERR_CUDA;

@@ -6,6 +6,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/lap5cg.h"
 #include "ring.cuh"
 
@@ -51,6 +53,13 @@ int solve_batched(int count, const int* nx, const int* ny, const int* ld, const 
 // Cluster-resident solve of a small grid (F64 / F32): *used = false when the
 // grid does not fit or the options ask for the streaming kernels.
 int try_small(const SolvePlan& p, cudaStream_t st, bool* used);
+
+// Batched solves: the instances that fit in one cluster's shared memory are
+// solved by the cluster-resident kernel (one cluster an instance); taken[k]
+// is set for them (count entries).
+int small_batched(int count, const int* nx, const int* ny, const int* ld, const void* const* b, void* const* x,
+                  double tol, int maxit, int variant, int precision, lap5cg_info* info, const lap5cg_opts& o,
+                  cudaStream_t st, std::vector<char>& taken);
 
 int solve_f64(const SolvePlan& p, cudaStream_t st);
 int solve_f32(const SolvePlan& p, cudaStream_t st);

@@ -12,7 +12,9 @@
 // those of the streaming kernels: Algorithm 1 (z = A p stored, as in
 // binary64) and Algorithm 2, fixed stencil add order, FMA axpys, FP64 dot
 // products (binary32: Dot2).
+#include <algorithm>
 #include <cooperative_groups.h>
+#include <vector>
 
 #include "cg_kernels.cuh"
 #include "launch.h"
@@ -216,13 +218,14 @@ __host__ __device__ inline size_t small_xchg_bytes(int ldp, size_t es) {
   return align_up((size_t)4 * ldp * es, 16) + (size_t)2 * 16 * 2 * sizeof(double);
 }
 
+// One cluster-resident solve (the whole body of the kernels below).  red and
+// scal are static shared memory of the calling kernel (scal: NewCG's gamma,
+// delta, alpha, beta and continue / stop / status), dsm its dynamic shared
+// memory.
 template <class T>
-__global__ void __launch_bounds__(512, 1) k_small(const SmallArgs<T> a) {
+__device__ __forceinline__ void small_body(const SmallArgs<T>& a, double* red, double* scal, unsigned char* dsm) {
   using M = typename Math<T>::type;
   using Acc = typename AccOf<M>::type;
-  __shared__ double red[kRedDoubles];
-  __shared__ double scal[5];  // NewCG: gamma, delta, alpha, beta, continue / stop / status
-  extern __shared__ __align__(16) unsigned char dsm[];
   auto cl = cgx::this_cluster();
   const int rank = (int)cl.block_rank(), C = (int)cl.num_blocks();
   int r0, nr;
@@ -535,6 +538,33 @@ done:
   cl.sync();  // no CTA leaves while a neighbour may still read its shared memory
 }
 
+template <class T>
+__global__ void __launch_bounds__(512, 1) k_small(const SmallArgs<T> a) {
+  __shared__ double red[kRedDoubles];
+  __shared__ double scal[5];
+  extern __shared__ __align__(16) unsigned char dsm[];
+  small_body<T>(a, red, scal, dsm);
+}
+
+// Many small instances in one launch: cluster i of the grid solves instance i
+// (batched solves of grids that fit in one cluster's shared memory).
+constexpr int kSmallBatchMax = 96;
+template <class T>
+struct SmallBatchArgs {
+  int C;  // CTAs per cluster (= per instance)
+  int n;  // instances in this launch
+  SmallArgs<T> a[kSmallBatchMax];
+};
+
+template <class T>
+__global__ void __launch_bounds__(512, 1) k_small_batch(const SmallBatchArgs<T> sb) {
+  __shared__ double red[kRedDoubles];
+  __shared__ double scal[5];
+  extern __shared__ __align__(16) unsigned char dsm[];
+  const int i = (int)blockIdx.x / sb.C;
+  if (i < sb.n) small_body<T>(sb.a[i], red, scal, dsm);  // whole clusters take the same branch
+}
+
 // Shared memory a cluster-resident solve needs per CTA (0 if it does not fit).
 template <class T>
 static size_t small_smem(int nx, int ny, int variant, int C, int* R_out, int* ldp_out) {
@@ -603,6 +633,94 @@ static int try_small_t(const SolvePlan& p, cudaStream_t st, bool* used) {
   void* args[] = {&a};
   if (cudaLaunchKernelExC(&lc, fn, args) != cudaSuccess) return LAP5CG_ERR_CUDA;
   *used = true;
+  return LAP5CG_OK;
+}
+
+// Batched solves: instances of F64 / F32 shape that fit in one cluster's
+// shared memory (and at least one row a CTA) are solved by k_small_batch, one
+// cluster an instance, kSmallBatchMax a launch; taken[k] marks them.  The
+// options that ask for the streaming kernels for single solves do so here.
+template <class T>
+static int small_batched_t(int count, const int* nx, const int* ny, const int* ld, const void* const* b,
+                           void* const* x, double tol, int maxit, int variant, lap5cg_info* info,
+                           const lap5cg_opts& o, cudaStream_t st, std::vector<char>& taken) {
+  if (o.resident < 0 || o.ring_slots != 0 || o.rr_period > 0 || o.reproducible || o.stabilized) return LAP5CG_OK;
+  DevProps dp;
+  int rc = dev_props(&dp);
+  if (rc != LAP5CG_OK) return rc;
+  int C = o.team_ctas;
+  if (C != 1 && C != 2 && C != 4 && C != 8 && C != 16) C = 16;
+  const int wpc = o.warps_per_cta > 0 ? (o.warps_per_cta > 16 ? 16 : o.warps_per_cta) : 8;
+  std::vector<int> pick;
+  std::vector<SmallArgs<T>> args;
+  size_t smem_max = 0;
+  for (int k = 0; k < count; ++k) {
+    if (ny[k] < C) continue;
+    int R, ldp;
+    const size_t smem = small_smem<T>(nx[k], ny[k], variant, C, &R, &ldp);
+    if (smem + sizeof(double) * kRedDoubles + 1024 > (size_t)dp.max_smem_optin) continue;
+    SmallArgs<T> a;
+    a.nx = nx[k];
+    a.ny = ny[k];
+    a.ld = ld[k];
+    a.R = R;
+    a.ldp = ldp;
+    a.b = static_cast<const T*>(b[k]);
+    a.x = static_cast<T*>(x[k]);
+    a.info = info + k;
+    a.history = nullptr;
+    a.tol = tol;
+    a.maxit = maxit;
+    a.true_res = o.true_residual;
+    a.variant = variant;
+    args.push_back(a);
+    pick.push_back(k);
+    if (smem > smem_max) smem_max = smem;
+  }
+  if (pick.empty()) return LAP5CG_OK;
+  const void* fn = reinterpret_cast<const void*>(&k_small_batch<T>);
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max) != cudaSuccess)
+    return LAP5CG_ERR_CUDA;
+  if (C > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+    return LAP5CG_ERR_CUDA;
+  cudaLaunchConfig_t lc = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  lc.gridDim = dim3(C);
+  lc.blockDim = dim3(32 * wpc);
+  lc.dynamicSmemBytes = smem_max;
+  lc.stream = st;
+  lc.attrs = attr;
+  lc.numAttrs = 1;
+  int nclusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&nclusters, fn, &lc) != cudaSuccess || nclusters < 1) {
+    cudaGetLastError();
+    return LAP5CG_OK;  // this cluster shape cannot run here: the persistent kernel takes them all
+  }
+  for (size_t first = 0; first < pick.size(); first += kSmallBatchMax) {
+    SmallBatchArgs<T> sb;
+    sb.C = C;
+    sb.n = (int)std::min<size_t>(kSmallBatchMax, pick.size() - first);
+    for (int i = 0; i < sb.n; ++i) sb.a[i] = args[first + i];
+    lc.gridDim = dim3(sb.n * C);
+    void* kargs[] = {&sb};
+    if (cudaLaunchKernelExC(&lc, fn, kargs) != cudaSuccess) return LAP5CG_ERR_CUDA;
+    for (int i = 0; i < sb.n; ++i) taken[pick[first + i]] = 1;
+  }
+  return LAP5CG_OK;
+}
+
+int small_batched(int count, const int* nx, const int* ny, const int* ld, const void* const* b, void* const* x,
+                  double tol, int maxit, int variant, int precision, lap5cg_info* info, const lap5cg_opts& o,
+                  cudaStream_t st, std::vector<char>& taken) {
+  taken.assign(count, 0);
+  if (precision == LAP5CG_PREC_F64)
+    return small_batched_t<double>(count, nx, ny, ld, b, x, tol, maxit, variant, info, o, st, taken);
+  if (precision == LAP5CG_PREC_F32)
+    return small_batched_t<float>(count, nx, ny, ld, b, x, tol, maxit, variant, info, o, st, taken);
   return LAP5CG_OK;
 }
 

@@ -29,6 +29,10 @@ def _make(shapes, dtype=np.float64, seed0=100):
     return out
 
 
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
 def _run(batch, **kw):
     bs = [torch.from_numpy(b).cuda() for _, b in batch]
     xs, info = lap5cg.cg_solve_batched(bs, nx_list=[nx for nx, _ in batch], **kw)
@@ -172,3 +176,49 @@ def test_batched_invalid_arguments():
     b = torch.zeros((8, 8), dtype=torch.float64, device="cuda")
     with pytest.raises(lap5cg.Lap5cgError):
         lap5cg.cg_solve_batched([b], tol=1e-8, maxit=10, precision="ir_f32", variant="newcg")
+
+
+@pytest.mark.parametrize("variant", ["classic", "newcg"])
+def test_batched_small_instances_take_the_resident_kernel(variant):
+    # 100 instances that fit in one cluster's shared memory (two launches of
+    # the cluster-resident kernel, 96 a launch) mixed with three that do not
+    # (the persistent kernel): every one against the oracle, in caller order
+    rng = np.random.default_rng(17)
+    shapes = [(int(rng.integers(16, 90)), int(rng.integers(16, 90))) for _ in range(100)]
+    shapes[10:10] = [(700, 300), (300, 700), (1100, 90)]
+    bs = []
+    for k, (nx, ny) in enumerate(shapes):
+        bs.append(gen.uniform_rhs(nx, ny, seed=500 + k, ld=gen.pitch(nx, 8, 32)))
+    xs, info = lap5cg.cg_solve_batched([_dev(b) for b in bs], tol=1e-10, maxit=100000, variant=variant,
+                                       precision="f64", nx_list=[s[0] for s in shapes])
+    recs = lap5cg.decode_info(info)
+    for k, (nx, ny) in enumerate(shapes):
+        xo, io = oracle.cg_solve(bs[k], variant=variant, tol=1e-10, maxit=100000, nx=nx)
+        rec = recs[k]
+        assert rec["status"] == lap5cg.OK, (k, rec)
+        assert abs(rec["iters"] - io["iters"]) <= 2, (k, rec, io)
+        kappa = gen.condition_number(nx, ny)
+        assert _rel(xs[k].cpu().numpy()[:, :nx], xo[:, :nx]) <= kappa * max(1e-10, io["relres_true"]), k
+
+
+def test_batched_one_small_instance_is_as_fast_as_a_single_solve():
+    # the paper's 100 x 100 grid through cg_solve_batched takes the same
+    # cluster-resident kernel as cg_solve: within 1.5x of its time
+    b = _dev(gen.uniform_rhs(100, 100, seed=1))
+    times = {}
+    for path in ("single", "batched"):
+        def run():
+            if path == "single":
+                return lap5cg.cg_solve(b, tol=1e-8, maxit=10000, variant="newcg")[1]
+            return lap5cg.cg_solve_batched([b], tol=1e-8, maxit=10000, variant="newcg", precision="f64")[1]
+        run()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(10):
+            info = run()
+        e1.record()
+        torch.cuda.synchronize()
+        assert lap5cg.decode_info(info)[0]["status"] == lap5cg.OK
+        times[path] = e0.elapsed_time(e1) / 10
+    assert times["batched"] <= 1.5 * times["single"], times
