@@ -21,7 +21,11 @@
  * Ownership: the caller owns every buffer (inputs, outputs, workspace, info).
  * No entry point below allocates device memory at call time, and the library
  * keeps no mutable global state apart from a per-device cache of device
- * properties.  One exception to "the caller owns every buffer":
+ * properties and, for the classic multigrid-preconditioned solve (MG_F32,
+ * MG_F64), a cache of up to eight instantiated CUDA graphs keyed by device,
+ * shape, workspace address and V-cycle options: the first solve of a key
+ * builds and instantiates its graph (driver-side resources, freed when the
+ * entry is evicted), later ones launch it.  One exception to "the caller owns every buffer":
  * cg_solve_classic_f64_noalloc uses a fixed 8.25 MiB __device__ array of the
  * library as scratch; the CUDA runtime commits it on a device when it loads
  * the library's module there (with lazy module loading, at the first call

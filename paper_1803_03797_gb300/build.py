@@ -17,7 +17,7 @@ LIB = os.path.join(PKG, "_lib", "liblap5cg.so")
 HEADER = os.path.join(ROOT, "include", "lap5cg.h")
 
 SOURCES = ["api.cu", "stencil.cu", "cg_f64.cu", "cg_f32.cu", "ir.cu", "noalloc.cu", "batched.cu", "tune.cu", "small.cu", "mg.cu",
-           "probe.cu"]
+           "mg_graph.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr", "-Xptxas", "-warn-spills", "-Werror", "cross-execution-space-call"]

@@ -165,3 +165,96 @@ def test_unaligned_pitch_is_staged(variant):
     assert r1["status"] == r2["status"] == lap5cg.OK
     assert r1["iters"] == r2["iters"]
     assert _rel(x1, x2) <= 1e-13
+
+
+# ---------------------------------------------------------------------------
+# The classic form runs as a cached CUDA graph; under stream capture it runs as
+# the persistent kernel.  Both track the oracle.
+# ---------------------------------------------------------------------------
+def _ws_for(nx, ny, ld, precision="mg_f64", nrhs=1):
+    return torch.empty(lap5cg.workspace_size(nx, ny, ld, "classic", precision, nrhs), dtype=torch.uint8,
+                       device="cuda")
+
+
+def test_cached_graph_rebinds_rhs_solution_and_limits():
+    # one workspace, so every call below hits the same cached graph: the
+    # right-hand side, the solution buffer, tol and maxit change per call
+    nx, ny = 300, 200
+    ld = gen.pitch(nx, 8)
+    ws = _ws_for(nx, ny, ld)
+    bs = [gen.uniform_rhs(nx, ny, seed=s, ld=ld) for s in (31, 32)]
+    runs = [(0, 0.0, 4), (1, 0.0, 6), (0, 1e-6, 500), (0, 0.0, 4)]
+    first = None
+    for which, tol, k in runs:
+        out = torch.zeros((ny, ld), dtype=torch.float64, device="cuda")
+        x, info = lap5cg.cg_solve(_dev(bs[which]), tol=tol, maxit=k, precision="mg_f64", nx=nx, workspace=ws, out=out)
+        rec = lap5cg.decode_info(info)[0]
+        xo, io = oracle.cg_pcg(bs[which], tol=tol, maxit=k, nx=nx)
+        assert rec["iters"] == io["iters"] and rec["status"] == io["status"], (which, tol, k, rec, io)
+        xg = x.cpu().numpy()[:, :nx]
+        assert _rel(xg, xo[:, :nx]) <= 1e-11
+        if first is None:
+            first = xg
+    np.testing.assert_array_equal(xg, first)  # the same call again: bit-identical
+
+
+def test_stacked_right_hand_sides_share_one_graph():
+    nx, ny, nrhs = 130, 67, 3
+    ld = gen.pitch(nx, 8)
+    b = np.stack([gen.uniform_rhs(nx, ny, seed=40 + k, ld=ld) for k in range(nrhs)])
+    x, info = lap5cg.cg_solve(_dev(b), tol=0.0, maxit=5, precision="mg_f64", nx=nx)
+    recs = lap5cg.decode_info(info)
+    for k in range(nrhs):
+        xo, io = oracle.cg_pcg(b[k], tol=0.0, maxit=5, nx=nx)
+        assert recs[k]["iters"] == io["iters"] == 5
+        assert _rel(x[k].cpu().numpy()[:, :nx], xo[:, :nx]) <= 1e-11
+
+
+@pytest.mark.parametrize("precision", ["mg_f64", "mg_f32"])
+def test_history_matches_oracle(precision):
+    nx, ny, K = 300, 200, 8
+    b = gen.uniform_rhs(nx, ny, seed=55, ld=gen.pitch(nx, 8))
+    hist = torch.full((K + 1,), float("nan"), dtype=torch.float64, device="cuda")
+    x, info = lap5cg.cg_solve(_dev(b), tol=0.0, maxit=K, precision=precision, nx=nx,
+                              opts=lap5cg.default_opts(history=hist.data_ptr()))
+    _, io, ho = oracle.cg_pcg(b, tol=0.0, maxit=K, nx=nx, history=True)
+    h = hist.cpu().numpy()
+    # binary64 V-cycle: same steps as the oracle; binary32: a rounded M
+    np.testing.assert_allclose(h, ho, rtol=1e-9 if precision == "mg_f64" else 1e-4)
+
+
+def test_captured_solve_takes_persistent_kernel_and_tracks_oracle():
+    nx, ny, k = 513, 130, 5
+    ld = gen.pitch(nx, 8)
+    b = _dev(gen.uniform_rhs(nx, ny, seed=61, ld=ld))
+    ws = _ws_for(nx, ny, ld)
+    info = torch.empty(lap5cg.INFO_BYTES, dtype=torch.uint8, device="cuda")
+    x = torch.zeros((ny, ld), dtype=torch.float64, device="cuda")
+    eager, einfo = lap5cg.cg_solve(b, tol=0.0, maxit=k, precision="mg_f64", nx=nx)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.graph(g, stream=s):
+        x.zero_()
+        lap5cg.cg_solve(b, tol=0.0, maxit=k, precision="mg_f64", nx=nx, workspace=ws, info=info, out=x)
+    xo, io = oracle.cg_pcg(b.cpu().numpy(), tol=0.0, maxit=k, nx=nx)
+    for rep in range(2):
+        x.fill_(7.0)
+        g.replay()
+        torch.cuda.synchronize()
+        rec = lap5cg.decode_info(info)[0]
+        assert rec["iters"] == io["iters"] == k and rec["status"] == io["status"]
+        assert _rel(x.cpu().numpy()[:, :nx], xo[:, :nx]) <= 1e-11
+    assert _rel(eager.cpu().numpy()[:, :nx], xo[:, :nx]) <= 1e-11
+
+
+def test_graph_cache_eviction_keeps_results_right():
+    # more shapes than the cache holds, then the first one again
+    shapes = [(100 + 8 * i, 90 + 4 * i) for i in range(10)] + [(100, 90)]
+    for nx, ny in shapes:
+        b = gen.uniform_rhs(nx, ny, seed=nx + ny, ld=gen.pitch(nx, 8))
+        x, rec = _solve(b, nx, "mg_f64", 0.0, 3)
+        xo, io = oracle.cg_pcg(b, tol=0.0, maxit=3, nx=nx)
+        assert rec["iters"] == io["iters"] == 3
+        assert _rel(x, xo[:, :nx]) <= 1e-11
