@@ -107,6 +107,8 @@ def _load(path):
     L.ora_cg_ir.argtypes = [i, i, i, vp, vp, d, i, i, d, i, ctypes.POINTER(Info)]
     L.ora_inner_cg_f32.argtypes = [i, i, i, vp, vp, d, i, i, vp, ctypes.POINTER(i)]
     L.ora_inner_cg_f32.restype = i
+    L.ora_ir_keep_step.argtypes = [d, d, d, d]
+    L.ora_ir_keep_step.restype = i
     for name in ("ora_cg_classic", "ora_cg_newcg", "ora_cg_ir"):
         getattr(L, name).restype = i
     L.ora_repro_blocks.argtypes = [i, i, i, vp, vp, vp]
@@ -277,6 +279,13 @@ def inner_cg_f32(rin, tol_in=1e-4, maxit_in=1000, storage="f32", nx=None):
     if k < 0:
         raise ValueError("invalid arguments")
     return d, r, k, bool(brk.value)
+
+
+def ir_keep_step(rr_new, rr_old, d_r_old, d_r_new):
+    """The refinement's acceptance rule for a step x <- x + d: True when the
+    FP64 residual fell (rr_new < rr_old) or the error's energy fell by at least
+    half of (d, r_old) > 0, i.e. (d, r_new) >= -(d, r_old) / 2."""
+    return bool(lib().ora_ir_keep_step(float(rr_new), float(rr_old), float(d_r_old), float(d_r_new)))
 
 
 def cg_solve(b, variant="classic", **kw):

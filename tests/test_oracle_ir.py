@@ -23,6 +23,7 @@ import torch
 
 import lap5_inputs as gen
 import oracle
+from tests.helpers import kron_laplacian
 
 U32 = 2.0 ** -24
 
@@ -182,17 +183,24 @@ def _composed_ir(b, nx, max_outer, storage, tol_in, maxit_in):
     """FP64 iterative refinement written out from its definition: r = b - A x
     and (r, r) in binary64 (oracle stencil and index-order dot, both pinned
     elsewhere), r rounded to binary32, the inner solve (pinned above), x += d
-    in binary64; a step whose residual is not below the previous one is undone
-    and ends the solve (the stagnation guard)."""
+    in binary64.  A step whose residual is not below the previous one is kept
+    when it lowered the error's energy by at least half of (d, r_old) > 0 --
+    (d, r_new) >= -(d, r_old) / 2 (the rule is pinned against the energy's
+    definition below) -- and otherwise undone, which ends the solve."""
     x = np.zeros_like(b)
-    d, rr_prev, total, outer, reverted = None, None, 0, 0, False
+    d, rr_prev, total, outer, reverted, kept = None, None, 0, 0, False, 0
+    dro = 0.0
     while True:
         r = b - oracle.lap5_apply(x, nx=nx)
         rr = oracle.dot(r, r, nx=nx)
         if outer > 0 and not rr < rr_prev:
-            x = x - d.astype(np.float64)
-            reverted = True
-            break
+            drn = oracle.dot(d.astype(np.float64), r, nx=nx)
+            if dro > 0.0 and drn >= -0.5 * dro:
+                kept += 1
+            else:
+                x = x - d.astype(np.float64)
+                reverted = True
+                break
         rr_prev = rr
         if outer >= max_outer:
             break
@@ -200,29 +208,72 @@ def _composed_ir(b, nx, max_outer, storage, tol_in, maxit_in):
                                            storage=storage, nx=nx)
         assert not brk
         total += k
+        dro = oracle.dot(d.astype(np.float64), r, nx=nx)
         x = x + d.astype(np.float64)
         outer += 1
-    return x, total, outer, reverted
+    return x, total, outer, reverted, kept
 
 
-@pytest.mark.parametrize("n,storage,tol_in,maxit_in,max_outer,guard", [
-    (40, "f32", 1e-4, 500, 3, False),
-    (40, "bf16pr", 1e-2, 500, 3, False),
-    (64, "bf16pr", 1e-2, 20, 6, False),
-    (64, "bf16pr", 1e-2, 5, 12, True),    # the guard undoes step 4
-    (96, "bf16pr", 0.5, 10, 12, True),
+@pytest.mark.parametrize("n,storage,tol_in,maxit_in,max_outer,guard,kept", [
+    (40, "f32", 1e-4, 500, 3, False, False),
+    (40, "bf16pr", 1e-2, 500, 3, False, False),
+    (64, "bf16pr", 1e-2, 20, 6, False, False),
+    (64, "bf16pr", 1e-2, 5, 12, False, True),   # truncated inner solves: 2-norm up, energy down
+    (96, "bf16pr", 0.5, 10, 12, False, True),
+    (64, "f32", 0.0, 384, 6, True, False),      # at the FP64 floor the guard undoes step 4
 ])
-def test_refinement_equals_its_composition(n, storage, tol_in, maxit_in, max_outer, guard):
+def test_refinement_equals_its_composition(n, storage, tol_in, maxit_in, max_outer, guard, kept):
     b = gen.uniform_rhs(n, n, seed=81)
     x, info = oracle.cg_ir(b, tol=0.0, max_outer=max_outer, inner=storage, tol_in=tol_in, maxit_in=maxit_in)
-    xc, total, outer, reverted = _composed_ir(b, n, max_outer, storage, tol_in, maxit_in)
+    xc, total, outer, reverted, nkept = _composed_ir(b, n, max_outer, storage, tol_in, maxit_in)
     assert reverted == guard
+    assert (nkept > 0) == kept
     assert info["outer_iters"] == outer and info["iters"] == total
     assert info["status"] == oracle.NOT_CONVERGED
     np.testing.assert_array_equal(x[:, :n], xc[:, :n])
-    # the solve returns the better iterate: its residual is the smallest seen
+    # an undone step returns the iterate before it: the residual reported is
+    # that of the returned x
     if guard:
         assert info["relres_true"] <= info["relres_recursive"] * (1 + 1e-12)
+
+
+def _energy_cases(n=12, seed=3):
+    """Steps d for a residual r_old with known outcomes, from dense algebra:
+    d = s e (e = A^-1 r_old), e plus a rough vector that raises the 2-norm but
+    hardly the energy, and rough vectors alone."""
+    A = kron_laplacian(n, n).toarray()
+    rng = np.random.default_rng(seed)
+    s1 = np.sin(np.pi * np.arange(1, n + 1) / (n + 1))
+    r_old = np.outer(s1, s1).reshape(-1) + 0.05 * rng.standard_normal(n * n)
+    e = np.linalg.solve(A, r_old)
+    chk = np.indices((n, n)).sum(axis=0) % 2 * 2.0 - 1.0  # the roughest mode's sign pattern
+    j = (chk * np.outer(s1, s1)).reshape(-1)
+    t = 2.0 * np.linalg.norm(r_old) / np.linalg.norm(A @ j)  # ||A t j|| = 2 ||r_old||
+    cases = [s * e for s in (0.3, 0.7, 1.0, 1.4, 1.6, 2.0, 2.5)]
+    cases += [e + t * j, e - t * j, e + 3 * t * j, t * j, -t * j, 0.5 * e + 10 * t * j]
+    return A, r_old, e, cases
+
+
+def test_keep_rule_follows_the_energy_definition():
+    A, r_old, e, cases = _energy_cases()
+    E_old = e @ A @ e
+    saw_raised_and_kept = saw_reverted = False
+    for d in cases:
+        r_new = r_old - A @ d
+        rr_old, rr_new = r_old @ r_old, r_new @ r_new
+        e_new = e - d
+        drop = E_old - e_new @ A @ e_new        # energy removed, from its definition
+        claim = d @ r_old
+        want = rr_new < rr_old or (claim > 0 and drop >= 0.5 * claim)
+        assert abs(drop - 0.5 * claim) > 1e-6 * abs(claim)  # no borderline case
+        got = oracle.ir_keep_step(rr_new, rr_old, d @ r_old, d @ r_new)
+        assert got == want, (rr_new / rr_old, drop / claim)
+        saw_raised_and_kept |= got and rr_new >= rr_old
+        saw_reverted |= not got
+    assert saw_raised_and_kept and saw_reverted
+    # a zero step claims nothing and is undone (the solve would otherwise
+    # repeat it until the outer cap)
+    assert not oracle.ir_keep_step(r_old @ r_old, r_old @ r_old, 0.0, 0.0)
 
 
 def test_refinement_contracts_by_the_inner_tolerance():

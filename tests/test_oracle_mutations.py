@@ -45,7 +45,10 @@ IR_MUTATIONS = {
     "inner_p_not_rounded_to_bf16": ("p[t] = stor(r[t] + bt * p[t], bf);", "p[t] = r[t] + bt * p[t];"),
     "ir_update_sign": ("x[(size_t)j * ld + i] = x[(size_t)j * ld + i] + (double)d[(size_t)j * ld + i];",
                        "x[(size_t)j * ld + i] = x[(size_t)j * ld + i] - (double)d[(size_t)j * ld + i];"),
-    "ir_guard_dropped": ("if (outer > 0 && !(rr < rr_prev)) {", "if (0) {"),
+    "ir_guard_dropped": ("if (outer > 0 && !ora_ir_keep_step(", "if (0 && !ora_ir_keep_step("),
+    "ir_keep_half_sign": ("return dro > 0.0 && drn >= -0.5 * dro;", "return dro > 0.0 && drn >= 0.5 * dro;"),
+    "ir_keep_energy_ignored": ("return dro > 0.0 && drn >= -0.5 * dro;", "return 0;"),
+    "ir_keep_claim_unchecked": ("return dro > 0.0 && drn >= -0.5 * dro;", "return drn >= -0.5 * dro;"),
 }
 MUTATIONS.update(IR_MUTATIONS)
 
@@ -136,8 +139,10 @@ def _ir_pins_pass():
               lambda: t.test_inner_f32_tracks_fp64_algorithm1(25),
               lambda: t.test_inner_matches_restatement_bit_for_bit("bf16pr"),
               lambda: t.test_inner_matches_restatement_bit_for_bit("f32"),
-              lambda: t.test_refinement_equals_its_composition(40, "f32", 1e-4, 500, 3, False),
-              lambda: t.test_refinement_equals_its_composition(64, "bf16pr", 1e-2, 5, 12, True)]
+              lambda: t.test_refinement_equals_its_composition(40, "f32", 1e-4, 500, 3, False, False),
+              lambda: t.test_refinement_equals_its_composition(64, "bf16pr", 1e-2, 5, 12, False, True),
+              lambda: t.test_refinement_equals_its_composition(64, "f32", 0.0, 384, 6, True, False),
+              t.test_keep_rule_follows_the_energy_definition]
     for check in checks:
         try:
             check()
