@@ -3,9 +3,11 @@
 // (Algorithm 1 of arxiv 1803.03797) stored in binary32, or with p and r
 // stored as bf16.
 //
-//   outer passes (binary64): x <- x + d, then r = b - A x with (r, r) and,
-//                          once, (b, b); r is rounded to the inner storage and
-//                          becomes the inner right-hand side.
+//   outer passes (binary64): x <- x + d with (d, A d), then r = b - A x with
+//                          (r, r), (d, r) and, once, (b, b); r is rounded to
+//                          the inner storage and becomes the inner right-hand
+//                          side.  A step that raised (r, r) is kept only if it
+//                          lowered the error's A-norm (see the guard below).
 //   inner CG (binary32 arithmetic, Dot2 dot products) on A d = r_in from d = 0,
 //   two fused passes per iteration as in the binary64 classic kernel.
 // The outer residual, the update of x and their dot products are the only
@@ -53,6 +55,7 @@ __device__ void ir_solve(const IrArgs<TR>& a, Team& tm, double* red, unsigned ch
 
   int status = LAP5CG_NOT_CONVERGED, total = 0, outer = 0;
   double bb = 0.0, rr = 0.0, rr_prev = 0.0, relres_true = nan("");
+  double dad = 0.0, drn = 0.0;  // (d, A d) and (d, r_new) of the last correction
   bool aborted = false, have_d = false, reverting = false;
   double thr = 0.0;
 
@@ -63,8 +66,7 @@ __device__ void ir_solve(const IrArgs<TR>& a, Team& tm, double* red, unsigned ch
     // updating x inside the stencil pass would let a neighbour read an
     // already-updated halo value.  (d was published by the barrier that ended
     // the last inner pass.)
-    if (have_d) {
-      const double sgn = reverting ? -1.0 : 1.0;  // x - d undoes a rejected correction
+    if (have_d && reverting) {  // x - d undoes a rejected correction
       struct DU { double x[VO]; float d[VO]; };
       for (int u = wk.gw; u < a.uo.nunits; u += wk.nw) {
         int s, y0, y1;
@@ -77,26 +79,68 @@ __device__ void ir_solve(const IrArgs<TR>& a, Team& tm, double* red, unsigned ch
         auto finish = [&](int j, const DU& dd) {
           double xv[VO];
 #pragma unroll
-          for (int k = 0; k < VO; ++k) xv[k] = dd.x[k] + sgn * (double)dd.d[k];
+          for (int k = 0; k < VO; ++k) xv[k] = dd.x[k] - (double)dd.d[k];
           store_row<VO>(a.x, j, xl, c.nx, xv);
         };
         stream_rows<DU>(y0, y1, wk.rev(), load, finish);
       }
       ++wk.pc;
       if (!tm.sync(red)) { aborted = true; goto done; }
+    } else if (have_d) {
+      // x += d, and (d, A d) with the binary64 stencil of the binary32 d (a
+      // march over d: it reads no x at halo points)
+      Acc64 aad;
+      struct DU { double x[VO]; };
+      for (int u = wk.gw; u < a.uo.nunits; u += wk.nw) {
+        int s, y0, y1;
+        unit_bounds(a.uo, u, c.ny, s, y0, y1);
+        const int xs = s * 32 * VO, xl = Lanes<VO>::first(xs, wk.lane);
+        const int nval = c.nx - xl;
+        auto field = [&](int j, FRow<VO, double>& f) {
+          if (j < 0 || j >= c.ny) { f.zero(); return; }
+          float dv[VO];
+          load_row<VO>(a.d, j, xl, c.nx, dv);
+#pragma unroll
+          for (int k = 0; k < VO; ++k) f.f[k] = (double)dv[k];
+          const int xh = xs + 32 * VO;
+          f.hl = (wk.lane == 0 && xs > 0) ? (double)a.d.row(j)[xs - 1] : 0.0;
+          f.hr = (wk.lane == 31 && xh < c.nx) ? (double)a.d.row(j)[xh] : 0.0;
+        };
+        auto load = [&](int j, DU& dd) { load_row<VO>(a.x, j, xl, c.nx, dd.x); };
+        auto finish = [&](int j, const DU& dd, const FRow<VO, double>& S, const FRow<VO, double>& C,
+                          const FRow<VO, double>& N) {
+          double xv[VO], ad[VO];
+          stencil_row<VO>(S, C, N, wk.lane, ad);
+#pragma unroll
+          for (int k = 0; k < VO; ++k) {
+            xv[k] = dd.x[k] + C.f[k];
+            if (Lanes<VO>::col(k) < nval) aad.add(C.f[k], ad[k]);
+          }
+          store_row<VO>(a.x, j, xl, c.nx, xv);
+        };
+        march<VO, double, DU>(y0, y1, wk.rev(), field, load, finish);
+      }
+      ++wk.pc;
+      double v[1] = {aad.value()}, o[1];
+      if (!tm.template reduce<1>(v, o, red)) { aborted = true; goto done; }
+      dad = o[0];
     }
     double g_in;
     {
-      Acc64 abb, arr;
+      Acc64 abb, arr, adr;
       Acc32 agi;
-      struct D { double b[VO]; };
+      const bool with_d = have_d && !reverting;  // (d, r_new) for the step's energy test
+      struct D { double b[VO]; float d[VO]; };
       for (int u = wk.gw; u < a.uo.nunits; u += wk.nw) {
         int s, y0, y1;
         unit_bounds(a.uo, u, c.ny, s, y0, y1);
         const int xs = s * 32 * VO, xl = Lanes<VO>::first(xs, wk.lane);
         const int nval = c.nx - xl;  // columns from xl to the grid edge
         auto field = [&](int j, FRow<VO, double>& f) { field_plain<VO>(a.x, c.nx, c.ny, j, xl, xs, wk.lane, f); };
-        auto load = [&](int j, D& dd) { load_row<VO>(a.b, j, xl, c.nx, dd.b); };
+        auto load = [&](int j, D& dd) {
+          load_row<VO>(a.b, j, xl, c.nx, dd.b);
+          if (with_d) load_row<VO>(a.d, j, xl, c.nx, dd.d);
+        };
         auto finish = [&](int j, const D& dd, const FRow<VO, double>& S, const FRow<VO, double>& C,
                           const FRow<VO, double>& N) {
           double ax[VO];
@@ -110,6 +154,7 @@ __device__ void ir_solve(const IrArgs<TR>& a, Team& tm, double* red, unsigned ch
               if (outer == 0) abb.add(dd.b[k], dd.b[k]);
               arr.add(rv, rv);
               agi.add(ri[k], ri[k]);
+              if (with_d) adr.add((double)dd.d[k], rv);
             }
           }
           store_row<VO>(a.r, j, xl, c.nx, ri);
@@ -117,8 +162,9 @@ __device__ void ir_solve(const IrArgs<TR>& a, Team& tm, double* red, unsigned ch
         march<VO, double, D>(y0, y1, wk.rev(), field, load, finish);
       }
       ++wk.pc;
-      double v[3] = {abb.value(), arr.value(), agi.value()}, o[3];
-      if (!tm.template reduce<3>(v, o, red)) { aborted = true; goto done; }
+      double v[4] = {abb.value(), arr.value(), agi.value(), adr.value()}, o[4];
+      if (!tm.template reduce<4>(v, o, red)) { aborted = true; goto done; }
+      drn = o[3];
       if (outer == 0) {
         bb = o[0];
         if (!isfinite(bb)) { status = LAP5CG_ERR_NONFINITE; goto done; }
@@ -140,12 +186,20 @@ __device__ void ir_solve(const IrArgs<TR>& a, Team& tm, double* red, unsigned ch
     if (reverting) { status = LAP5CG_NOT_CONVERGED; goto done; }
     if (rr <= thr) { status = LAP5CG_OK; goto done; }
     if (outer > 0 && !(rr < rr_prev)) {
-      // stagnation guard: the last correction did not lower the FP64 residual
-      // (the inner precision cannot resolve this system): undo it (x -= d),
-      // recompute the residual and stop with the better iterate
-      reverting = true;
-      have_d = true;
-      continue;
+      // The FP64 residual did not fall.  Keep the step if it lowered the
+      // error's A-norm by at least half of what it claims: the energy falls by
+      // (d, r_old) + (d, r_new), with (d, r_old) = (d, r_new) + (d, A d) > 0,
+      // so the test is (d, r_new) >= -(d, r_old) / 2.  A truncated CG
+      // correction has (d, r_new) = 0 in exact arithmetic; one made of
+      // rounding noise has (d, A d) dominant.  Otherwise undo it (x -= d),
+      // recompute the residual and stop with the better iterate.
+      if (!have_d) { status = LAP5CG_NOT_CONVERGED; goto done; }  // the inner solve made no correction
+      const double dro = drn + dad;
+      if (!(dro > 0.0 && drn >= -0.5 * dro)) {
+        reverting = true;
+        have_d = true;
+        continue;
+      }
     }
     rr_prev = rr;
     if (outer >= a.max_outer || total >= c.maxit) { status = LAP5CG_NOT_CONVERGED; goto done; }

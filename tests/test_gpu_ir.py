@@ -152,3 +152,41 @@ def test_ir_config_size_against_oracle_reference(precision, n):
           "max|x - x*|/max|x*| %.3g (bound %.3g)" % (precision, n, rec["outer_iters"], rec["iters"],
                                                      rec["relres_true"], np.max(np.abs(x - xr)) / np.max(np.abs(xr)),
                                                      bound / np.max(np.abs(xr))))
+
+
+# ---------------------------------------------------------------------------
+# The refinement's guard: a step that raised the FP64 residual is kept when it
+# lowered the error's energy (the oracle's rule), and undone at the FP64 floor.
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("batched", [False, True])
+def test_ir_keeps_energy_lowering_steps_like_the_oracle(batched):
+    # truncated bf16 inner solves (5 iterations): every other step raises the
+    # 2-norm residual but lowers the energy; the oracle keeps all 12 steps
+    n = 64
+    b = gen.uniform_rhs(n, n, seed=81)
+    _, io = oracle.cg_ir(b, tol=0.0, max_outer=12, inner="bf16pr", tol_in=1e-2, maxit_in=5)
+    assert io["outer_iters"] == 12 and io["status"] == oracle.NOT_CONVERGED
+    opts = lap5cg.default_opts(tol_inner=1e-2, maxit_inner=5, max_outer=12)
+    if batched:  # the team kernel of the batched solve runs the same refinement
+        _, info = lap5cg.cg_solve_batched([_dev(b)], tol=0.0, maxit=10 ** 6, precision="ir_bf16pr", opts=opts)
+    else:
+        _, info = lap5cg.cg_solve(_dev(b), tol=0.0, maxit=10 ** 6, precision="ir_bf16pr", opts=opts)
+    rec = lap5cg.decode_info(info)[0]
+    assert rec["status"] == lap5cg.NOT_CONVERGED and rec["outer_iters"] == 12 and rec["iters"] == 60, rec
+    assert 0.5 * io["relres_true"] <= rec["relres_true"] <= 2.0 * io["relres_true"], (rec, io)
+
+
+def test_ir_guard_undoes_a_step_at_the_fp64_floor():
+    # binary32 inner solves run 384 iterations each: by the fourth step the
+    # FP64 residual is at rounding level and the correction is noise
+    n = 64
+    b = gen.uniform_rhs(n, n, seed=81)
+    _, io = oracle.cg_ir(b, tol=0.0, max_outer=6, inner="f32", tol_in=0.0, maxit_in=384)
+    assert io["outer_iters"] < 6 and io["status"] == oracle.NOT_CONVERGED
+    opts = lap5cg.default_opts(tol_inner=1e-300, maxit_inner=384, max_outer=6)
+    x, info = lap5cg.cg_solve(_dev(b), tol=0.0, maxit=10 ** 6, precision="ir_f32", opts=opts)
+    rec = lap5cg.decode_info(info)[0]
+    assert rec["status"] == lap5cg.NOT_CONVERGED and rec["outer_iters"] < 6, rec
+    assert rec["relres_true"] <= 1e-14
+    # the undone step leaves the iterate before it: recursive = true residual
+    assert abs(rec["relres_true"] - rec["relres_recursive"]) <= 1e-3 * rec["relres_true"]
