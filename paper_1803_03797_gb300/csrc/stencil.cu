@@ -8,8 +8,15 @@
 // from HBM about once.  Not persistent, no grid barrier: enough independent
 // warps keep the loads in flight.  (Measured at 8192^2 binary32: 5.6 TB/s,
 // against 4.2 TB/s for a row march with one row of look-ahead.)
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <atomic>
+#include <mutex>
+
 #include "common.cuh"
 #include "launch.h"
+#include "ring.cuh"
 
 namespace lap5 {
 
@@ -159,6 +166,223 @@ static int launch_apply_bf16x16(int nx, int ny, int ld, const void* x, void* y, 
   return cudaGetLastError() == cudaSuccess ? LAP5CG_OK : LAP5CG_ERR_CUDA;
 }
 
+// bf16 storage through TMA tiles.  A tile is 16 output rows of 256 columns;
+// its operand rows (18 of 256 columns) and the one-column halos left and right
+// (two 8-column boxes, the narrowest 16-byte box) land in shared memory by
+// three tensor copies.  The tensor map spans exactly nx x ny, so every operand
+// outside the grid -- the Dirichlet boundary, the ragged right and bottom
+// edges -- arrives as the copy's zero fill, and no load is masked.  Persistent
+// CTAs walk the tiles with three stages in flight; each thread finishes one
+// 8-column vector in each of kTmaRowsPerThread rows with the arithmetic of the
+// register kernel above, so the results are bit-identical.
+constexpr int kTmaW = 256, kTmaH = 16, kTmaStages = 3, kTmaThreads = 256;
+constexpr int kTmaRowsPerThread = kTmaH / (kTmaThreads / 32);
+static_assert(kTmaH % (kTmaThreads / 32) == 0, "whole rows a warp");
+constexpr int kTmaMainBytes = kTmaW * (kTmaH + 2) * 2;                // 9216
+constexpr int kTmaHaloBytes = 8 * (kTmaH + 2) * 2;                    // 288
+constexpr int kTmaHaloStride = (kTmaHaloBytes + 127) / 128 * 128;     // 128-byte aligned slots
+static_assert(kTmaMainBytes % 128 == 0 && kTmaHaloStride >= kTmaHaloBytes, "stage layout");
+static_assert(kTmaH + 2 <= 256 && kTmaW <= 256, "tensor-copy box extents");
+constexpr int kTmaStageBytes = kTmaMainBytes + 2 * kTmaHaloStride;
+constexpr uint32_t kTmaTx = kTmaMainBytes + 2 * kTmaHaloBytes;
+
+// Diagnostics: stages whose copy did not land within the wait limit, plus
+// 65536 for each CTA that found its shared memory misaligned for the copies
+// (and wrote nothing).
+__device__ int g_apply_tma_timeouts;
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// Bounded wait on a stage's barrier; false when it ran out (the copy is
+// waited for once more, also bounded, so that none is in flight at exit).
+__device__ __forceinline__ bool tma_wait(uint32_t bar, uint32_t parity) {
+  for (int round = 0; round < 2; ++round) {
+    const unsigned long long t0 = global_ns();
+    unsigned spins = 0;
+    for (;;) {
+      uint32_t ok;
+      asm volatile(
+          "{\n\t.reg .pred p;\n\t"
+          "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+          "selp.u32 %0, 1, 0, p;\n\t}"
+          : "=r"(ok)
+          : "r"(bar), "r"(parity), "r"(kSuspendHintNs)
+          : "memory");
+      if (ok) return round == 0;
+      if ((++spins & 63u) == 0u && global_ns() - t0 > 1000000000ull) break;
+    }
+    if (round == 0 && threadIdx.x == 0) atomicAdd(&g_apply_tma_timeouts, 1);
+  }
+  return false;
+}
+
+__global__ void __launch_bounds__(kTmaThreads) k_lap5_apply_bf16_tma(const __grid_constant__ CUtensorMap mmain,
+                                                                    const __grid_constant__ CUtensorMap mhalo,
+                                                                    int nx, int ny, int ld, uint16_t* __restrict__ y,
+                                                                    int tiles_x, int ntiles) {
+  // stages first, then the barriers; no static shared memory, so the stages
+  // start at the (aligned) beginning of the dynamic window
+  extern __shared__ __align__(128) unsigned char tsm[];
+  const uint32_t base = smem_u32(tsm), bar0 = base + (uint32_t)(kTmaStages * kTmaStageBytes);
+  if (base & 127u) {  // tensor copies need 128-byte aligned destinations
+    if (threadIdx.x == 0) atomicAdd(&g_apply_tma_timeouts, 1 << 16);
+    return;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) {
+    for (int sidx = 0; sidx < kTmaStages; ++sidx)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8u * sidx) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  auto issue = [&](int t, int sidx) {  // thread 0
+    const int x0 = (t % tiles_x) * kTmaW, y0 = (t / tiles_x) * kTmaH;
+    const uint32_t bar = bar0 + 8u * sidx, dst = base + (uint32_t)(sidx * kTmaStageBytes);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kTmaTx) : "memory");
+    tma_load_2d(dst, &mmain, x0, y0 - 1, bar);
+    tma_load_2d(dst + kTmaMainBytes, &mhalo, x0 - 8, y0 - 1, bar);
+    tma_load_2d(dst + kTmaMainBytes + kTmaHaloStride, &mhalo, x0 + kTmaW, y0 - 1, bar);
+  };
+  const int first = blockIdx.x, step = gridDim.x;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < kTmaStages; ++k)
+      if (first + k * step < ntiles) issue(first + k * step, k);
+  bool ok = true;
+  int k = 0;
+  for (int t = first; t < ntiles; t += step, ++k) {
+    const int sidx = k % kTmaStages;
+    ok = tma_wait(bar0 + 8u * sidx, (uint32_t)((k / kTmaStages) & 1)) && ok;
+    const unsigned char* st = tsm + sidx * kTmaStageBytes;
+    const uint16_t* mrow = reinterpret_cast<const uint16_t*>(st);
+    const uint16_t* hl = reinterpret_cast<const uint16_t*>(st + kTmaMainBytes);
+    const uint16_t* hr = reinterpret_cast<const uint16_t*>(st + kTmaMainBytes + kTmaHaloStride);
+    const int x0 = (t % tiles_x) * kTmaW, y0 = (t / tiles_x) * kTmaH;
+    const int xc = x0 + 8 * lane;
+#pragma unroll
+    for (int h = 0; h < kTmaRowsPerThread; ++h) {
+      const int r = warp + (kTmaThreads / 32) * h;  // output row y0 + r; operand rows r .. r + 2 of the stage
+      const uint4 rs = *reinterpret_cast<const uint4*>(mrow + r * kTmaW + 8 * lane);
+      const uint4 rc = *reinterpret_cast<const uint4*>(mrow + (r + 1) * kTmaW + 8 * lane);
+      const uint4 rn = *reinterpret_cast<const uint4*>(mrow + (r + 2) * kTmaW + 8 * lane);
+      const uint32_t ws[4] = {rs.x, rs.y, rs.z, rs.w}, wc[4] = {rc.x, rc.y, rc.z, rc.w},
+                     wn[4] = {rn.x, rn.y, rn.z, rn.w};
+      float S[8], C[8], N[8], Y[8];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        S[2 * m] = bf_lo(ws[m]);
+        S[2 * m + 1] = bf_hi(ws[m]);
+        C[2 * m] = bf_lo(wc[m]);
+        C[2 * m + 1] = bf_hi(wc[m]);
+        N[2 * m] = bf_lo(wn[m]);
+        N[2 * m + 1] = bf_hi(wn[m]);
+      }
+      float left = __shfl_sync(0xffffffffu, C[7], (lane + 31) & 31);
+      float right = __shfl_sync(0xffffffffu, C[0], (lane + 1) & 31);
+      if (lane == 0) left = bf_widen(hl[(r + 1) * 8 + 7]);
+      if (lane == 31) right = bf_widen(hr[(r + 1) * 8]);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const float w = q == 0 ? left : C[q - 1];
+        const float e = q == 7 ? right : C[q + 1];
+        float acc = 4.f * C[q];
+        acc -= w;
+        acc -= e;
+        acc -= S[q];
+        acc -= N[q];
+        Y[q] = acc;
+      }
+      const int j = y0 + r;
+      if (!ok || j >= ny || xc >= nx) continue;
+      uint16_t* dst = y + (size_t)j * ld + xc;
+      const uint4 o = make_uint4(bf_pack2(Y[0], Y[1]), bf_pack2(Y[2], Y[3]), bf_pack2(Y[4], Y[5]),
+                                 bf_pack2(Y[6], Y[7]));
+      if (xc + 8 <= nx) {
+        *reinterpret_cast<uint4*>(dst) = o;
+      } else {
+        const uint32_t w[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          if (xc + q < nx) dst[q] = (uint16_t)((q & 1) ? (w[q >> 1] >> 16) : (w[q >> 1] & 0xffffu));
+      }
+    }
+    __syncthreads();  // every thread is done with this stage
+    if (threadIdx.x == 0 && t + kTmaStages * step < ntiles) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(t + kTmaStages * step, sidx);
+    }
+  }
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// LAP5CG_ERR_UNSUPPORTED when the tensor maps cannot be made (the caller
+// takes the register kernel).
+static int launch_apply_bf16_tma(int nx, int ny, int ld, const void* x, void* y, cudaStream_t st) {
+  const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return LAP5CG_ERR_UNSUPPORTED;
+  CUtensorMap mmain, mhalo;
+  const cuuint64_t dims[2] = {(cuuint64_t)nx, (cuuint64_t)ny};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  const cuuint32_t box_main[2] = {(cuuint32_t)kTmaW, (cuuint32_t)(kTmaH + 2)};
+  const cuuint32_t box_halo[2] = {8u, (cuuint32_t)(kTmaH + 2)};
+  const cuuint32_t estr[2] = {1u, 1u};
+  void* gx = const_cast<void*>(x);
+  if (enc(&mmain, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, gx, dims, strides, box_main, estr,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS ||
+      enc(&mhalo, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, gx, dims, strides, box_halo, estr,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return LAP5CG_ERR_UNSUPPORTED;
+  const int tiles_x = (nx + kTmaW - 1) / kTmaW;
+  const long long nt = (long long)tiles_x * ((ny + kTmaH - 1) / kTmaH);
+  if (nt > 0x7fffffffLL) return LAP5CG_ERR_UNSUPPORTED;
+  const size_t smem = (size_t)kTmaStages * kTmaStageBytes + 8 * kTmaStages;
+  static std::once_flag attr_once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(attr_once, [&] {
+    attr_err = cudaFuncSetAttribute(k_lap5_apply_bf16_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  });
+  if (attr_err != cudaSuccess) return LAP5CG_ERR_CUDA;
+  DevProps dp;
+  const int rc = dev_props(&dp);
+  if (rc != LAP5CG_OK) return rc;
+  // resident CTAs an SM, per device (the occupancy query costs microseconds of
+  // host time, which a kernel of tens of microseconds would otherwise wait for)
+  static std::atomic<int> occ_cache[128];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return LAP5CG_ERR_CUDA;
+  int occ = occ_cache[dev].load(std::memory_order_relaxed);
+  if (occ == 0) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_lap5_apply_bf16_tma, kTmaThreads, smem) != cudaSuccess ||
+        occ < 1)
+      occ = 1;
+    occ_cache[dev].store(occ, std::memory_order_relaxed);
+  }
+  const long long grid = std::min<long long>(nt, (long long)occ * dp.sms);
+  k_lap5_apply_bf16_tma<<<(unsigned)grid, kTmaThreads, smem, st>>>(mmain, mhalo, nx, ny, ld, static_cast<uint16_t*>(y),
+                                                                  tiles_x, (int)nt);
+  return cudaGetLastError() == cudaSuccess ? LAP5CG_OK : LAP5CG_ERR_CUDA;
+}
+
 template <class T, int V>
 static int launch_apply(int nx, int ny, int ld, const void* x, void* y, cudaStream_t st) {
   constexpr int R = kApplyRows;
@@ -185,7 +409,11 @@ int apply_dispatch(int nx, int ny, int ld, int dtype, const void* x, void* y, cu
       if (ld % 4 == 0 && aligned(x, 16) && aligned(y, 16)) return launch_apply<float, 8>(nx, ny, ld, x, y, st);
       return launch_apply<float, 1>(nx, ny, ld, x, y, st);
     case LAP5CG_DT_BF16:
-      if (ld % 8 == 0 && aligned(x, 16) && aligned(y, 16)) return launch_apply_bf16x16(nx, ny, ld, x, y, st);
+      if (ld % 8 == 0 && aligned(x, 16) && aligned(y, 16)) {
+        const int rc = launch_apply_bf16_tma(nx, ny, ld, x, y, st);
+        if (rc != LAP5CG_ERR_UNSUPPORTED) return rc;
+        return launch_apply_bf16x16(nx, ny, ld, x, y, st);
+      }
       if (ld % 4 == 0 && aligned(x, 8) && aligned(y, 8)) return launch_apply<bf16s, 4>(nx, ny, ld, x, y, st);
       return launch_apply<bf16s, 1>(nx, ny, ld, x, y, st);
     default:

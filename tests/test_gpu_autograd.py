@@ -86,12 +86,15 @@ def test_gradient_workload_2048x16(precision):
     g = b.grad.detach().cpu().numpy()
     rhs = x.detach().cpu().numpy() - xt0
     # The adjoint equation A g = x - x_target for every right-hand side,
-    # residual by the oracle's stencil.  Binary64 CG stops on its recursive
-    # residual (1e-10); the adjoint right-hand side x - x_target is dominated
-    # by the Gaussian x_target, and for it the true residual of binary64 CG
-    # levels off above the recursive one (CG's attainable accuracy: rounding
-    # in the x and r recurrences, here ~1e-9 at kappa = 1.7e6); the
-    # refinement and multigrid paths stop on the FP64 true residual itself.
+    # residual by the oracle's stencil.  The adjoint right-hand side is
+    # dominated by the smooth forward solution (||x|| ~ 1.2e5 against
+    # ||x_target|| ~ 2e3).  Binary64 CG stops on its recursive residual
+    # (1e-10), and its true residual levels off above that (attainable
+    # accuracy: rounding in the x and r recurrences, here ~3e-9 at
+    # kappa = 1.7e6); the refinement and multigrid paths stop on the FP64 true
+    # residual itself.  For the refinement, kappa * u32 ~ 0.1 on these smooth
+    # modes: its first binary32 correction can raise the residual's 2-norm
+    # while removing nearly all of the error's energy, and the guard keeps it.
     rels = []
     for s in range(k):
         res = rhs[s] - oracle.lap5_apply(g[s])

@@ -44,19 +44,22 @@ def test_f32_bit_exact(nx, ny, pitch):
     np.testing.assert_array_equal(y[:, :nx], ref[:, :nx])
 
 
-@pytest.mark.parametrize("nx,ny", [(1, 1), (3, 5), (64, 64), (129, 70), (300, 257), (513, 19), (1000, 37),
-                                   (2049, 17)])
-@pytest.mark.parametrize("pitch", ["tight", "aligned", "quad"])
+@pytest.mark.parametrize("nx,ny", [(1, 1), (3, 5), (7, 16), (8, 300), (64, 64), (129, 70), (256, 16), (256, 33),
+                                   (264, 1), (300, 257), (513, 19), (1000, 37), (2049, 17)])
+@pytest.mark.parametrize("pitch", ["tight", "aligned", "quad", "wide"])
 def test_bf16_bit_exact(nx, ny, pitch):
-    # aligned: ld a multiple of 8 (sixteen columns a lane, two 16-byte groups);
-    # quad: ld = 4 mod 8 (four columns a lane); tight: scalar accesses
-    ld = {"tight": nx, "aligned": gen.pitch(nx, 2), "quad": gen.pitch(nx, 2) + 4}[pitch]
+    # aligned / wide: ld a multiple of 8 (TMA tiles of 16 rows x 256 columns,
+    # the zero fill standing for every operand outside the grid); quad:
+    # ld = 4 mod 8 (four columns a lane); tight: scalar accesses
+    ld = {"tight": nx, "aligned": gen.pitch(nx, 2), "quad": gen.pitch(nx, 2) + 4, "wide": gen.pitch(nx, 2) + 24}[pitch]
     xf = gen.uniform_rhs(nx, ny, seed=nx + ny, ld=ld, dtype=np.float32)
     xb = oracle.f32_to_bf16_bits(xf)
+    xb[:, nx:] = 0x4049  # padding (3.14) must not leak into the result
     xt = torch.from_numpy(xb.view(np.int16)).to("cuda").view(torch.bfloat16)
     y = lap5cg.lap5_apply(xt, nx=nx).view(torch.int16).cpu().numpy().view(np.uint16)
     ref = oracle.lap5_apply(xb, nx=nx, dtype="bf16")
     np.testing.assert_array_equal(y[:, :nx], ref[:, :nx])
+    assert not y[:, nx:].any()  # padding untouched (the output started at zero)
 
 
 def test_eigenvector_closed_form_on_gpu():
