@@ -567,7 +567,9 @@ def main():
     ap.add_argument("--profile-f32", type=int, default=0,
                     help="profiling only: run the binary32 8192^2 solve for this many iterations and exit")
     ap.add_argument("--profile-apply", type=int, default=0,
-                    help="profiling case: lap5_apply on an N x N binary32 grid, twice (for ncu)")
+                    help="profiling case: lap5_apply on an N x N grid, twice (for ncu)")
+    ap.add_argument("--profile-apply-dtype", default="f32", choices=["f32", "bf16", "f64"],
+                    help="storage type of the --profile-apply case")
     ap.add_argument("--profile-mg", type=int, default=0,
                     help="profiling only: solve the n^2 manufactured problem to 1e-10 twice with the multigrid-"
                          "preconditioned CG (binary32 V-cycle) and exit")
@@ -584,12 +586,14 @@ def main():
     if args.profile_apply:
         lap5cg.lib()
         n = args.profile_apply
-        xa = torch.from_numpy(gen.uniform_rhs(n, n, seed=5).astype(np.float32)).to(torch.device("cuda", 0))
+        dt = {"f32": torch.float32, "bf16": torch.bfloat16, "f64": torch.float64}[args.profile_apply_dtype]
+        xa = torch.from_numpy(gen.uniform_rhs(n, n, seed=5)).to(torch.device("cuda", 0)).to(dt)
         ya = torch.empty_like(xa)
         for _ in range(2):
             lap5cg.lap5_apply(xa, out=ya)
         torch.cuda.synchronize()
-        print(json.dumps({"profiling_case": {"lap5_apply": "f32", "n": n, "checksum": float(ya.double().sum())}}))
+        print(json.dumps({"profiling_case": {"lap5_apply": args.profile_apply_dtype, "n": n,
+                                             "checksum": float(ya.double().sum())}}))
         return 0
 
     if args.profile_mg:

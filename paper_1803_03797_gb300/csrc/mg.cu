@@ -111,7 +111,7 @@ __device__ __forceinline__ void pcg_solve(const PcgArgs<TM>& a, const MgLevel<TM
             load_row<V>(a.r, j, xl, c.nx, rv);
             load_row<V>(Grid<const TM>{vc.it(0), L0.ld}, j, xl, c.nx, zt);
 #pragma unroll
-            for (int k = 0; k < V; ++k) zv[k] = (double)zt[k];
+            for (int k = 0; k < V; ++k) zv[k] = mg_widen(zt[k]);
             acc_dot<V>(arz, j, rv, zv, c.nx - xl);
           }
         }
@@ -139,7 +139,7 @@ __device__ __forceinline__ void pcg_solve(const PcgArgs<TM>& a, const MgLevel<TM
           const int xs = s * 32 * V, xl = Lanes<V>::first(xs, wk.lane);
           const int nval = c.nx - xl;
           auto zone = [&](int j, int x) -> double {
-            return (x < 0 || x >= c.nx) ? 0.0 : (double)gz.row(j)[x];
+            return (x < 0 || x >= c.nx) ? 0.0 : mg_widen(gz.row(j)[x]);
           };
           auto pone = [&](int j, int x) -> double { return (x < 0 || x >= c.nx) ? 0.0 : pold.row(j)[x]; };
           auto field = [&](int j, FRow<V, double>& f) {
@@ -148,14 +148,14 @@ __device__ __forceinline__ void pcg_solve(const PcgArgs<TM>& a, const MgLevel<TM
             load_row<V>(gz, j, xl, c.nx, zt);
             if (first) {
 #pragma unroll
-              for (int k = 0; k < V; ++k) f.f[k] = (double)zt[k];
+              for (int k = 0; k < V; ++k) f.f[k] = mg_widen(zt[k]);
               f.hl = (wk.lane == 0) ? zone(j, xs - 1) : 0.0;
               f.hr = (wk.lane == 31) ? zone(j, xs + 32 * V) : 0.0;
             } else {
               double pv[V];
               load_row<V>(pold, j, xl, c.nx, pv);
 #pragma unroll
-              for (int k = 0; k < V; ++k) f.f[k] = __fma_rn(beta, pv[k], (double)zt[k]);
+              for (int k = 0; k < V; ++k) f.f[k] = __fma_rn(beta, pv[k], mg_widen(zt[k]));
               f.hl = (wk.lane == 0) ? __fma_rn(beta, pone(j, xs - 1), zone(j, xs - 1)) : 0.0;
               f.hr = (wk.lane == 31) ? __fma_rn(beta, pone(j, xs + 32 * V), zone(j, xs + 32 * V)) : 0.0;
             }

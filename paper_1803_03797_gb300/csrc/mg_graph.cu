@@ -52,7 +52,7 @@ __global__ void k_gm_bind(GmBind* bd, const double* b, double* x, lap5cg_info* i
   if (threadIdx.x == 0 && blockIdx.x == 0) *bd = GmBind{b, x, info, history, tol, maxit, 0};
 }
 
-enum { GP_JAC = 0, GP_JAC_DOT, GP_RES, GP_RESTRICT, GP_PROLONG };
+enum { GP_JAC = 0, GP_JAC_DOT, GP_RES, GP_RESTRICT, GP_PROLONG, GP_RES_RESTRICT, GP_PROLONG_JAC };
 
 // Block-wide sums of NV per-thread values into part[blockIdx.x * 2 + k].
 template <int NV>
@@ -131,36 +131,409 @@ __global__ void __launch_bounds__(kGmThreads) k_gm_pass(const GmScal* sc, double
   }
 }
 
+// Jacobi sweep / residual of a big level in the layout of lap5_apply: each
+// warp takes R = 2 output rows of one strip of 32 V columns and loads its R + 2
+// operand rows and R right-hand-side rows before finishing the first, so no
+// load waits on another (binary32: V = 8, two 16-byte groups a lane; binary64:
+// V = 2).  CTAs stride over the tiles (8 warps x R rows x one strip).  Same
+// arithmetic per point as mg_stencil_pass.
+template <class TM> struct GmSweepVec { static constexpr int V = sizeof(TM) == 4 ? 8 : 2; };
+
+// from_b: the input iterate is the level's first sweep from zero, c b, which is
+// formed from b here (the producer of b then stores no iterate).
+template <class TM, int MODE>
+__global__ void __launch_bounds__(kGmThreads) k_gm_sweep(const GmScal* sc, double*, MgLevel<TM> L, const TM* in,
+                                                          TM* out, Grid<const double>, int from_b) {
+  if (sc->stop) return;
+  constexpr int V = GmSweepVec<TM>::V, R = 2;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpc = blockDim.x >> 5;
+  const int ns = (L.nx + 32 * V - 1) / (32 * V);
+  const int band = wpc * R;
+  const int ntiles = ns * ((L.ny + band - 1) / band);
+  const Grid<const TM> gi{in, L.ld}, gb{L.b, L.ld};
+  const Grid<TM> go{out, L.ld};
+  const TM c = (TM)kMgC;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int st = t % ns;
+    const int jb = (t / ns) * band + warp * R;
+    if (jb >= L.ny) continue;
+    const int xs = st * 32 * V, xl = Lanes<V>::first(xs, lane);
+    FRow<V, TM> f[R + 2];  // operand rows jb - 1 .. jb + R
+    TM bv[R][V];
+#pragma unroll
+    for (int k = 0; k < R + 2; ++k) {
+      field_plain<V>(from_b ? gb : gi, L.nx, L.ny, jb - 1 + k, xl, xs, lane, f[k]);
+      if (from_b) {
+#pragma unroll
+        for (int q = 0; q < V; ++q) f[k].f[q] = c * f[k].f[q];
+        f[k].hl = c * f[k].hl;
+        f[k].hr = c * f[k].hr;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      if (jb + k < L.ny) {
+        load_row<V>(gb, jb + k, xl, L.nx, bv[k]);
+      } else {
+#pragma unroll
+        for (int q = 0; q < V; ++q) bv[k][q] = TM(0);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      const int j = jb + k;
+      if (j >= L.ny) break;
+      TM ax[V], o[V];
+      stencil_row<V>(f[k], f[k + 1], f[k + 2], lane, ax);
+#pragma unroll
+      for (int q = 0; q < V; ++q)
+        o[q] = MODE == GP_RES ? bv[k][q] - ax[q] : mg_fma(c, bv[k][q] - ax[q], f[k + 1].f[q]);
+      store_row<V>(go, j, xl, L.nx, o);
+    }
+  }
+}
+
 // The levels of at most kMgCtaPoints points, from `first` (whose b and first
-// sweep the restriction wrote) down to the coarsest and back, on one CTA.
+// sweep the restriction wrote) down to the coarsest and back, on one CTA with
+// every level resident in its shared memory: level `first`'s b and u are
+// copied in, the point-wise passes above run between CTA barriers, and level
+// `first`'s final iterate is copied back to the buffer the next pass reads.
 template <class TM>
 struct GmLevels {
   MgLevel<TM> lv[kMgMaxLevels];
 };
 
+// Shared memory of k_gm_small: b, u, v of every level from `first` on.
 template <class TM>
+__host__ __device__ inline size_t gm_small_array_bytes(const MgLevel<TM>& L) {
+  return align_up((size_t)L.ny * (size_t)L.ld * sizeof(TM), 16);
+}
+template <class TM>
+static size_t gm_small_smem(const MgLevel<TM>* lv, int first, int nlev) {
+  size_t s = 0;
+  for (int l = first; l < nlev; ++l) s += 3 * gm_small_array_bytes(lv[l]);
+  return s;
+}
+
+// Residual and restriction in one pass (a level's residual is read only by
+// the restriction): C.b = P^T (b - A u), C.u = c C.b.  Two coarse columns a
+// lane (fine columns f0 .. f0+3 of the lane and f0+4 of the next, as in
+// mg_restrict); coarse rows march upwards, and the fine residual rows 2J,
+// 2J+1, 2J+2 are formed in registers from a march over u, the even row shared
+// between consecutive coarse rows.  The residual and the restriction take the
+// operations of mg_stencil_pass and mg_restrict in the same order, so C.b is
+// the same as from the two passes; the level's residual is never stored.
+// write_u = 0: C.u (c C.b) is not stored; its first reader forms it from C.b.
+template <class TM>
+__global__ void __launch_bounds__(kGmThreads) k_gm_res_restrict(const GmScal* sc, MgLevel<TM> F, const TM* u,
+                                                                MgLevel<TM> C, int write_u) {
+  if (sc->stop) return;
+  const Sched s = gm_sched(0);
+  const Units un = make_units(C.nx, C.ny, 2, s.nw, 2);
+  const Grid<const TM> gu{u, F.ld}, gb{F.b, F.ld};
+  const Grid<TM> gcb{C.b, C.ld}, gcu{C.u, C.ld};
+  const TM c = (TM)kMgC;
+  for (int w = s.w; w < un.nunits; w += s.nw) {
+    int st, y0, y1;
+    unit_bounds(un, w, C.ny, st, y0, y1);
+    const int xs = st * 128, f0 = xs + 4 * s.lane, I0 = f0 / 2;
+    auto field = [&](int j, FRow<4, TM>& f) { field_plain<4>(gu, F.nx, F.ny, j, f0, xs, s.lane, f); };
+    // residual of fine row j at columns f0 .. f0+4 (zero outside the grid)
+    auto res_row = [&](int j, const FRow<4, TM>& S, const FRow<4, TM>& Cr, const FRow<4, TM>& N, TM (&r)[5]) {
+      if (j < 0 || j >= F.ny) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) r[k] = TM(0);
+        return;
+      }
+      TM ax[4], bv[4];
+      stencil_row<4>(S, Cr, N, s.lane, ax);
+      load_row<4>(gb, j, f0, F.nx, bv);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) r[k] = f0 + k < F.nx ? bv[k] - ax[k] : TM(0);
+      TM e = __shfl_down_sync(0xffffffffu, r[0], 1);
+      if (s.lane == 31) {  // column xs + 128: the next strip's first, formed here
+        const int xe = xs + 128;
+        e = TM(0);
+        if (xe < F.nx) {
+          TM acc = TM(4) * Cr.hr;
+          acc -= Cr.f[3];
+          acc -= xe + 1 < F.nx ? gu.row(j)[xe + 1] : TM(0);
+          acc -= S.hr;
+          acc -= N.hr;
+          e = gb.row(j)[xe] - acc;
+        }
+      }
+      r[4] = e;
+    };
+    FRow<4, TM> fS, fC, fN;
+    TM lo[5], mid[5], hi[5];
+    int j = 2 * y0;
+    field(j - 1, fS);
+    field(j, fC);
+    field(j + 1, fN);
+    res_row(j, fS, fC, fN, lo);
+    for (int J = y0; J < y1; ++J) {
+      fS = fC; fC = fN; field(2 * J + 2, fN);
+      res_row(2 * J + 1, fS, fC, fN, mid);
+      fS = fC; fC = fN; field(2 * J + 3, fN);
+      res_row(2 * J + 2, fS, fC, fN, hi);
+      TM bc[2], uc[2];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int wq = 2 * q, m = wq + 1, e = wq + 2;
+        const TM s1 = ((mid[wq] + mid[e]) + lo[m]) + hi[m];
+        const TM s2 = ((lo[wq] + lo[e]) + hi[wq]) + hi[e];
+        bc[q] = TM(0.25) * ((TM(4) * mid[m] + TM(2) * s1) + s2);
+        uc[q] = c * bc[q];
+      }
+      store_row<2>(gcb, J, I0, C.nx, bc);
+      if (write_u) store_row<2>(gcu, J, I0, C.nx, uc);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) lo[k] = hi[k];
+    }
+  }
+}
+
+// Prolongation and the first post-smoothing sweep in one pass: out = u' + c (b -
+// A u') with u' = u + P e, u' formed in registers (never stored).  Tiles as in
+// k_gm_sweep, with one group of four columns a lane (the prolongation's lane
+// layout); the coarse values a lane needs (3 coarse rows x 3 columns, 4 for
+// lane 31's halo) are read once per tile.  u' takes mg_prolong's operations
+// and the sweep mg_stencil_pass's, in the same order.
+template <class TM>
+__global__ void __launch_bounds__(kGmThreads) k_gm_prolong_jac(const GmScal* sc, MgLevel<TM> L, const TM* u,
+                                                               MgLevel<TM> C, const TM* e, TM* out) {
+  if (sc->stop) return;
+  constexpr int V = 4, R = 2;
+  static_assert(R == 2, "cv holds the three coarse rows of R + 2 = 4 fine rows");
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpc = blockDim.x >> 5;
+  const int ns = (L.nx + 32 * V - 1) / (32 * V);
+  const int band = wpc * R;
+  const int ntiles = ns * ((L.ny + band - 1) / band);
+  const Grid<const TM> gu{u, L.ld}, gb{L.b, L.ld}, ge{e, C.ld};
+  const Grid<TM> go{out, L.ld};
+  const TM c = (TM)kMgC;
+  auto ce = [&](int I, int J) -> TM { return (I < 0 || I >= C.nx || J < 0 || J >= C.ny) ? TM(0) : ge.row(J)[I]; };
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int st = t % ns;
+    const int jb = (t / ns) * band + warp * R;  // even
+    if (jb >= L.ny) continue;
+    const int xs = st * 32 * V, f0 = xs + 4 * lane, I0 = f0 / 2, Jc0 = jb / 2 - 1;
+    // coarse rows Jc0 .. Jc0+2, columns I0-1 .. I0+2 (the last for lane 31's halo)
+    TM cv[3][4];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) cv[a][q] = (q == 3 && lane != 31) ? TM(0) : ce(I0 - 1 + q, Jc0 + a);
+    // u' of fine row j = jb - 1 + k: the lane's 4 columns, and the strip's halo
+    // columns (jb is even: k = 0, 2 are odd rows on coarse row k / 2 of cv,
+    // k = 1, 3 even rows between coarse rows (k - 1) / 2 and (k + 1) / 2)
+    auto field = [&](int k, FRow<V, TM>& f) {
+      const int j = jb - 1 + k;
+      if (j < 0 || j >= L.ny) { f.zero(); return; }
+      field_plain<V>(gu, L.nx, L.ny, j, f0, xs, lane, f);
+      TM v[4], vl, vr;
+      if ((k & 1) == 0) {
+        const int a = k >> 1;
+        v[0] = TM(0.5) * (cv[a][0] + cv[a][1]);
+        v[1] = cv[a][1];
+        v[2] = TM(0.5) * (cv[a][1] + cv[a][2]);
+        v[3] = cv[a][2];
+        vl = cv[a][0];                                  // column f0 - 1 (odd): coarse I0 - 1
+        vr = TM(0.5) * (cv[a][2] + cv[a][3]);           // column f0 + 4 (even)
+      } else {
+        const int ia = (k + 1) >> 1, ib = ia - 1;
+        v[0] = TM(0.25) * ((cv[ib][0] + cv[ib][1]) + (cv[ia][0] + cv[ia][1]));
+        v[1] = TM(0.5) * (cv[ib][1] + cv[ia][1]);
+        v[2] = TM(0.25) * ((cv[ib][1] + cv[ib][2]) + (cv[ia][1] + cv[ia][2]));
+        v[3] = TM(0.5) * (cv[ib][2] + cv[ia][2]);
+        vl = TM(0.5) * (cv[ib][0] + cv[ia][0]);
+        vr = TM(0.25) * ((cv[ib][2] + cv[ib][3]) + (cv[ia][2] + cv[ia][3]));
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) f.f[k] = f0 + k < L.nx ? f.f[k] + v[k] : TM(0);
+      if (lane == 0) f.hl = (xs >= 1 && xs - 1 < L.nx) ? f.hl + vl : TM(0);
+      if (lane == 31) f.hr = (xs + 32 * V < L.nx) ? f.hr + vr : TM(0);
+    };
+    FRow<V, TM> fr[R + 2];
+#pragma unroll
+    for (int k = 0; k < R + 2; ++k) field(k, fr[k]);
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      const int j = jb + k;
+      if (j >= L.ny) break;
+      TM ax[V], bv[V], o[V];
+      load_row<V>(gb, j, f0, L.nx, bv);
+      stencil_row<V>(fr[k], fr[k + 1], fr[k + 2], lane, ax);
+#pragma unroll
+      for (int q = 0; q < V; ++q) o[q] = mg_fma(c, bv[q] - ax[q], fr[k + 1].f[q]);
+      store_row<V>(go, j, f0, L.nx, o);
+    }
+  }
+}
+
+// Point-wise forms of the V-cycle's passes for the single-CTA levels: one
+// thread a point, no warp-level march (at a few thousand points a pass the
+// march's dependent row chain, not bandwidth, set the time).  Same operations
+// in the same order as mg_stencil_pass, mg_restrict and mg_prolong.
+template <class TM>
+__device__ __forceinline__ TM tiny_at(const TM* g, int nx, int ny, int ld, int i, int j) {
+  return (i < 0 || i >= nx || j < 0 || j >= ny) ? TM(0) : g[j * ld + i];
+}
+
+template <class TM, bool JAC>
+__device__ void tiny_stencil(const MgLevel<TM>& L, const TM* in, TM* out) {
+  const TM c = (TM)kMgC;
+  const int n = L.nx * L.ny;
+  for (int p = threadIdx.x; p < n; p += blockDim.x) {
+    const int j = p / L.nx, i = p - j * L.nx;
+    const TM C = in[j * L.ld + i];
+    TM acc = TM(4) * C;
+    acc -= tiny_at(in, L.nx, L.ny, L.ld, i - 1, j);
+    acc -= tiny_at(in, L.nx, L.ny, L.ld, i + 1, j);
+    acc -= tiny_at(in, L.nx, L.ny, L.ld, i, j - 1);
+    acc -= tiny_at(in, L.nx, L.ny, L.ld, i, j + 1);
+    const TM b = L.b[j * L.ld + i];
+    out[j * L.ld + i] = JAC ? mg_fma(c, b - acc, C) : b - acc;
+  }
+}
+
+// coarse C.b = P^T res, C.u = c C.b
+template <class TM>
+__device__ void tiny_restrict(const MgLevel<TM>& F, const TM* res, const MgLevel<TM>& C) {
+  const TM c = (TM)kMgC;
+  const int n = C.nx * C.ny;
+  for (int p = threadIdx.x; p < n; p += blockDim.x) {
+    const int J = p / C.nx, I = p - J * C.nx;
+    const int fi = 2 * I + 1, fj = 2 * J + 1;
+    auto r = [&](int di, int dj) { return tiny_at(res, F.nx, F.ny, F.ld, fi + di, fj + dj); };
+    const TM s1 = ((r(-1, 0) + r(1, 0)) + r(0, -1)) + r(0, 1);
+    const TM s2 = ((r(-1, -1) + r(1, -1)) + r(-1, 1)) + r(1, 1);
+    const TM bc = TM(0.25) * ((TM(4) * r(0, 0) + TM(2) * s1) + s2);
+    C.b[J * C.ld + I] = bc;
+    C.u[J * C.ld + I] = c * bc;
+  }
+}
+
+// f += P e
+template <class TM>
+__device__ void tiny_prolong(const MgLevel<TM>& F, TM* f, const MgLevel<TM>& C, const TM* e) {
+  const int n = F.nx * F.ny;
+  for (int p = threadIdx.x; p < n; p += blockDim.x) {
+    const int j = p / F.nx, i = p - j * F.nx;
+    auto ce = [&](int I, int J) { return tiny_at(e, C.nx, C.ny, C.ld, I, J); };
+    TM v;
+    if (j & 1) {
+      const int J = j >> 1;
+      v = (i & 1) ? ce(i >> 1, J) : TM(0.5) * (ce((i >> 1) - 1, J) + ce(i >> 1, J));
+    } else {
+      const int J = j >> 1;
+      if (i & 1) {
+        const int I = i >> 1;
+        v = TM(0.5) * (ce(I, J - 1) + ce(I, J));
+      } else {
+        const int I = i >> 1;
+        v = TM(0.25) * ((ce(I - 1, J - 1) + ce(I, J - 1)) + (ce(I - 1, J) + ce(I, J)));
+      }
+    }
+    f[j * F.ld + i] += v;
+  }
+}
+
+// The V-cycle from level `first` down to the coarsest and back with the
+// point-wise passes, CTA barriers between them; returns the parity of the
+// buffer that holds level `first`'s result (0: u, 1: v).
+template <class TM>
+__device__ int tiny_vcycle(const MgLevel<TM>* lv, int nlev, int first, int nu, int nu_c) {
+  int cur[kMgMaxLevels];
+  auto it = [&](int l) -> TM* { return cur[l] ? lv[l].v : lv[l].u; };
+  auto other = [&](int l) -> TM* { return cur[l] ? lv[l].u : lv[l].v; };
+  auto jac = [&](int l) {
+    tiny_stencil<TM, true>(lv[l], it(l), other(l));
+    cur[l] ^= 1;
+    __syncthreads();
+  };
+  cur[first] = 0;
+  for (int l = first; l < nlev - 1; ++l) {
+    for (int k = 1; k < nu; ++k) jac(l);
+    tiny_stencil<TM, false>(lv[l], it(l), other(l));
+    __syncthreads();
+    tiny_restrict(lv[l], other(l), lv[l + 1]);
+    __syncthreads();
+    cur[l + 1] = 0;
+  }
+  for (int k = 1; k < nu_c; ++k) jac(nlev - 1);
+  for (int l = nlev - 2; l >= first; --l) {
+    tiny_prolong(lv[l], it(l), lv[l + 1], it(l + 1));
+    __syncthreads();
+    for (int k = 0; k < nu; ++k) jac(l);
+  }
+  return cur[first];
+}
+
+// The levels [first, nlev) on the calling CTA (every thread of it), resident
+// in its dynamic shared memory when SMEM (else in global memory); level
+// `first`'s final iterate ends in its global buffer (u or v as the V-cycle's
+// parity says).  lv: a shared-memory array of kMgMaxLevels descriptors.
+template <class TM, bool SMEM>
+__device__ void gm_small_levels(const GmLevels<TM>& levels, int nlev, int first, int nu, int nu_c,
+                                unsigned char* gsm, MgLevel<TM>* lv) {
+  if (threadIdx.x == 0) {
+    size_t off = 0;
+    for (int l = 0; l < kMgMaxLevels; ++l) {
+      MgLevel<TM> L = levels.lv[l];
+      if (SMEM && l >= first && l < nlev) {
+        const size_t nb = gm_small_array_bytes(L);
+        L.b = reinterpret_cast<TM*>(gsm + off);
+        L.u = reinterpret_cast<TM*>(gsm + off + nb);
+        L.v = reinterpret_cast<TM*>(gsm + off + 2 * nb);
+        off += 3 * nb;
+      }
+      lv[l] = L;
+    }
+  }
+  __syncthreads();
+  // level `first`'s first sweep from zero, c b, formed here (its producer may
+  // not have stored it)
+  const MgLevel<TM>& G = levels.lv[first];
+  const int n0 = G.ny * G.ld;
+  const TM c = (TM)kMgC;
+  for (int i = threadIdx.x; i < n0; i += blockDim.x) {
+    const TM bi = G.b[i];
+    if (SMEM) lv[first].b[i] = bi;
+    lv[first].u[i] = c * bi;
+  }
+  __syncthreads();
+  const int par = tiny_vcycle<TM>(lv, nlev, first, nu, nu_c);
+  if (SMEM) {
+    const TM* res = par ? lv[first].v : lv[first].u;
+    TM* dst = par ? G.v : G.u;
+    for (int i = threadIdx.x; i < n0; i += blockDim.x) dst[i] = res[i];
+  }
+}
+
+// Which buffer holds level l's iterate after a V-cycle from l: 2 nu - 1 sweeps
+// (nu - 1 down, nu up), or nu_c - 1 on the coarsest level.
+__host__ __device__ inline int gm_final_parity(int l, int nlev, int nu, int nu_c) {
+  return (l < nlev - 1 ? 2 * nu - 1 : nu_c - 1) & 1;
+}
+
+// SMEM = false: the levels stay in global memory (shapes whose levels do not
+// fit in shared memory, e.g. one column wide with a padded pitch).
+template <class TM, bool SMEM>
 __global__ void __launch_bounds__(512) k_gm_small(const GmScal* sc, GmLevels<TM> levels, int nlev, int first, int nu,
                                                   int nu_c) {
   if (sc->stop) return;
-  __shared__ double red[kRedDoubles];
+  extern __shared__ __align__(16) unsigned char gsm[];
   __shared__ MgLevel<TM> lv[kMgMaxLevels];
-  if (threadIdx.x < kMgMaxLevels) lv[threadIdx.x] = levels.lv[threadIdx.x];
-  __syncthreads();
-  GridTeam tm{nullptr, 0, 0ull};  // never synchronised: every level here is CTA-local
-  const int wpc = blockDim.x >> 5;
-  const Sched cta{(int)(threadIdx.x >> 5), wpc, (int)(threadIdx.x & 31), false};
-  Vcycle<TM> vc{nlev, first, nu, nu_c, lv, tm, red, cta, cta, Grid<const double>{nullptr, 0}, nullptr, {}, true,
-                false, 0u};
-  vc.cur[first] = 0;
-  for (int l = first; l < nlev - 1; ++l) vc.down(l);
-  vc.sweeps(nlev - 1, nu_c, false);
-  for (int l = nlev - 2; l >= first; --l) vc.up(l);
+  gm_small_levels<TM, SMEM>(levels, nlev, first, nu, nu_c, gsm, lv);
 }
 
-// r = b - A x, level 0: b = r (rounded to TM), u = c b; partials (b, b), (r, r).
+// r = b - A x, level 0: b = r (rounded to TM), u = c b (write_u); partials
+// (b, b), (r, r).
 template <class TM>
 __global__ void __launch_bounds__(kGmThreads) k_gm_init(const GmBind* bd, double* part, int nx, int ny, int ld,
-                                                         Grid<double> r, MgLevel<TM> L0) {
+                                                         Grid<double> r, MgLevel<TM> L0, int write_u) {
   constexpr int V = 2;
   const Grid<const double> b{bd->b, ld};
   const Grid<double> x{bd->x, ld};
@@ -181,7 +554,20 @@ __global__ void __launch_bounds__(kGmThreads) k_gm_init(const GmBind* bd, double
                       const FRow<V, double>& N) {
       double ax[V], rv[V];
       TM rb[V], ru[V];
-      stencil_row<V>(S, C, N, s.lane, ax);
+      // x = 0 on these three rows (the usual zero start): A x = 0 without the
+      // binary64 stencil, whose 4 operations a point on the FP64 pipe are most
+      // of this pass (a warp-uniform test on the bits)
+      bool zero = ((__double_as_longlong(C.hl) | __double_as_longlong(C.hr)) << 1) == 0;
+#pragma unroll
+      for (int k = 0; k < V; ++k)
+        zero = zero && ((__double_as_longlong(S.f[k]) | __double_as_longlong(C.f[k]) |
+                         __double_as_longlong(N.f[k])) << 1) == 0;
+      if (__all_sync(0xffffffffu, zero)) {
+#pragma unroll
+        for (int k = 0; k < V; ++k) ax[k] = 0.0;
+      } else {
+        stencil_row<V>(S, C, N, s.lane, ax);
+      }
 #pragma unroll
       for (int k = 0; k < V; ++k) {
         rv[k] = d.b[k] - ax[k];
@@ -192,7 +578,7 @@ __global__ void __launch_bounds__(kGmThreads) k_gm_init(const GmBind* bd, double
       acc_dot<V>(arr, j, rv, rv, nval);
       store_row<V>(r, j, xl, nx, rv);
       store_row<V>(g0b, j, xl, nx, rb);
-      store_row<V>(g0u, j, xl, nx, ru);
+      if (write_u) store_row<V>(g0u, j, xl, nx, ru);
     };
     march<V, double, D>(y0, y1, false, field, load, finish);
   }
@@ -265,7 +651,7 @@ __global__ void __launch_bounds__(kGmThreads) k_gm_pq(const GmScal* sc, double* 
     unit_bounds(un, u, ny, st, y0, y1);
     const int xs = st * 32 * V, xl = Lanes<V>::first(xs, s.lane);
     const int nval = nx - xl;
-    auto zone = [&](int j, int xx) -> double { return (xx < 0 || xx >= nx) ? 0.0 : (double)gz.row(j)[xx]; };
+    auto zone = [&](int j, int xx) -> double { return (xx < 0 || xx >= nx) ? 0.0 : mg_widen(gz.row(j)[xx]); };
     auto pone = [&](int j, int xx) -> double { return (xx < 0 || xx >= nx) ? 0.0 : pold.row(j)[xx]; };
     auto field = [&](int j, FRow<V, double>& f) {
       if (j < 0 || j >= ny) { f.zero(); return; }
@@ -273,14 +659,14 @@ __global__ void __launch_bounds__(kGmThreads) k_gm_pq(const GmScal* sc, double* 
       load_row<V>(gz, j, xl, nx, zt);
       if (first) {
 #pragma unroll
-        for (int k = 0; k < V; ++k) f.f[k] = (double)zt[k];
+        for (int k = 0; k < V; ++k) f.f[k] = mg_widen(zt[k]);
         f.hl = (s.lane == 0) ? zone(j, xs - 1) : 0.0;
         f.hr = (s.lane == 31) ? zone(j, xs + 32 * V) : 0.0;
       } else {
         double pv[V];
         load_row<V>(pold, j, xl, nx, pv);
 #pragma unroll
-        for (int k = 0; k < V; ++k) f.f[k] = __fma_rn(beta, pv[k], (double)zt[k]);
+        for (int k = 0; k < V; ++k) f.f[k] = __fma_rn(beta, pv[k], mg_widen(zt[k]));
         f.hl = (s.lane == 0) ? __fma_rn(beta, pone(j, xs - 1), zone(j, xs - 1)) : 0.0;
         f.hr = (s.lane == 31) ? __fma_rn(beta, pone(j, xs + 32 * V), zone(j, xs + 32 * V)) : 0.0;
       }
@@ -313,11 +699,12 @@ __global__ void __launch_bounds__(256) k_gm_alpha(GmScal* sc, const double* part
   sc->cur ^= 1;
 }
 
-// x += alpha p, r -= alpha q, partial (r, r); level 0: b = r, u = c b.
+// x += alpha p, r -= alpha q, partial (r, r); level 0: b = r, u = c b (write_u).
 template <class TM>
 __global__ void __launch_bounds__(kGmThreads) k_gm_xr(const GmScal* sc, const GmBind* bd, double* part, int nx,
                                                        int ny, int ld, Grid<double> r, Grid<double> p0,
-                                                       Grid<double> p1, Grid<double> q, MgLevel<TM> L0, int rev) {
+                                                       Grid<double> p1, Grid<double> q, MgLevel<TM> L0, int rev,
+                                                       int write_u) {
   if (sc->stop) return;
   constexpr int V = 2;
   const Grid<double> x{bd->x, ld};
@@ -354,7 +741,7 @@ __global__ void __launch_bounds__(kGmThreads) k_gm_xr(const GmScal* sc, const Gm
       store_row<V>(x, j, xl, nx, xv);
       store_row<V>(r, j, xl, nx, rv);
       store_row<V>(g0b, j, xl, nx, rb);
-      store_row<V>(g0u, j, xl, nx, ru);
+      if (write_u) store_row<V>(g0u, j, xl, nx, ru);
     };
     stream_rows<D>(y0, y1, s.rev, load, finish);
   }
@@ -455,44 +842,62 @@ struct GmPassRec {
   int kind, level, rev;
   const TM* in;
   TM* out;
+  const TM* e;     // GP_PROLONG_JAC: the coarse iterate
+  int from_b = 0;  // GP_JAC: the input iterate is c b, formed from the level's b
 };
 
 // The V-cycle's passes on the big levels as Vcycle::run executes them (buffer
 // parities and march directions), with the single-CTA levels as one entry
-// (kind -1).  Returns the buffer that holds level 0's result (M^-1 r).
+// (kind -1).  fuse (binary32 V-cycle): residual + restriction and
+// prolongation + first post-smoothing sweep are single passes, and where every
+// level's first reader of its first sweep c b is a Jacobi sweep (*write_u =
+// false), that sweep forms c b from b and no producer stores it.  (A binary64
+// V-cycle keeps the separate passes: its fused forms measured slower, the
+// arithmetic, not the traffic, being its limit.)  Returns the buffer that
+// holds level 0's result (M^-1 r).
 template <class TM>
-static int gm_pass_list(const PcgArgs<TM>& a, std::vector<GmPassRec<TM>>& out) {
+static int gm_pass_list(const PcgArgs<TM>& a, bool fuse, std::vector<GmPassRec<TM>>& out, bool* write_u) {
   const int L = a.nlev, nu = a.nu;
+  *write_u = !fuse || nu < 2 || (a.lsmall >= L && a.nu_c < 2);
+  const int fb = *write_u ? 0 : 1;
   int cur[kMgMaxLevels] = {0};
   unsigned pc = 0;
   auto it = [&](int l) -> TM* { return cur[l] ? a.lv[l].v : a.lv[l].u; };
   auto other = [&](int l) -> TM* { return cur[l] ? a.lv[l].u : a.lv[l].v; };
-  auto jac = [&](int l, bool last) {
-    out.push_back({last ? GP_JAC_DOT : GP_JAC, l, (int)(pc++ & 1u), it(l), other(l)});
+  auto jac = [&](int l, bool last, int from_b) {
+    out.push_back({last ? GP_JAC_DOT : GP_JAC, l, (int)(pc++ & 1u), it(l), other(l), nullptr, from_b});
     cur[l] ^= 1;
   };
-  auto sweeps = [&](int l, int n, bool final0) {
-    for (int k = 1; k < n; ++k) jac(l, final0 && l == 0 && k == n - 1);
+  auto sweeps = [&](int l, int n, bool final0) {  // sweeps 2 .. n (the first, c b, came with b)
+    for (int k = 1; k < n; ++k) jac(l, final0 && l == 0 && k == n - 1, k == 1 ? fb : 0);
   };
   const int big_end = a.lsmall < L - 1 ? a.lsmall : L - 1;
   for (int l = 0; l < big_end; ++l) {  // down: pre-smoothing, residual, restriction
     sweeps(l, nu, false);
-    out.push_back({GP_RES, l, (int)(pc++ & 1u), it(l), other(l)});
-    out.push_back({GP_RESTRICT, l, (int)(pc++ & 1u), other(l), nullptr});
+    if (fuse) {
+      out.push_back({GP_RES_RESTRICT, l, (int)(pc++ & 1u), it(l), nullptr, nullptr});
+    } else {
+      out.push_back({GP_RES, l, (int)(pc++ & 1u), it(l), other(l), nullptr});
+      out.push_back({GP_RESTRICT, l, (int)(pc++ & 1u), other(l), nullptr, nullptr});
+    }
     cur[l + 1] = 0;
   }
   if (a.lsmall >= L) {
     sweeps(L - 1, a.nu_c, false);
   } else {
-    out.push_back({-1, big_end, 0, nullptr, nullptr});
-    // the single-CTA kernel leaves level big_end's iterate after 2 nu - 1
-    // sweeps (nu - 1 down, nu up), or nu_c - 1 if it is the coarsest
-    const int flips = big_end < L - 1 ? 2 * nu - 1 : a.nu_c - 1;
-    cur[big_end] = flips & 1;
+    out.push_back({-1, big_end, 0, nullptr, nullptr, nullptr});
+    cur[big_end] = gm_final_parity(big_end, L, nu, a.nu_c);
   }
   for (int l = big_end - 1; l >= 0; --l) {  // up: prolongation, post-smoothing
-    out.push_back({GP_PROLONG, l, (int)(pc++ & 1u), it(l + 1), it(l)});
-    for (int k = 0; k < nu; ++k) jac(l, l == 0 && k == nu - 1);
+    int k0 = 0;
+    if (fuse && !(l == 0 && nu == 1)) {  // (level 0's only sweep is the (r, z) sweep: not fused)
+      out.push_back({GP_PROLONG_JAC, l, (int)(pc++ & 1u), it(l), other(l), it(l + 1)});
+      cur[l] ^= 1;
+      k0 = 1;
+    } else {
+      out.push_back({GP_PROLONG, l, (int)(pc++ & 1u), it(l + 1), it(l), nullptr});
+    }
+    for (int k = k0; k < nu; ++k) jac(l, l == 0 && k == nu - 1, 0);
   }
   return cur[0];
 }
@@ -512,12 +917,13 @@ static std::mutex g_gm_mu;
 static std::vector<std::pair<GmKey, cudaGraphExec_t>> g_gm_cache;  // most recent last
 constexpr size_t kGmCacheSize = 8;
 
-static int gm_add(cudaGraph_t g, cudaGraphNode_t* prev, const void* fn, unsigned grid, unsigned block, void** args) {
+static int gm_add(cudaGraph_t g, cudaGraphNode_t* prev, const void* fn, unsigned grid, unsigned block, void** args,
+                  unsigned smem = 0) {
   cudaKernelNodeParams kp = {};
   kp.func = const_cast<void*>(fn);
   kp.gridDim = dim3(grid);
   kp.blockDim = dim3(block);
-  kp.sharedMemBytes = 0;
+  kp.sharedMemBytes = smem;
   kp.kernelParams = args;
   kp.extra = nullptr;
   cudaGraphNode_t n;
@@ -548,12 +954,21 @@ static int gm_build(const SolvePlan& p, const PcgArgs<TM>& a, cudaGraphExec_t* e
   const void* f_xr = reinterpret_cast<const void*>(&k_gm_xr<TM>);
   const void* f_true = reinterpret_cast<const void*>(&k_gm_true);
   const int nb_pass = gm_blocks(f_pass, kGmThreads, dp.sms);
+  const void* f_sweep_j = reinterpret_cast<const void*>(&k_gm_sweep<TM, GP_JAC>);
+  const void* f_sweep_r = reinterpret_cast<const void*>(&k_gm_sweep<TM, GP_RES>);
+  const int nb_sweep = gm_blocks(f_sweep_j, kGmThreads, dp.sms);
+  const void* f_rr = reinterpret_cast<const void*>(&k_gm_res_restrict<TM>);
+  const void* f_pj = reinterpret_cast<const void*>(&k_gm_prolong_jac<TM>);
+  const int nb_rr = gm_blocks(f_rr, kGmThreads, dp.sms);
+  const int nb_pj = gm_blocks(f_pj, kGmThreads, dp.sms);
   const int nb_init = gm_blocks(f_init, kGmThreads, dp.sms);
   const int nb_pq = gm_blocks(f_pq, kGmThreads, dp.sms);
   const int nb_xr = gm_blocks(f_xr, kGmThreads, dp.sms);
   const int nb_true = gm_blocks(f_true, kGmThreads, dp.sms);
   std::vector<GmPassRec<TM>> passes;
-  const int zbuf = gm_pass_list<TM>(a, passes);
+  bool wu = true;
+  const int zbuf = gm_pass_list<TM>(a, sizeof(TM) == 4, passes, &wu);
+  int write_u = wu ? 1 : 0;
 
   cudaGraph_t g = nullptr;
   if (cudaGraphCreate(&g, 0) != cudaSuccess) return LAP5CG_ERR_CUDA;
@@ -569,7 +984,7 @@ static int gm_build(const SolvePlan& p, const PcgArgs<TM>& a, cudaGraphExec_t* e
   Grid<double> gr = a.r, gp0 = a.p0, gp1 = a.p1, gq = a.q;
   MgLevel<TM> L0 = a.lv[0];
   {
-    void* args[] = {&bd, &part, &nx_, &ny_, &ld_, &gr, &L0};
+    void* args[] = {&bd, &part, &nx_, &ny_, &ld_, &gr, &L0, &write_u};
     if ((rc = gm_add(g, &prev, f_init, nb_init, kGmThreads, args)) != LAP5CG_OK) return fail(rc);
   }
   int nbi = nb_init;
@@ -596,8 +1011,19 @@ static int gm_build(const SolvePlan& p, const PcgArgs<TM>& a, cudaGraphExec_t* e
         for (int l = 0; l < kMgMaxLevels; ++l) lv.lv[l] = a.lv[l];
         int nlev = a.nlev, first = pr.level, nu = a.nu, nu_c = a.nu_c;
         void* args[] = {&sc, &lv, &nlev, &first, &nu, &nu_c};
-        if ((rc = gm_add(body, &bp, reinterpret_cast<const void*>(&k_gm_small<TM>), 1, 512, args)) != LAP5CG_OK)
-          return fail(rc);
+        // the levels in shared memory where they fit
+        size_t smem = gm_small_smem<TM>(a.lv, first, nlev);
+        const void* fs = reinterpret_cast<const void*>(&k_gm_small<TM, true>);
+        cudaFuncAttributes fa;
+        if (cudaFuncGetAttributes(&fa, fs) != cudaSuccess) return fail(LAP5CG_ERR_CUDA);
+        if (smem + fa.sharedSizeBytes <= (size_t)dp.max_smem_optin) {
+          if (cudaFuncSetAttribute(fs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+            return fail(LAP5CG_ERR_CUDA);
+        } else {
+          fs = reinterpret_cast<const void*>(&k_gm_small<TM, false>);
+          smem = 0;
+        }
+        if ((rc = gm_add(body, &bp, fs, 1, 512, args, (unsigned)smem)) != LAP5CG_OK) return fail(rc);
         continue;
       }
       MgLevel<TM> L = a.lv[pr.level];
@@ -605,8 +1031,52 @@ static int gm_build(const SolvePlan& p, const PcgArgs<TM>& a, cudaGraphExec_t* e
       int kind = pr.kind, rev = pr.rev;
       const TM* in = pr.in;
       TM* out = pr.out;
+      const int wpc = kGmThreads / 32;
+      if (kind == GP_RES_RESTRICT) {
+        const Units un = make_units(Lc.nx, Lc.ny, 2, 1ll << 40, 2);
+        const int grid = (int)std::min<long long>(((long long)un.nunits + wpc - 1) / wpc, nb_rr);
+        const TM* uin = in;
+        void* rargs[] = {&sc, &L, &uin, &Lc, &write_u};
+        if ((rc = gm_add(body, &bp, f_rr, (unsigned)(grid < 1 ? 1 : grid), kGmThreads, rargs)) != LAP5CG_OK)
+          return fail(rc);
+        continue;
+      }
+      if (kind == GP_PROLONG_JAC) {
+        const long long ntiles = (long long)((L.nx + 127) / 128) * ((L.ny + 2 * wpc - 1) / (2 * wpc));
+        const int grid = (int)std::min<long long>(ntiles, nb_pj);
+        const TM* uin = in;
+        const TM* ein = pr.e;
+        void* pargs[] = {&sc, &L, &uin, &Lc, &ein, &out};
+        if ((rc = gm_add(body, &bp, f_pj, (unsigned)grid, kGmThreads, pargs)) != LAP5CG_OK) return fail(rc);
+        continue;
+      }
+      if (kind == GP_JAC || kind == GP_RES) {
+        // sweeps and residuals: the tiled kernel, as many CTAs as tiles up to
+        // the resident maximum.  (The (r, z) sweep stays on the march kernel:
+        // measured at 4096^2 the tiled form with the binary64 r rows took 111
+        // against 79 microseconds -- its 104 registers halve the occupancy.)
+        const int V = GmSweepVec<TM>::V;
+        const long long ntiles = (long long)((L.nx + 32 * V - 1) / (32 * V)) * ((L.ny + 2 * wpc - 1) / (2 * wpc));
+        const void* fk = kind == GP_JAC ? f_sweep_j : f_sweep_r;
+        const int grid = (int)std::min<long long>(ntiles, nb_sweep);
+        int from_b = pr.from_b;
+        void* sargs[] = {&sc, &part, &L, &in, &out, &grc, &from_b};
+        if ((rc = gm_add(body, &bp, fk, (unsigned)grid, kGmThreads, sargs)) != LAP5CG_OK) return fail(rc);
+        continue;
+      }
       void* args[] = {&sc, &part, &L, &Lc, &kind, &rev, &in, &out, &grc};
-      if ((rc = gm_add(body, &bp, f_pass, nb_pass, kGmThreads, args)) != LAP5CG_OK) return fail(rc);
+      // restriction and prolongation: as many CTAs as the pass has warp units
+      // (two-row units), up to the resident maximum -- the small levels' passes
+      // launch a few CTAs, not a full grid of idle ones.  The (r, z) sweep keeps
+      // the full grid: k_gm_rz adds nb_pass partial sums.
+      int grid = nb_pass;
+      if (kind != GP_JAC_DOT) {
+        const long long kAll = 1ll << 40;
+        const Units un = kind == GP_RESTRICT ? make_units(Lc.nx, Lc.ny, 2, kAll, 2) : make_units(L.nx, L.ny, 4, kAll, 2);
+        const long long need = ((long long)un.nunits + wpc - 1) / wpc;
+        if (need < grid) grid = need < 1 ? 1 : (int)need;
+      }
+      if ((rc = gm_add(body, &bp, f_pass, (unsigned)grid, kGmThreads, args)) != LAP5CG_OK) return fail(rc);
     }
     int nbp = nb_pass;
     {
@@ -626,7 +1096,7 @@ static int gm_build(const SolvePlan& p, const PcgArgs<TM>& a, cudaGraphExec_t* e
         return fail(rc);
     }
     {
-      void* args[] = {&sc, &bd, &part, &nx_, &ny_, &ld_, &gr, &gp0, &gp1, &gq, &L0, &rev0};
+      void* args[] = {&sc, &bd, &part, &nx_, &ny_, &ld_, &gr, &gp0, &gp1, &gq, &L0, &rev0, &write_u};
       if ((rc = gm_add(body, &bp, f_xr, nb_xr, kGmThreads, args)) != LAP5CG_OK) return fail(rc);
     }
     int nbx = nb_xr;

@@ -43,6 +43,25 @@ template <class TM> struct MgVec { static constexpr int V = 16 / (int)sizeof(TM)
 __device__ __forceinline__ float mg_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double mg_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
 
+// binary32 -> binary64 widening (exact) from the IEEE 754 formats: for a
+// normal number the sign moves to bit 63, the exponent is re-biased by
+// 1023 - 127 and the 23 fraction bits move up by 29; zeros keep their sign.
+// Integer operations only: on GB300 the FP64 pipe (2 operations an SM a clock)
+// is the limit of the binary64 PCG passes, and a hardware conversion would
+// take a slot of it.  Subnormal, infinite and NaN inputs take the hardware
+// conversion.
+__device__ __forceinline__ double mg_widen(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e = (u >> 23) & 0xffu;
+  const unsigned long long s = (unsigned long long)(u >> 31) << 63;
+  if (e - 1u < 254u)
+    return __longlong_as_double(
+        (long long)(s | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(u & 0x7fffffu) << 29)));
+  if ((u << 1) == 0u) return __longlong_as_double((long long)s);
+  return (double)f;
+}
+__device__ __forceinline__ double mg_widen(double d) { return d; }
+
 // Damped Jacobi sweep (JAC) out = in + c (b - A in), or residual out = b - A in;
 // with DOT also accumulates (r, out) against the binary64 grid r (level 0).
 template <class TM, bool JAC, bool DOT>
@@ -71,7 +90,7 @@ __device__ void mg_stencil_pass(const Sched& s, const MgLevel<TM>& L, const TM* 
         double rv[V], zv[V];
         load_row<V>(r, j, xl, L.nx, rv);
 #pragma unroll
-        for (int k = 0; k < V; ++k) zv[k] = (double)o[k];
+        for (int k = 0; k < V; ++k) zv[k] = mg_widen(o[k]);
         acc_dot<V>(acc, j, rv, zv, nval);
       }
     };
@@ -205,9 +224,9 @@ __device__ __forceinline__ void field_wide(const Grid<const TM>& g, int nx, int 
   TM t[V];
   load_row<V>(g, j, x, nx, t);
 #pragma unroll
-  for (int k = 0; k < V; ++k) f.f[k] = (double)t[k];
-  f.hl = (lane == 0 && xs >= 1 && xs - 1 < nx) ? (double)g.row(j)[xs - 1] : 0.0;
-  f.hr = (lane == 31 && xs + 32 * V < nx) ? (double)g.row(j)[xs + 32 * V] : 0.0;
+  for (int k = 0; k < V; ++k) f.f[k] = mg_widen(t[k]);
+  f.hl = (lane == 0 && xs >= 1 && xs - 1 < nx) ? mg_widen(g.row(j)[xs - 1]) : 0.0;
+  f.hr = (lane == 31 && xs + 32 * V < nx) ? mg_widen(g.row(j)[xs + 32 * V]) : 0.0;
 }
 
 template <class TM>

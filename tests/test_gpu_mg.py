@@ -36,7 +36,10 @@ def _rel(a, b):
 # (1, 1) .. (63, 63): the whole hierarchy on one CTA; (300, 200): levels 0 and 1
 # grid-wide, the rest on one CTA; (1, 200), (200, 1): no coarse grid at all
 SHAPES = [(1, 1), (2, 2), (3, 5), (15, 15), (16, 16), (63, 63), (100, 100), (130, 67), (300, 200), (255, 257),
-          (1, 200), (200, 1), (513, 130)]
+          (1, 200), (200, 1), (513, 130), (1000, 9), (3, 8000)]
+# (1000, 9): level 1 (499 x 4) is the coarsest and fits one CTA's shared
+# memory; (3, 8000): level 1 (1 x 3999) has a pitch of 4, too large for shared
+# memory, so its single-CTA kernel works in global memory
 
 
 @pytest.mark.parametrize("nx,ny", SHAPES)
@@ -258,3 +261,35 @@ def test_graph_cache_eviction_keeps_results_right():
         xo, io = oracle.cg_pcg(b, tol=0.0, maxit=3, nx=nx)
         assert rec["iters"] == io["iters"] == 3
         assert _rel(x, xo[:, :nx]) <= 1e-11
+
+
+@pytest.mark.parametrize("nx,ny", [(300, 200), (513, 130)])
+def test_nonzero_start_tracks_oracle(nx, ny):
+    # x0 != 0 on part of the grid: the first residual takes the stencil there
+    ld = gen.pitch(nx, 8)
+    b = gen.uniform_rhs(nx, ny, seed=71, ld=ld)
+    x0 = np.zeros_like(b)
+    x0[ny // 3: ny // 2, : nx // 2] = gen.uniform_rhs(nx, ny, seed=72, ld=ld)[ny // 3: ny // 2, : nx // 2]
+    for k in (1, 4):
+        x, info = lap5cg.cg_solve(_dev(b), x0=_dev(x0), tol=0.0, maxit=k, precision="mg_f64", nx=nx)
+        rec = lap5cg.decode_info(info)[0]
+        xo, io = oracle.cg_pcg(b, x0=x0, tol=0.0, maxit=k, nx=nx)
+        assert rec["iters"] == io["iters"] == k
+        assert _rel(x.cpu().numpy()[:, :nx], xo[:, :nx]) <= 1e-11
+
+
+@pytest.mark.parametrize("opt", [dict(mg_nu=1), dict(mg_nu=3), dict(mg_levels=2), dict(mg_levels=2, mg_coarse_sweeps=1),
+                                 dict(mg_coarse_sweeps=2)])
+def test_binary32_vcycle_options_converge_to_oracle(opt):
+    # the binary32 V-cycle's fused passes and its first sweeps formed from b,
+    # under the options that change which pass reads a level's first sweep
+    nx, ny = 300, 200
+    tol = 1e-10
+    b = gen.uniform_rhs(nx, ny, seed=19, ld=gen.pitch(nx, 8))
+    x, rec = _solve(b, nx, "mg_f32", tol, 3000, **opt)
+    assert rec["status"] == lap5cg.OK and rec["relres_true"] <= 1.5 * tol, rec
+    xt, _ = oracle.cg_pcg(b, tol=1e-13, maxit=500, nx=nx)
+    assert _rel(x, xt[:, :nx]) <= gen.condition_number(nx, ny) * 2 * tol
+    # the binary64 V-cycle with the same options: same iteration count within a few
+    _, r64 = _solve(b, nx, "mg_f64", tol, 3000, **opt)
+    assert abs(rec["iters"] - r64["iters"]) <= max(3, r64["iters"] // 5), (rec, r64)
