@@ -139,11 +139,11 @@ __global__ void __launch_bounds__(kGmThreads) k_gm_pass(const GmScal* sc, double
 // arithmetic per point as mg_stencil_pass.
 template <class TM> struct GmSweepVec { static constexpr int V = sizeof(TM) == 4 ? 8 : 2; };
 
-// from_b: the input iterate is the level's first sweep from zero, c b, which is
+// FROM_B: the input iterate is the level's first sweep from zero, c b, which is
 // formed from b here (the producer of b then stores no iterate).
-template <class TM, int MODE>
+template <class TM, int MODE, bool FROM_B = false>
 __global__ void __launch_bounds__(kGmThreads) k_gm_sweep(const GmScal* sc, double*, MgLevel<TM> L, const TM* in,
-                                                          TM* out, Grid<const double>, int from_b) {
+                                                          TM* out, Grid<const double>) {
   if (sc->stop) return;
   constexpr int V = GmSweepVec<TM>::V, R = 2;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpc = blockDim.x >> 5;
@@ -162,8 +162,8 @@ __global__ void __launch_bounds__(kGmThreads) k_gm_sweep(const GmScal* sc, doubl
     TM bv[R][V];
 #pragma unroll
     for (int k = 0; k < R + 2; ++k) {
-      field_plain<V>(from_b ? gb : gi, L.nx, L.ny, jb - 1 + k, xl, xs, lane, f[k]);
-      if (from_b) {
+      field_plain<V>(FROM_B ? gb : gi, L.nx, L.ny, jb - 1 + k, xl, xs, lane, f[k]);
+      if constexpr (FROM_B) {
 #pragma unroll
         for (int q = 0; q < V; ++q) f[k].f[q] = c * f[k].f[q];
         f[k].hl = c * f[k].hl;
@@ -956,6 +956,8 @@ static int gm_build(const SolvePlan& p, const PcgArgs<TM>& a, cudaGraphExec_t* e
   const int nb_pass = gm_blocks(f_pass, kGmThreads, dp.sms);
   const void* f_sweep_j = reinterpret_cast<const void*>(&k_gm_sweep<TM, GP_JAC>);
   const void* f_sweep_r = reinterpret_cast<const void*>(&k_gm_sweep<TM, GP_RES>);
+  // (c b formed from b: binary32 V-cycles only)
+  const void* f_sweep_jb = reinterpret_cast<const void*>(&k_gm_sweep<TM, GP_JAC, sizeof(TM) == 4>);
   const int nb_sweep = gm_blocks(f_sweep_j, kGmThreads, dp.sms);
   const void* f_rr = reinterpret_cast<const void*>(&k_gm_res_restrict<TM>);
   const void* f_pj = reinterpret_cast<const void*>(&k_gm_prolong_jac<TM>);
@@ -1057,10 +1059,9 @@ static int gm_build(const SolvePlan& p, const PcgArgs<TM>& a, cudaGraphExec_t* e
         // against 79 microseconds -- its 104 registers halve the occupancy.)
         const int V = GmSweepVec<TM>::V;
         const long long ntiles = (long long)((L.nx + 32 * V - 1) / (32 * V)) * ((L.ny + 2 * wpc - 1) / (2 * wpc));
-        const void* fk = kind == GP_JAC ? f_sweep_j : f_sweep_r;
+        const void* fk = kind == GP_RES ? f_sweep_r : pr.from_b ? f_sweep_jb : f_sweep_j;
         const int grid = (int)std::min<long long>(ntiles, nb_sweep);
-        int from_b = pr.from_b;
-        void* sargs[] = {&sc, &part, &L, &in, &out, &grc, &from_b};
+        void* sargs[] = {&sc, &part, &L, &in, &out, &grc};
         if ((rc = gm_add(body, &bp, fk, (unsigned)grid, kGmThreads, sargs)) != LAP5CG_OK) return fail(rc);
         continue;
       }
