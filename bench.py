@@ -295,12 +295,25 @@ def time_to_solution(lap5cg, torch, dev, n, rhs, tol=1e-10):
                                           ("pcg_mg_f32", "classic", "mg_f32", 0, 0), ("pcg_mg_f64", "classic", "mg_f64", 0, 0),
                                           ("pipelined_pcg_mg_f64", "newcg", "mg_f64", 0, 0)):
         opts = lap5cg.default_opts(rr_period=rr, stabilized=stab)
-        # warm-up (first launch of each kernel) on a 512^2 corner, not the full solve
-        lap5cg.cg_solve(b[:512, :512].contiguous(), tol=tol, maxit=10 ** 6, variant=variant, precision=prec, opts=opts)
+        # buffers allocated before the timed solve (an allocation inside it
+        # would leave the GPU idle while the host allocates)
+        ws = torch.empty(lap5cg.workspace_size(n, n, n, variant, prec), dtype=torch.uint8, device=dev)
+        x = torch.zeros_like(b)
+        info = torch.empty(lap5cg.INFO_BYTES, dtype=torch.uint8, device=dev)
+        if prec.startswith("mg"):
+            # warm-up: the full solve (milliseconds), which also instantiates the
+            # multigrid graph for this shape and workspace (cached afterwards)
+            lap5cg.cg_solve(b, tol=tol, maxit=10 ** 6, variant=variant, precision=prec, opts=opts, workspace=ws,
+                            out=x, info=info)
+        else:
+            # warm-up (first launch of each kernel) on a 512^2 corner, not the full solve (seconds)
+            lap5cg.cg_solve(b[:512, :512].contiguous(), tol=tol, maxit=10 ** 6, variant=variant, precision=prec,
+                            opts=opts)
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        x, info = lap5cg.cg_solve(b, tol=tol, maxit=10 ** 6, variant=variant, precision=prec, opts=opts)
+        x, info = lap5cg.cg_solve(b, tol=tol, maxit=10 ** 6, variant=variant, precision=prec, opts=opts, workspace=ws,
+                                  out=x, info=info)
         e1.record()
         torch.cuda.synchronize(dev)
         rec = lap5cg.decode_info(info)[0]

@@ -52,7 +52,7 @@ __global__ void k_gm_bind(GmBind* bd, const double* b, double* x, lap5cg_info* i
   if (threadIdx.x == 0 && blockIdx.x == 0) *bd = GmBind{b, x, info, history, tol, maxit, 0};
 }
 
-enum { GP_JAC = 0, GP_JAC_DOT, GP_RES, GP_RESTRICT, GP_PROLONG, GP_RES_RESTRICT, GP_PROLONG_JAC };
+enum { GP_JAC = 0, GP_JAC_DOT, GP_RES, GP_RESTRICT, GP_PROLONG, GP_RES_RESTRICT, GP_PROLONG_JAC, GP_JAC_RES_RESTRICT };
 
 // Block-wide sums of NV per-thread values into part[blockIdx.x * 2 + k].
 template <int NV>
@@ -138,14 +138,19 @@ __global__ void __launch_bounds__(kGmThreads) k_gm_pass(const GmScal* sc, double
 // V = 2).  CTAs stride over the tiles (8 warps x R rows x one strip).  Same
 // arithmetic per point as mg_stencil_pass.
 template <class TM> struct GmSweepVec { static constexpr int V = sizeof(TM) == 4 ? 8 : 2; };
+// the (r, z) sweep: one group of columns a lane (its binary64 r rows would
+// double the registers of the two-group layout)
+template <class TM> struct GmDotVec { static constexpr int V = sizeof(TM) == 4 ? 4 : 2; };
+constexpr bool kGmTiledDot = true;
+constexpr bool kGmFuseDescent = true;
 
 // FROM_B: the input iterate is the level's first sweep from zero, c b, which is
 // formed from b here (the producer of b then stores no iterate).
 template <class TM, int MODE, bool FROM_B = false>
-__global__ void __launch_bounds__(kGmThreads) k_gm_sweep(const GmScal* sc, double*, MgLevel<TM> L, const TM* in,
-                                                          TM* out, Grid<const double>) {
+__global__ void __launch_bounds__(kGmThreads) k_gm_sweep(const GmScal* sc, double* part, MgLevel<TM> L,
+                                                          const TM* in, TM* out, Grid<const double> r) {
   if (sc->stop) return;
-  constexpr int V = GmSweepVec<TM>::V, R = 2;
+  constexpr int V = MODE == GP_JAC_DOT ? GmDotVec<TM>::V : GmSweepVec<TM>::V, R = 2;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpc = blockDim.x >> 5;
   const int ns = (L.nx + 32 * V - 1) / (32 * V);
   const int band = wpc * R;
@@ -153,6 +158,7 @@ __global__ void __launch_bounds__(kGmThreads) k_gm_sweep(const GmScal* sc, doubl
   const Grid<const TM> gi{in, L.ld}, gb{L.b, L.ld};
   const Grid<TM> go{out, L.ld};
   const TM c = (TM)kMgC;
+  Acc64 acc;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int st = t % ns;
     const int jb = (t / ns) * band + warp * R;
@@ -189,7 +195,18 @@ __global__ void __launch_bounds__(kGmThreads) k_gm_sweep(const GmScal* sc, doubl
       for (int q = 0; q < V; ++q)
         o[q] = MODE == GP_RES ? bv[k][q] - ax[q] : mg_fma(c, bv[k][q] - ax[q], f[k + 1].f[q]);
       store_row<V>(go, j, xl, L.nx, o);
+      if constexpr (MODE == GP_JAC_DOT) {
+        double rv[V], zv[V];
+        load_row<V>(r, j, xl, L.nx, rv);
+#pragma unroll
+        for (int q = 0; q < V; ++q) zv[q] = mg_widen(o[q]);
+        acc_dot<V>(acc, j, rv, zv, L.nx - xl);
+      }
     }
+  }
+  if constexpr (MODE == GP_JAC_DOT) {
+    const double v[1] = {acc.value()};
+    gm_partials<1>(v, part);
   }
 }
 
@@ -294,6 +311,152 @@ __global__ void __launch_bounds__(kGmThreads) k_gm_res_restrict(const GmScal* sc
   }
 }
 
+// A level's whole descent for nu = 2 in one pass (binary32 V-cycle): the
+// second pre-smoothing sweep v = c b + c (b - A c b) (the first, c b, from
+// zero), stored, and from v the residual b - A v restricted to the coarse
+// level as in k_gm_res_restrict.  The march runs over b: v rows are formed one
+// row ahead of the residual rows that need them (b two rows ahead).  The
+// strip's halo columns of v (xs - 1; xs + 128 and xs + 129 for the residual
+// at the next strip's first column) are formed point-wise by lanes 0 and 31.
+// A unit stores the v rows of its coarse rows (fine rows 2 y0 .. 2 y1 - 1; the
+// last unit also the rows above), the last strip also the columns past it.
+// Same operations in the same order as the separate sweep and residual.
+template <class TM>
+__global__ void __launch_bounds__(kGmThreads) k_gm_jac_res_restrict(const GmScal* sc, MgLevel<TM> F, TM* vout,
+                                                                    MgLevel<TM> C, int write_u) {
+  if (sc->stop) return;
+  const Sched s = gm_sched(0);
+  const Units un = make_units(C.nx, C.ny, 2, s.nw, 2);
+  const Grid<const TM> gb{F.b, F.ld};
+  const Grid<TM> gv{vout, F.ld}, gcb{C.b, C.ld}, gcu{C.u, C.ld};
+  const TM c = (TM)kMgC;
+  const int lane = s.lane;
+  auto cb_at = [&](int i, int x) -> TM {
+    return (i < 0 || i >= F.ny || x < 0 || x >= F.nx) ? TM(0) : c * gb.row(i)[x];
+  };
+  auto v_at = [&](int i, int x) -> TM {  // the sweep at one point
+    if (i < 0 || i >= F.ny || x < 0 || x >= F.nx) return TM(0);
+    const TM cc = cb_at(i, x);
+    TM acc = TM(4) * cc;
+    acc -= cb_at(i, x - 1);
+    acc -= cb_at(i, x + 1);
+    acc -= cb_at(i - 1, x);
+    acc -= cb_at(i + 1, x);
+    return mg_fma(c, gb.row(i)[x] - acc, cc);
+  };
+  for (int w = s.w; w < un.nunits; w += s.nw) {
+    int st, y0, y1;
+    unit_bounds(un, w, C.ny, st, y0, y1);
+    const int xs = st * 128, f0 = xs + 4 * lane, I0 = f0 / 2;
+    const bool last_strip = (st == un.ns - 1), top = (y1 == C.ny);
+    auto cb_row = [&](int i, FRow<4, TM>& f) {  // c b of row i (zero outside the grid)
+      field_plain<4>(gb, F.nx, F.ny, i, f0, xs, lane, f);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) f.f[k] = c * f.f[k];
+      f.hl = c * f.hl;
+      f.hr = c * f.hr;
+    };
+    // v of row i from c b rows i-1, i, i+1; hr2: v at xs + 129 (lane 31)
+    auto v_row = [&](int i, const FRow<4, TM>& S, const FRow<4, TM>& Cr, const FRow<4, TM>& N, FRow<4, TM>& v,
+                     TM& hr2) {
+      if (i < 0 || i >= F.ny) {
+        v.zero();
+        hr2 = TM(0);
+        return;
+      }
+      TM ax[4], bv[4];
+      stencil_row<4>(S, Cr, N, lane, ax);
+      load_row<4>(gb, i, f0, F.nx, bv);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) v.f[k] = f0 + k < F.nx ? mg_fma(c, bv[k] - ax[k], Cr.f[k]) : TM(0);
+      v.hl = (lane == 0) ? v_at(i, xs - 1) : TM(0);
+      v.hr = (lane == 31) ? v_at(i, xs + 128) : TM(0);
+      hr2 = (lane == 31) ? v_at(i, xs + 129) : TM(0);
+    };
+    auto store_v = [&](int i, const FRow<4, TM>& v, TM hr2) {
+      if (i < 0 || i >= F.ny) return;
+      store_row<4>(gv, i, f0, F.nx, v.f);
+      if (last_strip && lane == 31) {  // columns past the last strip
+        if (xs + 128 < F.nx) gv.row(i)[xs + 128] = v.hr;
+        if (xs + 129 < F.nx) gv.row(i)[xs + 129] = hr2;
+      }
+    };
+    // residual of row j at columns f0 .. f0+4 from v rows j-1, j, j+1
+    auto res_row = [&](int j, const FRow<4, TM>& S, const FRow<4, TM>& Cr, TM crh2, const FRow<4, TM>& N,
+                       TM (&r)[5]) {
+      if (j < 0 || j >= F.ny) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) r[k] = TM(0);
+        return;
+      }
+      TM ax[4], bv[4];
+      stencil_row<4>(S, Cr, N, lane, ax);
+      load_row<4>(gb, j, f0, F.nx, bv);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) r[k] = f0 + k < F.nx ? bv[k] - ax[k] : TM(0);
+      TM e = __shfl_down_sync(0xffffffffu, r[0], 1);
+      if (lane == 31) {
+        const int xe = xs + 128;
+        e = TM(0);
+        if (xe < F.nx) {
+          TM acc = TM(4) * Cr.hr;
+          acc -= Cr.f[3];
+          acc -= crh2;
+          acc -= S.hr;
+          acc -= N.hr;
+          e = gb.row(j)[xe] - acc;
+        }
+      }
+      r[4] = e;
+    };
+    // march state: c b rows (bA, bB, bC) = rows i-1, i, i+1 of the next v row i;
+    // v rows (vS, vC, vN) with their hr2 for the next residual row
+    FRow<4, TM> bA, bB, bC, vS, vC, vN;
+    TM hS, hC, hN;
+    int i = 2 * y0 - 1;  // next v row
+    cb_row(i - 1, bA);
+    cb_row(i, bB);
+    cb_row(i + 1, bC);
+    v_row(i, bA, bB, bC, vS, hS);
+    auto next_v = [&](FRow<4, TM>& v, TM& h) {  // v row i + 1, advancing the c b rows
+      ++i;
+      bA = bB;
+      bB = bC;
+      cb_row(i + 1, bC);
+      v_row(i, bA, bB, bC, v, h);
+    };
+    next_v(vC, hC);  // row 2 y0
+    next_v(vN, hN);  // row 2 y0 + 1
+    store_v(2 * y0, vC, hC);
+    TM lo[5], mid[5], hi[5];
+    res_row(2 * y0, vS, vC, hC, vN, lo);
+    for (int J = y0; J < y1; ++J) {
+      vS = vC; vC = vN; hC = hN;
+      next_v(vN, hN);  // row 2J + 2
+      res_row(2 * J + 1, vS, vC, hC, vN, mid);
+      store_v(2 * J + 1, vC, hC);
+      vS = vC; vC = vN; hC = hN;
+      next_v(vN, hN);  // row 2J + 3
+      res_row(2 * J + 2, vS, vC, hC, vN, hi);
+      if (J + 1 < y1 || top) store_v(2 * J + 2, vC, hC);
+      TM bcv[2], ucv[2];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int wq = 2 * q, m = wq + 1, e = wq + 2;
+        const TM s1 = ((mid[wq] + mid[e]) + lo[m]) + hi[m];
+        const TM s2 = ((lo[wq] + lo[e]) + hi[wq]) + hi[e];
+        bcv[q] = TM(0.25) * ((TM(4) * mid[m] + TM(2) * s1) + s2);
+        ucv[q] = c * bcv[q];
+      }
+      store_row<2>(gcb, J, I0, C.nx, bcv);
+      if (write_u) store_row<2>(gcu, J, I0, C.nx, ucv);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) lo[k] = hi[k];
+    }
+    if (top) store_v(2 * y1 + 1, vN, hN);  // the grid's last fine row, above the last coarse row's
+  }
+}
+
 // Prolongation and the first post-smoothing sweep in one pass: out = u' + c (b -
 // A u') with u' = u + P e, u' formed in registers (never stored).  Tiles as in
 // k_gm_sweep, with one group of four columns a lane (the prolongation's lane
@@ -370,105 +533,6 @@ __global__ void __launch_bounds__(kGmThreads) k_gm_prolong_jac(const GmScal* sc,
       store_row<V>(go, j, f0, L.nx, o);
     }
   }
-}
-
-// Point-wise forms of the V-cycle's passes for the single-CTA levels: one
-// thread a point, no warp-level march (at a few thousand points a pass the
-// march's dependent row chain, not bandwidth, set the time).  Same operations
-// in the same order as mg_stencil_pass, mg_restrict and mg_prolong.
-template <class TM>
-__device__ __forceinline__ TM tiny_at(const TM* g, int nx, int ny, int ld, int i, int j) {
-  return (i < 0 || i >= nx || j < 0 || j >= ny) ? TM(0) : g[j * ld + i];
-}
-
-template <class TM, bool JAC>
-__device__ void tiny_stencil(const MgLevel<TM>& L, const TM* in, TM* out) {
-  const TM c = (TM)kMgC;
-  const int n = L.nx * L.ny;
-  for (int p = threadIdx.x; p < n; p += blockDim.x) {
-    const int j = p / L.nx, i = p - j * L.nx;
-    const TM C = in[j * L.ld + i];
-    TM acc = TM(4) * C;
-    acc -= tiny_at(in, L.nx, L.ny, L.ld, i - 1, j);
-    acc -= tiny_at(in, L.nx, L.ny, L.ld, i + 1, j);
-    acc -= tiny_at(in, L.nx, L.ny, L.ld, i, j - 1);
-    acc -= tiny_at(in, L.nx, L.ny, L.ld, i, j + 1);
-    const TM b = L.b[j * L.ld + i];
-    out[j * L.ld + i] = JAC ? mg_fma(c, b - acc, C) : b - acc;
-  }
-}
-
-// coarse C.b = P^T res, C.u = c C.b
-template <class TM>
-__device__ void tiny_restrict(const MgLevel<TM>& F, const TM* res, const MgLevel<TM>& C) {
-  const TM c = (TM)kMgC;
-  const int n = C.nx * C.ny;
-  for (int p = threadIdx.x; p < n; p += blockDim.x) {
-    const int J = p / C.nx, I = p - J * C.nx;
-    const int fi = 2 * I + 1, fj = 2 * J + 1;
-    auto r = [&](int di, int dj) { return tiny_at(res, F.nx, F.ny, F.ld, fi + di, fj + dj); };
-    const TM s1 = ((r(-1, 0) + r(1, 0)) + r(0, -1)) + r(0, 1);
-    const TM s2 = ((r(-1, -1) + r(1, -1)) + r(-1, 1)) + r(1, 1);
-    const TM bc = TM(0.25) * ((TM(4) * r(0, 0) + TM(2) * s1) + s2);
-    C.b[J * C.ld + I] = bc;
-    C.u[J * C.ld + I] = c * bc;
-  }
-}
-
-// f += P e
-template <class TM>
-__device__ void tiny_prolong(const MgLevel<TM>& F, TM* f, const MgLevel<TM>& C, const TM* e) {
-  const int n = F.nx * F.ny;
-  for (int p = threadIdx.x; p < n; p += blockDim.x) {
-    const int j = p / F.nx, i = p - j * F.nx;
-    auto ce = [&](int I, int J) { return tiny_at(e, C.nx, C.ny, C.ld, I, J); };
-    TM v;
-    if (j & 1) {
-      const int J = j >> 1;
-      v = (i & 1) ? ce(i >> 1, J) : TM(0.5) * (ce((i >> 1) - 1, J) + ce(i >> 1, J));
-    } else {
-      const int J = j >> 1;
-      if (i & 1) {
-        const int I = i >> 1;
-        v = TM(0.5) * (ce(I, J - 1) + ce(I, J));
-      } else {
-        const int I = i >> 1;
-        v = TM(0.25) * ((ce(I - 1, J - 1) + ce(I, J - 1)) + (ce(I - 1, J) + ce(I, J)));
-      }
-    }
-    f[j * F.ld + i] += v;
-  }
-}
-
-// The V-cycle from level `first` down to the coarsest and back with the
-// point-wise passes, CTA barriers between them; returns the parity of the
-// buffer that holds level `first`'s result (0: u, 1: v).
-template <class TM>
-__device__ int tiny_vcycle(const MgLevel<TM>* lv, int nlev, int first, int nu, int nu_c) {
-  int cur[kMgMaxLevels];
-  auto it = [&](int l) -> TM* { return cur[l] ? lv[l].v : lv[l].u; };
-  auto other = [&](int l) -> TM* { return cur[l] ? lv[l].u : lv[l].v; };
-  auto jac = [&](int l) {
-    tiny_stencil<TM, true>(lv[l], it(l), other(l));
-    cur[l] ^= 1;
-    __syncthreads();
-  };
-  cur[first] = 0;
-  for (int l = first; l < nlev - 1; ++l) {
-    for (int k = 1; k < nu; ++k) jac(l);
-    tiny_stencil<TM, false>(lv[l], it(l), other(l));
-    __syncthreads();
-    tiny_restrict(lv[l], other(l), lv[l + 1]);
-    __syncthreads();
-    cur[l + 1] = 0;
-  }
-  for (int k = 1; k < nu_c; ++k) jac(nlev - 1);
-  for (int l = nlev - 2; l >= first; --l) {
-    tiny_prolong(lv[l], it(l), lv[l + 1], it(l + 1));
-    __syncthreads();
-    for (int k = 0; k < nu; ++k) jac(l);
-  }
-  return cur[first];
 }
 
 // The levels [first, nlev) on the calling CTA (every thread of it), resident
@@ -873,6 +937,12 @@ static int gm_pass_list(const PcgArgs<TM>& a, bool fuse, std::vector<GmPassRec<T
   };
   const int big_end = a.lsmall < L - 1 ? a.lsmall : L - 1;
   for (int l = 0; l < big_end; ++l) {  // down: pre-smoothing, residual, restriction
+    if (fuse && kGmFuseDescent && nu == 2) {  // the one explicit sweep, residual and restriction: one pass
+      out.push_back({GP_JAC_RES_RESTRICT, l, (int)(pc++ & 1u), nullptr, other(l), nullptr});
+      cur[l] ^= 1;
+      cur[l + 1] = 0;
+      continue;
+    }
     sweeps(l, nu, false);
     if (fuse) {
       out.push_back({GP_RES_RESTRICT, l, (int)(pc++ & 1u), it(l), nullptr, nullptr});
@@ -958,10 +1028,15 @@ static int gm_build(const SolvePlan& p, const PcgArgs<TM>& a, cudaGraphExec_t* e
   const void* f_sweep_r = reinterpret_cast<const void*>(&k_gm_sweep<TM, GP_RES>);
   // (c b formed from b: binary32 V-cycles only)
   const void* f_sweep_jb = reinterpret_cast<const void*>(&k_gm_sweep<TM, GP_JAC, sizeof(TM) == 4>);
+  const void* f_sweep_d = reinterpret_cast<const void*>(&k_gm_sweep<TM, GP_JAC_DOT>);
+  const int nb_dot_max = gm_blocks(f_sweep_d, kGmThreads, dp.sms);
+  int nb_dot = nb_pass;  // CTAs of the (r, z) sweep
   const int nb_sweep = gm_blocks(f_sweep_j, kGmThreads, dp.sms);
   const void* f_rr = reinterpret_cast<const void*>(&k_gm_res_restrict<TM>);
   const void* f_pj = reinterpret_cast<const void*>(&k_gm_prolong_jac<TM>);
   const int nb_rr = gm_blocks(f_rr, kGmThreads, dp.sms);
+  const void* f_jrr = reinterpret_cast<const void*>(&k_gm_jac_res_restrict<TM>);
+  const int nb_jrr = gm_blocks(f_jrr, kGmThreads, dp.sms);
   const int nb_pj = gm_blocks(f_pj, kGmThreads, dp.sms);
   const int nb_init = gm_blocks(f_init, kGmThreads, dp.sms);
   const int nb_pq = gm_blocks(f_pq, kGmThreads, dp.sms);
@@ -1034,6 +1109,14 @@ static int gm_build(const SolvePlan& p, const PcgArgs<TM>& a, cudaGraphExec_t* e
       const TM* in = pr.in;
       TM* out = pr.out;
       const int wpc = kGmThreads / 32;
+      if (kind == GP_JAC_RES_RESTRICT) {
+        const Units un = make_units(Lc.nx, Lc.ny, 2, 1ll << 40, 2);
+        const int grid = (int)std::min<long long>(((long long)un.nunits + wpc - 1) / wpc, nb_jrr);
+        void* jargs[] = {&sc, &L, &out, &Lc, &write_u};
+        if ((rc = gm_add(body, &bp, f_jrr, (unsigned)(grid < 1 ? 1 : grid), kGmThreads, jargs)) != LAP5CG_OK)
+          return fail(rc);
+        continue;
+      }
       if (kind == GP_RES_RESTRICT) {
         const Units un = make_units(Lc.nx, Lc.ny, 2, 1ll << 40, 2);
         const int grid = (int)std::min<long long>(((long long)un.nunits + wpc - 1) / wpc, nb_rr);
@@ -1050,6 +1133,15 @@ static int gm_build(const SolvePlan& p, const PcgArgs<TM>& a, cudaGraphExec_t* e
         const TM* ein = pr.e;
         void* pargs[] = {&sc, &L, &uin, &Lc, &ein, &out};
         if ((rc = gm_add(body, &bp, f_pj, (unsigned)grid, kGmThreads, pargs)) != LAP5CG_OK) return fail(rc);
+        continue;
+      }
+      if (kind == GP_JAC_DOT && kGmTiledDot) {
+        const int V = GmDotVec<TM>::V;
+        const long long ntiles = (long long)((L.nx + 32 * V - 1) / (32 * V)) * ((L.ny + 2 * wpc - 1) / (2 * wpc));
+        const int grid = (int)std::min<long long>(ntiles, nb_dot_max);
+        nb_dot = grid;  // the partial sums k_gm_rz adds
+        void* sargs[] = {&sc, &part, &L, &in, &out, &grc};
+        if ((rc = gm_add(body, &bp, f_sweep_d, (unsigned)grid, kGmThreads, sargs)) != LAP5CG_OK) return fail(rc);
         continue;
       }
       if (kind == GP_JAC || kind == GP_RES) {
@@ -1079,7 +1171,7 @@ static int gm_build(const SolvePlan& p, const PcgArgs<TM>& a, cudaGraphExec_t* e
       }
       if ((rc = gm_add(body, &bp, f_pass, (unsigned)grid, kGmThreads, args)) != LAP5CG_OK) return fail(rc);
     }
-    int nbp = nb_pass;
+    int nbp = nb_dot;
     {
       void* args[] = {&sc, &part, &nbp};
       if ((rc = gm_add(body, &bp, reinterpret_cast<const void*>(&k_gm_rz), 1, 256, args)) != LAP5CG_OK)

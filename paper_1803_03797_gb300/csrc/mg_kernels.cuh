@@ -229,6 +229,105 @@ __device__ __forceinline__ void field_wide(const Grid<const TM>& g, int nx, int 
   f.hr = (lane == 31 && xs + 32 * V < nx) ? mg_widen(g.row(j)[xs + 32 * V]) : 0.0;
 }
 
+// Point-wise forms of the V-cycle's passes for the single-CTA levels: one
+// thread a point, no warp-level march (at a few thousand points a pass the
+// march's dependent row chain, not bandwidth, set the time).  Same operations
+// in the same order as mg_stencil_pass, mg_restrict and mg_prolong.
+template <class TM>
+__device__ __forceinline__ TM tiny_at(const TM* g, int nx, int ny, int ld, int i, int j) {
+  return (i < 0 || i >= nx || j < 0 || j >= ny) ? TM(0) : g[j * ld + i];
+}
+
+template <class TM, bool JAC>
+__device__ void tiny_stencil(const MgLevel<TM>& L, const TM* in, TM* out) {
+  const TM c = (TM)kMgC;
+  const int n = L.nx * L.ny;
+  for (int p = threadIdx.x; p < n; p += blockDim.x) {
+    const int j = p / L.nx, i = p - j * L.nx;
+    const TM C = in[j * L.ld + i];
+    TM acc = TM(4) * C;
+    acc -= tiny_at(in, L.nx, L.ny, L.ld, i - 1, j);
+    acc -= tiny_at(in, L.nx, L.ny, L.ld, i + 1, j);
+    acc -= tiny_at(in, L.nx, L.ny, L.ld, i, j - 1);
+    acc -= tiny_at(in, L.nx, L.ny, L.ld, i, j + 1);
+    const TM b = L.b[j * L.ld + i];
+    out[j * L.ld + i] = JAC ? mg_fma(c, b - acc, C) : b - acc;
+  }
+}
+
+// coarse C.b = P^T res, C.u = c C.b
+template <class TM>
+__device__ void tiny_restrict(const MgLevel<TM>& F, const TM* res, const MgLevel<TM>& C) {
+  const TM c = (TM)kMgC;
+  const int n = C.nx * C.ny;
+  for (int p = threadIdx.x; p < n; p += blockDim.x) {
+    const int J = p / C.nx, I = p - J * C.nx;
+    const int fi = 2 * I + 1, fj = 2 * J + 1;
+    auto r = [&](int di, int dj) { return tiny_at(res, F.nx, F.ny, F.ld, fi + di, fj + dj); };
+    const TM s1 = ((r(-1, 0) + r(1, 0)) + r(0, -1)) + r(0, 1);
+    const TM s2 = ((r(-1, -1) + r(1, -1)) + r(-1, 1)) + r(1, 1);
+    const TM bc = TM(0.25) * ((TM(4) * r(0, 0) + TM(2) * s1) + s2);
+    C.b[J * C.ld + I] = bc;
+    C.u[J * C.ld + I] = c * bc;
+  }
+}
+
+// f += P e
+template <class TM>
+__device__ void tiny_prolong(const MgLevel<TM>& F, TM* f, const MgLevel<TM>& C, const TM* e) {
+  const int n = F.nx * F.ny;
+  for (int p = threadIdx.x; p < n; p += blockDim.x) {
+    const int j = p / F.nx, i = p - j * F.nx;
+    auto ce = [&](int I, int J) { return tiny_at(e, C.nx, C.ny, C.ld, I, J); };
+    TM v;
+    if (j & 1) {
+      const int J = j >> 1;
+      v = (i & 1) ? ce(i >> 1, J) : TM(0.5) * (ce((i >> 1) - 1, J) + ce(i >> 1, J));
+    } else {
+      const int J = j >> 1;
+      if (i & 1) {
+        const int I = i >> 1;
+        v = TM(0.5) * (ce(I, J - 1) + ce(I, J));
+      } else {
+        const int I = i >> 1;
+        v = TM(0.25) * ((ce(I - 1, J - 1) + ce(I, J - 1)) + (ce(I - 1, J) + ce(I, J)));
+      }
+    }
+    f[j * F.ld + i] += v;
+  }
+}
+
+// The V-cycle from level `first` down to the coarsest and back with the
+// point-wise passes, CTA barriers between them; returns the parity of the
+// buffer that holds level `first`'s result (0: u, 1: v).
+template <class TM>
+__device__ int tiny_vcycle(const MgLevel<TM>* lv, int nlev, int first, int nu, int nu_c) {
+  int cur[kMgMaxLevels];
+  auto it = [&](int l) -> TM* { return cur[l] ? lv[l].v : lv[l].u; };
+  auto other = [&](int l) -> TM* { return cur[l] ? lv[l].u : lv[l].v; };
+  auto jac = [&](int l) {
+    tiny_stencil<TM, true>(lv[l], it(l), other(l));
+    cur[l] ^= 1;
+    __syncthreads();
+  };
+  cur[first] = 0;
+  for (int l = first; l < nlev - 1; ++l) {
+    for (int k = 1; k < nu; ++k) jac(l);
+    tiny_stencil<TM, false>(lv[l], it(l), other(l));
+    __syncthreads();
+    tiny_restrict(lv[l], other(l), lv[l + 1]);
+    __syncthreads();
+    cur[l + 1] = 0;
+  }
+  for (int k = 1; k < nu_c; ++k) jac(nlev - 1);
+  for (int l = nlev - 2; l >= first; --l) {
+    tiny_prolong(lv[l], it(l), lv[l + 1], it(l + 1));
+    __syncthreads();
+    for (int k = 0; k < nu; ++k) jac(l);
+  }
+  return cur[first];
+}
+
 template <class TM>
 struct Vcycle {
   int nlev, lsmall, nu, nu_c;  // as in PcgArgs
@@ -322,13 +421,11 @@ struct Vcycle {
     if (lsmall >= L) {  // the coarsest level is big
       if (!sweeps(L - 1, nu_c, L == 1)) return false;
     } else {
-      exec = blockIdx.x == 0;  // CTA 0 alone; the others follow the buffers
-      const unsigned pc0 = pc;
-      for (int l = big_end; l < L - 1; ++l) down(l);
-      sweeps(L - 1, nu_c, L == 1);
-      for (int l = L - 2; l >= big_end; --l) up(l);
-      pc = pc0;  // CTA 0 counted its passes; every CTA resumes from the same count
-      exec = true;
+      // CTA 0 alone runs the levels [big_end, L) with the point-wise passes
+      // (the warp march's dependent row chain, not bandwidth, sets the time at
+      // these sizes); every CTA knows where level big_end's result ends
+      if (blockIdx.x == 0) (void)tiny_vcycle<TM>(lv, L, big_end, nu, nu_c);
+      cur[big_end] = (big_end < L - 1 ? 2 * nu - 1 : nu_c - 1) & 1;
       if (!tm.sync(red)) return false;  // publishes CTA 0's levels
     }
     for (int l = big_end - 1; l >= 0; --l)

@@ -293,3 +293,20 @@ def test_binary32_vcycle_options_converge_to_oracle(opt):
     # the binary64 V-cycle with the same options: same iteration count within a few
     _, r64 = _solve(b, nx, "mg_f64", tol, 3000, **opt)
     assert abs(rec["iters"] - r64["iters"]) <= max(3, r64["iters"] // 5), (rec, r64)
+
+
+@pytest.mark.parametrize("nx,ny", [(100, 100), (129, 130), (130, 129), (257, 258), (300, 200), (513, 130), (1000, 9),
+                                   (385, 387)])
+def test_binary32_vcycle_fixed_iterations_near_oracle(nx, ny):
+    # The binary32 V-cycle (fused passes, first sweeps formed from b, levels in
+    # shared memory) against the oracle's binary64 one at fixed iterations: they
+    # differ by binary32 rounding only, so every element agrees to ~1e-6.  Shapes
+    # whose coarse width is a multiple of 64 leave fine columns past the last
+    # strip (129, 257, 385); odd and even heights leave fine rows above the last
+    # coarse row.
+    b = gen.uniform_rhs(nx, ny, seed=nx * 5 + ny, ld=gen.pitch(nx, 8))
+    for k in (1, 2, 4):
+        x, rec = _solve(b, nx, "mg_f32", 0.0, k)
+        xo, io = oracle.cg_pcg(b, tol=0.0, maxit=k, nx=nx)
+        assert rec["iters"] == io["iters"] == k
+        assert _rel(x, xo[:, :nx]) <= 2e-5, (k, _rel(x, xo[:, :nx]))
