@@ -32,7 +32,8 @@ constexpr int kGmMaxBlocks = 4096;  // partial-sum slots
 // Solve state in device memory (the workspace's control block).
 struct GmScal {
   double bb, thr, rr, gamma, alpha, beta;
-  int iters, status, stop, cur, zero_x, pad;
+  int iters, status, stop, cur, zero_x;
+  int xpend;  // x += alpha p of the last x, r pass is still to be applied (k_gm_pq or k_gm_xfinal)
 };
 
 // Per-call arguments, written by k_gm_bind before each graph launch, so that
@@ -694,22 +695,27 @@ __global__ void __launch_bounds__(256) k_gm_rz(GmScal* sc, const double* part, i
   sc->gamma = rz;
 }
 
-// p = z + beta p (halo included), q = A p, partial (p, q).
+// p = z + beta p (halo included), q = A p, partial (p, q); and the previous
+// iteration's x += alpha p with that p (read here anyway), deferred from the
+// x, r pass (which then moves 16 bytes a point fewer).
 template <class TM>
-__global__ void __launch_bounds__(kGmThreads) k_gm_pq(const GmScal* sc, double* part, int nx, int ny,
-                                                       Grid<double> p0, Grid<double> p1, Grid<double> q,
-                                                       MgLevel<TM> L0, int zbuf, int rev) {
+__global__ void __launch_bounds__(kGmThreads) k_gm_pq(const GmScal* sc, const GmBind* bd, double* part, int nx,
+                                                       int ny, int ld, Grid<double> p0, Grid<double> p1,
+                                                       Grid<double> q, MgLevel<TM> L0, int zbuf, int rev) {
   if (sc->stop) return;
   constexpr int V = 2;
   const Sched s = gm_sched(rev);
   const Units un = make_units(nx, ny, V, s.nw, 2);
   const double beta = sc->beta;
   const bool first = (sc->iters == 0);
+  const bool xp = sc->xpend != 0;
+  const double alpha_old = sc->alpha;
+  const Grid<double> x{bd->x, ld};
   const Grid<double> pold = sc->cur ? p1 : p0;
   const Grid<double> pnew = sc->cur ? p0 : p1;
   const Grid<const TM> gz{zbuf ? L0.v : L0.u, L0.ld};
   Acc64 apq;
-  struct D { int dummy; };
+  struct D { double x[V], p[V]; };
   for (int u = s.w; u < un.nunits; u += s.nw) {
     int st, y0, y1;
     unit_bounds(un, u, ny, st, y0, y1);
@@ -735,13 +741,25 @@ __global__ void __launch_bounds__(kGmThreads) k_gm_pq(const GmScal* sc, double* 
         f.hr = (s.lane == 31) ? __fma_rn(beta, pone(j, xs + 32 * V), zone(j, xs + 32 * V)) : 0.0;
       }
     };
-    auto load = [&](int, D&) {};
-    auto finish = [&](int j, const D&, const FRow<V, double>& S, const FRow<V, double>& C, const FRow<V, double>& N) {
+    auto load = [&](int j, D& d) {
+      if (xp) {
+        load_row<V>(x, j, xl, nx, d.x);
+        load_row<V>(pold, j, xl, nx, d.p);
+      }
+    };
+    auto finish = [&](int j, const D& d, const FRow<V, double>& S, const FRow<V, double>& C,
+                      const FRow<V, double>& N) {
       double qv[V];
       stencil_row<V>(S, C, N, s.lane, qv);
       store_row<V>(pnew, j, xl, nx, C.f);
       store_row<V>(q, j, xl, nx, qv);
       acc_dot<V>(apq, j, C.f, qv, nval);
+      if (xp) {
+        double xv[V];
+#pragma unroll
+        for (int k = 0; k < V; ++k) xv[k] = __fma_rn(alpha_old, d.p[k], d.x[k]);
+        store_row<V>(x, j, xl, nx, xv);
+      }
     };
     march<V, double, D>(y0, y1, s.rev, field, load, finish);
   }
@@ -754,6 +772,7 @@ __global__ void __launch_bounds__(256) k_gm_alpha(GmScal* sc, const double* part
   if (sc->stop) return;
   const double pq = gm_total(part, nb, 0);
   if (threadIdx.x != 0) return;
+  sc->xpend = 0;  // k_gm_pq applied the previous x update
   if (!(pq > 0.0) || !isfinite(pq)) {
     sc->status = LAP5CG_ERR_BREAKDOWN;
     sc->stop = 1;
@@ -763,46 +782,40 @@ __global__ void __launch_bounds__(256) k_gm_alpha(GmScal* sc, const double* part
   sc->cur ^= 1;
 }
 
-// x += alpha p, r -= alpha q, partial (r, r); level 0: b = r, u = c b (write_u).
+// r -= alpha q, partial (r, r); level 0: b = r, u = c b (write_u).  (x += alpha p
+// is left to the next p, q pass or, after the loop, to k_gm_xfinal.)
 template <class TM>
-__global__ void __launch_bounds__(kGmThreads) k_gm_xr(const GmScal* sc, const GmBind* bd, double* part, int nx,
-                                                       int ny, int ld, Grid<double> r, Grid<double> p0,
-                                                       Grid<double> p1, Grid<double> q, MgLevel<TM> L0, int rev,
+__global__ void __launch_bounds__(kGmThreads) k_gm_xr(const GmScal* sc, double* part, int nx, int ny,
+                                                       Grid<double> r, Grid<double> q, MgLevel<TM> L0, int rev,
                                                        int write_u) {
   if (sc->stop) return;
   constexpr int V = 2;
-  const Grid<double> x{bd->x, ld};
   const Sched s = gm_sched(rev);
   const Units un = make_units(nx, ny, V, s.nw, 2);
   const double alpha = sc->alpha;
-  const Grid<double> p = sc->cur ? p1 : p0;  // the p formed by k_gm_pq (cur was flipped since)
   const Grid<TM> g0b{L0.b, L0.ld}, g0u{L0.u, L0.ld};
   const TM cm = (TM)kMgC;
   Acc64 arr;
-  struct D { double x[V], r[V], p[V], q[V]; };
+  struct D { double r[V], q[V]; };
   for (int u = s.w; u < un.nunits; u += s.nw) {
     int st, y0, y1;
     unit_bounds(un, u, ny, st, y0, y1);
     const int xl = Lanes<V>::first(st * 32 * V, s.lane);
     const int nval = nx - xl;
     auto load = [&](int j, D& d) {
-      load_row<V>(x, j, xl, nx, d.x);
       load_row<V>(r, j, xl, nx, d.r);
-      load_row<V>(p, j, xl, nx, d.p);
       load_row<V>(q, j, xl, nx, d.q);
     };
     auto finish = [&](int j, const D& d) {
-      double xv[V], rv[V];
+      double rv[V];
       TM rb[V], ru[V];
 #pragma unroll
       for (int k = 0; k < V; ++k) {
-        xv[k] = __fma_rn(alpha, d.p[k], d.x[k]);
         rv[k] = __fma_rn(-alpha, d.q[k], d.r[k]);
         rb[k] = (TM)rv[k];
         ru[k] = cm * rb[k];
       }
       acc_dot<V>(arr, j, rv, rv, nval);
-      store_row<V>(x, j, xl, nx, xv);
       store_row<V>(r, j, xl, nx, rv);
       store_row<V>(g0b, j, xl, nx, rb);
       if (write_u) store_row<V>(g0u, j, xl, nx, ru);
@@ -827,6 +840,7 @@ __global__ void __launch_bounds__(256) k_gm_check(GmScal* sc, const GmBind* bd, 
   GmScal s = *sc;
   s.rr = rr;
   s.iters += 1;
+  s.xpend = 1;  // this iteration's x += alpha p is pending
   if (history) history[s.iters] = sqrt(rr / s.bb);
   if (!isfinite(rr)) {
     s.status = LAP5CG_ERR_NONFINITE;
@@ -839,6 +853,20 @@ __global__ void __launch_bounds__(256) k_gm_check(GmScal* sc, const GmBind* bd, 
   }
   *sc = s;
   cudaGraphSetConditional(h, s.stop ? 0u : 1u);
+}
+
+// After the loop: the pending x += alpha p (the last x, r pass's).
+__global__ void __launch_bounds__(kGmThreads) k_gm_xfinal(const GmScal* sc, const GmBind* bd, int nx, int ny, int ld,
+                                                           Grid<double> p0, Grid<double> p1) {
+  if (!sc->xpend) return;
+  const double alpha = sc->alpha;
+  const Grid<double> p = sc->cur ? p1 : p0;
+  double* x = bd->x;
+  const long long n = (long long)nx * ny;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(t / nx), i = (int)(t - (long long)j * nx);
+    x[(size_t)j * ld + i] = __fma_rn(alpha, p.row(j)[i], x[(size_t)j * ld + i]);
+  }
 }
 
 // After the loop: x = 0 for b = 0; partial (r, r) of the true residual b - A x.
@@ -1179,7 +1207,7 @@ static int gm_build(const SolvePlan& p, const PcgArgs<TM>& a, cudaGraphExec_t* e
     }
     int zb = zbuf, rev1 = 1, rev0 = 0;
     {
-      void* args[] = {&sc, &part, &nx_, &ny_, &gp0, &gp1, &gq, &L0, &zb, &rev1};
+      void* args[] = {&sc, &bd, &part, &nx_, &ny_, &ld_, &gp0, &gp1, &gq, &L0, &zb, &rev1};
       if ((rc = gm_add(body, &bp, f_pq, nb_pq, kGmThreads, args)) != LAP5CG_OK) return fail(rc);
     }
     int nbq = nb_pq;
@@ -1189,7 +1217,7 @@ static int gm_build(const SolvePlan& p, const PcgArgs<TM>& a, cudaGraphExec_t* e
         return fail(rc);
     }
     {
-      void* args[] = {&sc, &bd, &part, &nx_, &ny_, &ld_, &gr, &gp0, &gp1, &gq, &L0, &rev0, &write_u};
+      void* args[] = {&sc, &part, &nx_, &ny_, &gr, &gq, &L0, &rev0, &write_u};
       if ((rc = gm_add(body, &bp, f_xr, nb_xr, kGmThreads, args)) != LAP5CG_OK) return fail(rc);
     }
     int nbx = nb_xr;
@@ -1200,6 +1228,12 @@ static int gm_build(const SolvePlan& p, const PcgArgs<TM>& a, cudaGraphExec_t* e
     }
   }
   prev = loop;
+  {
+    const void* f_xf = reinterpret_cast<const void*>(&k_gm_xfinal);
+    void* args[] = {&sc, &bd, &nx_, &ny_, &ld_, &gp0, &gp1};
+    if ((rc = gm_add(g, &prev, f_xf, gm_blocks(f_xf, kGmThreads, dp.sms), kGmThreads, args)) != LAP5CG_OK)
+      return fail(rc);
+  }
   int tr = p.opts.true_residual;
   {
     void* args[] = {&sc, &bd, &part, &nx_, &ny_, &ld_, &tr};
