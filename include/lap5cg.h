@@ -94,7 +94,13 @@ typedef enum { LAP5CG_CLASSIC = 0, LAP5CG_NEWCG = 1 } lap5cg_variant;
  *              recurrences need an exactly linear M; see MG_F64).
  *   MG_F64:    the same with the V-cycle in binary64; LAP5CG_NEWCG runs the
  *              pipelined form (Algorithm 2 with M: one fused pass and one grid
- *              reduction per iteration besides M^-1). */
+ *              reduction per iteration besides M^-1).
+ *              MG_F32 / MG_F64 with LAP5CG_CLASSIC run as a CUDA graph (one
+ *              kernel per pass, the iterations looped on the device by a
+ *              conditional node; cached, see Ownership), or as one persistent
+ *              kernel when the stream is being captured into the caller's
+ *              graph; the pipelined form is always one persistent kernel.
+ *              Concurrent calls must not share a workspace. */
 typedef enum {
   LAP5CG_PREC_F64 = 0, LAP5CG_PREC_F32 = 1, LAP5CG_PREC_IR_F32 = 2, LAP5CG_PREC_IR_BF16PR = 3,
   LAP5CG_PREC_MG_F32 = 4, LAP5CG_PREC_MG_F64 = 5
