@@ -257,7 +257,7 @@ def cg_ir(b, x0=None, tol=1e-10, max_outer=60, inner="f32", tol_in=None, maxit_i
     if tol_in is None:
         tol_in = 1e-4 if inner == "f32" else 1e-2
     if maxit_in is None:  # the inner iteration cap of each refinement step
-        maxit_in = 4 * (nx + ny) + 50 if inner == "f32" else nx + ny + 50
+        maxit_in = 4 * (nx + ny) + 50 if inner == "f32" else 2 * (nx + ny) + 50
     info = Info()
     lib().ora_cg_ir(nx, ny, ld, _ptr(b), _ptr(x), tol, max_outer, storage, tol_in, maxit_in, ctypes.byref(info))
     return x, info.as_dict()
