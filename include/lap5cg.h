@@ -129,7 +129,7 @@ typedef struct {
   int32_t min_rows;         /* minimum rows per warp unit; 0 = default (2) */
   int32_t true_residual;    /* 1 (default) recompute ||b - A x|| at exit, 0 skip */
   int32_t maxit_inner;      /* IR: inner iteration cap per refinement step; 0 = default
-                               (IR_F32: 4 (nx + ny) + 50; IR_BF16PR: nx + ny + 50) */
+                               (IR_F32: 4 (nx + ny) + 50; IR_BF16PR: 2 (nx + ny) + 50) */
   int32_t max_outer;        /* IR: refinement step cap; 0 = default (60) */
   double tol_inner;         /* IR: inner relative tolerance; <= 0 = default (1e-4 F32, 1e-2 BF16) */
   double timeout_s;         /* device barrier time limit in seconds; <= 0 = default (2 s) */

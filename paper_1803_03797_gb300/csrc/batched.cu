@@ -115,7 +115,8 @@ __device__ __forceinline__ void solve_ir_instance(const BatchArgs& a, const Batc
   s.d = Grid<float>{reinterpret_cast<float*>(base + 3 * vr + vf), ldi};
   s.store_z = a.store_z > 0 ? 1 : 0;
   s.max_outer = a.max_outer;
-  s.maxit_inner = a.maxit_inner > 0 ? a.maxit_inner : 4 * (e.nx + e.ny) + 50;
+  // the single solves' inner caps: binary32 4 (nx + ny) + 50, bf16 p, r 2 (nx + ny) + 50
+  s.maxit_inner = a.maxit_inner > 0 ? a.maxit_inner : (sizeof(T) == 2 ? 2 : 4) * (e.nx + e.ny) + 50;
   s.tol_inner = a.tol_inner;
   s.uo = make_units(e.nx, e.ny, 2, W, a.min_rows);
   ir_solve<T, V, 2, R>(s, tm, red, dsm);

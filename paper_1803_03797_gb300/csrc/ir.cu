@@ -80,12 +80,11 @@ static int solve_ir_t(const SolvePlan& p, cudaStream_t st) {
   a.d = Grid<float>{reinterpret_cast<float*>(base + 3 * vr + vf), ldi};
   a.store_z = p.opts.store_z > 0 ? 1 : 0;  // binary32 inner passes are bandwidth bound: recompute A p
   a.max_outer = p.opts.max_outer > 0 ? p.opts.max_outer : 60;
-  // inner cap: binary32 4 (nx + ny) + 50; bf16 p, r nx + ny + 50 -- past about that many
-  // iterations a bf16 inner solve on the smooth residuals of later refinement
-  // steps stops contracting (measured at 8192^2: a cap of 65586 stalls the
-  // refinement at 1e-2, 16384 reaches 1e-10)
+  // inner cap: binary32 4 (nx + ny) + 50; bf16 p, r 2 (nx + ny) + 50, the measured
+  // best for time to 1e-10 at 4096^2 (5.3 s against 6.3 s with nx + ny + 50;
+  // at 8192^2 every cap from 4096 to 65586 converges, in 72 to 89 s)
   a.maxit_inner = p.opts.maxit_inner > 0 ? p.opts.maxit_inner
-                                         : (sizeof(TR) == 2 ? p.nx + p.ny + 50 : 4 * (p.nx + p.ny) + 50);
+                                         : (sizeof(TR) == 2 ? 2 * (p.nx + p.ny) + 50 : 4 * (p.nx + p.ny) + 50);
   a.tol_inner = p.opts.tol_inner > 0.0 ? p.opts.tol_inner : (sizeof(TR) == 2 ? 1e-2 : 1e-4);
   void* args[] = {&a};
   return cooperative_launch(fn, cfg, args, st, rg);
