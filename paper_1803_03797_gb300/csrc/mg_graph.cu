@@ -350,24 +350,27 @@ __global__ void __launch_bounds__(kGmThreads) k_gm_jac_res_restrict(const GmScal
     unit_bounds(un, w, C.ny, st, y0, y1);
     const int xs = st * 128, f0 = xs + 4 * lane, I0 = f0 / 2;
     const bool last_strip = (st == un.ns - 1), top = (y1 == C.ny);
-    auto cb_row = [&](int i, FRow<4, TM>& f) {  // c b of row i (zero outside the grid)
+    // c b of row i (zero outside the grid), and b itself for the lane's columns
+    auto cb_row = [&](int i, FRow<4, TM>& f, TM (&raw)[4]) {
       field_plain<4>(gb, F.nx, F.ny, i, f0, xs, lane, f);
 #pragma unroll
-      for (int k = 0; k < 4; ++k) f.f[k] = c * f.f[k];
+      for (int k = 0; k < 4; ++k) {
+        raw[k] = f.f[k];
+        f.f[k] = c * f.f[k];
+      }
       f.hl = c * f.hl;
       f.hr = c * f.hr;
     };
-    // v of row i from c b rows i-1, i, i+1; hr2: v at xs + 129 (lane 31)
-    auto v_row = [&](int i, const FRow<4, TM>& S, const FRow<4, TM>& Cr, const FRow<4, TM>& N, FRow<4, TM>& v,
-                     TM& hr2) {
+    // v of row i from c b rows i-1, i, i+1 (bv: b of row i); hr2: v at xs + 129 (lane 31)
+    auto v_row = [&](int i, const FRow<4, TM>& S, const FRow<4, TM>& Cr, const TM (&bv)[4], const FRow<4, TM>& N,
+                     FRow<4, TM>& v, TM& hr2) {
       if (i < 0 || i >= F.ny) {
         v.zero();
         hr2 = TM(0);
         return;
       }
-      TM ax[4], bv[4];
+      TM ax[4];
       stencil_row<4>(S, Cr, N, lane, ax);
-      load_row<4>(gb, i, f0, F.nx, bv);
 #pragma unroll
       for (int k = 0; k < 4; ++k) v.f[k] = f0 + k < F.nx ? mg_fma(c, bv[k] - ax[k], Cr.f[k]) : TM(0);
       v.hl = (lane == 0) ? v_at(i, xs - 1) : TM(0);
@@ -382,17 +385,16 @@ __global__ void __launch_bounds__(kGmThreads) k_gm_jac_res_restrict(const GmScal
         if (xs + 129 < F.nx) gv.row(i)[xs + 129] = hr2;
       }
     };
-    // residual of row j at columns f0 .. f0+4 from v rows j-1, j, j+1
+    // residual of row j at columns f0 .. f0+4 from v rows j-1, j, j+1 (bv: b of row j)
     auto res_row = [&](int j, const FRow<4, TM>& S, const FRow<4, TM>& Cr, TM crh2, const FRow<4, TM>& N,
-                       TM (&r)[5]) {
+                       const TM (&bv)[4], TM (&r)[5]) {
       if (j < 0 || j >= F.ny) {
 #pragma unroll
         for (int k = 0; k < 5; ++k) r[k] = TM(0);
         return;
       }
-      TM ax[4], bv[4];
+      TM ax[4];
       stencil_row<4>(S, Cr, N, lane, ax);
-      load_row<4>(gb, j, f0, F.nx, bv);
 #pragma unroll
       for (int k = 0; k < 4; ++k) r[k] = f0 + k < F.nx ? bv[k] - ax[k] : TM(0);
       TM e = __shfl_down_sync(0xffffffffu, r[0], 1);
@@ -410,35 +412,42 @@ __global__ void __launch_bounds__(kGmThreads) k_gm_jac_res_restrict(const GmScal
       }
       r[4] = e;
     };
-    // march state: c b rows (bA, bB, bC) = rows i-1, i, i+1 of the next v row i;
-    // v rows (vS, vC, vN) with their hr2 for the next residual row
+    // march state: c b rows (bA, bB, bC) = rows i-1, i, i+1 of the last v row i,
+    // with b of the same rows (rA, rB, rC); v rows (vS, vC, vN) with their hr2
+    // for the next residual row (whose b row is then rA)
     FRow<4, TM> bA, bB, bC, vS, vC, vN;
+    TM rA[4], rB[4], rC[4];
     TM hS, hC, hN;
-    int i = 2 * y0 - 1;  // next v row
-    cb_row(i - 1, bA);
-    cb_row(i, bB);
-    cb_row(i + 1, bC);
-    v_row(i, bA, bB, bC, vS, hS);
-    auto next_v = [&](FRow<4, TM>& v, TM& h) {  // v row i + 1, advancing the c b rows
+    int i = 2 * y0 - 1;  // the last v row formed
+    cb_row(i - 1, bA, rA);
+    cb_row(i, bB, rB);
+    cb_row(i + 1, bC, rC);
+    v_row(i, bA, bB, rB, bC, vS, hS);
+    auto next_v = [&](FRow<4, TM>& v, TM& h) {  // v row i + 1, advancing the b rows
       ++i;
       bA = bB;
       bB = bC;
-      cb_row(i + 1, bC);
-      v_row(i, bA, bB, bC, v, h);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        rA[k] = rB[k];
+        rB[k] = rC[k];
+      }
+      cb_row(i + 1, bC, rC);
+      v_row(i, bA, bB, rB, bC, v, h);
     };
     next_v(vC, hC);  // row 2 y0
     next_v(vN, hN);  // row 2 y0 + 1
     store_v(2 * y0, vC, hC);
     TM lo[5], mid[5], hi[5];
-    res_row(2 * y0, vS, vC, hC, vN, lo);
+    res_row(2 * y0, vS, vC, hC, vN, rA, lo);
     for (int J = y0; J < y1; ++J) {
       vS = vC; vC = vN; hC = hN;
       next_v(vN, hN);  // row 2J + 2
-      res_row(2 * J + 1, vS, vC, hC, vN, mid);
+      res_row(2 * J + 1, vS, vC, hC, vN, rA, mid);
       store_v(2 * J + 1, vC, hC);
       vS = vC; vC = vN; hC = hN;
       next_v(vN, hN);  // row 2J + 3
-      res_row(2 * J + 2, vS, vC, hC, vN, hi);
+      res_row(2 * J + 2, vS, vC, hC, vN, rA, hi);
       if (J + 1 < y1 || top) store_v(2 * J + 2, vC, hC);
       TM bcv[2], ucv[2];
 #pragma unroll
