@@ -474,7 +474,8 @@ def reproducible_workload(lap5cg, torch, dev, b, iters=500, reps=2):
 
 
 def targets_summary(extras, roofline):
-    """The benchmark spec's figures as flat scalars (None where not measured)."""
+    """The headline targets (HBM fractions, FP64 fraction, times to 1e-10 and their speedups) as flat scalars
+    (None where not measured)."""
     def get(*path):
         d = extras
         for k in path:
