@@ -350,9 +350,11 @@ __global__ void __launch_bounds__(kGmThreads) k_gm_jac_res_restrict(const GmScal
     unit_bounds(un, w, C.ny, st, y0, y1);
     const int xs = st * 128, f0 = xs + 4 * lane, I0 = f0 / 2;
     const bool last_strip = (st == un.ns - 1), top = (y1 == C.ny);
-    // c b of row i (zero outside the grid), and b itself for the lane's columns
-    auto cb_row = [&](int i, FRow<4, TM>& f, TM (&raw)[4]) {
-      field_plain<4>(gb, F.nx, F.ny, i, f0, xs, lane, f);
+    // b of row i (zero outside the grid) as loaded, then scaled to c b with b
+    // itself kept for the lane's columns; the march loads a row one step
+    // before it scales and uses it, so the load's latency overlaps a row's work
+    auto b_load = [&](int i, FRow<4, TM>& f) { field_plain<4>(gb, F.nx, F.ny, i, f0, xs, lane, f); };
+    auto cb_scale = [&](FRow<4, TM>& f, TM (&raw)[4]) {
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         raw[k] = f.f[k];
@@ -360,6 +362,10 @@ __global__ void __launch_bounds__(kGmThreads) k_gm_jac_res_restrict(const GmScal
       }
       f.hl = c * f.hl;
       f.hr = c * f.hr;
+    };
+    auto cb_row = [&](int i, FRow<4, TM>& f, TM (&raw)[4]) {
+      b_load(i, f);
+      cb_scale(f, raw);
     };
     // v of row i from c b rows i-1, i, i+1 (bv: b of row i); hr2: v at xs + 129 (lane 31)
     auto v_row = [&](int i, const FRow<4, TM>& S, const FRow<4, TM>& Cr, const TM (&bv)[4], const FRow<4, TM>& N,
@@ -415,24 +421,27 @@ __global__ void __launch_bounds__(kGmThreads) k_gm_jac_res_restrict(const GmScal
     // march state: c b rows (bA, bB, bC) = rows i-1, i, i+1 of the last v row i,
     // with b of the same rows (rA, rB, rC); v rows (vS, vC, vN) with their hr2
     // for the next residual row (whose b row is then rA)
-    FRow<4, TM> bA, bB, bC, vS, vC, vN;
+    FRow<4, TM> bA, bB, bC, bD, vS, vC, vN;  // bD: b of row i + 2, loaded ahead
     TM rA[4], rB[4], rC[4];
     TM hS, hC, hN;
     int i = 2 * y0 - 1;  // the last v row formed
     cb_row(i - 1, bA, rA);
     cb_row(i, bB, rB);
     cb_row(i + 1, bC, rC);
+    b_load(i + 2, bD);
     v_row(i, bA, bB, rB, bC, vS, hS);
     auto next_v = [&](FRow<4, TM>& v, TM& h) {  // v row i + 1, advancing the b rows
       ++i;
       bA = bB;
       bB = bC;
+      bC = bD;
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         rA[k] = rB[k];
         rB[k] = rC[k];
       }
-      cb_row(i + 1, bC, rC);
+      cb_scale(bC, rC);
+      b_load(i + 2, bD);
       v_row(i, bA, bB, rB, bC, v, h);
     };
     next_v(vC, hC);  // row 2 y0
