@@ -1269,8 +1269,8 @@ static int gm_build(const SolvePlan& p, const PcgArgs<TM>& a, cudaGraphExec_t* e
 }
 
 // Classic MG-PCG through the cached graph; *used = false when this shape
-// takes the persistent kernel (the fine grid itself is a single-CTA level, or
-// the stream is capturing).
+// takes the persistent kernel (the fine grid itself is a single-CTA level, the
+// stream is capturing, or the graph cannot be built).
 template <class TM>
 int solve_mg_graph(const SolvePlan& p, const PcgArgs<TM>& a, cudaStream_t st, bool* used) {
   *used = false;
@@ -1294,7 +1294,10 @@ int solve_mg_graph(const SolvePlan& p, const PcgArgs<TM>& a, cudaStream_t st, bo
     }
   if (!exec) {
     const int rc = gm_build<TM>(p, a, &exec);
-    if (rc != LAP5CG_OK) return rc;
+    if (rc != LAP5CG_OK) {  // a driver without conditional graph nodes: the persistent kernel solves
+      cudaGetLastError();
+      return LAP5CG_OK;
+    }
     if (g_gm_cache.size() >= kGmCacheSize) {
       cudaGraphExecDestroy(g_gm_cache.front().second);
       g_gm_cache.erase(g_gm_cache.begin());
