@@ -379,9 +379,15 @@ __global__ void __launch_bounds__(kGmThreads) k_gm_jac_res_restrict(const GmScal
       stencil_row<4>(S, Cr, N, lane, ax);
 #pragma unroll
       for (int k = 0; k < 4; ++k) v.f[k] = f0 + k < F.nx ? mg_fma(c, bv[k] - ax[k], Cr.f[k]) : TM(0);
-      v.hl = (lane == 0) ? v_at(i, xs - 1) : TM(0);
-      v.hr = (lane == 31) ? v_at(i, xs + 128) : TM(0);
-      hr2 = (lane == 31) ? v_at(i, xs + 129) : TM(0);
+      // the three halo points in one divergent branch: lane 0 forms column
+      // xs - 1, lane 31 column xs + 128 and lane 30 column xs + 129, which
+      // lane 31 then takes by a shuffle
+      TM h = TM(0);
+      if (lane == 0 || lane >= 30) h = v_at(i, lane == 0 ? xs - 1 : lane == 31 ? xs + 128 : xs + 129);
+      const TM h30 = __shfl_up_sync(0xffffffffu, h, 1);
+      v.hl = (lane == 0) ? h : TM(0);
+      v.hr = (lane == 31) ? h : TM(0);
+      hr2 = (lane == 31) ? h30 : TM(0);
     };
     auto store_v = [&](int i, const FRow<4, TM>& v, TM hr2) {
       if (i < 0 || i >= F.ny) return;
