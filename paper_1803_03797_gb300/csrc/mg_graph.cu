@@ -354,21 +354,22 @@ __global__ void __launch_bounds__(kGmThreads) k_gm_jac_res_restrict(const GmScal
     // itself kept for the lane's columns; the march loads a row one step
     // before it scales and uses it, so the load's latency overlaps a row's work
     auto b_load = [&](int i, FRow<4, TM>& f) { field_plain<4>(gb, F.nx, F.ny, i, f0, xs, lane, f); };
-    auto cb_scale = [&](FRow<4, TM>& f, TM (&raw)[4]) {
+    auto cb_scale = [&](FRow<4, TM>& f, TM (&raw)[5]) {
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         raw[k] = f.f[k];
         f.f[k] = c * f.f[k];
       }
+      raw[4] = f.hr;  // lane 31: b at column xs + 128, for the residual there
       f.hl = c * f.hl;
       f.hr = c * f.hr;
     };
-    auto cb_row = [&](int i, FRow<4, TM>& f, TM (&raw)[4]) {
+    auto cb_row = [&](int i, FRow<4, TM>& f, TM (&raw)[5]) {
       b_load(i, f);
       cb_scale(f, raw);
     };
     // v of row i from c b rows i-1, i, i+1 (bv: b of row i); hr2: v at xs + 129 (lane 31)
-    auto v_row = [&](int i, const FRow<4, TM>& S, const FRow<4, TM>& Cr, const TM (&bv)[4], const FRow<4, TM>& N,
+    auto v_row = [&](int i, const FRow<4, TM>& S, const FRow<4, TM>& Cr, const TM (&bv)[5], const FRow<4, TM>& N,
                      FRow<4, TM>& v, TM& hr2) {
       if (i < 0 || i >= F.ny) {
         v.zero();
@@ -399,7 +400,7 @@ __global__ void __launch_bounds__(kGmThreads) k_gm_jac_res_restrict(const GmScal
     };
     // residual of row j at columns f0 .. f0+4 from v rows j-1, j, j+1 (bv: b of row j)
     auto res_row = [&](int j, const FRow<4, TM>& S, const FRow<4, TM>& Cr, TM crh2, const FRow<4, TM>& N,
-                       const TM (&bv)[4], TM (&r)[5]) {
+                       const TM (&bv)[5], TM (&r)[5]) {
       if (j < 0 || j >= F.ny) {
 #pragma unroll
         for (int k = 0; k < 5; ++k) r[k] = TM(0);
@@ -419,16 +420,16 @@ __global__ void __launch_bounds__(kGmThreads) k_gm_jac_res_restrict(const GmScal
           acc -= crh2;
           acc -= S.hr;
           acc -= N.hr;
-          e = gb.row(j)[xe] - acc;
+          e = bv[4] - acc;
         }
       }
       r[4] = e;
     };
     // march state: c b rows (bA, bB, bC) = rows i-1, i, i+1 of the last v row i,
-    // with b of the same rows (rA, rB, rC); v rows (vS, vC, vN) with their hr2
+    // with b of the same rows (rA, rB, rC; element 4: column xs + 128); v rows (vS, vC, vN) with their hr2
     // for the next residual row (whose b row is then rA)
     FRow<4, TM> bA, bB, bC, bD, vS, vC, vN;  // bD: b of row i + 2, loaded ahead
-    TM rA[4], rB[4], rC[4];
+    TM rA[5], rB[5], rC[5];
     TM hS, hC, hN;
     int i = 2 * y0 - 1;  // the last v row formed
     cb_row(i - 1, bA, rA);
@@ -442,7 +443,7 @@ __global__ void __launch_bounds__(kGmThreads) k_gm_jac_res_restrict(const GmScal
       bB = bC;
       bC = bD;
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
+      for (int k = 0; k < 5; ++k) {
         rA[k] = rB[k];
         rB[k] = rC[k];
       }

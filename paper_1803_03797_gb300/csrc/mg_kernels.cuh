@@ -302,7 +302,7 @@ __device__ void tiny_prolong(const MgLevel<TM>& F, TM* f, const MgLevel<TM>& C, 
 // buffer that holds level `first`'s result (0: u, 1: v).
 template <class TM>
 __device__ int tiny_vcycle(const MgLevel<TM>* lv, int nlev, int first, int nu, int nu_c) {
-  int cur[kMgMaxLevels];
+  int cur[kMgMaxLevels] = {};  // 0: the level's iterate is in u, 1: in v
   auto it = [&](int l) -> TM* { return cur[l] ? lv[l].v : lv[l].u; };
   auto other = [&](int l) -> TM* { return cur[l] ? lv[l].u : lv[l].v; };
   auto jac = [&](int l) {
