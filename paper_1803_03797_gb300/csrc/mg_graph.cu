@@ -588,10 +588,21 @@ __device__ void gm_small_levels(const GmLevels<TM>& levels, int nlev, int first,
   const MgLevel<TM>& G = levels.lv[first];
   const int n0 = G.ny * G.ld;
   const TM c = (TM)kMgC;
-  for (int i = threadIdx.x; i < n0; i += blockDim.x) {
-    const TM bi = G.b[i];
-    if (SMEM) lv[first].b[i] = bi;
-    lv[first].u[i] = c * bi;
+  for (int i0 = threadIdx.x; i0 < n0; i0 += 4 * blockDim.x) {  // four loads in flight a thread
+    TM bi[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int i = i0 + k * (int)blockDim.x;
+      bi[k] = i < n0 ? G.b[i] : TM(0);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int i = i0 + k * (int)blockDim.x;
+      if (i < n0) {
+        if (SMEM) lv[first].b[i] = bi[k];
+        lv[first].u[i] = c * bi[k];
+      }
+    }
   }
   __syncthreads();
   const int par = tiny_vcycle<TM>(lv, nlev, first, nu, nu_c);

@@ -238,12 +238,29 @@ __device__ __forceinline__ TM tiny_at(const TM* g, int nx, int ny, int ld, int i
   return (i < 0 || i >= nx || j < 0 || j >= ny) ? TM(0) : g[j * ld + i];
 }
 
+// f(i, j) at the thread's points of an nx x ny level: point p = j nx + i for
+// p = threadIdx.x, + blockDim.x, ...; (i, j) advanced by the stride's row and
+// column steps (two divisions a pass, none a point).
+template <class F>
+__device__ __forceinline__ void tiny_for(int nx, int ny, F&& f) {
+  const int n = nx * ny;
+  const int sj = (int)blockDim.x / nx, si = (int)blockDim.x - sj * nx;
+  int j = (int)threadIdx.x / nx, i = (int)threadIdx.x - j * nx;
+  for (int p = threadIdx.x; p < n; p += blockDim.x) {
+    f(i, j);
+    i += si;
+    j += sj;
+    if (i >= nx) {
+      i -= nx;
+      ++j;
+    }
+  }
+}
+
 template <class TM, bool JAC>
 __device__ void tiny_stencil(const MgLevel<TM>& L, const TM* in, TM* out) {
   const TM c = (TM)kMgC;
-  const int n = L.nx * L.ny;
-  for (int p = threadIdx.x; p < n; p += blockDim.x) {
-    const int j = p / L.nx, i = p - j * L.nx;
+  tiny_for(L.nx, L.ny, [&](int i, int j) {
     const TM C = in[j * L.ld + i];
     TM acc = TM(4) * C;
     acc -= tiny_at(in, L.nx, L.ny, L.ld, i - 1, j);
@@ -252,16 +269,14 @@ __device__ void tiny_stencil(const MgLevel<TM>& L, const TM* in, TM* out) {
     acc -= tiny_at(in, L.nx, L.ny, L.ld, i, j + 1);
     const TM b = L.b[j * L.ld + i];
     out[j * L.ld + i] = JAC ? mg_fma(c, b - acc, C) : b - acc;
-  }
+  });
 }
 
 // coarse C.b = P^T res, C.u = c C.b
 template <class TM>
 __device__ void tiny_restrict(const MgLevel<TM>& F, const TM* res, const MgLevel<TM>& C) {
   const TM c = (TM)kMgC;
-  const int n = C.nx * C.ny;
-  for (int p = threadIdx.x; p < n; p += blockDim.x) {
-    const int J = p / C.nx, I = p - J * C.nx;
+  tiny_for(C.nx, C.ny, [&](int I, int J) {
     const int fi = 2 * I + 1, fj = 2 * J + 1;
     auto r = [&](int di, int dj) { return tiny_at(res, F.nx, F.ny, F.ld, fi + di, fj + dj); };
     const TM s1 = ((r(-1, 0) + r(1, 0)) + r(0, -1)) + r(0, 1);
@@ -269,15 +284,13 @@ __device__ void tiny_restrict(const MgLevel<TM>& F, const TM* res, const MgLevel
     const TM bc = TM(0.25) * ((TM(4) * r(0, 0) + TM(2) * s1) + s2);
     C.b[J * C.ld + I] = bc;
     C.u[J * C.ld + I] = c * bc;
-  }
+  });
 }
 
 // f += P e
 template <class TM>
 __device__ void tiny_prolong(const MgLevel<TM>& F, TM* f, const MgLevel<TM>& C, const TM* e) {
-  const int n = F.nx * F.ny;
-  for (int p = threadIdx.x; p < n; p += blockDim.x) {
-    const int j = p / F.nx, i = p - j * F.nx;
+  tiny_for(F.nx, F.ny, [&](int i, int j) {
     auto ce = [&](int I, int J) { return tiny_at(e, C.nx, C.ny, C.ld, I, J); };
     TM v;
     if (j & 1) {
@@ -294,7 +307,7 @@ __device__ void tiny_prolong(const MgLevel<TM>& F, TM* f, const MgLevel<TM>& C, 
       }
     }
     f[j * F.ld + i] += v;
-  }
+  });
 }
 
 // The V-cycle from level `first` down to the coarsest and back with the
