@@ -109,26 +109,18 @@ __device__ __forceinline__ Sched gm_sched(int rev) {
                rev != 0};
 }
 
-// One V-cycle pass on a big level (see the GP_ kinds); in / out are the
-// level's buffers, Lc the next coarser level (restriction, prolongation).
+// Restriction (GP_RESTRICT: Lc.b = P^T in, in the level's residual) or
+// prolongation (GP_PROLONG: out, the level's iterate, += P in, in the coarser
+// level's iterate) on a big level, with the row march.
 template <class TM>
-__global__ void __launch_bounds__(kGmThreads) k_gm_pass(const GmScal* sc, double* part, MgLevel<TM> L,
-                                                         MgLevel<TM> Lc, int kind, int rev, const TM* in, TM* out,
-                                                         Grid<const double> r) {
+__global__ void __launch_bounds__(kGmThreads) k_gm_pass(const GmScal* sc, MgLevel<TM> L, MgLevel<TM> Lc, int kind,
+                                                         int rev, const TM* in, TM* out) {
   if (sc->stop) return;  // the solve has ended (uniform over the grid)
   const Sched s = gm_sched(rev);
-  Acc64 acc;
-  switch (kind) {
-    case GP_JAC: mg_stencil_pass<TM, true, false>(s, L, in, out, r, acc); break;
-    case GP_JAC_DOT: {
-      mg_stencil_pass<TM, true, true>(s, L, in, out, r, acc);
-      const double v[1] = {acc.value()};
-      gm_partials<1>(v, part);
-      break;
-    }
-    case GP_RES: mg_stencil_pass<TM, false, false>(s, L, in, out, r, acc); break;
-    case GP_RESTRICT: mg_restrict(s, L, in, Lc); break;      // in: the level's residual
-    default: mg_prolong(s, L, out, Lc, in); break;            // out (fine iterate) += P in (coarse iterate)
+  if (kind == GP_RESTRICT) {
+    mg_restrict(s, L, in, Lc);
+  } else {
+    mg_prolong(s, L, out, Lc, in);
   }
 }
 
@@ -142,8 +134,6 @@ template <class TM> struct GmSweepVec { static constexpr int V = sizeof(TM) == 4
 // the (r, z) sweep: one group of columns a lane (its binary64 r rows would
 // double the registers of the two-group layout)
 template <class TM> struct GmDotVec { static constexpr int V = sizeof(TM) == 4 ? 4 : 2; };
-constexpr bool kGmTiledDot = true;
-constexpr bool kGmFuseDescent = true;
 
 // FROM_B: the input iterate is the level's first sweep from zero, c b, which is
 // formed from b here (the producer of b then stores no iterate).
@@ -1001,7 +991,7 @@ static int gm_pass_list(const PcgArgs<TM>& a, bool fuse, std::vector<GmPassRec<T
   };
   const int big_end = a.lsmall < L - 1 ? a.lsmall : L - 1;
   for (int l = 0; l < big_end; ++l) {  // down: pre-smoothing, residual, restriction
-    if (fuse && kGmFuseDescent && nu == 2) {  // the one explicit sweep, residual and restriction: one pass
+    if (fuse && nu == 2) {  // the one explicit sweep, residual and restriction: one pass
       out.push_back({GP_JAC_RES_RESTRICT, l, (int)(pc++ & 1u), nullptr, other(l), nullptr});
       cur[l] ^= 1;
       cur[l + 1] = 0;
@@ -1199,7 +1189,7 @@ static int gm_build(const SolvePlan& p, const PcgArgs<TM>& a, cudaGraphExec_t* e
         if ((rc = gm_add(body, &bp, f_pj, (unsigned)grid, kGmThreads, pargs)) != LAP5CG_OK) return fail(rc);
         continue;
       }
-      if (kind == GP_JAC_DOT && kGmTiledDot) {
+      if (kind == GP_JAC_DOT) {
         const int V = GmDotVec<TM>::V;
         const long long ntiles = (long long)((L.nx + 32 * V - 1) / (32 * V)) * ((L.ny + 2 * wpc - 1) / (2 * wpc));
         const int grid = (int)std::min<long long>(ntiles, nb_dot_max);
@@ -1210,9 +1200,9 @@ static int gm_build(const SolvePlan& p, const PcgArgs<TM>& a, cudaGraphExec_t* e
       }
       if (kind == GP_JAC || kind == GP_RES) {
         // sweeps and residuals: the tiled kernel, as many CTAs as tiles up to
-        // the resident maximum.  (The (r, z) sweep stays on the march kernel:
-        // measured at 4096^2 the tiled form with the binary64 r rows took 111
-        // against 79 microseconds -- its 104 registers halve the occupancy.)
+        // the resident maximum (binary32: two groups of four columns a lane;
+        // the (r, z) sweep above keeps one, since its binary64 r rows in the
+        // two-group layout took 104 registers and ran slower)
         const int V = GmSweepVec<TM>::V;
         const long long ntiles = (long long)((L.nx + 32 * V - 1) / (32 * V)) * ((L.ny + 2 * wpc - 1) / (2 * wpc));
         const void* fk = kind == GP_RES ? f_sweep_r : pr.from_b ? f_sweep_jb : f_sweep_j;
@@ -1221,13 +1211,13 @@ static int gm_build(const SolvePlan& p, const PcgArgs<TM>& a, cudaGraphExec_t* e
         if ((rc = gm_add(body, &bp, fk, (unsigned)grid, kGmThreads, sargs)) != LAP5CG_OK) return fail(rc);
         continue;
       }
-      void* args[] = {&sc, &part, &L, &Lc, &kind, &rev, &in, &out, &grc};
-      // restriction and prolongation: as many CTAs as the pass has warp units
-      // (two-row units), up to the resident maximum -- the small levels' passes
-      // launch a few CTAs, not a full grid of idle ones.  The (r, z) sweep keeps
-      // the full grid: k_gm_rz adds nb_pass partial sums.
+      // restriction and prolongation (the binary64 V-cycle's separate passes):
+      // as many CTAs as the pass has warp units (two-row units), up to the
+      // resident maximum -- the small levels' passes launch a few CTAs, not a
+      // full grid of idle ones
+      void* args[] = {&sc, &L, &Lc, &kind, &rev, &in, &out};
       int grid = nb_pass;
-      if (kind != GP_JAC_DOT) {
+      {
         const long long kAll = 1ll << 40;
         const Units un = kind == GP_RESTRICT ? make_units(Lc.nx, Lc.ny, 2, kAll, 2) : make_units(L.nx, L.ny, 4, kAll, 2);
         const long long need = ((long long)un.nunits + wpc - 1) / wpc;
