@@ -584,6 +584,10 @@ def main():
                     help="profiling case: lap5_apply on an N x N grid, twice (for ncu)")
     ap.add_argument("--profile-apply-dtype", default="f32", choices=["f32", "bf16", "f64"],
                     help="storage type of the --profile-apply case")
+    ap.add_argument("--profile-solve", default="", choices=["", "newcg_stable_4096", "newcg_small_100"],
+                    help="profiling case, solved twice: newcg_stable_4096 = the stabilised NewCG on the 4096^2 "
+                         "manufactured problem, 20 fixed iterations; newcg_small_100 = NewCG on a 100^2 uniform "
+                         "right-hand side to 1e-8 (the cluster-resident kernel)")
     ap.add_argument("--profile-mg", type=int, default=0,
                     help="profiling only: solve the n^2 manufactured problem to 1e-10 twice with the multigrid-"
                          "preconditioned CG (binary32 V-cycle) and exit")
@@ -608,6 +612,21 @@ def main():
         torch.cuda.synchronize()
         print(json.dumps({"profiling_case": {"lap5_apply": args.profile_apply_dtype, "n": n,
                                              "checksum": float(ya.double().sum())}}))
+        return 0
+
+    if args.profile_solve:
+        lap5cg.lib()
+        if args.profile_solve == "newcg_stable_4096":
+            bp = gen.manufactured_rhs(4096, 4096, seed=SEED)
+            kw = dict(tol=0.0, maxit=20, opts=lap5cg.default_opts(stabilized=1, true_residual=0))
+        else:
+            bp = gen.uniform_rhs(100, 100, seed=1)
+            kw = dict(tol=1e-8, maxit=10000)
+        bd = torch.from_numpy(bp).to(torch.device("cuda", 0))
+        for _ in range(2):
+            _, info = lap5cg.cg_solve(bd, variant="newcg", **kw)
+        torch.cuda.synchronize()
+        print(json.dumps({"profiling_case": dict(lap5cg.decode_info(info)[0], case=args.profile_solve)}))
         return 0
 
     if args.profile_mg:
