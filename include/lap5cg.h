@@ -25,7 +25,9 @@
  * MG_F64), a cache of up to eight instantiated CUDA graphs keyed by device,
  * shape, workspace address and V-cycle options: the first solve of a key
  * builds and instantiates its graph (driver-side resources, freed when the
- * entry is evicted), later ones launch it.  One exception to "the caller owns every buffer":
+ * entry is evicted or by lap5cg_release_graphs), later ones launch it.  The
+ * graphs belong to the device's context: an application that resets a device
+ * (cudaDeviceReset) calls lap5cg_release_graphs first.  One exception to "the caller owns every buffer":
  * cg_solve_classic_f64_noalloc uses a fixed 8.25 MiB __device__ array of the
  * library as scratch; the CUDA runtime commits it on a device when it loads
  * the library's module there (with lazy module loading, at the first call
@@ -305,6 +307,18 @@ LAP5CG_API int lap5cg_tune_batched(int count, const int* nx, const int* ny, cons
  * Returns LAP5CG_OK, LAP5CG_ERR_INVALID_ARG (NULL outputs) or LAP5CG_ERR_CUDA.
  */
 LAP5CG_API int lap5cg_fp64_rate(double* fma_per_s, double* add_per_s, void* stream);
+
+/*
+ * Frees every cached graph of the classic multigrid-preconditioned solve, on
+ * every device (see Ownership above).  Call it before resetting a device or
+ * destroying its primary context: the cached graphs belong to that context.
+ * A graph still running is freed by the driver when it completes.  The next
+ * classic MG_F32 / MG_F64 solve of a shape builds its graph again.  Safe to
+ * call from any host thread at any time (the cache has a lock); allocates
+ * nothing.  Returns LAP5CG_OK, or LAP5CG_ERR_CUDA if a graph could not be
+ * destroyed (the cache is emptied all the same).
+ */
+LAP5CG_API int lap5cg_release_graphs(void);
 
 /* Largest ny*ld that cg_solve_classic_f64_noalloc accepts. */
 #define LAP5CG_NOALLOC_MAX_POINTS 262144

@@ -89,6 +89,8 @@ def lib():
         DP = ctypes.POINTER(ctypes.c_double)
         L.lap5cg_fp64_rate.argtypes = [DP, DP, vp]
         L.lap5cg_fp64_rate.restype = i
+        L.lap5cg_release_graphs.argtypes = []
+        L.lap5cg_release_graphs.restype = i
         L.lap5cg_tune.argtypes = [i, i, i, vp, vp, i, i, i, vp, sz, vp, ctypes.POINTER(Opts), DP, vp]
         L.lap5cg_tune.restype = i
         L.lap5cg_tune_batched.argtypes = [i, IP, IP, IP, VPP, VPP, i, i, i, vp, sz, vp, ctypes.POINTER(Opts), DP, vp]
@@ -99,7 +101,7 @@ def lib():
 
 EXPORTED = ("lap5cg_opts_default", "lap5cg_status_string", "lap5_apply", "cg_workspace_size", "cg_solve",
             "cg_batched_workspace_size", "cg_solve_batched", "cg_solve_classic_f64_noalloc", "lap5cg_tune",
-            "lap5cg_tune_batched", "lap5cg_fp64_rate")
+            "lap5cg_tune_batched", "lap5cg_fp64_rate", "lap5cg_release_graphs")
 NOALLOC_MAX_POINTS = 262144
 
 
@@ -329,6 +331,14 @@ def cg_solve_classic_f64_noalloc(b: torch.Tensor, x0: torch.Tensor = None, tol: 
     if rc != OK:
         raise Lap5cgError(rc, "cg_solve_classic_f64_noalloc")
     return x, info
+
+
+def release_graphs():
+    """Free the library's cached multigrid graphs on every device (before a
+    device reset; the next classic multigrid solve builds its graph again)."""
+    rc = lib().lap5cg_release_graphs()
+    if rc != OK:
+        raise Lap5cgError(rc, "lap5cg_release_graphs")
 
 
 def fp64_rate(device=None):

@@ -1322,4 +1322,22 @@ int solve_mg_graph(const SolvePlan& p, const PcgArgs<TM>& a, cudaStream_t st, bo
 template int solve_mg_graph<float>(const SolvePlan&, const PcgArgs<float>&, cudaStream_t, bool*);
 template int solve_mg_graph<double>(const SolvePlan&, const PcgArgs<double>&, cudaStream_t, bool*);
 
+// Every cached graph destroyed on its own device; the caller's current device
+// is restored.
+static int gm_release_all() {
+  std::lock_guard<std::mutex> lock(g_gm_mu);
+  int rc = LAP5CG_OK, dev0 = 0;
+  const bool have_dev = cudaGetDevice(&dev0) == cudaSuccess;
+  for (const auto& e : g_gm_cache) {
+    if (cudaSetDevice(e.first.dev) != cudaSuccess || cudaGraphExecDestroy(e.second) != cudaSuccess)
+      rc = LAP5CG_ERR_CUDA;
+  }
+  g_gm_cache.clear();
+  if (have_dev) cudaSetDevice(dev0);
+  if (rc != LAP5CG_OK) cudaGetLastError();
+  return rc;
+}
+
 }  // namespace lap5
+
+extern "C" LAP5CG_API int lap5cg_release_graphs(void) { return lap5::gm_release_all(); }

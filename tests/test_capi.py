@@ -34,6 +34,11 @@ def test_library_exports_every_declared_symbol():
     assert set(lap5cg.EXPORTED) <= set(declared_functions())
 
 
+def test_release_graphs_with_an_empty_cache():
+    # no graph has been built in this process: nothing to free, no device needed
+    assert lap5cg.lib().lap5cg_release_graphs() == lap5cg.OK
+
+
 def test_status_strings():
     for code in (0, 1, -1, -2, -3, -4, -5, -6, -7):
         assert lap5cg.status_string(code) != "unknown status"

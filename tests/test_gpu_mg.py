@@ -179,6 +179,33 @@ def _ws_for(nx, ny, ld, precision="mg_f64", nrhs=1):
                        device="cuda")
 
 
+def test_release_graphs_then_rebuild_gives_the_same_bits():
+    # a cached graph freed (once idle, once while its solve is still running)
+    # and built again on the next call: the same kernels, so the same bits
+    nx, ny = 300, 200
+    ld = gen.pitch(nx, 8)
+    b = _dev(gen.uniform_rhs(nx, ny, seed=83, ld=ld))
+    ws = _ws_for(nx, ny, ld, "mg_f32")
+    info = torch.empty(lap5cg.INFO_BYTES, dtype=torch.uint8, device="cuda")
+    outs = []
+    for release in ("none", "idle", "running"):
+        x = torch.zeros((ny, ld), dtype=torch.float64, device="cuda")
+        if release == "idle":
+            torch.cuda.synchronize()
+            lap5cg.release_graphs()
+        lap5cg.cg_solve(b, tol=1e-10, maxit=500, precision="mg_f32", nx=nx, workspace=ws, info=info, out=x)
+        if release == "running":
+            lap5cg.release_graphs()  # the graph is in flight: the driver frees it on completion
+        torch.cuda.synchronize()
+        rec = lap5cg.decode_info(info)[0]
+        assert rec["status"] == lap5cg.OK and rec["relres_true"] <= 1.5e-10, rec
+        outs.append(x.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+    lap5cg.release_graphs()
+    x, info2 = lap5cg.cg_solve(b, tol=1e-10, maxit=500, precision="mg_f32", nx=nx, workspace=ws)
+    assert np.array_equal(x.cpu().numpy()[:, :nx], outs[0][:, :nx])
+
+
 def test_cached_graph_rebinds_rhs_solution_and_limits():
     # one workspace, so every call below hits the same cached graph: the
     # right-hand side, the solution buffer, tol and maxit change per call
