@@ -21,17 +21,19 @@
  * Ownership: the caller owns every buffer (inputs, outputs, workspace, info).
  * No entry point below allocates device memory at call time, and the library
  * keeps no mutable global state apart from a per-device cache of device
- * properties and, for the classic multigrid-preconditioned solve (MG_F32,
- * MG_F64), a cache of up to eight instantiated CUDA graphs keyed by device,
- * shape, workspace address and V-cycle options: the first solve of a key
- * builds and instantiates its graph (driver-side resources, freed when the
- * entry is evicted or by lap5cg_release_graphs), later ones launch it.  The
- * graphs belong to the device's context: an application that resets a device
- * (cudaDeviceReset) calls lap5cg_release_graphs first.  One exception to "the caller owns every buffer":
- * cg_solve_classic_f64_noalloc uses a fixed 8.25 MiB __device__ array of the
- * library as scratch; the CUDA runtime commits it on a device when it loads
- * the library's module there (with lazy module loading, at the first call
- * into the library on that device, not at dlopen).
+ * properties (with the bf16 lap5_apply kernel's occupancy and whether its
+ * shared-memory size is set; a refused launch sets it again) and, for the
+ * classic multigrid-preconditioned solve (MG_F32, MG_F64), a cache of up to
+ * eight instantiated CUDA graphs keyed by device, shape, workspace address and
+ * V-cycle options: the first solve of a key builds and instantiates its graph
+ * (driver-side resources, freed when the entry is evicted or by
+ * lap5cg_release_graphs), later ones launch it.  The graphs belong to the
+ * device's context: an application that resets a device (cudaDeviceReset)
+ * calls lap5cg_release_graphs first.  One exception to "the caller owns every
+ * buffer": cg_solve_classic_f64_noalloc uses a fixed 8.25 MiB __device__ array
+ * of the library as scratch; the CUDA runtime commits it on a device when it
+ * loads the library's module there (with lazy module loading, at the first
+ * call into the library on that device, not at dlopen).
  *
  * Ordering: every call is asynchronous on the given CUDA stream (a
  * cudaStream_t passed as void*; NULL = the legacy default stream).  The return

@@ -356,20 +356,26 @@ static int launch_apply_bf16_tma(int nx, int ny, int ld, const void* x, void* y,
   const long long nt = (long long)tiles_x * ((ny + kTmaH - 1) / kTmaH);
   if (nt > 0x7fffffffLL) return LAP5CG_ERR_UNSUPPORTED;
   const size_t smem = (size_t)kTmaStages * kTmaStageBytes + 8 * kTmaStages;
-  static std::once_flag attr_once;
-  static cudaError_t attr_err = cudaSuccess;
-  std::call_once(attr_once, [&] {
-    attr_err = cudaFuncSetAttribute(k_lap5_apply_bf16_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  });
-  if (attr_err != cudaSuccess) return LAP5CG_ERR_CUDA;
   DevProps dp;
   const int rc = dev_props(&dp);
   if (rc != LAP5CG_OK) return rc;
-  // resident CTAs an SM, per device (the occupancy query costs microseconds of
-  // host time, which a kernel of tens of microseconds would otherwise wait for)
-  static std::atomic<int> occ_cache[128];
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return LAP5CG_ERR_CUDA;
+  // The shared-memory size attribute, set once per device (its host cost would
+  // show in front of a kernel of tens of microseconds), and set again with the
+  // launch retried once if a launch is refused (a device reset drops it).
+  static std::atomic<int> attr_set[128];
+  auto set_attr = [&]() {
+    return cudaFuncSetAttribute(k_lap5_apply_bf16_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
+           cudaSuccess;
+  };
+  if (!attr_set[dev].load(std::memory_order_relaxed)) {
+    if (!set_attr()) return LAP5CG_ERR_CUDA;
+    attr_set[dev].store(1, std::memory_order_relaxed);
+  }
+  // resident CTAs an SM, per device (the occupancy query costs microseconds of
+  // host time as well)
+  static std::atomic<int> occ_cache[128];
   int occ = occ_cache[dev].load(std::memory_order_relaxed);
   if (occ == 0) {
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_lap5_apply_bf16_tma, kTmaThreads, smem) != cudaSuccess ||
@@ -378,9 +384,14 @@ static int launch_apply_bf16_tma(int nx, int ny, int ld, const void* x, void* y,
     occ_cache[dev].store(occ, std::memory_order_relaxed);
   }
   const long long grid = std::min<long long>(nt, (long long)occ * dp.sms);
-  k_lap5_apply_bf16_tma<<<(unsigned)grid, kTmaThreads, smem, st>>>(mmain, mhalo, nx, ny, ld, static_cast<uint16_t*>(y),
-                                                                  tiles_x, (int)nt);
-  return cudaGetLastError() == cudaSuccess ? LAP5CG_OK : LAP5CG_ERR_CUDA;
+  auto launch = [&]() {
+    k_lap5_apply_bf16_tma<<<(unsigned)grid, kTmaThreads, smem, st>>>(mmain, mhalo, nx, ny, ld,
+                                                                    static_cast<uint16_t*>(y), tiles_x, (int)nt);
+    return cudaGetLastError();
+  };
+  cudaError_t e = launch();
+  if (e != cudaSuccess && set_attr()) e = launch();
+  return e == cudaSuccess ? LAP5CG_OK : LAP5CG_ERR_CUDA;
 }
 
 template <class T, int V>
