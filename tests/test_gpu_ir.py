@@ -40,10 +40,16 @@ def test_ir_reaches_fp64_accuracy(precision, nx, ny):
     assert _rel(x.cpu().numpy()[:, :nx], xo[:, :nx]) <= max(kappa * 2 * tol, 1e-13)
     if nx * ny > 16:
         assert rec["outer_iters"] >= 2
-    # the oracle's refinement takes a similar number of steps
+    # the oracle's refinement takes the same refinement steps and, within the
+    # rounding of the inner dot products (binary32 Dot2 / bf16 storage summed in
+    # another order), the same inner iterations: measured on a GB300, outer
+    # steps equal on every shape here, inner totals within 1 (binary32) and
+    # 3.5 % (bf16 p, r)
     xi, ii = oracle.cg_ir(b, tol=tol, inner="f32" if precision == "ir_f32" else "bf16pr", nx=nx)
     assert ii["status"] == oracle.OK
-    assert abs(rec["outer_iters"] - ii["outer_iters"]) <= max(2, ii["outer_iters"] // 2)
+    assert abs(rec["outer_iters"] - ii["outer_iters"]) <= 1, (rec, ii)
+    slack = max(3, ii["iters"] // 100) if precision == "ir_f32" else max(5, ii["iters"] // 20)
+    assert abs(rec["iters"] - ii["iters"]) <= slack, (rec, ii)
 
 
 @pytest.mark.parametrize("precision", ["ir_f32", "ir_bf16pr"])
