@@ -1,6 +1,8 @@
 // mg_graph.cu -- the multigrid-preconditioned CG (Algorithm 1 with M^-1 one
 // V-cycle; precisions MG_F32 / MG_F64, classic variant) as a CUDA graph: one
-// ordinary kernel per pass, each at the occupancy its own registers allow,
+// ordinary kernel per pass (or per fused group of passes: a level's descent,
+// prolongation with the first post-smoothing sweep, level 0's last sweep with
+// (r, z)), each at the occupancy its own registers allow,
 // and the PCG iterations looped on the device by a WHILE conditional node
 // whose condition the convergence check sets.  Scalars stay in device memory;
 // there is no host round trip per iteration and no grid barrier (the kernel
@@ -16,9 +18,9 @@
 // which buffer each pass reads and writes, the march direction) into one
 // kernel node per pass; the levels of at most kMgCtaPoints points run in one
 // single-CTA kernel node.  Instantiated graphs are cached per call signature
-// (device, shape, workspace, V-cycle options); a small kernel writes each
-// call's b, x, info, history, tol and maxit into the workspace before the
-// cached graph is launched.
+// (device, shape, workspace, V-cycle options; lap5cg_release_graphs frees
+// them all); a small kernel writes each call's b, x, info, history, tol and
+// maxit into the workspace before the cached graph is launched.
 #include <mutex>
 #include <vector>
 
